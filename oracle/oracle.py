@@ -1,0 +1,201 @@
+"""ctypes front end of the FP64 CPU oracle (``gfs_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by the package's smoke
+check and by the benchmark's CPU-baseline leg.  The CUDA library never
+imports, links or executes anything here, and nothing here calls the library.
+
+Every function takes and returns numpy arrays in FP64 (positions (n,3)
+row-major, values (n,)).  Candidate ids are ``g = i * (K + 1) + k``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gfs_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "libgfs_oracle.so")
+
+TOL = 1e-6  # App. B: "all other tolerances are 1e-6"
+
+CODE_SURVIVOR, CODE_OPPOSITE, CODE_SAMPLE, CODE_OUTSIDE, CODE_INVALID, CODE_LOWER = range(6)
+FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 16, 32, 64, 128
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP contraction off) and return the path."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        L.orc_icosphere.argtypes = [i32, P, i64]
+        L.orc_icosphere.restype = i32
+        L.orc_keep_one.argtypes = [P, P, i64, P, i32, f64, i32, i64, i32]
+        L.orc_keep_one.restype = i32
+        L.orc_keep_all.argtypes = [P, P, i64, P, i32, f64, i32, P]
+        L.orc_keep_all.restype = None
+        L.orc_collect.argtypes = [P, P, i64, P, i32, P, P, P, P]
+        L.orc_collect.restype = i64
+        L.orc_query.argtypes = [P, P, i64, P, P, P, i64, f64, i32, P, i64, P, P, P, P]
+        L.orc_query.restype = None
+        L.orc_query_lazy.argtypes = [P, P, i64, P, i32, f64, i32, i32, P, i64, P, P, P, P]
+        L.orc_query_lazy.restype = None
+        L.orc_grad.argtypes = [P, P, i64, P, i32, P, i64, P, P, P, P, P, P, P]
+        L.orc_grad.restype = None
+        L.orc_insert.argtypes = [P, P, i64, P, i32, f64, i32, i32, P, i64, P, P, P]
+        L.orc_insert.restype = i64
+        L.orc_insert_state.argtypes = [P, P, P, P, P, P]
+        L.orc_insert_state.restype = i64
+        L.orc_exact_rmin.argtypes = [P, P, i64, f64, i32, P, i32]
+        L.orc_exact_rmin.restype = f64
+        _lib = L
+    return _lib
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None and a.size else None
+
+
+def icosphere(tau: int) -> np.ndarray:
+    K = 10 * 4 ** tau + 2
+    out = np.zeros((K, 3), dtype=np.float64)
+    k = lib().orc_icosphere(tau, _ptr(out), K)
+    if k != K:
+        raise ValueError(f"icosphere construction failed for tau={tau}")
+    return out
+
+
+def keep_one(p, s, U, i, k, tol=TOL, box_cull=True) -> bool:
+    p, s, U = _c(p, np.float64), _c(s, np.float64), _c(U, np.float64)
+    return bool(lib().orc_keep_one(_ptr(p), _ptr(s), s.shape[0], _ptr(U), U.shape[0], tol, int(box_cull), i, k))
+
+
+def keep_all(p, s, U, tol=TOL, box_cull=True) -> np.ndarray:
+    """(n, K) uint8 keep mask of every candidate (brute force, O(n^2 K))."""
+    p, s, U = _c(p, np.float64), _c(s, np.float64), _c(U, np.float64)
+    n, K = s.shape[0], U.shape[0]
+    keep = np.zeros((n, K), dtype=np.uint8)
+    if n:
+        lib().orc_keep_all(_ptr(p), _ptr(s), n, _ptr(U), K, tol, int(box_cull), _ptr(keep))
+    return keep
+
+
+def collect(p, s, U, keep):
+    """Survivor list (g, sphere, q) in ascending g from a keep mask."""
+    p, s, U, keep = _c(p, np.float64), _c(s, np.float64), _c(U, np.float64), _c(keep, np.uint8)
+    n, K = s.shape[0], U.shape[0]
+    c = int(keep.sum())
+    g = np.zeros(c, np.int64)
+    sph = np.zeros(c, np.int64)
+    q = np.zeros((c, 3), np.float64)
+    if c:
+        lib().orc_collect(_ptr(p), _ptr(s), n, _ptr(U), K, _ptr(keep), _ptr(g), _ptr(sph), _ptr(q))
+    return g, sph, q
+
+
+def query(p, s, surv, x, tol=TOL, clamp_opp=True):
+    """Brute-force consistent value at every row of x against the survivor
+    list ``surv = (g, sphere, q)``.  Returns (value, argmin, flags, gap)."""
+    p, s, x = _c(p, np.float64), _c(s, np.float64), _c(x, np.float64)
+    g, sph, q = (_c(surv[0], np.int64), _c(surv[1], np.int64), _c(surv[2], np.float64))
+    m = x.shape[0]
+    val = np.zeros(m, np.float64)
+    arg = np.zeros(m, np.int64)
+    fl = np.zeros(m, np.int32)
+    gap = np.zeros(m, np.float64)
+    if m:
+        lib().orc_query(_ptr(p), _ptr(s), s.shape[0], _ptr(g), _ptr(sph), _ptr(q), g.shape[0], tol,
+                        int(clamp_opp), _ptr(x), m, _ptr(val), _ptr(arg), _ptr(fl), _ptr(gap))
+    return val, arg, fl, gap
+
+
+def query_lazy(p, s, U, x, tol=TOL, box_cull=True, clamp_opp=True):
+    """Same result as ``query`` on the full survivor list, computing keep
+    decisions only for candidates that could be nearest (large inputs)."""
+    p, s, U, x = _c(p, np.float64), _c(s, np.float64), _c(U, np.float64), _c(x, np.float64)
+    m = x.shape[0]
+    val = np.zeros(m, np.float64)
+    arg = np.zeros(m, np.int64)
+    fl = np.zeros(m, np.int32)
+    gap = np.zeros(m, np.float64)
+    if m:
+        lib().orc_query_lazy(_ptr(p), _ptr(s), s.shape[0], _ptr(U), U.shape[0], tol, int(box_cull),
+                             int(clamp_opp), _ptr(x), m, _ptr(val), _ptr(arg), _ptr(fl), _ptr(gap))
+    return val, arg, fl, gap
+
+
+def grad(p, s, U, x, value, argmin, flags, gup):
+    """Analytic gradient through the argmin: (grad_x (m,3), grad_p (n,3),
+    grad_s (n,)) for upstream gradient ``gup`` (m,)."""
+    p, s, U, x = _c(p, np.float64), _c(s, np.float64), _c(U, np.float64), _c(x, np.float64)
+    value, argmin = _c(value, np.float64), _c(argmin, np.int64)
+    flags, gup = _c(flags, np.int32), _c(gup, np.float64)
+    m, n = x.shape[0], s.shape[0]
+    gx = np.zeros((m, 3), np.float64)
+    gp = np.zeros((n, 3), np.float64)
+    gs = np.zeros(n, np.float64)
+    if m:
+        lib().orc_grad(_ptr(p), _ptr(s), n, _ptr(U), U.shape[0], _ptr(x), m, _ptr(value), _ptr(argmin),
+                       _ptr(flags), _ptr(gup), _ptr(gx), _ptr(gp), _ptr(gs))
+    return gx, gp, gs
+
+
+def insert(p, s, U, y, tol=TOL, box_cull=True, clamp_opp=True):
+    """Sequential greedy insertion of the rows of y.  Returns (value, argmin,
+    flags) per insertion and the final state dict."""
+    p, s, U, y = _c(p, np.float64), _c(s, np.float64), _c(U, np.float64), _c(y, np.float64)
+    T = y.shape[0]
+    val = np.zeros(T, np.float64)
+    arg = np.zeros(T, np.int64)
+    fl = np.zeros(T, np.int32)
+    L = lib()
+    L.orc_insert(_ptr(p), _ptr(s), s.shape[0], _ptr(U), U.shape[0], tol, int(box_cull), int(clamp_opp),
+                 _ptr(y), T, _ptr(val), _ptr(arg), _ptr(fl))
+    nsph = ctypes.c_int64(0)
+    ns = L.orc_insert_state(None, None, None, None, None, ctypes.byref(nsph))
+    P = np.zeros((nsph.value, 3))
+    S = np.zeros(nsph.value)
+    g = np.zeros(ns, np.int64)
+    sph = np.zeros(ns, np.int64)
+    q = np.zeros((ns, 3))
+    L.orc_insert_state(_ptr(P), _ptr(S), _ptr(g) if ns else None, _ptr(sph) if ns else None,
+                       _ptr(q) if ns else None, None)
+    order = np.argsort(g, kind="stable")
+    state = {"p": P, "s": S, "g": g[order], "sph": sph[order], "q": q[order]}
+    return val, arg, fl, state
+
+
+def exact_rmin(p, s, x, sigma, tol=TOL, box_cull=False) -> float:
+    """Exact minimum valid radius (T/U/D grow-to points, brute force)."""
+    p, s, x = _c(p, np.float64), _c(s, np.float64), _c(x, np.float64)
+    return float(lib().orc_exact_rmin(_ptr(p), _ptr(s), s.shape[0], tol, int(box_cull), _ptr(x), int(sigma)))
+
+
+def solve(p, s, tau, x, tol=TOL, box_cull=True, clamp_opp=True):
+    """Whole path on small inputs: icosphere, P build, query."""
+    U = icosphere(tau)
+    keep = keep_all(p, s, U, tol, box_cull)
+    surv = collect(p, s, U, keep)
+    return keep, surv, query(p, s, surv, x, tol, clamp_opp)

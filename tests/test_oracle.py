@@ -1,0 +1,391 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these checks re-types an oracle formula: each compares the oracle
+with a closed form, an invariant, a special case or brute force of a
+different formulation, chosen so that a dropped term, a wrong sign or index,
+or a transposed operand fails at least one of them.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from paper_2605_01919_gb300 import workloads as W
+
+PHI = (1 + 5 ** 0.5) / 2
+
+
+# ----------------------------------------------------------------------------
+# icosphere (candidate directions)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tau", range(0, 6))
+def test_icosphere_counts_and_norms(orc, tau):
+    U = orc.icosphere(tau)
+    assert U.shape == (10 * 4 ** tau + 2, 3)          # 12, 42, 162, 642, ...
+    assert np.abs(np.linalg.norm(U, axis=1) - 1).max() < 4e-16
+
+
+def test_icosphere_base_is_regular_icosahedron(orc):
+    U = orc.icosphere(0)
+    G = U @ U.T
+    # a regular icosahedron: every vertex has 5 neighbours at cos = 1/sqrt5,
+    # 5 at -1/sqrt5 and one antipode
+    for row in G:
+        vals = np.sort(row)
+        assert abs(vals[-1] - 1) < 1e-15 and abs(vals[0] + 1) < 1e-15
+        assert np.sum(np.abs(vals - 1 / 5 ** 0.5) < 1e-12) == 5
+        assert np.sum(np.abs(vals + 1 / 5 ** 0.5) < 1e-12) == 5
+    # first vertex is (-1, phi, 0) / |.|
+    n = math.sqrt(1 + PHI * PHI)
+    assert np.allclose(U[0], [-1 / n, PHI / n, 0], atol=1e-15)
+
+
+@pytest.mark.parametrize("tau", range(0, 5))
+def test_icosphere_antipodal_exact(orc, tau):
+    U = orc.icosphere(tau)
+    keys = {tuple(u) for u in U}
+    assert all(tuple(-u) in keys for u in U)
+
+
+@pytest.mark.parametrize("tau", range(0, 5))
+def test_icosphere_prefix(orc, tau):
+    # vertices never move, so S_tau is a subset of S_tau+1 (as a prefix)
+    a, b = orc.icosphere(tau), orc.icosphere(tau + 1)
+    assert np.array_equal(a, b[: a.shape[0]])
+
+
+@pytest.mark.parametrize("tau", [1, 2, 3])
+def test_icosphere_topology(orc, tau):
+    """Geodesic subdivision: 12 vertices of degree 5, all others degree 6,
+    and every new vertex is the normalised midpoint of two older ones."""
+    U = orc.icosphere(tau)
+    K = U.shape[0]
+    G = U @ U.T
+    np.fill_diagonal(G, -2)
+    nearest = G.max(axis=1)
+    # neighbours: within a factor of the nearest neighbour's angle
+    ang = np.arccos(np.clip(G, -1, 1))
+    amin = np.arccos(np.clip(nearest, -1, 1))
+    deg = np.sum(ang < 1.35 * amin[:, None], axis=1)
+    assert np.sum(deg == 5) == 12 and np.sum(deg == 6) == K - 12
+    prev = orc.icosphere(tau - 1)
+    P = prev.shape[0]
+    for k in range(P, K):
+        m = prev[:, None, :] + prev[None, :, :]
+        nm = np.linalg.norm(m, axis=2, keepdims=True)
+        m = m / np.where(nm > 0, nm, 1.0)          # antipodal pairs sum to 0
+        d = np.abs(m - U[k]).max(axis=2)
+        assert d.min() < 1e-15
+
+
+# ----------------------------------------------------------------------------
+# P build: which candidates survive
+# ----------------------------------------------------------------------------
+
+def test_keep_single_sphere_all_in_box_survive(orc):
+    U = orc.icosphere(2)
+    p = np.array([[0.1, -0.2, 0.05]])
+    s = np.array([0.4])
+    keep = orc.keep_all(p, s, U)
+    assert keep.all()                      # n=1: nothing else can cover
+    s_big = np.array([1.5])
+    keep = orc.keep_all(np.zeros((1, 3)), s_big, U)
+    inbox = np.all(np.abs(1.5 * U) <= 1, axis=1)
+    assert np.array_equal(keep[0].astype(bool), inbox)
+    keep = orc.keep_all(np.zeros((1, 3)), s_big, U, box_cull=False)
+    assert keep.all()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_keep_two_spheres_cap_angle(orc, seed):
+    """A point r1 u of sphere 1 lies in ball 2 (centre c at distance d in
+    direction e) iff u.e > (r1^2 + d^2 - r2^2) / (2 r1 d) (law of cosines)."""
+    rng = np.random.default_rng(seed)
+    U = orc.icosphere(3)
+    r1, r2 = rng.uniform(0.2, 0.4), rng.uniform(0.2, 0.4)
+    e = rng.normal(size=3)
+    e /= np.linalg.norm(e)
+    d = rng.uniform(0.5 * (r1 + r2), 0.95 * (r1 + r2))
+    p = np.array([[0.0, 0.0, 0.0], d * e])
+    s = np.array([r1, -r2]) * (1 if seed % 2 else -1)     # either sign covers
+    keep = orc.keep_all(p, s, U, tol=0.0, box_cull=False)
+    cos_cap = (r1 * r1 + d * d - r2 * r2) / (2 * r1 * d)
+    ue = U @ e
+    far = np.abs(ue - cos_cap) > 1e-9
+    assert np.array_equal(keep[0][far].astype(bool), (ue < cos_cap)[far])
+    cos_cap2 = (r2 * r2 + d * d - r1 * r1) / (2 * r2 * d)
+    ue2 = U @ (-e)
+    far2 = np.abs(ue2 - cos_cap2) > 1e-9
+    assert np.array_equal(keep[1][far2].astype(bool), (ue2 < cos_cap2)[far2])
+
+
+def test_keep_concentric_and_touching(orc):
+    U = orc.icosphere(2)
+    p = np.zeros((2, 3))
+    keep = orc.keep_all(p, np.array([0.5, 0.2]), U)
+    assert keep[0].all() and not keep[1].any()
+    # spheres touching at one point: touching is allowed (open ball), so the
+    # contact candidate u = (1,0,0) of sphere 0 survives
+    p = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0]])
+    s = np.array([0.3, 0.2])
+    k = int(np.where(np.all(U == [1.0, 0.0, 0.0], axis=1))[0][0])
+    assert orc.keep_one(p, s, U, 0, k)
+    # pushed 2 tol closer the contact point is covered
+    p2 = np.array([[0.0, 0.0, 0.0], [0.5 - 3e-6, 0.0, 0.0]])
+    assert not orc.keep_one(p2, s, U, 0, k)
+
+
+def test_keep_zero_radius_covers_nothing(orc):
+    U = orc.icosphere(1)
+    p = np.array([[0.0, 0.0, 0.0], [0.1, 0.0, 0.0]])
+    s = np.array([0.0, 0.3])
+    keep = orc.keep_all(p, s, U)
+    assert not keep[0].any()               # the point sample sits in ball 1
+    assert keep[1].all()                   # a zero-radius ball covers nothing
+
+
+def test_sphere_grid_survivor_count_matches_independent_probe(orc):
+    """5,449 of 663,552 candidates survive on the 16^3 sphere grid at tau=2
+    with box culling, the count an independent numpy probe of the same rule
+    reported when the workloads were surveyed."""
+    w = W.sphere_grid()
+    keep = orc.keep_all(w.p, w.s, orc.icosphere(w.tau))
+    assert keep.size == 663_552 and int(keep.sum()) == 5449
+
+
+# ----------------------------------------------------------------------------
+# query: the consistent value
+# ----------------------------------------------------------------------------
+
+def _solve(orc, p, s, tau, x, **kw):
+    keep, surv, res = orc.solve(p, s, tau, x, **kw)
+    return res
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_query_single_sphere_closed_form(orc, seed):
+    """n = 1, x inside: survivors are the in-box candidates and
+    |x - p - r u|^2 = delta^2 + r^2 - 2 r delta (u . v)."""
+    rng = np.random.default_rng(seed)
+    U = orc.icosphere(3)
+    c = rng.uniform(-0.2, 0.2, 3)
+    r = rng.uniform(0.3, 0.6)
+    sign = 1 if seed % 2 else -1
+    x = c + rng.uniform(-0.15, 0.15, size=(20, 3))
+    val, arg, fl, _ = _solve(orc, c[None], np.array([sign * r]), 3, x)
+    for t in range(20):
+        v = x[t] - c
+        delta = np.linalg.norm(v)
+        cosang = U @ (v / delta)
+        k = int(np.argmax(cosang))
+        expect = math.sqrt(delta ** 2 + r ** 2 - 2 * r * delta * cosang[k])
+        assert fl[t] & 15 == orc.CODE_SURVIVOR
+        assert arg[t] == k                       # g = 0 * (K+1) + k
+        assert abs(val[t] - sign * expect) < 1e-12
+        # far bound = delta + r is never exceeded; LB = r - delta holds
+        assert not (fl[t] & (orc.FLAG_FAR_VIOL | orc.FLAG_LB_VIOL))
+
+
+def test_query_outside_sample_and_lower(orc):
+    p = np.array([[0.0, 0.0, 0.0]])
+    val, arg, fl, _ = _solve(orc, p, np.array([-0.3]), 2,
+                             np.array([[0.5, 0, 0], [0, 0, 0], [0.1, 0.1, 0]]))
+    assert fl[0] & 15 == orc.CODE_OUTSIDE and val[0] == 0          # Prop. 2 proof
+    assert fl[1] & 15 == orc.CODE_SAMPLE and val[1] == -0.3        # reproduction
+    assert fl[2] & 15 == orc.CODE_SURVIVOR and val[2] < 0
+    # every candidate outside the box -> fall back to LB = r - |x - p|,
+    # the exact single-sphere value
+    x = np.array([[0.2, -0.1, 0.3]])
+    val, arg, fl, _ = _solve(orc, np.zeros((1, 3)), np.array([3.0]), 2, x)
+    assert fl[0] & 15 == orc.CODE_LOWER and arg[0] == 0
+    assert abs(val[0] - (3.0 - np.linalg.norm(x[0]))) < 1e-15
+
+
+def test_query_plane_column_exact(orc):
+    """Samples of s = z above the plane z = 0; a query on a sample column at
+    height z_x has exact value z_x (B(x, z_x) lies in the column's ball and
+    touches the plane at the column's tangent point, a survivor)."""
+    a = np.linspace(-0.5, 0.5, 5)
+    z = np.linspace(0.1, 0.9, 5)
+    P = np.array(list(itertools.product(a, a, z)))
+    S = P[:, 2].copy()
+    xs = np.array([[a[1], a[3], 0.05], [a[2], a[2], 0.37], [a[4], a[0], 0.8]])
+    val, arg, fl, _ = _solve(orc, P, S, 1, xs)
+    assert np.all(fl & 15 == orc.CODE_SURVIVOR)
+    assert np.array_equal(val, xs[:, 2])
+
+
+def test_query_reproduces_inputs_and_is_eikonal(orc):
+    w = W.sphere_grid(N=8, up=2)
+    x = w.make_queries()
+    val, arg, fl, _ = _solve(orc, w.p, w.s, w.tau, x)
+    # every input position is in the upsampled grid: values reproduced bitwise
+    idx = {tuple(q): i for i, q in enumerate(x)}
+    for i in range(w.n):
+        t = idx[tuple(w.p[i])]
+        assert fl[t] & 15 == orc.CODE_SAMPLE and val[t] == w.s[i]
+    # no output ball intersects an opposite-sign input ball (Prop. 1 (i))
+    d = np.linalg.norm(x[:, None, :] - w.p[None, :, :], axis=2)
+    ok = (fl & 15) <= 1
+    opp = np.sign(val)[:, None] * np.sign(w.s)[None, :] < 0
+    gap = d - np.abs(w.s)[None, :] - np.abs(val)[:, None]
+    assert np.all(gap[ok][opp[ok]] > -1e-12)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_query_bracket_against_exact_rmin(orc, seed):
+    """LB <= exact r_min <= |s_tau| <= UB_opp on valid tiny inputs (tol = 0,
+    no box): the survivors are uncovered contour points, the opposite
+    tangent point lies beyond the sigma-contour, and every contour point is
+    outside each containing ball."""
+    p, s = W.tiny_random(14, seed)
+    rng = np.random.default_rng(100 + seed)
+    x = rng.uniform(-0.4, 0.4, size=(60, 3))
+    val, arg, fl, _ = _solve(orc, p, s, 2, x, tol=0.0, box_cull=False)
+    d = np.linalg.norm(x[:, None, :] - p[None], axis=2)
+    checked = 0
+    for t in range(60):
+        code = fl[t] & 15
+        if code not in (orc.CODE_SURVIVOR, orc.CODE_OPPOSITE):
+            continue
+        sig = 1 if val[t] > 0 else -1
+        ex = orc.exact_rmin(p, s, x[t], sig, tol=0.0)
+        same = np.sign(s) == sig
+        opp = np.sign(s) == -sig
+        lb = np.max(np.abs(s[same]) - d[t, same])
+        assert lb <= ex + 1e-9
+        assert ex <= abs(val[t]) + 1e-9
+        if opp.any():
+            assert abs(val[t]) <= np.min(d[t, opp] - np.abs(s[opp])) + 1e-12
+        checked += 1
+    assert checked > 10
+
+
+def test_query_monotone_in_tau_and_converges(orc):
+    p, s = W.tiny_random(10, 7)
+    x = np.random.default_rng(5).uniform(-0.3, 0.3, size=(12, 3))
+    prev = None
+    errs = []
+    ex = None
+    for tau in range(0, 6):
+        val, arg, fl, _ = _solve(orc, p, s, tau, x, tol=0.0, box_cull=False)
+        ok = (fl & 15) <= 1
+        if ex is None:
+            ex = np.array([orc.exact_rmin(p, s, x[t], 1 if val[t] > 0 else -1, tol=0.0)
+                           if ok[t] else np.nan for t in range(12)])
+        if prev is not None:
+            assert np.all(np.abs(val[ok]) <= np.abs(prev[ok]) + 1e-15)   # S_tau grows
+        prev = val
+        errs.append(np.nanmax(np.abs(val[ok]) - ex[ok]))
+    assert errs[-1] < errs[0] and errs[-1] < 0.02
+
+
+def test_query_lazy_equals_brute_force(orc):
+    w = W.sphere_grid()
+    U = orc.icosphere(w.tau)
+    keep = orc.keep_all(w.p, w.s, U)
+    surv = orc.collect(w.p, w.s, U, keep)
+    x = w.make_queries()
+    sel = np.random.default_rng(0).choice(x.shape[0], 60, replace=False)
+    a = orc.query(w.p, w.s, surv, x[sel])
+    b = orc.query_lazy(w.p, w.s, U, x[sel])
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+
+
+# ----------------------------------------------------------------------------
+# exact minimum radius (Sec. 6 algorithm) closed forms
+# ----------------------------------------------------------------------------
+
+def test_exact_rmin_single_and_pair(orc):
+    p = np.array([[0.1, 0.0, -0.1]])
+    x = np.array([0.2, 0.1, 0.0])
+    assert abs(orc.exact_rmin(p, np.array([0.5]), x, 1) - (0.5 - np.linalg.norm(x - p[0]))) < 1e-15
+    # two equal intersecting spheres, x at the circle centre: r_min = rho
+    r, d = 0.4, 0.5
+    p = np.array([[-d / 2, 0, 0], [d / 2, 0, 0]])
+    got = orc.exact_rmin(p, np.array([r, r]), np.zeros(3), 1)
+    assert abs(got - math.sqrt(r * r - d * d / 4)) < 1e-14
+
+
+# ----------------------------------------------------------------------------
+# gradient: analytic formulas against central differences of the value
+# ----------------------------------------------------------------------------
+
+def test_grad_matches_finite_differences(orc):
+    w = W.sphere_grid(N=8, up=2)
+    U = orc.icosphere(2)
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-0.9, 0.9, size=(40, 3))
+    keep = orc.keep_all(w.p, w.s, U)
+    surv = orc.collect(w.p, w.s, U, keep)
+    val, arg, fl, gap = orc.query(w.p, w.s, surv, x)
+    gup = np.ones(x.shape[0])
+    gx, gp, gs = orc.grad(w.p, w.s, U, x, val, arg, fl, gup)
+    h = 1e-7
+    tested = 0
+    for t in range(x.shape[0]):
+        code = fl[t] & 15
+        if code not in (0, 1) or gap[t] < 1e-4:
+            continue
+        for c in range(3):
+            xp, xm = x[t].copy(), x[t].copy()
+            xp[c] += h
+            xm[c] -= h
+            vp = orc.query(w.p, w.s, surv, xp[None])[0][0]
+            vm = orc.query(w.p, w.s, surv, xm[None])[0][0]
+            assert abs((vp - vm) / (2 * h) - gx[t, c]) < 1e-5
+        tested += 1
+        # derivative wrt the sample that set the value (survivor moves with it)
+        j = arg[t] // (U.shape[0] + 1) if code == 0 else arg[t]
+        sp, sm = w.s.copy(), w.s.copy()
+        sp[j] += h
+        sm[j] -= h
+        kp = orc.collect(w.p, sp, U, orc.keep_all(w.p, sp, U))
+        km = orc.collect(w.p, sm, U, orc.keep_all(w.p, sm, U))
+        vp = orc.query(w.p, sp, kp, x[t][None])[0][0]
+        vm = orc.query(w.p, sm, km, x[t][None])[0][0]
+        gsingle = orc.grad(w.p, w.s, U, x[t][None], val[t:t + 1], arg[t:t + 1], fl[t:t + 1],
+                           np.ones(1))[2][j]
+        assert abs((vp - vm) / (2 * h) - gsingle) < 1e-5
+        if tested >= 6:
+            break
+    assert tested >= 4
+
+
+# ----------------------------------------------------------------------------
+# greedy insertion: the incremental state equals a rebuild from scratch
+# ----------------------------------------------------------------------------
+
+def test_insert_state_equals_rebuild(orc):
+    w = W.sphere_grid(N=7, up=2)
+    U = orc.icosphere(1)
+    K = U.shape[0]
+    y = np.random.default_rng(11).uniform(-0.8, 0.8, size=(25, 3))
+    val, arg, fl, st = orc.insert(w.p, w.s, U, y)
+    inserted = np.isin(fl & 15, [0, 1, 5])
+    assert st["s"].shape[0] == w.n + inserted.sum()
+    assert np.array_equal(st["s"][w.n:], val[inserted])
+    # every candidate was tested against every sphere: the final survivor
+    # set is the brute-force keep set of the final spheres, plus witnesses
+    keep = orc.keep_all(st["p"], st["s"], U)
+    g_expect = set()
+    for i, k in zip(*np.nonzero(keep)):
+        g_expect.add(int(i) * (K + 1) + int(k))
+    g_got = set(int(g) for g in st["g"] if g % (K + 1) != K)
+    assert g_got == g_expect
+    # each inserted value is reproduced when queried afterwards
+    surv = (st["g"], st["sph"], st["q"])
+    v2, a2, f2, _ = orc.query(st["p"], st["s"], surv, y[inserted])
+    assert np.all(f2 & 15 == orc.CODE_SAMPLE) and np.array_equal(v2, val[inserted])
+
+
+def test_insert_first_value_equals_query(orc):
+    w = W.sphere_grid(N=7, up=2)
+    U = orc.icosphere(2)
+    y = np.array([[0.13, -0.21, 0.05], [0.3, 0.3, 0.3]])
+    val, arg, fl, _ = orc.insert(w.p, w.s, U, y[:1])
+    q = orc.solve(w.p, w.s, 2, y[:1])[2]
+    assert val[0] == q[0][0] and arg[0] == q[1][0] and fl[0] == q[2][0]
