@@ -1,0 +1,166 @@
+/*
+ * gfs.h -- C ABI of the GB300 consistent signed-distance library.
+ *
+ * The library evaluates the data-parallel hot path of "Greed for the
+ * Spheres" (consistent signed distance interpolation):
+ *
+ *  P build  -- every sample (p_i, s_i) is a sphere of radius |s_i| and sign
+ *              sign(s_i) (Sec. 3.1).  Candidate surface points are placed on
+ *              every sphere at the vertices of a geodesic icosphere of depth
+ *              tau, q_ik = p_i + |s_i| u_k, and a candidate survives when it
+ *              lies in the domain box [-1,1]^3 (App. B) and no other ball,
+ *              shrunk by tol, contains it (the "uncovered points" of
+ *              Prop. 1 (ii); the discrete stand-in for the grow-to points
+ *              T, U, D of Def. 1).
+ *  query    -- at a new point x: the sign from the balls containing x
+ *              (Sec. 4.3), the distance to the nearest surviving candidate
+ *              of that sign, clamped by the nearest tangent point of an
+ *              opposite-sign sphere (Def. 1 T; Sec. 4.3 upper bound), and
+ *              the Sec. 4.3 bound checks as flags.  This is the discrete
+ *              counterpart of the minimum valid radius of Prop. 2 / Sec. 6.
+ *  backward -- d s*(x) / d(x, p_i, s_i) through the argmin.
+ *  insert   -- the greedy sequential refinement loop (Sec. 4): each new
+ *              value is computed against the inputs and all values inserted
+ *              before it, then joins the sample set.
+ *
+ * Conventions shared by every call:
+ *  - Positions are FP64 (x, y, z) triples stored row-major (n x 3); values
+ *    are FP64.  Query points may be FP64 or FP32 triples.
+ *  - Every buffer argument is a DEVICE pointer unless the name ends in
+ *    `_host`; the caller owns all input and output buffers.  The library
+ *    owns the sphere/survivor hierarchies and scratch inside the context.
+ *  - All work is enqueued on the context's CUDA stream (cudaStream_t passed
+ *    as void*; NULL = legacy default stream).  A call returns once the work
+ *    is enqueued, except where noted (gfs_build reads back one counter).
+ *  - Return value: GFS_OK (0) or a GFS_ERR_* code; gfs_strerror() names it.
+ *    Per-query anomalies are flags, not errors.  There is no CPU fallback:
+ *    without a CUDA device every compute call fails with GFS_ERR_CUDA.
+ *  - Candidate ids: g = i * (K + 1) + k, K = 10 * 4^tau + 2, i the sphere's
+ *    index in input order (inserted spheres continue the numbering), k < K an
+ *    icosphere vertex; slot k = K holds an inserted sphere's witness point.
+ */
+#ifndef GFS_H
+#define GFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define GFS_OK 0
+#define GFS_ERR_ARG 1        /* invalid argument (null, negative size, bad option) */
+#define GFS_ERR_OOM 2        /* device allocation failed */
+#define GFS_ERR_CUDA 3       /* CUDA runtime error (no device, launch failure) */
+#define GFS_ERR_STATE 4      /* call order violated (e.g. query before build) */
+#define GFS_ERR_TIMEOUT 5    /* a capped device loop ran out of iterations */
+#define GFS_ERR_TOO_LARGE 6  /* sizes exceed the library's index ranges */
+
+/* ---- per-query result word (uint16) ------------------------------------ */
+/* low 4 bits: result code */
+#define GFS_CODE_SURVIVOR 0  /* value = distance to nearest surviving candidate; argmin = g */
+#define GFS_CODE_OPPOSITE 1  /* value = distance to nearest opposite tangent point; argmin = sphere */
+#define GFS_CODE_SAMPLE 2    /* x equals an input position; value = its sample; argmin = sphere */
+#define GFS_CODE_OUTSIDE 3   /* x lies in no (shrunk) ball: value 0; argmin = -1 */
+#define GFS_CODE_INVALID 4   /* x lies in balls of both signs: value NaN; argmin = -1 */
+#define GFS_CODE_LOWER 5     /* no candidate at all: value = lower bound; argmin = sphere */
+/* violation bits (Sec. 4.3 bound checks) */
+#define GFS_FLAG_LB_VIOL 0x10     /* |s| < LB - tol  (LB: nearest-tangent bound of the containing spheres) */
+#define GFS_FLAG_FAR_VIOL 0x20    /* |s| > FAR + tol (FAR: nearest far tangent point of any sphere) */
+#define GFS_FLAG_OPP_VIOL 0x40    /* |s| > UB_opp + tol (only possible with clamp_opp = 0) */
+#define GFS_FLAG_LOST_WITNESS 0x80 /* insertion: some sphere lost its last surviving candidate */
+
+/* ---- options ------------------------------------------------------------ */
+typedef struct {
+  int tau;          /* icosphere subdivision depth, 0..6 (K = 10*4^tau + 2 candidates per sphere) */
+  double tol;       /* coverage tolerance: q is covered by j iff |q-p_j| < |s_j| - tol (App. B: 1e-6) */
+  int box_cull;     /* 1: drop candidates outside [-1,1]^3 (App. B) */
+  int clamp_opp;    /* 1: clamp by the nearest opposite-sign tangent point (Sec. 4.3 upper bound) */
+  int precision;    /* 0: FP32 bulk arithmetic, predicates near a boundary re-decided in FP64;
+                       1: FP64 throughout (same results, slower) */
+  int reserved[7];  /* must be zero */
+} gfs_options;
+
+/* Fill *opt with the defaults: tau 3, tol 1e-6, box_cull 1, clamp_opp 1, precision 0. */
+void gfs_default_options(gfs_options* opt);
+
+typedef struct gfs_ctx gfs_ctx; /* opaque, library-owned */
+
+/* Create a context bound to the current CUDA device and the given stream.
+ * Errors: GFS_ERR_ARG (bad options), GFS_ERR_CUDA (no device), GFS_ERR_OOM. */
+int gfs_create(gfs_ctx** out, const gfs_options* opt, void* cuda_stream);
+
+/* Change the stream later calls are enqueued on. */
+int gfs_set_stream(gfs_ctx* ctx, void* cuda_stream);
+
+/* P build (Def. 1 discretised; Prop. 1 (ii) uncovered points).
+ * p_xyz: device, n*3 FP64, row-major sample positions.
+ * s:     device, n FP64 signed distance samples.
+ * Builds the sphere hierarchy, culls all n*K candidates and builds the
+ * survivor hierarchies.  Inputs are copied; the caller may free them after
+ * the call returns.  Synchronises the stream once to size the survivor set.
+ * Errors: GFS_ERR_ARG (n < 1, null), GFS_ERR_TOO_LARGE (n*(K+1) >= 2^32),
+ * GFS_ERR_OOM, GFS_ERR_CUDA. */
+int gfs_build(gfs_ctx* ctx, const double* p_xyz, const double* s, int64_t n);
+
+/* Consistent value at m query points (Prop. 2 / Sec. 6 minimum radius,
+ * discretised; Sec. 4.3 sign inference, bounds and checks).
+ * x:         device, m*3 FP64 (x_is_fp32 = 0) or FP32 (x_is_fp32 = 1) points.
+ * s_out:     device, m FP32 values (nullable).
+ * s64_out:   device, m FP64 values (nullable).
+ * argmin_out:device, m int64 (nullable): candidate id or sphere index, per code.
+ * flags_out: device, m uint16 result words (nullable).
+ * Errors: GFS_ERR_STATE (no build), GFS_ERR_ARG, GFS_ERR_CUDA. */
+int gfs_query(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, float* s_out, double* s64_out,
+              int64_t* argmin_out, uint16_t* flags_out);
+
+/* Adjoint of gfs_query through the argmin (the paper has no gradients; the
+ * value is piecewise a distance to a point or a sphere, differentiated here).
+ * argmin/flags/s: the forward outputs for the same x (device).
+ * grad_s: device, m FP32 upstream gradient.
+ * grad_x: device, m*3 FP32 output (nullable), overwritten.
+ * grad_p: device, n*3 FP32 output (nullable), overwritten.
+ * grad_sv:device, n FP32 output (nullable), overwritten.
+ * Per-sample sums are accumulated in 64-bit fixed point, so the result does
+ * not depend on scheduling order.  Errors: GFS_ERR_STATE, GFS_ERR_ARG. */
+int gfs_query_backward(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, const float* s,
+                       const int64_t* argmin, const uint16_t* flags, const float* grad_s, float* grad_x,
+                       float* grad_p, float* grad_sv);
+
+/* Copy the surviving candidate ids, ascending, into g_out (device, capacity
+ * cap); *count_host receives the number of survivors (host pointer).
+ * Errors: GFS_ERR_STATE, GFS_ERR_ARG (cap too small: *count_host still set). */
+int gfs_survivors(gfs_ctx* ctx, int64_t* g_out, int64_t cap, int64_t* count_host);
+
+/* Counters of the last build/query (host struct). */
+typedef struct {
+  int64_t n_spheres;        /* spheres in the current state */
+  int64_t n_candidates;     /* n * K generated by the last build */
+  int64_t n_survivors;      /* survivors (unique ids) */
+  int64_t n_survivors_pos;  /* survivors on positive or zero spheres */
+  int64_t n_survivors_neg;  /* survivors on negative or zero spheres */
+  int64_t cull_fp64_rechecks;  /* coverage predicates re-decided in FP64 by the build */
+  int64_t query_fp64_rechecks; /* predicates re-decided in FP64 by the last query */
+  int64_t query_deferred;      /* queries finished by the FP64 path in the last query */
+  int64_t tree_levels;         /* levels of the sphere hierarchy */
+} gfs_stats_t;
+
+/* Synchronises the stream and fills *out (host). */
+int gfs_stats(gfs_ctx* ctx, gfs_stats_t* out);
+
+/* The icosphere direction table the library uses (host computation, no
+ * device needed): writes K = 10*4^tau+2 rows of FP64 (x,y,z) into out_host
+ * (capacity cap_rows).  Returns K, or -1 on bad arguments. */
+int gfs_icosphere(int tau, double* out_host, int64_t cap_rows);
+
+const char* gfs_strerror(int status);
+
+/* Release the context and all library-owned device memory. */
+void gfs_destroy(gfs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GFS_H */

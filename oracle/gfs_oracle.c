@@ -379,28 +379,37 @@ void orc_query(const double* p, const double* s, int64_t n, const int64_t* sg, c
   }
 }
 
-/* Lazy variant for single queries on large inputs: the keep decision of a
- * candidate is evaluated only when the candidate could be the nearest.  The
- * only pruning is the triangle inequality | |x-p_i| - r_i | <= |x - q_ik|
- * (any point of sphere i is at least that far from x), applied with a
- * relative margin of 1e-12 so that rounding can never drop a candidate. */
-typedef struct { double lb; int64_t i; } orc_lbi;
-static int cmp_lbi(const void* a, const void* b) {
-  double x = ((const orc_lbi*)a)->lb, y = ((const orc_lbi*)b)->lb;
-  int64_t i = ((const orc_lbi*)a)->i, j = ((const orc_lbi*)b)->i;
-  if (x < y) return -1;
-  if (x > y) return 1;
-  return i < j ? -1 : (i > j);
+/* Lazy variant for single queries on large inputs: the same result as
+ * orc_query on the full survivor list, with keep decisions evaluated only for
+ * candidates that could be the nearest.  It uses two facts:
+ *  - a candidate nearer to x than LB - tol is covered (LB = r_j - |x - p_j|
+ *    for the sphere j that attains it: |q - p_j| <= |q - x| + |x - p_j| <
+ *    r_j - tol; a candidate of sphere j itself is never that near);
+ *  - any point of sphere i is at least | |x - p_i| - r_i | away from x.
+ * Candidates in the shell LB - tol <= |x - q| <= R are collected, sorted by
+ * (distance^2, id), and keep-tested in that order; the first kept one is the
+ * nearest survivor.  R starts just above LB and grows until a survivor is
+ * found, R passes UB_opp (the value is then the opposite tangent point), or R
+ * passes every candidate.  Margins of 1e-9 relative keep rounding on the
+ * safe side.  The gap output is not computed here (NaN). */
+typedef struct { double d2; int64_t g; } orc_cd;
+static int cmp_cd(const void* a, const void* b) {
+  const orc_cd* x = (const orc_cd*)a;
+  const orc_cd* y = (const orc_cd*)b;
+  if (x->d2 < y->d2) return -1;
+  if (x->d2 > y->d2) return 1;
+  return x->g < y->g ? -1 : (x->g > y->g);
 }
 
 void orc_query_lazy(const double* p, const double* s, int64_t n, const double* U, int K, double tol, int box_cull,
                     int clamp_opp, const double* x, int64_t m, double* value, int64_t* argmin, int32_t* flags,
                     double* gap) {
-  orc_lbi* order = (orc_lbi*)malloc(sizeof(orc_lbi) * (size_t)(n > 0 ? n : 1));
+  size_t cap = 1 << 16;
+  orc_cd* buf = (orc_cd*)malloc(sizeof(orc_cd) * cap);
+  double* lbs = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   for (int64_t t = 0; t < m; ++t) {
     const double* xq = x + 3 * t;
     orc_result R;
-    R.gap = ORC_INF;
     int64_t si = sample_index(p, n, xq);
     int sigma = 0, code = -1;
     if (si >= 0) {
@@ -412,47 +421,68 @@ void orc_query_lazy(const double* p, const double* s, int64_t n, const double* U
       R.argmin = -1;
       R.flags = code;
     } else {
-      int64_t no = 0;
-      for (int64_t i = 0; i < n; ++i) {
-        int c = sgn(s[i]);
-        if (c != sigma && c != 0) continue;
-        order[no].lb = fabs(sqrt(dist2(xq, p + 3 * i)) - fabs(s[i]));
-        order[no].i = i;
-        ++no;
+      double lbv = -ORC_INF, ub = ORC_INF, dmax = 0;
+      int64_t lbj = -1;
+      for (int64_t j = 0; j < n; ++j) {
+        double d = sqrt(dist2(xq, p + 3 * j)), r = fabs(s[j]);
+        int c = sgn(s[j]);
+        if (c == sigma && r - d > lbv) { lbv = r - d; lbj = j; }
+        if (c == -sigma && d - r < ub) ub = d - r;
+        lbs[j] = fabs(d - r);
+        if (d + r > dmax) dmax = d + r;
       }
-      qsort(order, (size_t)no, sizeof(orc_lbi), cmp_lbi);
-      double best = ORC_INF, second = ORC_INF;
+      double skip = lbv - tol - 1e-9 * (1.0 + fabs(lbv));
+      double skip2 = skip > 0 ? skip * skip : -1.0;
+      double width = 1e-4 + 1e-3 * fabs(lbv);
+      double best = ORC_INF;
       int64_t bestg = -1;
-      for (int64_t o = 0; o < no; ++o) {
-        double lim = second < ORC_INF ? sqrt(second) : ORC_INF;
-        if (order[o].lb > lim * (1.0 + 1e-12) + 1e-12) break;
-        int64_t i = order[o].i;
-        for (int k = 0; k < K; ++k) {
-          double q[3];
-          cand_pos(p + 3 * i, s[i], U + 3 * k, q);
-          if (box_cull && !inbox(q)) continue;
-          double d2 = dist2(xq, q);
-          int64_t g = i * (int64_t)(K + 1) + k;
-          int better = d2 < best || (d2 == best && g < bestg);
-          if (!better && !(d2 < second)) continue;
-          if (!orc_keep_one(p, s, n, U, K, tol, box_cull, i, k)) continue;
-          if (better) {
-            if (bestg >= 0) second = best < second ? best : second;
-            best = d2;
-            bestg = g;
-          } else {
-            second = d2;
+      for (;;) {
+        double lim = (lbv > 0 ? lbv : 0) + width;
+        int last = 0;
+        if (clamp_opp && ub < ORC_INF && lim >= ub) { lim = ub; last = 1; }
+        if (lim >= dmax) { lim = dmax; last = 1; }
+        double limm = lim * (1.0 + 1e-9) + 1e-12, lim2 = limm * limm;
+        size_t nc = 0;
+        for (int64_t i = 0; i < n; ++i) {
+          int c = sgn(s[i]);
+          if ((c != sigma && c != 0) || lbs[i] > limm) continue;
+          for (int k = 0; k < K; ++k) {
+            double q[3];
+            cand_pos(p + 3 * i, s[i], U + 3 * k, q);
+            if (box_cull && !inbox(q)) continue;
+            double d2 = dist2(xq, q);
+            if (d2 > lim2 || (i != lbj && d2 < skip2)) continue;
+            if (nc == cap) {
+              cap *= 2;
+              buf = (orc_cd*)realloc(buf, sizeof(orc_cd) * cap);
+            }
+            buf[nc].d2 = d2;
+            buf[nc].g = i * (int64_t)(K + 1) + k;
+            ++nc;
           }
         }
+        qsort(buf, nc, sizeof(orc_cd), cmp_cd);
+        for (size_t u = 0; u < nc; ++u) {
+          int64_t i = buf[u].g / (K + 1);
+          int k = (int)(buf[u].g % (K + 1));
+          if (orc_keep_one(p, s, n, U, K, tol, box_cull, i, k)) {
+            best = buf[u].d2;
+            bestg = buf[u].g;
+            break;
+          }
+        }
+        if (bestg >= 0 || last) break;
+        width *= 8.0;
       }
-      R = finish(p, s, n, tol, clamp_opp, xq, sigma, best, bestg, second);
+      R = finish(p, s, n, tol, clamp_opp, xq, sigma, best, bestg, ORC_INF);
     }
     value[t] = R.value;
     argmin[t] = R.argmin;
     flags[t] = R.flags;
-    if (gap) gap[t] = R.gap;
+    if (gap) gap[t] = 0.0 / 0.0;
   }
-  free(order);
+  free(buf);
+  free(lbs);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -1,0 +1,460 @@
+// C ABI of the library: context management and orchestration of the build,
+// query, backward and survivor-export calls declared in include/gfs.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <vector>
+
+#include "gfs.h"
+#include "gfs_kernels.h"
+
+using namespace gfs;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+int ensure(DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return GFS_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return GFS_ERR_OOM;
+  }
+  b.bytes = bytes;
+  return GFS_OK;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+// Level sizes of the implicit hierarchy over nitems items.
+void tree_layout(Tree& T, int64_t nitems) {
+  std::memset(&T, 0, sizeof(T));
+  T.nitems = nitems;
+  if (nitems <= 0) return;
+  int64_t c = (nitems + kLeaf - 1) / kLeaf, off = 0;
+  int L = 0;
+  for (;;) {
+    T.count[L] = c;
+    T.offset[L] = off;
+    off += c;
+    ++L;
+    if (c <= kFan || L == kMaxLevels) break;
+    c = (c + kFan - 1) / kFan;
+  }
+  T.nlevels = L;
+}
+
+int64_t tree_nodes(const Tree& T) {
+  return T.nlevels ? T.offset[T.nlevels - 1] + T.count[T.nlevels - 1] : 0;
+}
+
+#define GFS_CK(expr)                         \
+  do {                                       \
+    cudaError_t e_ = (expr);                 \
+    if (e_ != cudaSuccess) {                 \
+      cudaGetLastError();                    \
+      return GFS_ERR_CUDA;                   \
+    }                                        \
+  } while (0)
+
+#define GFS_TRY(expr)          \
+  do {                         \
+    int s_ = (expr);           \
+    if (s_ != GFS_OK) return s_; \
+  } while (0)
+
+}  // namespace
+
+struct gfs_ctx {
+  gfs_options opt{};
+  cudaStream_t stream = nullptr;
+  int K = 0, KS = 0;
+  DevBuf U32, U64;
+  // spheres
+  int64_t n = 0;
+  bool built = false;
+  DevBuf sph64, keys_in, keys_out, vals_in, vals_out, sph, thr, sid, bound_bits, consts, cnt, cub_temp;
+  Tree st{};
+  DevBuf st_lo, st_hi, st_rmin;
+  // survivors
+  DevBuf surv_raw[2], surv_sorted[2], vt_lo[2], vt_hi[2];
+  Tree vt[2]{};
+  unsigned int cap = 0;
+  unsigned int nsurv[2] = {0, 0};
+  // query / backward scratch
+  DevBuf defer, acc, witness64;
+  Counters host_cnt{};
+};
+
+namespace {
+
+int cub_ensure(gfs_ctx* c, size_t bytes) { return ensure(c->cub_temp, bytes); }
+
+int sort_u32_pairs(gfs_ctx* c, uint32_t* kin, uint32_t* kout, int* vin, int* vout, int64_t n) {
+  size_t bytes = 0;
+  GFS_CK(sort_pairs(nullptr, bytes, kin, kout, vin, vout, n, c->stream));
+  GFS_TRY(cub_ensure(c, bytes));
+  bytes = c->cub_temp.bytes;
+  GFS_CK(sort_pairs(c->cub_temp.p, bytes, kin, kout, vin, vout, n, c->stream));
+  return GFS_OK;
+}
+
+int build_point_tree(gfs_ctx* c, int cls) {
+  const int64_t ns = c->nsurv[cls];
+  Tree& T = c->vt[cls];
+  tree_layout(T, ns);
+  if (ns == 0) return GFS_OK;
+  GFS_TRY(ensure(c->keys_in, size_t(ns) * 4));
+  GFS_TRY(ensure(c->keys_out, size_t(ns) * 4));
+  GFS_TRY(ensure(c->vals_in, size_t(ns) * 4));
+  GFS_TRY(ensure(c->vals_out, size_t(ns) * 4));
+  GFS_TRY(ensure(c->surv_sorted[cls], size_t(ns) * sizeof(float4)));
+  GFS_CK(launch_point_keys(c->surv_raw[cls].as<float4>(), ns, c->keys_in.as<uint32_t>(), c->vals_in.as<int>(),
+                           c->stream));
+  GFS_TRY(sort_u32_pairs(c, c->keys_in.as<uint32_t>(), c->keys_out.as<uint32_t>(), c->vals_in.as<int>(),
+                         c->vals_out.as<int>(), ns));
+  GFS_CK(launch_gather_points(c->surv_raw[cls].as<float4>(), c->vals_out.as<int>(), ns,
+                              c->surv_sorted[cls].as<float4>(), c->stream));
+  const int64_t nodes = tree_nodes(T);
+  GFS_TRY(ensure(c->vt_lo[cls], size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->vt_hi[cls], size_t(nodes) * sizeof(float4)));
+  T.lo = c->vt_lo[cls].as<float4>();
+  T.hi = c->vt_hi[cls].as<float4>();
+  T.rmin = nullptr;
+  GFS_CK(launch_build_tree(c->surv_sorted[cls].as<float4>(), 0, T, c->stream));
+  return GFS_OK;
+}
+
+void fill_query_args(gfs_ctx* c, QueryArgs& a) {
+  std::memset(&a, 0, sizeof(a));
+  a.sph = c->sph.as<float4>();
+  a.thr = c->thr.as<float4>();
+  a.sid = c->sid.as<int>();
+  a.sph64 = c->sph64.as<D4>();
+  a.st = c->st;
+  a.n = c->n;
+  for (int k = 0; k < 2; ++k) {
+    a.surv[k] = c->surv_sorted[k].as<float4>();
+    a.vt[k] = c->vt[k];
+  }
+  a.U64 = c->U64.as<double>();
+  a.witness64 = c->witness64.as<double>();
+  a.K = c->K;
+  a.KS = c->KS;
+  a.tol32 = float(c->opt.tol);
+  a.tol = c->opt.tol;
+  a.clamp_opp = c->opt.clamp_opp;
+  a.bc = c->consts.as<BuildConsts>();
+  a.cnt = c->cnt.as<Counters>();
+}
+
+}  // namespace
+
+extern "C" {
+
+void gfs_default_options(gfs_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->tau = 3;
+  opt->tol = 1e-6;
+  opt->box_cull = 1;
+  opt->clamp_opp = 1;
+  opt->precision = 0;
+}
+
+const char* gfs_strerror(int status) {
+  switch (status) {
+    case GFS_OK: return "ok";
+    case GFS_ERR_ARG: return "invalid argument";
+    case GFS_ERR_OOM: return "device allocation failed";
+    case GFS_ERR_CUDA: return "CUDA runtime error";
+    case GFS_ERR_STATE: return "call order violated (build first)";
+    case GFS_ERR_TIMEOUT: return "capped device loop ran out of iterations";
+    case GFS_ERR_TOO_LARGE: return "sizes exceed the library's index range";
+    default: return "unknown status";
+  }
+}
+
+int gfs_create(gfs_ctx** out, const gfs_options* opt, void* cuda_stream) {
+  if (!out) return GFS_ERR_ARG;
+  *out = nullptr;
+  gfs_options o;
+  if (opt) o = *opt;
+  else gfs_default_options(&o);
+  if (o.tau < 0 || o.tau > 6 || !(o.tol >= 0.0) || o.tol > 0.1 || (o.precision != 0 && o.precision != 1))
+    return GFS_ERR_ARG;
+  for (int r : o.reserved)
+    if (r != 0) return GFS_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return GFS_ERR_CUDA;
+  }
+  gfs_ctx* c = new gfs_ctx();
+  c->opt = o;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->K = 10 * (1 << (2 * o.tau)) + 2;
+  c->KS = c->K + 1;
+  std::vector<double> U(size_t(c->K) * 3);
+  std::vector<float> U32(size_t(c->K) * 3);
+  if (gfs_icosphere(o.tau, U.data(), c->K) != c->K) {
+    delete c;
+    return GFS_ERR_ARG;
+  }
+  for (size_t t = 0; t < U.size(); ++t) U32[t] = float(U[t]);
+  int st = ensure(c->U64, U.size() * 8);
+  if (st == GFS_OK) st = ensure(c->U32, U32.size() * 4);
+  if (st == GFS_OK) st = ensure(c->bound_bits, 16);
+  if (st == GFS_OK) st = ensure(c->consts, sizeof(BuildConsts));
+  if (st == GFS_OK) st = ensure(c->cnt, sizeof(Counters));
+  if (st != GFS_OK) {
+    gfs_destroy(c);
+    return st;
+  }
+  if (cudaMemcpy(c->U64.p, U.data(), U.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->U32.p, U32.data(), U32.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(c->cnt.p, 0, sizeof(Counters)) != cudaSuccess) {
+    cudaGetLastError();
+    gfs_destroy(c);
+    return GFS_ERR_CUDA;
+  }
+  *out = c;
+  return GFS_OK;
+}
+
+int gfs_set_stream(gfs_ctx* c, void* cuda_stream) {
+  if (!c) return GFS_ERR_ARG;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  return GFS_OK;
+}
+
+int gfs_build(gfs_ctx* c, const double* p, const double* s, int64_t n) {
+  if (!c || !p || !s || n < 1) return GFS_ERR_ARG;
+  if (uint64_t(n) * uint64_t(c->KS) >= (uint64_t(1) << 32) || n >= (int64_t(1) << 30)) return GFS_ERR_TOO_LARGE;
+  c->built = false;
+  c->n = n;
+  cudaStream_t st = c->stream;
+  GFS_TRY(ensure(c->sph64, size_t(n) * sizeof(D4)));
+  GFS_TRY(ensure(c->keys_in, size_t(n) * 4));
+  GFS_TRY(ensure(c->keys_out, size_t(n) * 4));
+  GFS_TRY(ensure(c->vals_in, size_t(n) * 4));
+  GFS_TRY(ensure(c->vals_out, size_t(n) * 4));
+  GFS_TRY(ensure(c->sph, size_t(n) * sizeof(float4)));
+  GFS_TRY(ensure(c->thr, size_t(n) * sizeof(float4)));
+  GFS_TRY(ensure(c->sid, size_t(n) * 4));
+  GFS_CK(cudaMemsetAsync(c->bound_bits.p, 0, 16, st));
+  GFS_CK(cudaMemsetAsync(c->cnt.p, 0, sizeof(Counters), st));
+  // a2: sphere hierarchy
+  GFS_CK(launch_pack_inputs(p, s, n, c->sph64.as<D4>(), c->keys_in.as<uint32_t>(), c->vals_in.as<int>(),
+                            c->bound_bits.as<unsigned int>(), c->consts.as<BuildConsts>(), st));
+  GFS_TRY(sort_u32_pairs(c, c->keys_in.as<uint32_t>(), c->keys_out.as<uint32_t>(), c->vals_in.as<int>(),
+                         c->vals_out.as<int>(), n));
+  GFS_CK(launch_gather_spheres(c->sph64.as<D4>(), c->vals_out.as<int>(), n, c->consts.as<BuildConsts>(),
+                               float(c->opt.tol), c->opt.tol, c->sph.as<float4>(), c->thr.as<float4>(),
+                               c->sid.as<int>(), st));
+  tree_layout(c->st, n);
+  const int64_t nodes = tree_nodes(c->st);
+  GFS_TRY(ensure(c->st_lo, size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->st_hi, size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->st_rmin, size_t(nodes) * sizeof(float)));
+  c->st.lo = c->st_lo.as<float4>();
+  c->st.hi = c->st_hi.as<float4>();
+  c->st.rmin = c->st_rmin.as<float>();
+  GFS_CK(launch_build_tree(c->sph.as<float4>(), 1, c->st, st));
+  // a3: candidate generation and coverage culling
+  const uint64_t ncand = uint64_t(n) * uint64_t(c->K);
+  uint64_t cap = std::max<uint64_t>(uint64_t(1) << 16, ncand / 16 + 1024);
+  cap = std::min<uint64_t>(cap, ncand + 16);
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    c->cap = unsigned(std::min<uint64_t>(cap, 0xffffffffu));
+    GFS_TRY(ensure(c->surv_raw[0], size_t(c->cap) * sizeof(float4)));
+    GFS_TRY(ensure(c->surv_raw[1], size_t(c->cap) * sizeof(float4)));
+    GFS_CK(cudaMemsetAsync(c->cnt.p, 0, sizeof(Counters), st));
+    CullArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.sph = c->sph.as<float4>();
+    a.thr = c->thr.as<float4>();
+    a.sid = c->sid.as<int>();
+    a.sph64 = c->sph64.as<D4>();
+    a.U32 = c->U32.as<float>();
+    a.U64 = c->U64.as<double>();
+    a.K = c->K;
+    a.KS = c->KS;
+    a.tree = c->st;
+    a.tol32 = float(c->opt.tol);
+    a.tol = c->opt.tol;
+    a.box_cull = c->opt.box_cull;
+    a.bc = c->consts.as<BuildConsts>();
+    a.n = n;
+    a.surv[0] = c->surv_raw[0].as<float4>();
+    a.surv[1] = c->surv_raw[1].as<float4>();
+    a.cap = c->cap;
+    a.cnt = c->cnt.as<Counters>();
+    GFS_CK(launch_cull(a, st));
+    GFS_CK(cudaMemcpyAsync(&c->host_cnt, c->cnt.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    GFS_CK(cudaStreamSynchronize(st));
+    const unsigned int need = std::max(c->host_cnt.nsurv[0], c->host_cnt.nsurv[1]);
+    if (need <= c->cap) break;
+    cap = uint64_t(need) + need / 8 + 1024;
+    if (attempt == 2) return GFS_ERR_OOM;
+  }
+  c->nsurv[0] = c->host_cnt.nsurv[0];
+  c->nsurv[1] = c->host_cnt.nsurv[1];
+  // a4: survivor hierarchies, one per sign class
+  GFS_TRY(build_point_tree(c, 0));
+  GFS_TRY(build_point_tree(c, 1));
+  c->built = true;
+  return GFS_OK;
+}
+
+int gfs_query(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, float* s_out, double* s64_out,
+              int64_t* argmin_out, uint16_t* flags_out) {
+  if (!c || m < 0 || (m > 0 && !x)) return GFS_ERR_ARG;
+  if (!c->built) return GFS_ERR_STATE;
+  if (m >= (int64_t(1) << 32)) return GFS_ERR_TOO_LARGE;
+  if (m == 0) return GFS_OK;
+  QueryArgs a;
+  fill_query_args(c, a);
+  if (x_is_fp32) a.x32 = static_cast<const float*>(x);
+  else a.x64 = static_cast<const double*>(x);
+  a.m = m;
+  a.s_out = s_out;
+  a.s64_out = s64_out;
+  a.arg_out = argmin_out;
+  a.fl_out = flags_out;
+  if (c->opt.precision == 0) {
+    GFS_TRY(ensure(c->defer, size_t(m) * 4));
+    a.defer = c->defer.as<uint32_t>();
+    a.defer_cap = unsigned(m);
+  }
+  GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, query_rechecks), 0,
+                         sizeof(unsigned long long), c->stream));
+  GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, ndefer), 0, sizeof(unsigned int),
+                         c->stream));
+  GFS_CK(launch_query(a, c->opt.precision, c->stream));
+  return GFS_OK;
+}
+
+int gfs_query_backward(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, const float* s, const int64_t* argmin,
+                       const uint16_t* flags, const float* grad_s, float* grad_x, float* grad_p, float* grad_sv) {
+  if (!c || m < 0 || (m > 0 && (!x || !s || !argmin || !flags || !grad_s))) return GFS_ERR_ARG;
+  if (!c->built) return GFS_ERR_STATE;
+  const int64_t n = c->n;
+  GFS_TRY(ensure(c->acc, size_t(4 * n) * sizeof(long long)));
+  GFS_CK(cudaMemsetAsync(c->acc.p, 0, size_t(4 * n) * sizeof(long long), c->stream));
+  GradArgs a;
+  std::memset(&a, 0, sizeof(a));
+  if (x_is_fp32) a.x32 = static_cast<const float*>(x);
+  else a.x64 = static_cast<const double*>(x);
+  a.m = m;
+  a.s = s;
+  a.arg = argmin;
+  a.flags = flags;
+  a.grad_s = grad_s;
+  a.grad_x = grad_x;
+  a.sph64 = c->sph64.as<D4>();
+  a.U64 = c->U64.as<double>();
+  a.witness64 = c->witness64.as<double>();
+  a.K = c->K;
+  a.KS = c->KS;
+  a.acc_p = c->acc.as<long long>();
+  a.acc_s = c->acc.as<long long>() + 3 * n;
+  GFS_CK(launch_grad(a, n, grad_p, grad_sv, c->stream));
+  return GFS_OK;
+}
+
+int gfs_survivors(gfs_ctx* c, int64_t* g_out, int64_t cap, int64_t* count_host) {
+  if (!c || !count_host || cap < 0) return GFS_ERR_ARG;
+  if (!c->built) return GFS_ERR_STATE;
+  const int64_t tot = int64_t(c->nsurv[0]) + c->nsurv[1];
+  DevBuf ids, sorted, cnt;
+  int stt = ensure(ids, size_t(tot) * 4 + 16);
+  if (stt == GFS_OK) stt = ensure(sorted, size_t(tot) * 4 + 16);
+  if (stt == GFS_OK) stt = ensure(cnt, 16);
+  unsigned int hc = 0;
+  if (stt == GFS_OK) {
+    if (cudaMemsetAsync(cnt.p, 0, 4, c->stream) != cudaSuccess ||
+        launch_collect_ids(c->surv_raw[0].as<float4>(), c->nsurv[0], c->surv_raw[1].as<float4>(), c->nsurv[1],
+                           c->sph64.as<D4>(), c->KS, ids.as<uint32_t>(), cnt.as<unsigned int>(),
+                           c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&hc, cnt.p, 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      stt = GFS_ERR_CUDA;
+    }
+  }
+  if (stt == GFS_OK) {
+    *count_host = hc;
+    if (hc > 0 && cap >= int64_t(hc) && g_out) {
+      size_t bytes = 0;
+      if (sort_keys_u32(nullptr, bytes, ids.as<uint32_t>(), sorted.as<uint32_t>(), hc, c->stream) != cudaSuccess ||
+          cub_ensure(c, bytes) != GFS_OK) {
+        stt = GFS_ERR_CUDA;
+      } else {
+        bytes = c->cub_temp.bytes;
+        if (sort_keys_u32(c->cub_temp.p, bytes, ids.as<uint32_t>(), sorted.as<uint32_t>(), hc, c->stream) !=
+                cudaSuccess ||
+            launch_widen_ids(sorted.as<uint32_t>(), hc, g_out, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+          cudaGetLastError();
+          stt = GFS_ERR_CUDA;
+        }
+      }
+    } else if (cap < int64_t(hc)) {
+      stt = GFS_ERR_ARG;
+    }
+  }
+  release(ids);
+  release(sorted);
+  release(cnt);
+  return stt;
+}
+
+int gfs_stats(gfs_ctx* c, gfs_stats_t* out) {
+  if (!c || !out) return GFS_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  GFS_CK(cudaMemcpyAsync(&c->host_cnt, c->cnt.p, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+  GFS_CK(cudaStreamSynchronize(c->stream));
+  out->n_spheres = c->n;
+  out->n_candidates = c->n * c->K;
+  out->n_survivors_pos = c->nsurv[0];
+  out->n_survivors_neg = c->nsurv[1];
+  out->cull_fp64_rechecks = int64_t(c->host_cnt.cull_rechecks);
+  out->query_fp64_rechecks = int64_t(c->host_cnt.query_rechecks);
+  out->query_deferred = c->opt.precision == 0 ? int64_t(c->host_cnt.ndefer) : 0;
+  out->tree_levels = c->st.nlevels;
+  out->n_survivors = -1;  // unique count is available through gfs_survivors
+  return GFS_OK;
+}
+
+void gfs_destroy(gfs_ctx* c) {
+  if (!c) return;
+  DevBuf* bufs[] = {&c->U32, &c->U64, &c->sph64, &c->keys_in, &c->keys_out, &c->vals_in, &c->vals_out, &c->sph,
+                    &c->thr, &c->sid, &c->bound_bits, &c->consts, &c->cnt, &c->cub_temp, &c->st_lo, &c->st_hi,
+                    &c->st_rmin, &c->surv_raw[0], &c->surv_raw[1], &c->surv_sorted[0], &c->surv_sorted[1],
+                    &c->vt_lo[0], &c->vt_lo[1], &c->vt_hi[0], &c->vt_hi[1], &c->defer, &c->acc, &c->witness64};
+  for (DevBuf* b : bufs) release(*b);
+  delete c;
+}
+
+}  // extern "C"

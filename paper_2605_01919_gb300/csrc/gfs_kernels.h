@@ -1,0 +1,94 @@
+// Argument blocks and launch helpers of the device kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gfs.h"
+#include "gfs_internal.cuh"
+
+namespace gfs {
+
+struct CullArgs {
+  const float4* sph;     // sorted spheres (x, y, z, s) FP32
+  const float4* thr;     // sorted coverage thresholds (lo/hi for candidates, lo/hi for queries)
+  const int* sid;        // sorted slot -> input index
+  const D4* sph64;       // FP64 spheres in input order
+  const float* U32;      // K x 3 directions, FP32
+  const double* U64;     // K x 3 directions, FP64
+  int K, KS;             // K directions; KS = K + 1 ids per sphere
+  Tree tree;             // sphere hierarchy
+  float tol32;
+  double tol;
+  int box_cull;
+  const BuildConsts* bc;
+  int64_t n;
+  float4* surv[2];       // survivors per sign class (x, y, z, id bits)
+  unsigned int cap;      // capacity of each survivor list
+  Counters* cnt;
+};
+
+struct QueryArgs {
+  const float4* sph;
+  const float4* thr;
+  const int* sid;
+  const D4* sph64;
+  Tree st;
+  int64_t n;
+  const float4* surv[2];
+  Tree vt[2];
+  const double* U64;
+  const double* witness64;  // FP64 witness point per sphere (inserted spheres only)
+  int K, KS;
+  float tol32;
+  double tol;
+  int clamp_opp;
+  const BuildConsts* bc;
+  const double* x64;
+  const float* x32;
+  int64_t m;
+  float* s_out;
+  double* s64_out;
+  int64_t* arg_out;
+  uint16_t* fl_out;
+  uint32_t* defer;
+  unsigned int defer_cap;
+  Counters* cnt;
+};
+
+struct GradArgs {
+  const double* x64;
+  const float* x32;
+  int64_t m;
+  const float* s;
+  const int64_t* arg;
+  const uint16_t* flags;
+  const float* grad_s;
+  float* grad_x;
+  const D4* sph64;
+  const double* U64;
+  const double* witness64;
+  int K, KS;
+  long long* acc_p;  // 3n fixed-point accumulators
+  long long* acc_s;  // n fixed-point accumulators
+};
+
+cudaError_t launch_pack_inputs(const double* p, const double* s, int64_t n, D4* sph64, uint32_t* keys, int* vals,
+                               unsigned int* bound_bits, BuildConsts* bc, cudaStream_t st);
+cudaError_t sort_pairs(void* temp, size_t& temp_bytes, const uint32_t* kin, uint32_t* kout, const int* vin,
+                       int* vout, int64_t n, cudaStream_t st);
+cudaError_t sort_keys_u32(void* temp, size_t& temp_bytes, const uint32_t* kin, uint32_t* kout, int64_t n,
+                          cudaStream_t st);
+cudaError_t launch_gather_spheres(const D4* sph64, const int* order, int64_t n, const BuildConsts* bc, float tol32,
+                                  double tol, float4* sph, float4* thr, int* sid, cudaStream_t st);
+cudaError_t launch_build_tree(const float4* items, int is_sphere, Tree& T, cudaStream_t st);
+cudaError_t launch_point_keys(const float4* items, int64_t n, uint32_t* keys, int* vals, cudaStream_t st);
+cudaError_t launch_gather_points(const float4* src, const int* order, int64_t n, float4* dst, cudaStream_t st);
+cudaError_t launch_cull(const CullArgs& a, cudaStream_t st);
+cudaError_t launch_query(const QueryArgs& a, int precision, cudaStream_t st);
+cudaError_t launch_grad(const GradArgs& a, int64_t n, float* grad_p, float* grad_sv, cudaStream_t st);
+cudaError_t launch_collect_ids(const float4* s0, unsigned int n0, const float4* s1, unsigned int n1, const D4* sph64,
+                               int KS, uint32_t* out, unsigned int* count, cudaStream_t st);
+cudaError_t launch_widen_ids(const uint32_t* in, int64_t n, int64_t* out, cudaStream_t st);
+
+}  // namespace gfs

@@ -1,0 +1,230 @@
+"""Thin ctypes binding of the C ABI in include/gfs.h.
+
+Only argument marshalling happens here: torch tensors provide device memory
+and the current CUDA stream; every step of the computation runs in the
+library's kernels.  There is no CPU fallback: if the shared library or a CUDA
+device is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+CODE_SURVIVOR, CODE_OPPOSITE, CODE_SAMPLE, CODE_OUTSIDE, CODE_INVALID, CODE_LOWER = range(6)
+FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 0x10, 0x20, 0x40, 0x80
+
+EXPORTED = ["gfs_default_options", "gfs_create", "gfs_set_stream", "gfs_build", "gfs_query",
+            "gfs_query_backward", "gfs_survivors", "gfs_stats", "gfs_icosphere", "gfs_strerror",
+            "gfs_destroy"]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_int), ("tol", ctypes.c_double), ("box_cull", ctypes.c_int),
+                ("clamp_opp", ctypes.c_int), ("precision", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "n_spheres", "n_candidates", "n_survivors", "n_survivors_pos", "n_survivors_neg",
+        "cull_fp64_rechecks", "query_fp64_rechecks", "query_deferred", "tree_levels")]
+
+
+class GfsError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgfs.so (building it first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise GfsError(f"CUDA library not built: {path}")
+        _build.build()
+    L = ctypes.CDLL(path)
+    P, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    L.gfs_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.gfs_default_options.restype = None
+    L.gfs_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Options), P]
+    L.gfs_create.restype = i32
+    L.gfs_set_stream.argtypes = [P, P]
+    L.gfs_set_stream.restype = i32
+    L.gfs_build.argtypes = [P, P, P, i64]
+    L.gfs_build.restype = i32
+    L.gfs_query.argtypes = [P, P, i32, i64, P, P, P, P]
+    L.gfs_query.restype = i32
+    L.gfs_query_backward.argtypes = [P, P, i32, i64, P, P, P, P, P, P, P]
+    L.gfs_query_backward.restype = i32
+    L.gfs_survivors.argtypes = [P, P, i64, ctypes.POINTER(i64)]
+    L.gfs_survivors.restype = i32
+    L.gfs_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    L.gfs_stats.restype = i32
+    L.gfs_icosphere.argtypes = [i32, P, i64]
+    L.gfs_icosphere.restype = i32
+    L.gfs_strerror.argtypes = [i32]
+    L.gfs_strerror.restype = ctypes.c_char_p
+    L.gfs_destroy.argtypes = [P]
+    L.gfs_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _check(st: int):
+    if st != 0:
+        raise GfsError(f"gfs error {st}: {load().gfs_strerror(st).decode()}")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def icosphere(tau: int):
+    """The library's direction table (host computation), numpy (K, 3)."""
+    import numpy as np
+    K = 10 * 4 ** tau + 2
+    out = np.zeros((K, 3), dtype=np.float64)
+    k = load().gfs_icosphere(tau, out.ctypes.data_as(ctypes.c_void_p), K)
+    if k != K:
+        raise GfsError("icosphere construction failed")
+    return out
+
+
+class Context:
+    """A sample set with its candidate/survivor hierarchies on one device."""
+
+    def __init__(self, tau: int = 3, tol: float = 1e-6, box_cull: bool = True, clamp_opp: bool = True,
+                 precision: int = 0, stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise GfsError("no CUDA device: the consistent-SDF library has no CPU path")
+        L = load()
+        opt = Options()
+        L.gfs_default_options(ctypes.byref(opt))
+        opt.tau, opt.tol, opt.box_cull, opt.clamp_opp, opt.precision = tau, tol, int(box_cull), int(clamp_opp), precision
+        self.opt = opt
+        self.tau = tau
+        self.K = 10 * 4 ** tau + 2
+        self._stream = stream
+        h = ctypes.c_void_p()
+        _check(L.gfs_create(ctypes.byref(h), ctypes.byref(opt), self._stream_handle()))
+        self._h = h
+        self.n = 0
+        self.p = None
+        self.s = None
+
+    def _stream_handle(self):
+        st = self._stream if self._stream is not None else torch.cuda.current_stream()
+        return ctypes.c_void_p(st.cuda_stream)
+
+    def _sync_stream(self):
+        _check(load().gfs_set_stream(self._h, self._stream_handle()))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gfs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- P build -------------------------------------------------------------
+    def build(self, p: torch.Tensor, s: torch.Tensor):
+        assert p.is_cuda and s.is_cuda and p.dtype == torch.float64 and s.dtype == torch.float64
+        p = p.contiguous()
+        s = s.contiguous()
+        self._sync_stream()
+        _check(load().gfs_build(self._h, _ptr(p), _ptr(s), p.shape[0]))
+        self.n = p.shape[0]
+        self.p, self.s = p, s
+        return self
+
+    # -- query ---------------------------------------------------------------
+    def query(self, x: torch.Tensor, want_f64: bool = True):
+        assert x.is_cuda and x.dtype in (torch.float64, torch.float32) and x.shape[-1] == 3
+        x = x.contiguous()
+        m = x.shape[0]
+        dev = x.device
+        out = {
+            "s": torch.empty(m, dtype=torch.float32, device=dev),
+            "s64": torch.empty(m, dtype=torch.float64, device=dev) if want_f64 else None,
+            "argmin": torch.empty(m, dtype=torch.int64, device=dev),
+            "flags": torch.empty(m, dtype=torch.int16, device=dev),
+        }
+        self._sync_stream()
+        _check(load().gfs_query(self._h, _ptr(x), int(x.dtype == torch.float32), m, _ptr(out["s"]),
+                                _ptr(out["s64"]), _ptr(out["argmin"]), _ptr(out["flags"])))
+        return out
+
+    def query_into(self, x, s_out, s64_out, argmin_out, flags_out):
+        self._sync_stream()
+        _check(load().gfs_query(self._h, _ptr(x), int(x.dtype == torch.float32), x.shape[0], _ptr(s_out),
+                                _ptr(s64_out), _ptr(argmin_out), _ptr(flags_out)))
+
+    def backward(self, x, s, argmin, flags, grad_s, want_x=True, want_p=True, want_s=True):
+        m = x.shape[0]
+        dev = x.device
+        gx = torch.empty((m, 3), dtype=torch.float32, device=dev) if want_x else None
+        gp = torch.empty((self.n, 3), dtype=torch.float32, device=dev) if want_p else None
+        gs = torch.empty(self.n, dtype=torch.float32, device=dev) if want_s else None
+        self._sync_stream()
+        _check(load().gfs_query_backward(self._h, _ptr(x.contiguous()), int(x.dtype == torch.float32), m,
+                                         _ptr(s.contiguous()), _ptr(argmin.contiguous()),
+                                         _ptr(flags.contiguous()), _ptr(grad_s.contiguous().float()),
+                                         _ptr(gx), _ptr(gp), _ptr(gs)))
+        return gx, gp, gs
+
+    def survivors(self) -> torch.Tensor:
+        cnt = ctypes.c_int64(0)
+        self._sync_stream()
+        # first call sizes the output (status GFS_ERR_ARG when it is too small), second fills it
+        st = load().gfs_survivors(self._h, None, 0, ctypes.byref(cnt))
+        if st not in (0, 1):
+            _check(st)
+        out = torch.empty(max(cnt.value, 1), dtype=torch.int64, device="cuda")
+        _check(load().gfs_survivors(self._h, _ptr(out), out.numel(), ctypes.byref(cnt)))
+        return out[: cnt.value]
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(load().gfs_stats(self._h, ctypes.byref(st)))
+        return {n: getattr(st, n) for n, _ in Stats._fields_}
+
+
+class ConsistentSDF(torch.autograd.Function):
+    """s*(x) with a hand-written adjoint: gradients flow to the query points,
+    and to the sample positions and values through the argmin.
+
+    Usage: ``s = ConsistentSDF.apply(x, p, s_samples, ctx)`` where ``ctx`` is
+    a :class:`Context` built on (p, s_samples)."""
+
+    @staticmethod
+    def forward(fctx, x, p, s_samples, gctx: Context):
+        out = gctx.query(x, want_f64=False)
+        fctx.gctx = gctx
+        fctx.save_for_backward(x, out["s"], out["argmin"], out["flags"])
+        return out["s"]
+
+    @staticmethod
+    def backward(fctx, grad_s):
+        x, s, argmin, flags = fctx.saved_tensors
+        need_x, need_p, need_s = fctx.needs_input_grad[0], fctx.needs_input_grad[1], fctx.needs_input_grad[2]
+        gx, gp, gs = fctx.gctx.backward(x, s, argmin, flags, grad_s, need_x, need_p, need_s)
+        return (gx.to(x.dtype) if gx is not None else None,
+                gp.to(torch.float64) if gp is not None else None,
+                gs.to(torch.float64) if gs is not None else None, None)

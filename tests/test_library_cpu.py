@@ -1,0 +1,76 @@
+"""Host-side checks of the C-ABI library (no device needed): it builds for
+sm_103a, loads, exports every entry point include/gfs.h declares, and its
+host logic (icosphere table, option checks, error names) behaves."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def gfs():
+    from paper_2605_01919_gb300 import gfs as G
+    G.load()
+    return G
+
+
+def declared_symbols():
+    hdr = open(os.path.join(ROOT, "include", "gfs.h")).read()
+    return sorted(set(re.findall(r"\b(gfs_[a-z0-9_]+)\s*\(", hdr)))
+
+
+def test_exports_every_declared_symbol(gfs):
+    L = gfs.load()
+    names = declared_symbols()
+    assert len(names) >= 11
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) <= set(gfs.EXPORTED) | set(names)
+
+
+def test_icosphere_table_matches_oracle_bitwise(gfs, orc):
+    # two independent implementations of the documented construction
+    for tau in range(0, 6):
+        a, b = gfs.icosphere(tau), orc.icosphere(tau)
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
+def test_icosphere_bad_args(gfs):
+    L = gfs.load()
+    buf = np.zeros((12, 3))
+    assert L.gfs_icosphere(-1, buf.ctypes.data_as(ctypes.c_void_p), 12) == -1
+    assert L.gfs_icosphere(1, buf.ctypes.data_as(ctypes.c_void_p), 12) == -1   # needs 42 rows
+
+
+def test_option_validation_and_errors(gfs):
+    L = gfs.load()
+    opt = gfs.Options()
+    L.gfs_default_options(ctypes.byref(opt))
+    assert (opt.tau, opt.tol, opt.box_cull, opt.clamp_opp, opt.precision) == (3, 1e-6, 1, 1, 0)
+    h = ctypes.c_void_p()
+    bad = gfs.Options()
+    L.gfs_default_options(ctypes.byref(bad))
+    bad.tau = 9
+    assert L.gfs_create(ctypes.byref(h), ctypes.byref(bad), None) == 1       # GFS_ERR_ARG
+    bad.tau = 2
+    bad.reserved[0] = 5
+    assert L.gfs_create(ctypes.byref(h), ctypes.byref(bad), None) == 1
+    assert L.gfs_strerror(0) == b"ok"
+    assert b"argument" in L.gfs_strerror(1)
+    # null handles are rejected before touching a device
+    assert L.gfs_build(None, None, None, 5) == 1
+    assert L.gfs_query(None, None, 0, 1, None, None, None, None) == 1
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-device path")
+def test_no_device_fails_loudly(gfs):
+    L = gfs.load()
+    h = ctypes.c_void_p()
+    assert L.gfs_create(ctypes.byref(h), None, None) == 3                      # GFS_ERR_CUDA
+    with pytest.raises(gfs.GfsError):
+        gfs.Context()
