@@ -144,6 +144,10 @@ typedef struct {
   int64_t query_fp64_rechecks; /* predicates re-decided in FP64 by the last query */
   int64_t query_deferred;      /* queries finished by the FP64 path in the last query */
   int64_t tree_levels;         /* levels of the sphere hierarchy */
+  int64_t query_sphere_nodes;  /* sphere-hierarchy nodes expanded by the last query (sum over points) */
+  int64_t query_sphere_items;  /* spheres tested by the last query */
+  int64_t query_surv_nodes;    /* survivor-hierarchy nodes expanded by the last query */
+  int64_t query_band_passes;   /* FP64 passes over an error band that settled near-ties */
 } gfs_stats_t;
 
 /* Synchronises the stream and fills *out (host). */

@@ -349,6 +349,8 @@ int gfs_query(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, float* s_out,
   }
   GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, query_rechecks), 0,
                          sizeof(unsigned long long), c->stream));
+  GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, q_sphere_nodes), 0,
+                         4 * sizeof(unsigned long long), c->stream));
   GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, ndefer), 0, sizeof(unsigned int),
                          c->stream));
   GFS_CK(launch_query(a, c->opt.precision, c->stream));
@@ -443,6 +445,10 @@ int gfs_stats(gfs_ctx* c, gfs_stats_t* out) {
   out->query_fp64_rechecks = int64_t(c->host_cnt.query_rechecks);
   out->query_deferred = c->opt.precision == 0 ? int64_t(c->host_cnt.ndefer) : 0;
   out->tree_levels = c->st.nlevels;
+  out->query_sphere_nodes = int64_t(c->host_cnt.q_sphere_nodes);
+  out->query_sphere_items = int64_t(c->host_cnt.q_sphere_items);
+  out->query_surv_nodes = int64_t(c->host_cnt.q_surv_nodes);
+  out->query_band_passes = int64_t(c->host_cnt.q_band_passes);
   out->n_survivors = -1;  // unique count is available through gfs_survivors
   return GFS_OK;
 }

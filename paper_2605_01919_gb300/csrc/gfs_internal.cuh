@@ -128,6 +128,10 @@ struct Counters {
   unsigned int nsurv[2];
   unsigned int ndefer;
   unsigned int pad;
+  unsigned long long q_sphere_nodes;   // hierarchy nodes expanded by the query sphere pass
+  unsigned long long q_sphere_items;   // spheres tested by the query sphere pass
+  unsigned long long q_surv_nodes;     // nodes expanded by the survivor pass
+  unsigned long long q_band_passes;    // FP64 band passes run to settle near-ties
 };
 
 }  // namespace gfs

@@ -349,6 +349,115 @@ __device__ __forceinline__ void surv_pos64(const QueryArgs& a, uint32_t g, doubl
   }
 }
 
+// Warp-aggregated counter update (one atomic per warp)
+__device__ __forceinline__ void warp_count(unsigned long long* dst, unsigned long long v) {
+  const unsigned mask = __activemask();
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  if ((threadIdx.x & 31) == __ffs(mask) - 1 && v) atomicAdd(dst, v);
+}
+
+// FP64 band pass over the sphere hierarchy.  Finds, among the spheres whose
+// FP32 value lies at or below thr, the exact FP64 minimum and its input index
+// (ties to the lowest index).  mode 0: value |x-p| - r over sign class c;
+// mode 1: value |x-p| + r over all spheres.  The FP32 threshold is chosen so
+// that the exact minimiser always lies in the band.
+__device__ double band_sphere(const QueryArgs& a, const BuildConsts& bc, double x64, double y64, double z64, float x,
+                              float y, float z, int mode, int c, float thr, int& arg) {
+  const Tree& T = a.st;
+  const float grow = 1.f + 8.f * 5.9604644775390625e-8f;
+  double best = INFINITY;
+  arg = INT_MAX;
+  uint32_t stack[kStack];
+  int sp = 0;
+  const int top = T.nlevels - 1;
+  for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
+  while (sp > 0) {
+    const uint32_t nd = stack[--sp];
+    const int lev = node_level(nd);
+    const int64_t idx = node_index(nd);
+    if (lev == 0) {
+      const int64_t b = idx * kLeaf, e = min(b + kLeaf, a.n);
+      for (int64_t j = b; j < e; ++j) {
+        const float4 P = a.sph[j];
+        if (mode == 0 && (P.w == 0.f || int(P.w < 0.f) != c)) continue;
+        const float dx = x - P.x, dy = y - P.y, dz = z - P.z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float r = fabsf(P.w);
+        const float v = mode == 0 ? __fsqrt_rn(d2) - r : __fsqrt_rn(d2) + r;
+        if (!(v <= thr)) continue;
+        const int o = a.sid[j];
+        const D4 pj = a.sph64[o];
+        const double dl = __dsqrt_rn(ex_d2(x64, y64, z64, pj.x, pj.y, pj.z));
+        const double v64 = mode == 0 ? __dsub_rn(dl, fabs(pj.w)) : __dadd_rn(dl, fabs(pj.w));
+        if (v64 < best || (v64 == best && o < arg)) {
+          best = v64;
+          arg = o;
+        }
+      }
+    } else {
+      const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
+      const int64_t off = T.offset[lev - 1];
+      for (int64_t cc = cb; cc < ce; ++cc) {
+        const float4 L = T.lo[off + cc], H = T.hi[off + cc];
+        float t;
+        if (mode == 0) {
+          const float rm = c == 0 ? L.w : H.w;
+          if (!(rm > 0.f)) continue;
+          t = fmaf(thr + rm, grow, bc.eprune);
+        } else {
+          t = fmaf(thr - T.rmin[off + cc], grow, bc.eprune);
+        }
+        if (t > 0.f && box_d2(x, y, z, L, H) < t * t) stack[sp++] = pack_node(lev - 1, cc);
+      }
+    }
+  }
+  return best;
+}
+
+// FP64 band pass over a survivor hierarchy: exact nearest survivor among
+// those whose FP32 distance^2 is at most thr (ties to the lowest id).
+__device__ double band_surv(const QueryArgs& a, const BuildConsts& bc, int cls, double x64, double y64, double z64,
+                            float x, float y, float z, float thr, uint32_t& gbest) {
+  const Tree& T = a.vt[cls];
+  const float4* items = a.surv[cls];
+  const float grow = 1.f + 8.f * 5.9604644775390625e-8f;
+  const float thn = thr * grow + bc.ed_lin * __fsqrt_rn(thr) + 1e-30f;
+  double best = INFINITY;
+  gbest = 0xffffffffu;
+  uint32_t stack[kStack];
+  int sp = 0;
+  const int top = T.nlevels - 1;
+  for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
+  while (sp > 0) {
+    const uint32_t nd = stack[--sp];
+    const int lev = node_level(nd);
+    const int64_t idx = node_index(nd);
+    if (lev == 0) {
+      const int64_t b = idx * kLeaf, e = min(b + kLeaf, T.nitems);
+      for (int64_t j = b; j < e; ++j) {
+        const float4 P = items[j];
+        const float dx = x - P.x, dy = y - P.y, dz = z - P.z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (!(d2 <= thr)) continue;
+        const uint32_t g = __float_as_uint(P.w);
+        double qx, qy, qz;
+        surv_pos64(a, g, qx, qy, qz);
+        const double e2 = ex_d2(x64, y64, z64, qx, qy, qz);
+        if (e2 < best || (e2 == best && g < gbest)) {
+          best = e2;
+          gbest = g;
+        }
+      }
+    } else {
+      const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
+      const int64_t off = T.offset[lev - 1];
+      for (int64_t cc = cb; cc < ce; ++cc)
+        if (box_d2(x, y, z, T.lo[off + cc], T.hi[off + cc]) < thn) stack[sp++] = pack_node(lev - 1, cc);
+    }
+  }
+  return best;
+}
+
 __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
   const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (q >= a.m) return;
@@ -356,7 +465,7 @@ __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
   double x64, y64, z64;
   load_query(a, q, x64, y64, z64);
   const float x = float(x64), y = float(y64), z = float(z64);
-  unsigned long long rechecks = 0;
+  unsigned long long rechecks = 0, n_nodes = 0, n_items = 0, n_snodes = 0, n_band = 0;
   bool defer = !(fabs(x64) <= bc.A && fabs(y64) <= bc.A && fabs(z64) <= bc.A);
   const float grow = 1.f + 8.f * kU;
   const float ea2 = 2.f * bc.ea;
@@ -378,8 +487,10 @@ __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
       const uint32_t nd = stack[--sp];
       const int lev = node_level(nd);
       const int64_t idx = node_index(nd);
+      ++n_nodes;
       if (lev == 0) {
         const int64_t b = idx * kLeaf, e = min(b + kLeaf, a.n);
+        n_items += uint64_t(e - b);
         for (int64_t j = b; j < e; ++j) {
           const float4 P = a.sph[j];
           const float dx = x - P.x, dy = y - P.y, dz = z - P.z;
@@ -448,97 +559,127 @@ __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
       }
     }
   }
-  if (rechecks) atomicAdd(&a.cnt->query_rechecks, rechecks);
-  if (!defer && sample != INT_MAX) {
-    write_result(a, q, a.sph64[sample].w, sample, GFS_CODE_SAMPLE);
-    return;
+  int code = -1;
+  double value = 0.0;
+  int64_t arg = -1;
+  int flags = 0;
+  if (!defer) {
+    if (sample != INT_MAX) {
+      code = GFS_CODE_SAMPLE;
+      value = a.sph64[sample].w;
+      arg = sample;
+    } else if (cov[0] && cov[1]) {
+      code = GFS_CODE_INVALID;
+      value = __longlong_as_double(0x7ff8000000000000LL);
+    } else if (!cov[0] && !cov[1]) {
+      code = GFS_CODE_OUTSIDE;
+    }
+    if (code >= 0) flags = code;
   }
-  if (!defer && cov[0] && cov[1]) {
-    write_result(a, q, __longlong_as_double(0x7ff8000000000000LL), -1, GFS_CODE_INVALID);
-    return;
-  }
-  if (!defer && !cov[0] && !cov[1]) {
-    write_result(a, q, 0.0, -1, GFS_CODE_OUTSIDE);
-    return;
-  }
-  const int cs = cov[0] ? 0 : 1, co = 1 - cs;
-  // ---- pass over the survivors of x's sign -------------------------------
-  float bd = INFINITY, sd = INFINITY;
-  uint32_t gbest = 0xffffffffu;
-  if (!defer && a.vt[cs].nlevels > 0) {
-    const Tree& T = a.vt[cs];
-    const float4* items = a.surv[cs];
+  if (!defer && code < 0) {
+    const int cs = cov[0] ? 0 : 1, co = 1 - cs;
+    // ---- pass over the survivors of x's sign -----------------------------
+    float bd = INFINITY, sd = INFINITY;
+    uint32_t gbest = 0xffffffffu;
     auto band = [&](float D) { return bc.ed_lin * __fsqrt_rn(D) + bc.ed_quad * D + 1e-30f; };
-    float th = INFINITY, thn = INFINITY;  // threshold on d^2, and widened for nodes
-    uint32_t stack[kStack];
-    int sp = 0;
-    const int top = T.nlevels - 1;
-    for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
-    while (sp > 0) {
-      const uint32_t nd = stack[--sp];
-      const int lev = node_level(nd);
-      const int64_t idx = node_index(nd);
-      if (lev == 0) {
-        const int64_t b = idx * kLeaf, e = min(b + kLeaf, T.nitems);
-        for (int64_t j = b; j < e; ++j) {
-          const float4 P = items[j];
-          const float dx = x - P.x, dy = y - P.y, dz = z - P.z;
-          const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          if (d2 < th) {
-            if (d2 < bd) {
-              sd = bd;
-              bd = d2;
-              gbest = __float_as_uint(P.w);
-            } else {
-              sd = d2;
+    if (a.vt[cs].nlevels > 0) {
+      const Tree& T = a.vt[cs];
+      const float4* items = a.surv[cs];
+      float th = INFINITY, thn = INFINITY;  // threshold on d^2, and widened for nodes
+      uint32_t stack[kStack];
+      int sp = 0;
+      const int top = T.nlevels - 1;
+      for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
+      while (sp > 0) {
+        const uint32_t nd = stack[--sp];
+        const int lev = node_level(nd);
+        const int64_t idx = node_index(nd);
+        ++n_snodes;
+        if (lev == 0) {
+          const int64_t b = idx * kLeaf, e = min(b + kLeaf, T.nitems);
+          for (int64_t j = b; j < e; ++j) {
+            const float4 P = items[j];
+            const float dx = x - P.x, dy = y - P.y, dz = z - P.z;
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (d2 < th) {
+              if (d2 < bd) {
+                sd = bd;
+                bd = d2;
+                gbest = __float_as_uint(P.w);
+              } else {
+                sd = d2;
+              }
+              th = fminf(sd, bd + 2.f * band(bd));
+              thn = th * grow + bc.ed_lin * __fsqrt_rn(th) + 1e-30f;
             }
-            th = fminf(sd, bd + 2.f * band(bd));
-            thn = th * grow + bc.ed_lin * __fsqrt_rn(th) + 1e-30f;
           }
-        }
-      } else {
-        const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
-        const int64_t off = T.offset[lev - 1];
-        int best = -1;
-        float bestd = INFINITY;
-        uint32_t pend[kFan];
-        int np = 0;
-        for (int64_t c = cb; c < ce; ++c) {
-          const float d2 = box_d2(x, y, z, T.lo[off + c], T.hi[off + c]);
-          if (!(d2 < thn)) continue;
-          if (d2 < bestd) {
-            if (best >= 0) pend[np++] = pack_node(lev - 1, best);
-            best = int(c);
-            bestd = d2;
-          } else {
-            pend[np++] = pack_node(lev - 1, c);
+        } else {
+          const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
+          const int64_t off = T.offset[lev - 1];
+          int best = -1;
+          float bestd = INFINITY;
+          uint32_t pend[kFan];
+          int np = 0;
+          for (int64_t c = cb; c < ce; ++c) {
+            const float d2 = box_d2(x, y, z, T.lo[off + c], T.hi[off + c]);
+            if (!(d2 < thn)) continue;
+            if (d2 < bestd) {
+              if (best >= 0) pend[np++] = pack_node(lev - 1, best);
+              best = int(c);
+              bestd = d2;
+            } else {
+              pend[np++] = pack_node(lev - 1, c);
+            }
           }
+          for (int t = 0; t < np; ++t) stack[sp++] = pend[t];
+          if (best >= 0) stack[sp++] = pack_node(lev - 1, best);
         }
-        for (int t = 0; t < np; ++t) stack[sp++] = pend[t];
-        if (best >= 0) stack[sp++] = pack_node(lev - 1, best);
       }
     }
-    // certify the nearest survivor: no other survivor within the band
-    if (gbest != 0xffffffffu && !(sd >= bd + 2.f * band(bd))) defer = true;
-  }
-  // certify the nearest opposite tangent point
-  if (A[co].idx >= 0 && !(A[co].sec >= A[co].best + ea2)) defer = true;
-  double m = 0.0, ub = 0.0, ds = 0.0;
-  int code = 0;
-  int64_t arg = -1;
-  if (!defer) {
     const bool have_s = gbest != 0xffffffffu, have_u = A[co].idx >= 0;
+    // exact nearest survivor: direct when no other survivor lies in the
+    // error band, else an FP64 pass over the band
+    double ds = INFINITY;
     if (have_s) {
-      double qx, qy, qz;
-      surv_pos64(a, gbest, qx, qy, qz);
-      ds = __dsqrt_rn(ex_d2(x64, y64, z64, qx, qy, qz));
+      if (sd >= bd + 2.f * band(bd)) {
+        double qx, qy, qz;
+        surv_pos64(a, gbest, qx, qy, qz);
+        ds = __dsqrt_rn(ex_d2(x64, y64, z64, qx, qy, qz));
+      } else {
+        ++n_band;
+        ds = __dsqrt_rn(band_surv(a, bc, cs, x64, y64, z64, x, y, z, bd + 2.f * band(bd), gbest));
+      }
     }
+    // exact nearest opposite tangent point
+    double ub = INFINITY;
     int uj = -1;
     if (have_u) {
-      uj = a.sid[A[co].idx];
-      const D4 pj = a.sph64[uj];
-      ub = __dsub_rn(__dsqrt_rn(ex_d2(x64, y64, z64, pj.x, pj.y, pj.z)), fabs(pj.w));
+      if (A[co].sec >= A[co].best + ea2) {
+        uj = a.sid[A[co].idx];
+        const D4 pj = a.sph64[uj];
+        ub = __dsub_rn(__dsqrt_rn(ex_d2(x64, y64, z64, pj.x, pj.y, pj.z)), fabs(pj.w));
+      } else {
+        ++n_band;
+        ub = band_sphere(a, bc, x64, y64, z64, x, y, z, 0, co, A[co].best + ea2, uj);
+      }
     }
+    // exact lower bound LB (max over x's class of r - |x-p|) on demand
+    double lb = 0.0;
+    int lj = -1;
+    bool have_lb = false;
+    auto exact_lb = [&]() {
+      if (have_lb) return;
+      have_lb = true;
+      if (A[cs].sec >= A[cs].best + ea2) {
+        lj = a.sid[A[cs].idx];
+        const D4 pl = a.sph64[lj];
+        lb = __dsub_rn(fabs(pl.w), __dsqrt_rn(ex_d2(x64, y64, z64, pl.x, pl.y, pl.z)));
+      } else {
+        ++n_band;
+        lb = -band_sphere(a, bc, x64, y64, z64, x, y, z, 0, cs, A[cs].best + ea2, lj);
+      }
+    };
+    double m;
     if (have_s && (!a.clamp_opp || ds <= ub)) {
       code = GFS_CODE_SURVIVOR;
       m = ds;
@@ -548,56 +689,51 @@ __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
       m = ub;
       arg = uj;
     } else {
-      // lower bound of the containing spheres: needs its exact argmax
-      if (!(A[cs].sec >= A[cs].best + ea2)) {
-        defer = true;
+      exact_lb();
+      code = GFS_CODE_LOWER;
+      m = lb;
+      arg = lj;
+    }
+    if (m < 0.0) m = 0.0;
+    flags = code;
+    const double E = double(bc.ea) * 1.01 + 1e-15;
+    // LB_VIOL: m < LB - tol
+    const double lbt = -double(A[cs].best) - a.tol;
+    if (m < lbt - E) {
+      flags |= GFS_FLAG_LB_VIOL;
+    } else if (!(m > lbt + E)) {
+      exact_lb();
+      if (m < __dsub_rn(lb, a.tol)) flags |= GFS_FLAG_LB_VIOL;
+    }
+    // FAR_VIOL: m > FAR + tol
+    const double ft = double(F.best) + a.tol;
+    if (m > ft + E) {
+      flags |= GFS_FLAG_FAR_VIOL;
+    } else if (!(m < ft - E)) {
+      double far;
+      if (F.sec >= F.best + ea2) {
+        const D4 pf = a.sph64[a.sid[F.idx]];
+        far = __dadd_rn(__dsqrt_rn(ex_d2(x64, y64, z64, pf.x, pf.y, pf.z)), fabs(pf.w));
       } else {
-        const int lj = a.sid[A[cs].idx];
-        const D4 pl = a.sph64[lj];
-        m = __dsub_rn(fabs(pl.w), __dsqrt_rn(ex_d2(x64, y64, z64, pl.x, pl.y, pl.z)));
-        code = GFS_CODE_LOWER;
-        arg = lj;
+        ++n_band;
+        int fj;
+        far = band_sphere(a, bc, x64, y64, z64, x, y, z, 1, 0, F.best + ea2, fj);
       }
+      if (m > __dadd_rn(far, a.tol)) flags |= GFS_FLAG_FAR_VIOL;
     }
-    if (!defer) {
-      if (m < 0.0) m = 0.0;
-      int flags = code;
-      // LB_VIOL: m < LB - tol with LB = -min_{class}(|x-p|-r)
-      const double lb32 = -double(A[cs].best);
-      const double E = double(bc.ea) * 1.01 + 1e-15;
-      const double lbt = lb32 - a.tol;
-      if (m < lbt - E) {
-        flags |= GFS_FLAG_LB_VIOL;
-      } else if (!(m > lbt + E)) {
-        if (!(A[cs].sec >= A[cs].best + ea2)) {
-          defer = true;
-        } else {
-          const D4 pl = a.sph64[a.sid[A[cs].idx]];
-          const double lb = __dsub_rn(fabs(pl.w), __dsqrt_rn(ex_d2(x64, y64, z64, pl.x, pl.y, pl.z)));
-          if (m < __dsub_rn(lb, a.tol)) flags |= GFS_FLAG_LB_VIOL;
-        }
-      }
-      // FAR_VIOL: m > FAR + tol with FAR = min_all(|x-p|+r)
-      const double ft = double(F.best) + a.tol;
-      if (m > ft + E) {
-        flags |= GFS_FLAG_FAR_VIOL;
-      } else if (!(m < ft - E)) {
-        if (!(F.sec >= F.best + ea2)) {
-          defer = true;
-        } else {
-          const D4 pf = a.sph64[a.sid[F.idx]];
-          const double far = __dadd_rn(__dsqrt_rn(ex_d2(x64, y64, z64, pf.x, pf.y, pf.z)), fabs(pf.w));
-          if (m > __dadd_rn(far, a.tol)) flags |= GFS_FLAG_FAR_VIOL;
-        }
-      }
-      if (have_u && ub < __dsub_rn(m, a.tol)) flags |= GFS_FLAG_OPP_VIOL;
-      if (!defer) {
-        write_result(a, q, cs == 0 ? m : -m, arg, flags);
-        return;
-      }
-    }
+    if (have_u && ub < __dsub_rn(m, a.tol)) flags |= GFS_FLAG_OPP_VIOL;
+    value = cs == 0 ? m : -m;
   }
-  // the FP64 path finishes this query
+  warp_count(&a.cnt->query_rechecks, rechecks);
+  warp_count(&a.cnt->q_sphere_nodes, n_nodes);
+  warp_count(&a.cnt->q_sphere_items, n_items);
+  warp_count(&a.cnt->q_surv_nodes, n_snodes);
+  warp_count(&a.cnt->q_band_passes, n_band);
+  if (!defer) {
+    write_result(a, q, value, arg, flags);
+    return;
+  }
+  // outside the coordinate range the error bounds assume: FP64 path
   const unsigned int slot = atomicAdd(&a.cnt->ndefer, 1u);
   if (slot < a.defer_cap) a.defer[slot] = uint32_t(q);
 }

@@ -31,7 +31,8 @@ class Options(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "n_spheres", "n_candidates", "n_survivors", "n_survivors_pos", "n_survivors_neg",
-        "cull_fp64_rechecks", "query_fp64_rechecks", "query_deferred", "tree_levels")]
+        "cull_fp64_rechecks", "query_fp64_rechecks", "query_deferred", "tree_levels",
+        "query_sphere_nodes", "query_sphere_items", "query_surv_nodes", "query_band_passes")]
 
 
 class GfsError(RuntimeError):
