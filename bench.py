@@ -1,0 +1,341 @@
+"""Benchmark: consistent SDF queries per second, including the P build.
+
+One step = the whole hot path over one synthetic workload: build the sphere
+hierarchy, generate and cull all candidates (P build), build the survivor
+hierarchies, and evaluate the consistent value at every query point.
+Workload: 64^3 node grid over [-1,1]^3 sampling the union of 6 spheres and 4
+boxes (seeded), icosphere depth 3 (642 candidates per sample), 4x upsampled
+253^3 = 16,194,277 query points.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
+(a bounded sample per step, extrapolated to the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "union64_tau3_q253"
+CONFIG = {
+    "workload": WORKLOAD,
+    "samples": "64^3 node grid on [-1,1]^3, union of 6 spheres + 4 boxes (seed 2000)",
+    "tau": 3,
+    "candidates": 64 ** 3 * 642,
+    "queries": 253 ** 3,
+    "query_dtype": "f64",
+}
+METRIC = "consistent SDF queries/sec (incl. P build)"
+UNIT = "queries/s"
+SM_COUNT = 152
+FP32_LANES = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gfs", choices=["gfs", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--query-subsample", type=int, default=1,
+                    help="use every k-th query point (small cases for profiler captures)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ----------------------------------------------------------------------------
+def oracle_sample(w, x, n_keep: int, n_query: int, seed: int):
+    """Time keep decisions of n_keep random candidates and the consistent
+    value at n_query random queries (lazy FP64 oracle); return per-unit s."""
+    from oracle import oracle as O
+    U = O.icosphere(w.tau)
+    K = U.shape[0]
+    rng = np.random.default_rng(seed)
+    ii = rng.integers(0, w.n, n_keep)
+    kk = rng.integers(0, K, n_keep)
+    t0 = time.perf_counter()
+    for i, k in zip(ii, kk):
+        O.keep_one(w.p, w.s, U, int(i), int(k))
+    t_keep = (time.perf_counter() - t0) / n_keep
+    sel = rng.integers(0, x.shape[0], n_query)
+    t0 = time.perf_counter()
+    O.query_lazy(w.p, w.s, U, x[sel])
+    t_q = (time.perf_counter() - t0) / n_query
+    return t_keep, t_q, K
+
+
+def cpu_baseline_line(w, x, steps: int, n_keep: int = 400, n_query: int = 2):
+    tk, tq = [], []
+    K = 0
+    for st in range(steps):
+        a, b, K = oracle_sample(w, x, n_keep, n_query, seed=st)
+        tk.append(a)
+        tq.append(b)
+    t_keep, t_q = float(np.mean(tk)), float(np.mean(tq))
+    total = w.n * K * t_keep + x.shape[0] * t_q
+    return {
+        "value": x.shape[0] / total,
+        "unit": UNIT,
+        "cores": 1,
+        "kind": "oracle",
+        "sample": (f"{steps} x ({n_keep} random candidate keep decisions + {n_query} random queries, lazy FP64 "
+                   f"oracle, single thread); extrapolated to {w.n * K} candidates + {x.shape[0]} queries: "
+                   f"{t_keep * 1e3:.3f} ms/candidate, {t_q:.3f} s/query"),
+    }
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2605_01919_gb300 import workloads as W
+    w = W.union_grid()
+    x = w.make_queries()
+    cb = cpu_baseline_line(w, x, max(1, args.warmup + args.steps), n_keep=300, n_query=1)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * x.shape[0] / cb["value"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": CONFIG, "cpu_baseline": cb,
+        "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# the CUDA path
+# ----------------------------------------------------------------------------
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2605_01919_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_2605_01919_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        e = t.get(kernel)
+        if e and e.get("source_hash") == kernel_hash():
+            return e["dram_bytes_per_launch"]
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def run_gfs(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2605_01919_gb300 import gfs
+    from paper_2605_01919_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = W.union_grid()
+    xh = np.ascontiguousarray(w.make_queries()[:: args.query_subsample])
+    m, n = xh.shape[0], w.n
+    p = torch.from_numpy(w.p).to(dev)
+    s = torch.from_numpy(w.s).to(dev)
+    x = torch.from_numpy(xh).to(dev)
+    s_out = torch.empty(m, dtype=torch.float32, device=dev)
+    arg_out = torch.empty(m, dtype=torch.int64, device=dev)
+    fl_out = torch.empty(m, dtype=torch.int16, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ctx = gfs.Context(tau=w.tau, timing=True)
+
+    def step():
+        ctx.build(p, s)
+        ctx.query_into(x, s_out, None, arg_out, fl_out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phases = []
+    launches0 = ctx.stats()
+    stream = torch.cuda.current_stream()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)              # L2 flush between steps (outside the timed interval)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        phases.append(ctx.stats())         # synchronises; phase times from events on the library stream
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if rank == 0 else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    launches1 = phases[-1]
+    # own kernels, plus the radix-sort calls (each runs a handful of sort kernels)
+    own_launches = launches1["kernel_launches"] - launches0["kernel_launches"]
+    sort_calls = launches1["sort_calls"] - launches0["sort_calls"]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * m / (ms_per_step / 1e3)
+
+    # ---- end to end through the host-buffer entry point ----------------------
+    e2e = None
+    if not args.no_e2e:
+        ph = torch.from_numpy(w.p).pin_memory()
+        sh = torch.from_numpy(w.s).pin_memory()
+        xh_t = torch.from_numpy(xh).pin_memory()
+        so = torch.empty(m, dtype=torch.float32).pin_memory()
+        ao = torch.empty(m, dtype=torch.int64).pin_memory()
+        fo = torch.empty(m, dtype=torch.int16).pin_memory()
+        ctx_h = gfs.Context(tau=w.tau)
+        ctx_h.solve_host(ph, sh, xh_t, so, ao, fo)   # warm-up
+        torch.cuda.synchronize()
+        e_times = []
+        for k in range(max(1, min(args.steps, 3))):
+            flush.fill_(k & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx_h.solve_host(ph, sh, xh_t, so, ao, fo)
+            e_times.append(time.perf_counter() - t0)
+        ctx_h.close()
+        e_s = float(np.mean(e_times))
+        e2e = {"value": world * m / e_s, "unit": UNIT, "h2d_bytes_per_step": n * 24 + n * 8 + m * 24,
+               "d2h_bytes_per_step": m * (4 + 8 + 2), "ms_per_step": 1e3 * e_s}
+
+    # ---- roofline of the dominant kernel --------------------------------------
+    last = phases[-1]
+    q_fast = float(np.mean([ph_["ms_query_fast"] for ph_ in phases]))
+    q_exact = float(np.mean([ph_["ms_query_exact"] for ph_ in phases]))
+    cull = float(np.mean([ph_["ms_build_cull"] for ph_ in phases]))
+    build = float(np.mean([ph_["ms_build_total"] for ph_ in phases]))
+    pair_tests = last["query_sphere_items"] + last["query_surv_items"]
+    flops = 8.0 * pair_tests                       # 8 flops per (point, sphere|survivor) pair test
+    clock_mhz = 2070.0
+    peak = SM_COUNT * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
+    achieved = flops / (q_fast / 1e3) / 1e12 if q_fast > 0 else 0.0
+    roofline = {"kernel": "k_query_fast", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": recorded_traffic("k_query_fast"),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
+                "units_per_launch": pair_tests, "flops_per_unit": 8}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": dict(CONFIG, queries=m, parallelism=f"replicas{world}", l2="256 MiB buffer written between steps "
+                       "(outside the timed interval); queries (389 MB) exceed L2"),
+        "roofline": roofline,
+        "phases_ms": {"build_total": build, "cull": cull, "query_fast": q_fast, "query_exact": q_exact},
+        "counters": {k: last[k] for k in ("n_survivors_pos", "n_survivors_neg", "cull_fp64_rechecks",
+                                          "query_fp64_rechecks", "query_deferred", "query_sphere_nodes",
+                                          "query_sphere_items", "query_surv_nodes", "query_surv_items",
+                                          "query_band_passes", "tree_levels")},
+        "step_ms": step_ms,
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": own_launches,
+        "gpu_launches_note": f"own kernels in the timed region; plus {sort_calls} radix-sort calls",
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_line(w, xh, steps=2, n_keep=400, n_query=6)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gfs(a)

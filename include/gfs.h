@@ -79,7 +79,8 @@ typedef struct {
   int clamp_opp;    /* 1: clamp by the nearest opposite-sign tangent point (Sec. 4.3 upper bound) */
   int precision;    /* 0: FP32 bulk arithmetic, predicates near a boundary re-decided in FP64;
                        1: FP64 throughout (same results, slower) */
-  int reserved[7];  /* must be zero */
+  int timing;       /* 1: record CUDA events around each phase (read back by gfs_stats) */
+  int reserved[6];  /* must be zero */
 } gfs_options;
 
 /* Fill *opt with the defaults: tau 3, tol 1e-6, box_cull 1, clamp_opp 1, precision 0. */
@@ -148,10 +149,29 @@ typedef struct {
   int64_t query_sphere_items;  /* spheres tested by the last query */
   int64_t query_surv_nodes;    /* survivor-hierarchy nodes expanded by the last query */
   int64_t query_band_passes;   /* FP64 passes over an error band that settled near-ties */
+  int64_t query_surv_items;    /* survivors tested by the last query */
+  /* phase times of the last build / query in ms (timing = 1 only, else 0) */
+  double ms_build_total;       /* whole gfs_build */
+  double ms_build_cull;        /* candidate culling kernel */
+  double ms_query_fast;        /* FP32 query kernel */
+  double ms_query_exact;       /* FP64 kernel for queries outside the FP32 error model */
+  int64_t kernel_launches;     /* kernels this library has launched in this process (cumulative) */
+  int64_t sort_calls;          /* radix-sort calls (each launches a few library-sort kernels) */
 } gfs_stats_t;
 
 /* Synchronises the stream and fills *out (host). */
 int gfs_stats(gfs_ctx* ctx, gfs_stats_t* out);
+
+/* Whole path from HOST buffers: copies p_host (n*3 FP64) and s_host (n FP64)
+ * and x_host (m*3, FP64 or FP32) to library-owned device memory, runs
+ * gfs_build and gfs_query, and copies the FP32 values, argmins and result
+ * words back into s_out_host / argmin_out_host / flags_out_host (each
+ * nullable).  Host buffers should be page-locked for asynchronous copies.
+ * Returns after the results are in host memory (synchronises the stream).
+ * Errors: as gfs_build / gfs_query. */
+int gfs_solve_host(gfs_ctx* ctx, const double* p_host, const double* s_host, int64_t n, const void* x_host,
+                   int x_is_fp32, int64_t m, float* s_out_host, int64_t* argmin_out_host,
+                   uint16_t* flags_out_host);
 
 /* The icosphere direction table the library uses (host computation, no
  * device needed): writes K = 10*4^tau+2 rows of FP64 (x,y,z) into out_host

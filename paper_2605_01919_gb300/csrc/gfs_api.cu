@@ -104,6 +104,13 @@ struct gfs_ctx {
   // query / backward scratch
   DevBuf defer, acc, witness64;
   Counters host_cnt{};
+  // host-buffer path (gfs_solve_host)
+  DevBuf h_p, h_s, h_x, h_sout, h_arg, h_fl;
+  // phase events (timing = 1): build start, cull start, cull end, build end,
+  // query start, fast end, query end
+  cudaEvent_t ev[7] = {};
+  bool have_ev = false;
+  bool built_timed = false, query_timed = false;
 };
 
 namespace {
@@ -201,7 +208,8 @@ int gfs_create(gfs_ctx** out, const gfs_options* opt, void* cuda_stream) {
   gfs_options o;
   if (opt) o = *opt;
   else gfs_default_options(&o);
-  if (o.tau < 0 || o.tau > 6 || !(o.tol >= 0.0) || o.tol > 0.1 || (o.precision != 0 && o.precision != 1))
+  if (o.tau < 0 || o.tau > 6 || !(o.tol >= 0.0) || o.tol > 0.1 || (o.precision != 0 && o.precision != 1) ||
+      (o.timing != 0 && o.timing != 1))
     return GFS_ERR_ARG;
   for (int r : o.reserved)
     if (r != 0) return GFS_ERR_ARG;
@@ -231,6 +239,15 @@ int gfs_create(gfs_ctx** out, const gfs_options* opt, void* cuda_stream) {
     gfs_destroy(c);
     return st;
   }
+  if (o.timing) {
+    for (cudaEvent_t& e : c->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        gfs_destroy(c);
+        return GFS_ERR_CUDA;
+      }
+    c->have_ev = true;
+  }
   if (cudaMemcpy(c->U64.p, U.data(), U.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->U32.p, U32.data(), U32.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(c->cnt.p, 0, sizeof(Counters)) != cudaSuccess) {
@@ -252,8 +269,10 @@ int gfs_build(gfs_ctx* c, const double* p, const double* s, int64_t n) {
   if (!c || !p || !s || n < 1) return GFS_ERR_ARG;
   if (uint64_t(n) * uint64_t(c->KS) >= (uint64_t(1) << 32) || n >= (int64_t(1) << 30)) return GFS_ERR_TOO_LARGE;
   c->built = false;
+  c->built_timed = false;
   c->n = n;
   cudaStream_t st = c->stream;
+  if (c->have_ev) GFS_CK(cudaEventRecord(c->ev[0], st));
   GFS_TRY(ensure(c->sph64, size_t(n) * sizeof(D4)));
   GFS_TRY(ensure(c->keys_in, size_t(n) * 4));
   GFS_TRY(ensure(c->keys_out, size_t(n) * 4));
@@ -310,7 +329,9 @@ int gfs_build(gfs_ctx* c, const double* p, const double* s, int64_t n) {
     a.surv[1] = c->surv_raw[1].as<float4>();
     a.cap = c->cap;
     a.cnt = c->cnt.as<Counters>();
+    if (c->have_ev) GFS_CK(cudaEventRecord(c->ev[1], st));
     GFS_CK(launch_cull(a, st));
+    if (c->have_ev) GFS_CK(cudaEventRecord(c->ev[2], st));
     GFS_CK(cudaMemcpyAsync(&c->host_cnt, c->cnt.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     GFS_CK(cudaStreamSynchronize(st));
     const unsigned int need = std::max(c->host_cnt.nsurv[0], c->host_cnt.nsurv[1]);
@@ -323,6 +344,10 @@ int gfs_build(gfs_ctx* c, const double* p, const double* s, int64_t n) {
   // a4: survivor hierarchies, one per sign class
   GFS_TRY(build_point_tree(c, 0));
   GFS_TRY(build_point_tree(c, 1));
+  if (c->have_ev) {
+    GFS_CK(cudaEventRecord(c->ev[3], st));
+    c->built_timed = true;
+  }
   c->built = true;
   return GFS_OK;
 }
@@ -350,10 +375,17 @@ int gfs_query(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, float* s_out,
   GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, query_rechecks), 0,
                          sizeof(unsigned long long), c->stream));
   GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, q_sphere_nodes), 0,
-                         4 * sizeof(unsigned long long), c->stream));
+                         5 * sizeof(unsigned long long), c->stream));
   GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, ndefer), 0, sizeof(unsigned int),
                          c->stream));
-  GFS_CK(launch_query(a, c->opt.precision, c->stream));
+  if (c->have_ev) GFS_CK(cudaEventRecord(c->ev[4], c->stream));
+  if (c->opt.precision == 0) GFS_CK(launch_query_fast(a, c->stream));
+  if (c->have_ev) GFS_CK(cudaEventRecord(c->ev[5], c->stream));
+  GFS_CK(launch_query_exact(a, c->opt.precision == 1, c->stream));
+  if (c->have_ev) {
+    GFS_CK(cudaEventRecord(c->ev[6], c->stream));
+    c->query_timed = true;
+  }
   return GFS_OK;
 }
 
@@ -449,16 +481,69 @@ int gfs_stats(gfs_ctx* c, gfs_stats_t* out) {
   out->query_sphere_items = int64_t(c->host_cnt.q_sphere_items);
   out->query_surv_nodes = int64_t(c->host_cnt.q_surv_nodes);
   out->query_band_passes = int64_t(c->host_cnt.q_band_passes);
+  out->query_surv_items = int64_t(c->host_cnt.q_surv_items);
+  auto ms = [&](int a, int b) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, c->ev[a], c->ev[b]) != cudaSuccess) {
+      cudaGetLastError();
+      t = 0.f;
+    }
+    return double(t);
+  };
+  unsigned long long own = 0, sorts = 0;
+  launch_counts(&own, &sorts);
+  out->kernel_launches = int64_t(own);
+  out->sort_calls = int64_t(sorts);
+  if (c->have_ev && c->built_timed) {
+    out->ms_build_total = ms(0, 3);
+    out->ms_build_cull = ms(1, 2);
+  }
+  if (c->have_ev && c->query_timed) {
+    out->ms_query_fast = ms(4, 5);
+    out->ms_query_exact = ms(5, 6);
+  }
   out->n_survivors = -1;  // unique count is available through gfs_survivors
+  return GFS_OK;
+}
+
+int gfs_solve_host(gfs_ctx* c, const double* p_host, const double* s_host, int64_t n, const void* x_host,
+                   int x_is_fp32, int64_t m, float* s_out_host, int64_t* argmin_out_host,
+                   uint16_t* flags_out_host) {
+  if (!c || !p_host || !s_host || n < 1 || m < 0 || (m > 0 && !x_host)) return GFS_ERR_ARG;
+  cudaStream_t st = c->stream;
+  const size_t xb = size_t(m) * 3 * (x_is_fp32 ? 4 : 8);
+  GFS_TRY(ensure(c->h_p, size_t(n) * 24));
+  GFS_TRY(ensure(c->h_s, size_t(n) * 8));
+  GFS_TRY(ensure(c->h_x, xb));
+  GFS_TRY(ensure(c->h_sout, size_t(m) * 4));
+  GFS_TRY(ensure(c->h_arg, size_t(m) * 8));
+  GFS_TRY(ensure(c->h_fl, size_t(m) * 2));
+  GFS_CK(cudaMemcpyAsync(c->h_p.p, p_host, size_t(n) * 24, cudaMemcpyHostToDevice, st));
+  GFS_CK(cudaMemcpyAsync(c->h_s.p, s_host, size_t(n) * 8, cudaMemcpyHostToDevice, st));
+  if (m > 0) GFS_CK(cudaMemcpyAsync(c->h_x.p, x_host, xb, cudaMemcpyHostToDevice, st));
+  GFS_TRY(gfs_build(c, c->h_p.as<double>(), c->h_s.as<double>(), n));
+  GFS_TRY(gfs_query(c, c->h_x.p, x_is_fp32, m, s_out_host ? c->h_sout.as<float>() : nullptr, nullptr,
+                    argmin_out_host ? c->h_arg.as<int64_t>() : nullptr,
+                    flags_out_host ? c->h_fl.as<uint16_t>() : nullptr));
+  if (m > 0 && s_out_host) GFS_CK(cudaMemcpyAsync(s_out_host, c->h_sout.p, size_t(m) * 4, cudaMemcpyDeviceToHost, st));
+  if (m > 0 && argmin_out_host)
+    GFS_CK(cudaMemcpyAsync(argmin_out_host, c->h_arg.p, size_t(m) * 8, cudaMemcpyDeviceToHost, st));
+  if (m > 0 && flags_out_host)
+    GFS_CK(cudaMemcpyAsync(flags_out_host, c->h_fl.p, size_t(m) * 2, cudaMemcpyDeviceToHost, st));
+  GFS_CK(cudaStreamSynchronize(st));
   return GFS_OK;
 }
 
 void gfs_destroy(gfs_ctx* c) {
   if (!c) return;
+  if (c->have_ev)
+    for (cudaEvent_t e : c->ev)
+      if (e) cudaEventDestroy(e);
   DevBuf* bufs[] = {&c->U32, &c->U64, &c->sph64, &c->keys_in, &c->keys_out, &c->vals_in, &c->vals_out, &c->sph,
                     &c->thr, &c->sid, &c->bound_bits, &c->consts, &c->cnt, &c->cub_temp, &c->st_lo, &c->st_hi,
                     &c->st_rmin, &c->surv_raw[0], &c->surv_raw[1], &c->surv_sorted[0], &c->surv_sorted[1],
-                    &c->vt_lo[0], &c->vt_lo[1], &c->vt_hi[0], &c->vt_hi[1], &c->defer, &c->acc, &c->witness64};
+                    &c->vt_lo[0], &c->vt_lo[1], &c->vt_hi[0], &c->vt_hi[1], &c->defer, &c->acc, &c->witness64,
+                    &c->h_p, &c->h_s, &c->h_x, &c->h_sout, &c->h_arg, &c->h_fl};
   for (DevBuf* b : bufs) release(*b);
   delete c;
 }

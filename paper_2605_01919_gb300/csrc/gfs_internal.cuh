@@ -132,6 +132,7 @@ struct Counters {
   unsigned long long q_sphere_items;   // spheres tested by the query sphere pass
   unsigned long long q_surv_nodes;     // nodes expanded by the survivor pass
   unsigned long long q_band_passes;    // FP64 band passes run to settle near-ties
+  unsigned long long q_surv_items;     // survivors tested by the survivor pass
 };
 
 }  // namespace gfs

@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
   double x64, y64, z64;
   load_query(a, q, x64, y64, z64);
   const float x = float(x64), y = float(y64), z = float(z64);
-  unsigned long long rechecks = 0, n_nodes = 0, n_items = 0, n_snodes = 0, n_band = 0;
+  unsigned long long rechecks = 0, n_nodes = 0, n_items = 0, n_snodes = 0, n_sitems = 0, n_band = 0;
   bool defer = !(fabs(x64) <= bc.A && fabs(y64) <= bc.A && fabs(z64) <= bc.A);
   const float grow = 1.f + 8.f * kU;
   const float ea2 = 2.f * bc.ea;
@@ -597,6 +597,7 @@ __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
         ++n_snodes;
         if (lev == 0) {
           const int64_t b = idx * kLeaf, e = min(b + kLeaf, T.nitems);
+          n_sitems += uint64_t(e - b);
           for (int64_t j = b; j < e; ++j) {
             const float4 P = items[j];
             const float dx = x - P.x, dy = y - P.y, dz = z - P.z;
@@ -729,6 +730,7 @@ __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
   warp_count(&a.cnt->q_sphere_items, n_items);
   warp_count(&a.cnt->q_surv_nodes, n_snodes);
   warp_count(&a.cnt->q_band_passes, n_band);
+  warp_count(&a.cnt->q_surv_items, n_sitems);
   if (!defer) {
     write_result(a, q, value, arg, flags);
     return;
@@ -1002,28 +1004,40 @@ __global__ void k_widen_ids(const uint32_t* __restrict__ in, int64_t n, int64_t*
 // ---------------------------------------------------------------------------
 static inline unsigned int nblk(int64_t n, int b) { return (unsigned int)((n + b - 1) / b); }
 
+// kernels this library launched (own kernels; sorts counted as calls)
+static unsigned long long g_launches = 0, g_sort_calls = 0;
+void launch_counts(unsigned long long* own, unsigned long long* sorts) {
+  *own = g_launches;
+  *sorts = g_sort_calls;
+}
+
 cudaError_t launch_pack_inputs(const double* p, const double* s, int64_t n, D4* sph64, uint32_t* keys, int* vals,
                                unsigned int* bound_bits, BuildConsts* bc, cudaStream_t st) {
   unsigned int g = nblk(n, 256);
   if (g > 4096) g = 4096;
   k_pack_inputs<<<g, 256, 0, st>>>(p, s, n, sph64, keys, vals, bound_bits);
+  ++g_launches;
   k_consts<<<1, 1, 0, st>>>(bound_bits, bc);
+  ++g_launches;
   return cudaGetLastError();
 }
 
 cudaError_t sort_pairs(void* temp, size_t& temp_bytes, const uint32_t* kin, uint32_t* kout, const int* vin,
                        int* vout, int64_t n, cudaStream_t st) {
+  if (temp) ++g_sort_calls;
   return cub::DeviceRadixSort::SortPairs(temp, temp_bytes, kin, kout, vin, vout, n, 0, 30, st);
 }
 
 cudaError_t sort_keys_u32(void* temp, size_t& temp_bytes, const uint32_t* kin, uint32_t* kout, int64_t n,
                           cudaStream_t st) {
+  if (temp) ++g_sort_calls;
   return cub::DeviceRadixSort::SortKeys(temp, temp_bytes, kin, kout, n, 0, 32, st);
 }
 
 cudaError_t launch_gather_spheres(const D4* sph64, const int* order, int64_t n, const BuildConsts* bc, float tol32,
                                   double tol, float4* sph, float4* thr, int* sid, cudaStream_t st) {
   k_gather_spheres<<<nblk(n, 256), 256, 0, st>>>(sph64, order, n, bc, tol32, tol, sph, thr, sid);
+  ++g_launches;
   return cudaGetLastError();
 }
 
@@ -1031,39 +1045,52 @@ cudaError_t launch_build_tree(const float4* items, int is_sphere, Tree& T, cudaS
   if (T.nlevels == 0) return cudaSuccess;
   k_leaves<<<nblk(T.count[0], 128), 128, 0, st>>>(items, T.nitems, is_sphere, T.lo, T.hi,
                                                     is_sphere ? T.rmin : nullptr, T.count[0]);
+  ++g_launches;
   for (int l = 1; l < T.nlevels; ++l)
     k_level<<<nblk(T.count[l], 128), 128, 0, st>>>(T.lo, T.hi, is_sphere ? T.rmin : nullptr, T.offset[l - 1],
                                                    T.count[l - 1], T.offset[l], T.count[l]);
+    ++g_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_point_keys(const float4* items, int64_t n, uint32_t* keys, int* vals, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   k_point_keys<<<nblk(n, 256), 256, 0, st>>>(items, n, keys, vals);
+  ++g_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather_points(const float4* src, const int* order, int64_t n, float4* dst, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   k_gather_points<<<nblk(n, 256), 256, 0, st>>>(src, order, n, dst);
+  ++g_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_cull(const CullArgs& a, cudaStream_t st) {
   dim3 grid(nblk(a.n, 128), unsigned(a.K));
   k_cull<<<grid, 128, 0, st>>>(a);
+  ++g_launches;
   return cudaGetLastError();
 }
 
-cudaError_t launch_query(const QueryArgs& a, int precision, cudaStream_t st) {
+cudaError_t launch_query_fast(const QueryArgs& a, cudaStream_t st) {
   if (a.m == 0) return cudaSuccess;
-  if (precision == 1) {
+  k_query_fast<<<nblk(a.m, 128), 128, 0, st>>>(a);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_query_exact(const QueryArgs& a, int all, cudaStream_t st) {
+  if (a.m == 0) return cudaSuccess;
+  if (all) {
     k_query_exact_all<<<nblk(a.m, 128), 128, 0, st>>>(a);
+    ++g_launches;
   } else {
-    k_query_fast<<<nblk(a.m, 128), 128, 0, st>>>(a);
     unsigned int g = nblk(a.m, 128);
     if (g > 152u * 16u) g = 152u * 16u;
     k_query_exact_deferred<<<g, 128, 0, st>>>(a);
+    ++g_launches;
   }
   return cudaGetLastError();
 }
@@ -1079,12 +1106,14 @@ cudaError_t launch_collect_ids(const float4* s0, unsigned int n0, const float4* 
                                int KS, uint32_t* out, unsigned int* count, cudaStream_t st) {
   if (n0 + n1 == 0) return cudaSuccess;
   k_collect_ids<<<nblk(int64_t(n0) + n1, 256), 256, 0, st>>>(s0, n0, s1, n1, sph64, KS, out, count);
+  ++g_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_widen_ids(const uint32_t* in, int64_t n, int64_t* out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   k_widen_ids<<<nblk(n, 256), 256, 0, st>>>(in, n, out);
+  ++g_launches;
   return cudaGetLastError();
 }
 

@@ -85,10 +85,12 @@ cudaError_t launch_build_tree(const float4* items, int is_sphere, Tree& T, cudaS
 cudaError_t launch_point_keys(const float4* items, int64_t n, uint32_t* keys, int* vals, cudaStream_t st);
 cudaError_t launch_gather_points(const float4* src, const int* order, int64_t n, float4* dst, cudaStream_t st);
 cudaError_t launch_cull(const CullArgs& a, cudaStream_t st);
-cudaError_t launch_query(const QueryArgs& a, int precision, cudaStream_t st);
+cudaError_t launch_query_fast(const QueryArgs& a, cudaStream_t st);
+cudaError_t launch_query_exact(const QueryArgs& a, int all, cudaStream_t st);
 cudaError_t launch_grad(const GradArgs& a, int64_t n, float* grad_p, float* grad_sv, cudaStream_t st);
 cudaError_t launch_collect_ids(const float4* s0, unsigned int n0, const float4* s1, unsigned int n1, const D4* sph64,
                                int KS, uint32_t* out, unsigned int* count, cudaStream_t st);
+void launch_counts(unsigned long long* own, unsigned long long* sorts);
 cudaError_t launch_widen_ids(const uint32_t* in, int64_t n, int64_t* out, cudaStream_t st);
 
 }  // namespace gfs

@@ -18,21 +18,24 @@ CODE_SURVIVOR, CODE_OPPOSITE, CODE_SAMPLE, CODE_OUTSIDE, CODE_INVALID, CODE_LOWE
 FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 0x10, 0x20, 0x40, 0x80
 
 EXPORTED = ["gfs_default_options", "gfs_create", "gfs_set_stream", "gfs_build", "gfs_query",
-            "gfs_query_backward", "gfs_survivors", "gfs_stats", "gfs_icosphere", "gfs_strerror",
-            "gfs_destroy"]
+            "gfs_query_backward", "gfs_survivors", "gfs_stats", "gfs_solve_host", "gfs_icosphere",
+            "gfs_strerror", "gfs_destroy"]
 
 
 class Options(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_int), ("tol", ctypes.c_double), ("box_cull", ctypes.c_int),
-                ("clamp_opp", ctypes.c_int), ("precision", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("clamp_opp", ctypes.c_int), ("precision", ctypes.c_int), ("timing", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "n_spheres", "n_candidates", "n_survivors", "n_survivors_pos", "n_survivors_neg",
         "cull_fp64_rechecks", "query_fp64_rechecks", "query_deferred", "tree_levels",
-        "query_sphere_nodes", "query_sphere_items", "query_surv_nodes", "query_band_passes")]
+        "query_sphere_nodes", "query_sphere_items", "query_surv_nodes", "query_band_passes",
+        "query_surv_items")] + [(n, ctypes.c_double) for n in (
+        "ms_build_total", "ms_build_cull", "ms_query_fast", "ms_query_exact")] + [
+        (n, ctypes.c_int64) for n in ("kernel_launches", "sort_calls")]
 
 
 class GfsError(RuntimeError):
@@ -74,6 +77,8 @@ def load(build_if_missing: bool = True):
     L.gfs_survivors.restype = i32
     L.gfs_stats.argtypes = [P, ctypes.POINTER(Stats)]
     L.gfs_stats.restype = i32
+    L.gfs_solve_host.argtypes = [P, P, P, i64, P, i32, i64, P, P, P]
+    L.gfs_solve_host.restype = i32
     L.gfs_icosphere.argtypes = [i32, P, i64]
     L.gfs_icosphere.restype = i32
     L.gfs_strerror.argtypes = [i32]
@@ -108,13 +113,14 @@ class Context:
     """A sample set with its candidate/survivor hierarchies on one device."""
 
     def __init__(self, tau: int = 3, tol: float = 1e-6, box_cull: bool = True, clamp_opp: bool = True,
-                 precision: int = 0, stream: torch.cuda.Stream | None = None):
+                 precision: int = 0, stream: torch.cuda.Stream | None = None, timing: bool = False):
         if not torch.cuda.is_available():
             raise GfsError("no CUDA device: the consistent-SDF library has no CPU path")
         L = load()
         opt = Options()
         L.gfs_default_options(ctypes.byref(opt))
         opt.tau, opt.tol, opt.box_cull, opt.clamp_opp, opt.precision = tau, tol, int(box_cull), int(clamp_opp), precision
+        opt.timing = int(timing)
         self.opt = opt
         self.tau = tau
         self.K = 10 * 4 ** tau + 2
@@ -200,6 +206,18 @@ class Context:
         out = torch.empty(max(cnt.value, 1), dtype=torch.int64, device="cuda")
         _check(load().gfs_survivors(self._h, _ptr(out), out.numel(), ctypes.byref(cnt)))
         return out[: cnt.value]
+
+    def solve_host(self, p, s, x, s_out, argmin_out, flags_out):
+        """Whole path from host (numpy or pinned torch CPU) buffers."""
+        def ptr(a):
+            if a is None:
+                return None
+            return ctypes.c_void_p(a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data)
+        is32 = int((x.dtype == torch.float32) if isinstance(x, torch.Tensor) else (x.dtype.itemsize == 4))
+        self._sync_stream()
+        _check(load().gfs_solve_host(self._h, ptr(p), ptr(s), p.shape[0], ptr(x), is32, x.shape[0],
+                                     ptr(s_out), ptr(argmin_out), ptr(flags_out)))
+        self.n = p.shape[0]
 
     def stats(self) -> dict:
         st = Stats()

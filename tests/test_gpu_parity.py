@@ -96,7 +96,9 @@ def test_degenerate_inputs(G, orc):
                   [-0.4, 0.3, 0.2], [-0.4, 0.3, 0.2], [0.7, 0.7, 0.7]])
     s = np.array([0.3, 0.3, 0.2, 0.0, 0.05, -0.25, -0.1, 0.5])
     rng = np.random.default_rng(9)
-    x = np.concatenate([p, rng.uniform(-1, 1, size=(500, 3)), [[0.3, 0.0, 0.0], [0.25, 0.0, 0.0]]])
+    # the last point lies inside both ball 0 (+) and ball 5 (-), which overlap
+    x = np.concatenate([p, rng.uniform(-1, 1, size=(500, 3)), [[0.3, 0.0, 0.0], [0.25, 0.0, 0.0],
+                                                               [-0.219, 0.164, 0.109]]])
     for tau in (1, 2):
         surv, val, arg, fl = oracle_all(orc, p, s, tau, x)
         assert np.any((fl & 15) == 4)                     # invalid (both signs) occurs
