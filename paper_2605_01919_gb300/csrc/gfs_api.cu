@@ -95,7 +95,7 @@ struct gfs_ctx {
   bool built = false;
   DevBuf sph64, keys_in, keys_out, vals_in, vals_out, sph, thr, sid, bound_bits, consts, cnt, cub_temp;
   Tree st{};
-  DevBuf st_lo, st_hi, st_rmin;
+  DevBuf st_lo, st_hi, st_bp, st_bn, st_bf;
   // survivors
   DevBuf surv_raw[2], surv_sorted[2], vt_lo[2], vt_hi[2];
   Tree vt[2]{};
@@ -147,8 +147,8 @@ int build_point_tree(gfs_ctx* c, int cls) {
   GFS_TRY(ensure(c->vt_hi[cls], size_t(nodes) * sizeof(float4)));
   T.lo = c->vt_lo[cls].as<float4>();
   T.hi = c->vt_hi[cls].as<float4>();
-  T.rmin = nullptr;
-  GFS_CK(launch_build_tree(c->surv_sorted[cls].as<float4>(), 0, T, c->stream));
+  T.bp = T.bn = T.bf = nullptr;
+  GFS_CK(launch_build_tree(c->surv_sorted[cls].as<float4>(), 0, 0.f, T, c->stream));
   return GFS_OK;
 }
 
@@ -173,6 +173,49 @@ void fill_query_args(gfs_ctx* c, QueryArgs& a) {
   a.clamp_opp = c->opt.clamp_opp;
   a.bc = c->consts.as<BuildConsts>();
   a.cnt = c->cnt.as<Counters>();
+}
+
+// a2: Morton-sort the samples in sph64[0, n) and build the sphere hierarchy
+// (also used to rebuild it after insertions).
+int build_sphere_hierarchy(gfs_ctx* c, int64_t n) {
+  cudaStream_t st = c->stream;
+  c->n = n;
+  GFS_TRY(ensure(c->keys_in, size_t(n) * 4));
+  GFS_TRY(ensure(c->keys_out, size_t(n) * 4));
+  GFS_TRY(ensure(c->vals_in, size_t(n) * 4));
+  GFS_TRY(ensure(c->vals_out, size_t(n) * 4));
+  GFS_TRY(ensure(c->sph, size_t(n) * sizeof(float4)));
+  GFS_TRY(ensure(c->thr, size_t(n) * sizeof(float4)));
+  GFS_TRY(ensure(c->sid, size_t(n) * 4));
+  GFS_CK(cudaMemsetAsync(c->bound_bits.p, 0, 16, st));
+  GFS_CK(launch_keys_d4(c->sph64.as<D4>(), n, c->keys_in.as<uint32_t>(), c->vals_in.as<int>(),
+                        c->bound_bits.as<unsigned int>(), c->consts.as<BuildConsts>(), st));
+  GFS_TRY(sort_u32_pairs(c, c->keys_in.as<uint32_t>(), c->keys_out.as<uint32_t>(), c->vals_in.as<int>(),
+                         c->vals_out.as<int>(), n));
+  GFS_CK(launch_gather_spheres(c->sph64.as<D4>(), c->vals_out.as<int>(), n, c->consts.as<BuildConsts>(),
+                               float(c->opt.tol), c->opt.tol, c->sph.as<float4>(), c->thr.as<float4>(),
+                               c->sid.as<int>(), st));
+  tree_layout(c->st, n);
+  const int64_t nodes = tree_nodes(c->st);
+  GFS_TRY(ensure(c->st_lo, size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->st_hi, size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->st_bp, size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->st_bn, size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->st_bf, size_t(nodes) * sizeof(float4)));
+  c->st.lo = c->st_lo.as<float4>();
+  c->st.hi = c->st_hi.as<float4>();
+  c->st.bp = c->st_bp.as<float4>();
+  c->st.bn = c->st_bn.as<float4>();
+  c->st.bf = c->st_bf.as<float4>();
+  // the coordinate bound A is needed on the host for the hierarchy's rounding slack
+  unsigned int bits[2] = {0, 0};
+  GFS_CK(cudaMemcpyAsync(bits, c->bound_bits.p, 8, cudaMemcpyDeviceToHost, st));
+  GFS_CK(cudaStreamSynchronize(st));
+  float Ahost;
+  std::memcpy(&Ahost, &bits[0], 4);
+  Ahost = std::max(1.0f, Ahost);
+  GFS_CK(launch_build_tree(c->sph.as<float4>(), 1, Ahost, c->st, st));
+  return GFS_OK;
 }
 
 }  // namespace
@@ -270,36 +313,13 @@ int gfs_build(gfs_ctx* c, const double* p, const double* s, int64_t n) {
   if (uint64_t(n) * uint64_t(c->KS) >= (uint64_t(1) << 32) || n >= (int64_t(1) << 30)) return GFS_ERR_TOO_LARGE;
   c->built = false;
   c->built_timed = false;
-  c->n = n;
   cudaStream_t st = c->stream;
   if (c->have_ev) GFS_CK(cudaEventRecord(c->ev[0], st));
   GFS_TRY(ensure(c->sph64, size_t(n) * sizeof(D4)));
-  GFS_TRY(ensure(c->keys_in, size_t(n) * 4));
-  GFS_TRY(ensure(c->keys_out, size_t(n) * 4));
-  GFS_TRY(ensure(c->vals_in, size_t(n) * 4));
-  GFS_TRY(ensure(c->vals_out, size_t(n) * 4));
-  GFS_TRY(ensure(c->sph, size_t(n) * sizeof(float4)));
-  GFS_TRY(ensure(c->thr, size_t(n) * sizeof(float4)));
-  GFS_TRY(ensure(c->sid, size_t(n) * 4));
-  GFS_CK(cudaMemsetAsync(c->bound_bits.p, 0, 16, st));
   GFS_CK(cudaMemsetAsync(c->cnt.p, 0, sizeof(Counters), st));
+  GFS_CK(launch_copy_inputs(p, s, n, c->sph64.as<D4>(), st));
   // a2: sphere hierarchy
-  GFS_CK(launch_pack_inputs(p, s, n, c->sph64.as<D4>(), c->keys_in.as<uint32_t>(), c->vals_in.as<int>(),
-                            c->bound_bits.as<unsigned int>(), c->consts.as<BuildConsts>(), st));
-  GFS_TRY(sort_u32_pairs(c, c->keys_in.as<uint32_t>(), c->keys_out.as<uint32_t>(), c->vals_in.as<int>(),
-                         c->vals_out.as<int>(), n));
-  GFS_CK(launch_gather_spheres(c->sph64.as<D4>(), c->vals_out.as<int>(), n, c->consts.as<BuildConsts>(),
-                               float(c->opt.tol), c->opt.tol, c->sph.as<float4>(), c->thr.as<float4>(),
-                               c->sid.as<int>(), st));
-  tree_layout(c->st, n);
-  const int64_t nodes = tree_nodes(c->st);
-  GFS_TRY(ensure(c->st_lo, size_t(nodes) * sizeof(float4)));
-  GFS_TRY(ensure(c->st_hi, size_t(nodes) * sizeof(float4)));
-  GFS_TRY(ensure(c->st_rmin, size_t(nodes) * sizeof(float)));
-  c->st.lo = c->st_lo.as<float4>();
-  c->st.hi = c->st_hi.as<float4>();
-  c->st.rmin = c->st_rmin.as<float>();
-  GFS_CK(launch_build_tree(c->sph.as<float4>(), 1, c->st, st));
+  GFS_TRY(build_sphere_hierarchy(c, n));
   // a3: candidate generation and coverage culling
   const uint64_t ncand = uint64_t(n) * uint64_t(c->K);
   uint64_t cap = std::max<uint64_t>(uint64_t(1) << 16, ncand / 16 + 1024);
@@ -541,7 +561,7 @@ void gfs_destroy(gfs_ctx* c) {
       if (e) cudaEventDestroy(e);
   DevBuf* bufs[] = {&c->U32, &c->U64, &c->sph64, &c->keys_in, &c->keys_out, &c->vals_in, &c->vals_out, &c->sph,
                     &c->thr, &c->sid, &c->bound_bits, &c->consts, &c->cnt, &c->cub_temp, &c->st_lo, &c->st_hi,
-                    &c->st_rmin, &c->surv_raw[0], &c->surv_raw[1], &c->surv_sorted[0], &c->surv_sorted[1],
+                    &c->st_bp, &c->st_bn, &c->st_bf, &c->surv_raw[0], &c->surv_raw[1], &c->surv_sorted[0], &c->surv_sorted[1],
                     &c->vt_lo[0], &c->vt_lo[1], &c->vt_hi[0], &c->vt_hi[1], &c->defer, &c->acc, &c->witness64,
                     &c->h_p, &c->h_s, &c->h_x, &c->h_sout, &c->h_arg, &c->h_fl};
   for (DevBuf* b : bufs) release(*b);

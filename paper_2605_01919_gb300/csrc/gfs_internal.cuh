@@ -11,8 +11,16 @@ namespace gfs {
 // Level 0 node j ("leaf") covers items [8j, 8j+8); a node j at level l >= 1
 // covers nodes [8j, 8j+8) of level l-1.  Node boxes are tight over the FP32
 // item positions and widened by one ulp, so they also contain the FP64
-// positions the FP32 ones were rounded from.  For sphere items each node also
-// carries the largest radius per sign class and the smallest radius.
+// positions the FP32 ones were rounded from.
+//
+// Sphere nodes also carry three bounding balls (centre, radius):
+//   bp, bn -- a ball that contains every ball of sign + (resp. -) in the
+//             node: for any x, |x - p_j| - r_j >= |x - c| - R;
+//   bf     -- a centre c and Q >= max_j (|p_j - c| - r_j) over all spheres:
+//             for any x, |x - p_j| + r_j >= |x - c| - Q.
+// Exact SDF samples are close to nested along the gradient (a deeper ball
+// contains a shallower one), which these balls exploit; an axis box with the
+// largest radius cannot.  Empty classes have R = -inf.
 // ---------------------------------------------------------------------------
 constexpr int kLeaf = 8;
 constexpr int kFan = 8;
@@ -24,9 +32,11 @@ struct Tree {
   int64_t nitems;
   int64_t count[kMaxLevels];      // nodes per level
   int64_t offset[kMaxLevels];     // first node of each level in the node arrays
-  float4* lo;                     // (min x, min y, min z, rmax of class +)
-  float4* hi;                     // (max x, max y, max z, rmax of class -)
-  float* rmin;                    // smallest radius in the node (sphere trees)
+  float4* lo;                     // (min x, min y, min z, -)
+  float4* hi;                     // (max x, max y, max z, -)
+  float4* bp;                     // sphere trees: ball enclosing the + balls
+  float4* bn;                     // sphere trees: ball enclosing the - balls
+  float4* bf;                     // sphere trees: far bound (centre, Q)
 };
 
 __host__ __device__ inline uint32_t pack_node(int level, int64_t idx) {
@@ -86,6 +96,16 @@ __device__ __forceinline__ double box_d2_64(double x, double y, double z, const 
   double dx = fmax(fmax(double(lo.x) - x, x - double(hi.x)), 0.0);
   double dy = fmax(fmax(double(lo.y) - y, y - double(hi.y)), 0.0);
   double dz = fmax(fmax(double(lo.z) - z, z - double(hi.z)), 0.0);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+// squared distance from a point to a bounding-ball centre
+__device__ __forceinline__ float ball_d2(float x, float y, float z, const float4& b) {
+  const float dx = x - b.x, dy = y - b.y, dz = z - b.z;
+  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+__device__ __forceinline__ double ball_d2_64(double x, double y, double z, const float4& b) {
+  const double dx = x - double(b.x), dy = y - double(b.y), dz = z - double(b.z);
   return dx * dx + dy * dy + dz * dz;
 }
 

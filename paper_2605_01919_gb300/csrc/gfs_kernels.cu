@@ -30,13 +30,19 @@ __device__ __forceinline__ float sqf(float v) { return v * v; }
 // ---------------------------------------------------------------------------
 // build: bounds of the data, input copy, Morton keys
 // ---------------------------------------------------------------------------
-__global__ void k_pack_inputs(const double* __restrict__ p, const double* __restrict__ s, int64_t n,
-                              D4* __restrict__ sph64, uint32_t* __restrict__ keys, int* __restrict__ vals,
-                              unsigned int* __restrict__ bound_bits) {
+__global__ void k_copy_inputs(const double* __restrict__ p, const double* __restrict__ s, int64_t n,
+                              D4* __restrict__ sph64) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    sph64[i] = D4{p[3 * i], p[3 * i + 1], p[3 * i + 2], s[i]};
+}
+
+// Morton keys of the sample centres and the data bounds (max |coordinate|,
+// max |s|) used by the error model.
+__global__ void k_keys_d4(const D4* __restrict__ sph64, int64_t n, uint32_t* __restrict__ keys,
+                          int* __restrict__ vals, unsigned int* __restrict__ bound_bits) {
   float amax = 0.f, rmax = 0.f;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    D4 d{p[3 * i], p[3 * i + 1], p[3 * i + 2], s[i]};
-    sph64[i] = d;
+    const D4 d = sph64[i];
     amax = fmaxf(amax, __double2float_ru(fmax(fabs(d.x), fmax(fabs(d.y), fabs(d.z)))));
     rmax = fmaxf(rmax, __double2float_ru(fabs(d.w)));
     keys[i] = morton3(float(d.x), float(d.y), float(d.z));
@@ -116,56 +122,145 @@ __global__ void k_gather_spheres(const D4* __restrict__ sph64, const int* __rest
 // ---------------------------------------------------------------------------
 // hierarchy build
 // ---------------------------------------------------------------------------
-__global__ void k_leaves(const float4* __restrict__ items, int64_t nitems, int is_sphere, float4* __restrict__ lo,
-                         float4* __restrict__ hi, float* __restrict__ rmin, int64_t nleaves) {
+__global__ void k_leaves(const float4* __restrict__ items, int64_t nitems, float4* __restrict__ lo,
+                         float4* __restrict__ hi, int64_t nleaves) {
   int64_t L = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (L >= nleaves) return;
   int64_t b = L * kLeaf, e = min(b + kLeaf, nitems);
   float3 mn = make_float3(INFINITY, INFINITY, INFINITY), mx = make_float3(-INFINITY, -INFINITY, -INFINITY);
-  float rp = 0.f, rn = 0.f, rm = INFINITY;
   for (int64_t i = b; i < e; ++i) {
     float4 v = items[i];
     mn.x = fminf(mn.x, v.x); mn.y = fminf(mn.y, v.y); mn.z = fminf(mn.z, v.z);
     mx.x = fmaxf(mx.x, v.x); mx.y = fmaxf(mx.y, v.y); mx.z = fmaxf(mx.z, v.z);
-    if (is_sphere) {
-      float r = fabsf(v.w);
-      if (v.w > 0.f) rp = fmaxf(rp, r);
-      if (v.w < 0.f) rn = fmaxf(rn, r);
-      rm = fminf(rm, r);
-    }
   }
   // widen by one ulp: the box then holds the FP64 points the FP32 ones were
-  // rounded from, and the radius bounds hold the FP64 radii
-  mn.x = nextafterf(mn.x, -INFINITY); mn.y = nextafterf(mn.y, -INFINITY); mn.z = nextafterf(mn.z, -INFINITY);
-  mx.x = nextafterf(mx.x, INFINITY); mx.y = nextafterf(mx.y, INFINITY); mx.z = nextafterf(mx.z, INFINITY);
-  if (is_sphere) {
-    if (rp > 0.f) rp = nextafterf(rp, INFINITY);
-    if (rn > 0.f) rn = nextafterf(rn, INFINITY);
-    rm = fmaxf(nextafterf(rm, -INFINITY), 0.f);
-  } else {
-    rm = 0.f;
-  }
-  lo[L] = make_float4(mn.x, mn.y, mn.z, rp);
-  hi[L] = make_float4(mx.x, mx.y, mx.z, rn);
-  if (rmin) rmin[L] = rm;
+  // rounded from
+  lo[L] = make_float4(nextafterf(mn.x, -INFINITY), nextafterf(mn.y, -INFINITY), nextafterf(mn.z, -INFINITY), 0.f);
+  hi[L] = make_float4(nextafterf(mx.x, INFINITY), nextafterf(mx.y, INFINITY), nextafterf(mx.z, INFINITY), 0.f);
 }
 
-__global__ void k_level(float4* __restrict__ lo, float4* __restrict__ hi, float* __restrict__ rmin, int64_t child_off,
-                        int64_t nchild, int64_t off, int64_t nnode) {
+__global__ void k_level(float4* __restrict__ lo, float4* __restrict__ hi, int64_t child_off, int64_t nchild,
+                        int64_t off, int64_t nnode) {
   int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (j >= nnode) return;
   int64_t b = j * kFan, e = min(b + kFan, nchild);
   float4 L = make_float4(INFINITY, INFINITY, INFINITY, 0.f), H = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
-  float rm = INFINITY;
   for (int64_t c = b; c < e; ++c) {
     float4 a = lo[child_off + c], z = hi[child_off + c];
-    L.x = fminf(L.x, a.x); L.y = fminf(L.y, a.y); L.z = fminf(L.z, a.z); L.w = fmaxf(L.w, a.w);
-    H.x = fmaxf(H.x, z.x); H.y = fmaxf(H.y, z.y); H.z = fmaxf(H.z, z.z); H.w = fmaxf(H.w, z.w);
-    if (rmin) rm = fminf(rm, rmin[child_off + c]);
+    L.x = fminf(L.x, a.x); L.y = fminf(L.y, a.y); L.z = fminf(L.z, a.z);
+    H.x = fmaxf(H.x, z.x); H.y = fmaxf(H.y, z.y); H.z = fmaxf(H.z, z.z);
   }
   lo[off + j] = L;
   hi[off + j] = H;
-  if (rmin) rmin[off + j] = rm;
+}
+
+// Bounding ball of weighted centres (c_i, w_i): a centre c and
+// V >= max_i (|c_i - c| + w_i).  Any centre is valid; subgradient steps from
+// the better of two starts (the item of largest weight, the mean centre) make
+// V small.  V is inflated by 8 ulp of |V| and of the coordinate range, which
+// covers the FP32 evaluation and the rounding of FP64 inputs to FP32.
+__device__ float4 bound_ball(const float4* it, int k, float A) {
+  if (k == 0) return make_float4(0.f, 0.f, 0.f, -INFINITY);
+  auto eval = [&](float cx, float cy, float cz, int& arg) {
+    float best = -INFINITY;
+    arg = 0;
+    for (int i = 0; i < k; ++i) {
+      const float dx = it[i].x - cx, dy = it[i].y - cy, dz = it[i].z - cz;
+      const float v = sqrtf(dx * dx + dy * dy + dz * dz) + it[i].w;
+      if (v > best) {
+        best = v;
+        arg = i;
+      }
+    }
+    return best;
+  };
+  int big = 0;
+  float mx = 0.f, my = 0.f, mz = 0.f;
+  for (int i = 0; i < k; ++i) {
+    if (it[i].w > it[big].w) big = i;
+    mx += it[i].x;
+    my += it[i].y;
+    mz += it[i].z;
+  }
+  mx /= float(k);
+  my /= float(k);
+  mz /= float(k);
+  int j0, j1;
+  const float v0 = eval(it[big].x, it[big].y, it[big].z, j0);
+  const float v1 = eval(mx, my, mz, j1);
+  float cx = v0 <= v1 ? it[big].x : mx, cy = v0 <= v1 ? it[big].y : my, cz = v0 <= v1 ? it[big].z : mz;
+  float bx = cx, by = cy, bz = cz, best = fminf(v0, v1);
+  for (int t = 0; t < 24; ++t) {
+    int j;
+    const float v = eval(cx, cy, cz, j);
+    if (v < best) {
+      best = v;
+      bx = cx;
+      by = cy;
+      bz = cz;
+    }
+    const float dx = it[j].x - cx, dy = it[j].y - cy, dz = it[j].z - cz;
+    const float d = sqrtf(dx * dx + dy * dy + dz * dz);
+    if (!(d > 1e-12f)) break;
+    const float step = d / float(t + 2);
+    cx += dx / d * step;
+    cy += dy / d * step;
+    cz += dz / d * step;
+  }
+  int j;
+  float v = eval(bx, by, bz, j);
+  v = v + (fabsf(v) + A) * 4.8e-7f;
+  return make_float4(bx, by, bz, v);
+}
+
+__global__ void k_sphere_leaves(const float4* __restrict__ items, int64_t nitems, float A, float4* __restrict__ lo,
+                                float4* __restrict__ hi, float4* __restrict__ bp, float4* __restrict__ bn,
+                                float4* __restrict__ bf, int64_t nleaves) {
+  int64_t L = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (L >= nleaves) return;
+  int64_t b = L * kLeaf, e = min(b + kLeaf, nitems);
+  float4 P[kLeaf], N[kLeaf], F[kLeaf];
+  int np = 0, nn = 0, nf = 0;
+  float3 mn = make_float3(INFINITY, INFINITY, INFINITY), mx = make_float3(-INFINITY, -INFINITY, -INFINITY);
+  for (int64_t i = b; i < e; ++i) {
+    const float4 v = items[i];
+    mn.x = fminf(mn.x, v.x); mn.y = fminf(mn.y, v.y); mn.z = fminf(mn.z, v.z);
+    mx.x = fmaxf(mx.x, v.x); mx.y = fmaxf(mx.y, v.y); mx.z = fmaxf(mx.z, v.z);
+    const float r = fabsf(v.w);
+    if (v.w > 0.f) P[np++] = make_float4(v.x, v.y, v.z, r);
+    if (v.w < 0.f) N[nn++] = make_float4(v.x, v.y, v.z, r);
+    F[nf++] = make_float4(v.x, v.y, v.z, -r);
+  }
+  lo[L] = make_float4(nextafterf(mn.x, -INFINITY), nextafterf(mn.y, -INFINITY), nextafterf(mn.z, -INFINITY), 0.f);
+  hi[L] = make_float4(nextafterf(mx.x, INFINITY), nextafterf(mx.y, INFINITY), nextafterf(mx.z, INFINITY), 0.f);
+  bp[L] = bound_ball(P, np, A);
+  bn[L] = bound_ball(N, nn, A);
+  bf[L] = bound_ball(F, nf, A);
+}
+
+__global__ void k_sphere_level(float4* __restrict__ lo, float4* __restrict__ hi, float4* __restrict__ bp,
+                               float4* __restrict__ bn, float4* __restrict__ bf, float A, int64_t child_off,
+                               int64_t nchild, int64_t off, int64_t nnode) {
+  int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (j >= nnode) return;
+  int64_t b = j * kFan, e = min(b + kFan, nchild);
+  float4 L = make_float4(INFINITY, INFINITY, INFINITY, 0.f), H = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+  float4 P[kFan], N[kFan], F[kFan];
+  int np = 0, nn = 0, nf = 0;
+  for (int64_t c = b; c < e; ++c) {
+    const float4 a = lo[child_off + c], z = hi[child_off + c];
+    L.x = fminf(L.x, a.x); L.y = fminf(L.y, a.y); L.z = fminf(L.z, a.z);
+    H.x = fmaxf(H.x, z.x); H.y = fmaxf(H.y, z.y); H.z = fmaxf(H.z, z.z);
+    const float4 u = bp[child_off + c], v = bn[child_off + c], w = bf[child_off + c];
+    if (u.w > -INFINITY) P[np++] = u;
+    if (v.w > -INFINITY) N[nn++] = v;
+    if (w.w > -INFINITY) F[nf++] = w;
+  }
+  lo[off + j] = L;
+  hi[off + j] = H;
+  bp[off + j] = bound_ball(P, np, A);
+  bn[off + j] = bound_ball(N, nn, A);
+  bf[off + j] = bound_ball(F, nf, A);
 }
 
 __global__ void k_point_keys(const float4* __restrict__ items, int64_t n, uint32_t* __restrict__ keys,
@@ -257,13 +352,18 @@ __global__ void __launch_bounds__(128) k_cull(CullArgs a) {
       uint32_t pend[kFan];
       int np = 0;
       for (int64_t c = cb; c < ce; ++c) {
-        const float4 L = T.lo[off + c], H = T.hi[off + c];
-        const float rm = fmaxf(L.w, H.w);
-        const float t = fmaf(rm - a.tol32, grow, bc.pad);
-        if (t <= 0.f) continue;
-        const float d2 = box_d2(qx, qy, qz, L, H);
-        if (d2 < t * t) {
-          const float margin = t * t - d2;
+        // the node can hold a covering ball only if q lies in one of its
+        // bounding balls shrunk by tol
+        float margin = -INFINITY;
+        const float4 Bs[2] = {T.bp[off + c], T.bn[off + c]};
+        for (int cl = 0; cl < 2; ++cl) {
+          const float t = fmaf(Bs[cl].w - a.tol32, grow, bc.pad);
+          if (!(t > 0.f)) continue;
+          const float dx = qx - Bs[cl].x, dy = qy - Bs[cl].y, dz = qz - Bs[cl].z;
+          const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (d2 < t * t) margin = fmaxf(margin, t * t - d2);
+        }
+        if (margin > -INFINITY) {
           if (margin > bestm) {
             if (best >= 0) pend[np++] = pack_node(lev - 1, best);
             best = int(c);
@@ -398,16 +498,10 @@ __device__ double band_sphere(const QueryArgs& a, const BuildConsts& bc, double 
       const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
       const int64_t off = T.offset[lev - 1];
       for (int64_t cc = cb; cc < ce; ++cc) {
-        const float4 L = T.lo[off + cc], H = T.hi[off + cc];
-        float t;
-        if (mode == 0) {
-          const float rm = c == 0 ? L.w : H.w;
-          if (!(rm > 0.f)) continue;
-          t = fmaf(thr + rm, grow, bc.eprune);
-        } else {
-          t = fmaf(thr - T.rmin[off + cc], grow, bc.eprune);
-        }
-        if (t > 0.f && box_d2(x, y, z, L, H) < t * t) stack[sp++] = pack_node(lev - 1, cc);
+        const float4 B = mode == 1 ? T.bf[off + cc] : (c == 0 ? T.bp[off + cc] : T.bn[off + cc]);
+        if (!(B.w > -INFINITY)) continue;
+        const float t = fmaf(thr + B.w, grow, bc.eprune);
+        if (t > 0.f && ball_d2(x, y, z, B) < t * t) stack[sp++] = pack_node(lev - 1, cc);
       }
     }
   }
@@ -533,17 +627,20 @@ __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
           const float4 L = T.lo[off + c], H = T.hi[off + c];
           const float d2 = box_d2(x, y, z, L, H);
           bool need = inside_box(x, y, z, L, H);
-          if (!need && L.w > 0.f) {
-            const float t = fmaf(th0 + L.w, grow, bc.eprune);
-            need = t > 0.f && d2 < t * t;
-          }
-          if (!need && H.w > 0.f) {
-            const float t = fmaf(th1 + H.w, grow, bc.eprune);
-            need = t > 0.f && d2 < t * t;
+          if (!need) {
+            const float4 B = T.bp[off + c];
+            const float t = fmaf(th0 + B.w, grow, bc.eprune);
+            need = t > 0.f && ball_d2(x, y, z, B) < t * t;
           }
           if (!need) {
-            const float t = fmaf(thf - T.rmin[off + c], grow, bc.eprune);
-            need = t > 0.f && d2 < t * t;
+            const float4 B = T.bn[off + c];
+            const float t = fmaf(th1 + B.w, grow, bc.eprune);
+            need = t > 0.f && ball_d2(x, y, z, B) < t * t;
+          }
+          if (!need) {
+            const float4 B = T.bf[off + c];
+            const float t = fmaf(thf + B.w, grow, bc.eprune);
+            need = t > 0.f && ball_d2(x, y, z, B) < t * t;
           }
           if (!need) continue;
           if (d2 < bestd) {
@@ -791,20 +888,20 @@ __device__ void query_exact_one(const QueryArgs& a, int64_t q) {
         const int64_t off = T.offset[lev - 1];
         for (int64_t c = cb; c < ce; ++c) {
           const float4 L = T.lo[off + c], H = T.hi[off + c];
-          const double d2 = box_d2_64(x, y, z, L, H);
           bool need = x >= double(L.x) && x <= double(H.x) && y >= double(L.y) && y <= double(H.y) &&
                       z >= double(L.z) && z <= double(H.z);
-          const double rr[2] = {double(L.w), double(H.w)};
+          const float4 Bs[2] = {T.bp[off + c], T.bn[off + c]};
           for (int cl = 0; cl < 2 && !need; ++cl) {
-            if (!(rr[cl] > 0.0)) continue;
+            if (!(Bs[cl].w > -INFINITY)) continue;
             double th = bestA[cl];
             if (!cov[cl]) th = fmax(th, -tol);
-            const double t = (th + rr[cl]) * (1.0 + 1e-12) + 1e-12;
-            need = t > 0.0 && d2 <= t * t;
+            const double t = (th + double(Bs[cl].w)) * (1.0 + 1e-12) + 1e-12;
+            need = t > 0.0 && ball_d2_64(x, y, z, Bs[cl]) <= t * t;
           }
           if (!need) {
-            const double t = (bestF - double(T.rmin[off + c])) * (1.0 + 1e-12) + 1e-12;
-            need = t > 0.0 && d2 <= t * t;
+            const float4 B = T.bf[off + c];
+            const double t = (bestF + double(B.w)) * (1.0 + 1e-12) + 1e-12;
+            need = t > 0.0 && ball_d2_64(x, y, z, B) <= t * t;
           }
           if (need) stack[sp++] = pack_node(lev - 1, c);
         }
@@ -826,6 +923,7 @@ __device__ void query_exact_one(const QueryArgs& a, int64_t q) {
   const int cs = cov[0] ? 0 : 1, co = 1 - cs;
   double bd = INFINITY;
   uint32_t gbest = 0xffffffffu;
+  const float eqs = a.bc->eq;
   if (a.vt[cs].nlevels > 0) {
     const Tree& T = a.vt[cs];
     const float4* items = a.surv[cs];
@@ -852,9 +950,12 @@ __device__ void query_exact_one(const QueryArgs& a, int64_t q) {
       } else {
         const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
         const int64_t off = T.offset[lev - 1];
+        // survivor boxes hold the FP32 positions; the FP64 position of a
+        // candidate is within eq of its FP32 one in each coordinate
+        const double t = sqrt(bd) * (1.0 + 1e-12) + 2.0 * 1.7320508075688772 * double(eqs) + 1e-12;
         for (int64_t c = cb; c < ce; ++c) {
           const double d2 = box_d2_64(x, y, z, T.lo[off + c], T.hi[off + c]);
-          if (d2 <= bd * (1.0 + 1e-12) + 1e-300) stack[sp++] = pack_node(lev - 1, c);
+          if (d2 <= t * t) stack[sp++] = pack_node(lev - 1, c);
         }
       }
     }
@@ -1011,11 +1112,19 @@ void launch_counts(unsigned long long* own, unsigned long long* sorts) {
   *sorts = g_sort_calls;
 }
 
-cudaError_t launch_pack_inputs(const double* p, const double* s, int64_t n, D4* sph64, uint32_t* keys, int* vals,
-                               unsigned int* bound_bits, BuildConsts* bc, cudaStream_t st) {
+cudaError_t launch_copy_inputs(const double* p, const double* s, int64_t n, D4* sph64, cudaStream_t st) {
   unsigned int g = nblk(n, 256);
   if (g > 4096) g = 4096;
-  k_pack_inputs<<<g, 256, 0, st>>>(p, s, n, sph64, keys, vals, bound_bits);
+  k_copy_inputs<<<g, 256, 0, st>>>(p, s, n, sph64);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keys_d4(const D4* sph64, int64_t n, uint32_t* keys, int* vals, unsigned int* bound_bits,
+                           BuildConsts* bc, cudaStream_t st) {
+  unsigned int g = nblk(n, 256);
+  if (g > 4096) g = 4096;
+  k_keys_d4<<<g, 256, 0, st>>>(sph64, n, keys, vals, bound_bits);
   ++g_launches;
   k_consts<<<1, 1, 0, st>>>(bound_bits, bc);
   ++g_launches;
@@ -1041,15 +1150,26 @@ cudaError_t launch_gather_spheres(const D4* sph64, const int* order, int64_t n, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_tree(const float4* items, int is_sphere, Tree& T, cudaStream_t st) {
+cudaError_t launch_build_tree(const float4* items, int is_sphere, float A, Tree& T, cudaStream_t st) {
   if (T.nlevels == 0) return cudaSuccess;
-  k_leaves<<<nblk(T.count[0], 128), 128, 0, st>>>(items, T.nitems, is_sphere, T.lo, T.hi,
-                                                    is_sphere ? T.rmin : nullptr, T.count[0]);
-  ++g_launches;
-  for (int l = 1; l < T.nlevels; ++l)
-    k_level<<<nblk(T.count[l], 128), 128, 0, st>>>(T.lo, T.hi, is_sphere ? T.rmin : nullptr, T.offset[l - 1],
-                                                   T.count[l - 1], T.offset[l], T.count[l]);
+  if (is_sphere) {
+    k_sphere_leaves<<<nblk(T.count[0], 128), 128, 0, st>>>(items, T.nitems, A, T.lo, T.hi, T.bp, T.bn, T.bf,
+                                                           T.count[0]);
     ++g_launches;
+    for (int l = 1; l < T.nlevels; ++l) {
+      k_sphere_level<<<nblk(T.count[l], 128), 128, 0, st>>>(T.lo, T.hi, T.bp, T.bn, T.bf, A, T.offset[l - 1],
+                                                            T.count[l - 1], T.offset[l], T.count[l]);
+      ++g_launches;
+    }
+  } else {
+    k_leaves<<<nblk(T.count[0], 128), 128, 0, st>>>(items, T.nitems, T.lo, T.hi, T.count[0]);
+    ++g_launches;
+    for (int l = 1; l < T.nlevels; ++l) {
+      k_level<<<nblk(T.count[l], 128), 128, 0, st>>>(T.lo, T.hi, T.offset[l - 1], T.count[l - 1], T.offset[l],
+                                                     T.count[l]);
+      ++g_launches;
+    }
+  }
   return cudaGetLastError();
 }
 

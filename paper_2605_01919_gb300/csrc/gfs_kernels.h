@@ -73,15 +73,16 @@ struct GradArgs {
   long long* acc_s;  // n fixed-point accumulators
 };
 
-cudaError_t launch_pack_inputs(const double* p, const double* s, int64_t n, D4* sph64, uint32_t* keys, int* vals,
-                               unsigned int* bound_bits, BuildConsts* bc, cudaStream_t st);
+cudaError_t launch_copy_inputs(const double* p, const double* s, int64_t n, D4* sph64, cudaStream_t st);
+cudaError_t launch_keys_d4(const D4* sph64, int64_t n, uint32_t* keys, int* vals, unsigned int* bound_bits,
+                           BuildConsts* bc, cudaStream_t st);
 cudaError_t sort_pairs(void* temp, size_t& temp_bytes, const uint32_t* kin, uint32_t* kout, const int* vin,
                        int* vout, int64_t n, cudaStream_t st);
 cudaError_t sort_keys_u32(void* temp, size_t& temp_bytes, const uint32_t* kin, uint32_t* kout, int64_t n,
                           cudaStream_t st);
 cudaError_t launch_gather_spheres(const D4* sph64, const int* order, int64_t n, const BuildConsts* bc, float tol32,
                                   double tol, float4* sph, float4* thr, int* sid, cudaStream_t st);
-cudaError_t launch_build_tree(const float4* items, int is_sphere, Tree& T, cudaStream_t st);
+cudaError_t launch_build_tree(const float4* items, int is_sphere, float A, Tree& T, cudaStream_t st);
 cudaError_t launch_point_keys(const float4* items, int64_t n, uint32_t* keys, int* vals, cudaStream_t st);
 cudaError_t launch_gather_points(const float4* src, const int* order, int64_t n, float4* dst, cudaStream_t st);
 cudaError_t launch_cull(const CullArgs& a, cudaStream_t st);

@@ -179,11 +179,12 @@ def test_union_grid_full_size_sampled(G, orc):
     print("stats", st)
 
 
-def test_union_grid_full_size_fp32_equals_fp64_path(G):
+def test_union_grid_full_size_fp32_equals_fp64_path(G, orc):
     """At full size, the FP32-filtered path and the FP64 path agree on every
-    output (all 16.2M queries)."""
+    output (all 16.2M queries); any disagreement is settled by the oracle."""
     w = W.union_grid()
-    xt = torch.from_numpy(w.make_queries()).cuda()
+    xh = w.make_queries()
+    xt = torch.from_numpy(xh).cuda()
     res = []
     for precision in (0, 1):
         ctx = G.Context(tau=w.tau, precision=precision)
@@ -194,6 +195,11 @@ def test_union_grid_full_size_fp32_equals_fp64_path(G):
         ctx.close()
     a, b = res
     assert torch.equal(a["surv"], b["surv"])
-    assert torch.equal(a["flags"], b["flags"])
-    assert torch.equal(a["argmin"], b["argmin"])
-    assert torch.equal(a["s64"].view(torch.int64), b["s64"].view(torch.int64))
+    bad = ((a["flags"] != b["flags"]) | (a["argmin"] != b["argmin"]) |
+           (a["s64"].view(torch.int64) != b["s64"].view(torch.int64))).nonzero().flatten().numpy()
+    if bad.size:
+        sel = bad[:12]
+        v, arg, fl, _ = orc.query_lazy(w.p, w.s, orc.icosphere(w.tau), xh[sel])
+        fp32_ok = np.array_equal(a["argmin"].numpy()[sel], arg)
+        fp64_ok = np.array_equal(b["argmin"].numpy()[sel], arg)
+        pytest.fail(f"{bad.size} queries differ; FP32 path matches oracle: {fp32_ok}, FP64 path: {fp64_ok}")
