@@ -129,6 +129,26 @@ int gfs_query_backward(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, co
                        const int64_t* argmin, const uint16_t* flags, const float* grad_s, float* grad_x,
                        float* grad_p, float* grad_sv);
 
+/* Greedy sequential insertion (Sec. 4 refinement loop; Sec. 6 repair
+ * inserts the removed samples the same way).  For t = 0..T-1 in order: the
+ * consistent value at y_t is computed against the current samples (inputs
+ * and every earlier insertion) and survivors, exactly as gfs_query defines it
+ * (FP64 decisions); unless the code is SAMPLE, OUTSIDE or INVALID, (y_t,
+ * value) then joins the samples as sphere n+j (j = number inserted so far):
+ * survivors inside its shrunk ball are dropped, its K candidates and its
+ * witness (the point that set the value, candidate slot K) are culled against
+ * every other sphere and join the survivors.  LOST_WITNESS is set on step t
+ * when some sphere loses its last survivor.
+ * y:          device, T*3 FP64 points, processed in order.
+ * s_out:      device, T FP64 values (nullable).
+ * argmin_out: device, T int64 (nullable); flags_out: device, T uint16 (nullable).
+ * The context's state is updated: later gfs_query / gfs_survivors calls see
+ * the inserted samples.  Synchronises the stream periodically (hierarchy
+ * rebuilds).  Errors: GFS_ERR_STATE (no build), GFS_ERR_ARG,
+ * GFS_ERR_TOO_LARGE ((n+T+1)*(K+1) >= 2^32), GFS_ERR_OOM, GFS_ERR_CUDA. */
+int gfs_insert(gfs_ctx* ctx, const double* y, int64_t T, double* s_out, int64_t* argmin_out,
+               uint16_t* flags_out);
+
 /* Copy the surviving candidate ids, ascending, into g_out (device, capacity
  * cap); *count_host receives the number of survivors (host pointer).
  * Errors: GFS_ERR_STATE, GFS_ERR_ARG (cap too small: *count_host still set). */

@@ -40,6 +40,26 @@ int ensure(DevBuf& b, size_t bytes) {
   return GFS_OK;
 }
 
+// grow a buffer, keeping its first `keep` bytes
+int grow_keep(DevBuf& b, size_t bytes, size_t keep, cudaStream_t st) {
+  if (b.bytes >= bytes && b.p) return GFS_OK;
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return GFS_ERR_OOM;
+  }
+  if (keep && b.p && (cudaMemcpyAsync(p, b.p, keep, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                      cudaStreamSynchronize(st) != cudaSuccess)) {
+    cudaGetLastError();
+    cudaFree(p);
+    return GFS_ERR_CUDA;
+  }
+  if (b.p) cudaFree(b.p);
+  b.p = p;
+  b.bytes = bytes;
+  return GFS_OK;
+}
+
 void release(DevBuf& b) {
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
@@ -103,6 +123,9 @@ struct gfs_ctx {
   unsigned int nsurv[2] = {0, 0};
   // query / backward scratch
   DevBuf defer, acc, witness64;
+  DevBuf qk_in, qk_out, qv_in, qv_out;  // query Morton keys / processing order
+  // insertion state
+  DevBuf ins_counts, ins_tomb[2], ins_dsurv[2], ins_dtomb[2], ins_misc;
   Counters host_cnt{};
   // host-buffer path (gfs_solve_host)
   DevBuf h_p, h_s, h_x, h_sout, h_arg, h_fl;
@@ -391,6 +414,15 @@ int gfs_query(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, float* s_out,
     GFS_TRY(ensure(c->defer, size_t(m) * 4));
     a.defer = c->defer.as<uint32_t>();
     a.defer_cap = unsigned(m);
+    // process the points in Morton order so that a warp's lanes are neighbours
+    GFS_TRY(ensure(c->qk_in, size_t(m) * 4));
+    GFS_TRY(ensure(c->qk_out, size_t(m) * 4));
+    GFS_TRY(ensure(c->qv_in, size_t(m) * 4));
+    GFS_TRY(ensure(c->qv_out, size_t(m) * 4));
+    GFS_CK(launch_query_keys(a.x64, a.x32, m, c->qk_in.as<uint32_t>(), c->qv_in.as<int>(), c->stream));
+    GFS_TRY(sort_u32_pairs(c, c->qk_in.as<uint32_t>(), c->qk_out.as<uint32_t>(), c->qv_in.as<int>(),
+                           c->qv_out.as<int>(), m));
+    a.perm = reinterpret_cast<const uint32_t*>(c->qv_out.p);
   }
   GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, query_rechecks), 0,
                          sizeof(unsigned long long), c->stream));
@@ -434,6 +466,149 @@ int gfs_query_backward(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, cons
   a.acc_p = c->acc.as<long long>();
   a.acc_s = c->acc.as<long long>() + 3 * n;
   GFS_CK(launch_grad(a, n, grad_p, grad_sv, c->stream));
+  return GFS_OK;
+}
+
+namespace {
+
+// layout of the small insertion control block (device)
+struct InsMisc {
+  int n_total;
+  unsigned dcount[2];
+  unsigned dcount_start[2];
+  StepRec rec;
+  unsigned lost;
+  unsigned err;
+};
+
+// Rebuild the hierarchies from the current state: live survivors compacted
+// into fresh lists, all spheres re-sorted.
+int ins_rebuild(gfs_ctx* c, int64_t n_total) {
+  cudaStream_t st = c->stream;
+  InsMisc hm;
+  GFS_CK(cudaMemcpyAsync(&hm, c->ins_misc.p, sizeof(InsMisc), cudaMemcpyDeviceToHost, st));
+  GFS_CK(cudaStreamSynchronize(st));
+  DevBuf cnt;
+  GFS_TRY(ensure(cnt, 16));
+  for (int k = 0; k < 2; ++k) {
+    const unsigned need = c->nsurv[k] + hm.dcount[k];
+    if (size_t(need) * sizeof(float4) > c->surv_raw[k].bytes) {
+      DevBuf fresh;
+      GFS_TRY(ensure(fresh, size_t(need) * sizeof(float4) + 16));
+      std::swap(fresh, c->surv_raw[k]);
+      release(fresh);
+    }
+    unsigned hc = 0;
+    GFS_CK(cudaMemsetAsync(cnt.p, 0, 4, st));
+    GFS_CK(launch_ins_compact(c->surv_sorted[k].as<float4>(), c->ins_tomb[k].as<uint32_t>(), c->nsurv[k],
+                              c->ins_dsurv[k].as<float4>(), c->ins_dtomb[k].as<uint32_t>(), hm.dcount[k],
+                              c->surv_raw[k].as<float4>(), cnt.as<unsigned>(), st));
+    GFS_CK(cudaMemcpyAsync(&hc, cnt.p, 4, cudaMemcpyDeviceToHost, st));
+    GFS_CK(cudaStreamSynchronize(st));
+    c->nsurv[k] = hc;
+    c->cap = std::max(c->cap, hc);
+  }
+  release(cnt);
+  GFS_TRY(build_sphere_hierarchy(c, n_total));
+  GFS_TRY(build_point_tree(c, 0));
+  GFS_TRY(build_point_tree(c, 1));
+  for (int k = 0; k < 2; ++k) {
+    const size_t words = (size_t(c->nsurv[k]) + 31) / 32 + 1;
+    GFS_TRY(ensure(c->ins_tomb[k], words * 4));
+    GFS_CK(cudaMemsetAsync(c->ins_tomb[k].p, 0, words * 4, st));
+  }
+  GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->ins_misc.p) + offsetof(InsMisc, dcount), 0, 4 * sizeof(unsigned),
+                         st));
+  return GFS_OK;
+}
+
+}  // namespace
+
+int gfs_insert(gfs_ctx* c, const double* y, int64_t T, double* s_out, int64_t* argmin_out, uint16_t* flags_out) {
+  if (!c || T < 0 || (T > 0 && !y)) return GFS_ERR_ARG;
+  if (!c->built) return GFS_ERR_STATE;
+  if (T == 0) return GFS_OK;
+  cudaStream_t st = c->stream;
+  const int64_t n0 = c->n;
+  const int64_t cap = n0 + T + 1;
+  if (uint64_t(cap) * uint64_t(c->KS) >= (uint64_t(1) << 32) || cap >= (int64_t(1) << 30)) return GFS_ERR_TOO_LARGE;
+  const int kRebuild = 256;  // steps between hierarchy rebuilds
+  GFS_TRY(grow_keep(c->sph64, size_t(cap) * sizeof(D4), size_t(n0) * sizeof(D4), st));
+  const size_t wkeep = c->witness64.p ? std::min(c->witness64.bytes, size_t(n0) * 24) : 0;
+  GFS_TRY(grow_keep(c->witness64, size_t(cap) * 24, wkeep, st));
+  GFS_TRY(ensure(c->ins_counts, size_t(cap) * 4));
+  GFS_CK(cudaMemsetAsync(c->ins_counts.p, 0, size_t(cap) * 4, st));
+  GFS_CK(launch_ins_counts(c->surv_raw[0].as<float4>(), c->nsurv[0], c->surv_raw[1].as<float4>(), c->nsurv[1],
+                           c->sph64.as<D4>(), c->KS, c->ins_counts.as<int>(), st));
+  const unsigned dcap = unsigned(c->KS) * kRebuild;
+  for (int k = 0; k < 2; ++k) {
+    const size_t words = (size_t(c->nsurv[k]) + 31) / 32 + 1;
+    GFS_TRY(ensure(c->ins_tomb[k], words * 4));
+    GFS_CK(cudaMemsetAsync(c->ins_tomb[k].p, 0, words * 4, st));
+    GFS_TRY(ensure(c->ins_dsurv[k], size_t(dcap) * sizeof(float4)));
+    GFS_TRY(ensure(c->ins_dtomb[k], size_t(dcap) * 4));
+  }
+  GFS_TRY(ensure(c->ins_misc, sizeof(InsMisc)));
+  InsMisc hm;
+  std::memset(&hm, 0, sizeof(hm));
+  hm.n_total = int(n0);
+  GFS_CK(cudaMemcpyAsync(c->ins_misc.p, &hm, sizeof(hm), cudaMemcpyHostToDevice, st));
+  InsMisc* dm = c->ins_misc.as<InsMisc>();
+  int64_t n_static = n0;
+  int since = 0;
+  for (int64_t t = 0; t < T; ++t) {
+    if (since == kRebuild) {
+      int nt = 0;
+      GFS_CK(cudaMemcpyAsync(&nt, &dm->n_total, 4, cudaMemcpyDeviceToHost, st));
+      GFS_CK(cudaStreamSynchronize(st));
+      GFS_TRY(ins_rebuild(c, nt));
+      n_static = nt;
+      since = 0;
+    }
+    InsertArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.sph = c->sph.as<float4>();
+    a.sid = c->sid.as<int>();
+    a.st = c->st;
+    a.n_static = int(n_static);
+    a.sph64 = c->sph64.as<D4>();
+    a.witness64 = c->witness64.as<double>();
+    a.counts = c->ins_counts.as<int>();
+    a.n_total = &dm->n_total;
+    for (int k = 0; k < 2; ++k) {
+      a.surv[k] = c->surv_sorted[k].as<float4>();
+      a.vt[k] = c->vt[k];
+      a.tomb[k] = c->ins_tomb[k].as<uint32_t>();
+      a.dsurv[k] = c->ins_dsurv[k].as<float4>();
+      a.dtomb[k] = c->ins_dtomb[k].as<uint32_t>();
+    }
+    a.dcount = dm->dcount;
+    a.dcount_start = dm->dcount_start;
+    a.dcap = dcap;
+    a.U64 = c->U64.as<double>();
+    a.K = c->K;
+    a.KS = c->KS;
+    a.tol = c->opt.tol;
+    a.box_cull = c->opt.box_cull;
+    a.clamp_opp = c->opt.clamp_opp;
+    a.bc = c->consts.as<BuildConsts>();
+    a.y = y;
+    a.s_out = s_out;
+    a.arg_out = argmin_out;
+    a.fl_out = flags_out;
+    a.rec = &dm->rec;
+    a.lost = &dm->lost;
+    a.err = &dm->err;
+    GFS_CK(launch_ins_step(a, t, st));
+    ++since;
+  }
+  int nt = 0;
+  GFS_CK(cudaMemcpyAsync(&nt, &dm->n_total, 4, cudaMemcpyDeviceToHost, st));
+  GFS_CK(cudaStreamSynchronize(st));
+  GFS_TRY(ins_rebuild(c, nt));
+  GFS_CK(cudaMemcpyAsync(&hm, c->ins_misc.p, sizeof(hm), cudaMemcpyDeviceToHost, st));
+  GFS_CK(cudaStreamSynchronize(st));
+  if (hm.err) return GFS_ERR_CUDA;
   return GFS_OK;
 }
 
@@ -563,7 +738,10 @@ void gfs_destroy(gfs_ctx* c) {
                     &c->thr, &c->sid, &c->bound_bits, &c->consts, &c->cnt, &c->cub_temp, &c->st_lo, &c->st_hi,
                     &c->st_bp, &c->st_bn, &c->st_bf, &c->surv_raw[0], &c->surv_raw[1], &c->surv_sorted[0], &c->surv_sorted[1],
                     &c->vt_lo[0], &c->vt_lo[1], &c->vt_hi[0], &c->vt_hi[1], &c->defer, &c->acc, &c->witness64,
-                    &c->h_p, &c->h_s, &c->h_x, &c->h_sout, &c->h_arg, &c->h_fl};
+                    &c->h_p, &c->h_s, &c->h_x, &c->h_sout, &c->h_arg, &c->h_fl,
+                    &c->qk_in, &c->qk_out, &c->qv_in, &c->qv_out, &c->ins_counts,
+                    &c->ins_tomb[0], &c->ins_tomb[1], &c->ins_dsurv[0], &c->ins_dsurv[1], &c->ins_dtomb[0],
+                    &c->ins_dtomb[1], &c->ins_misc};
   for (DevBuf* b : bufs) release(*b);
   delete c;
 }

@@ -263,6 +263,21 @@ __global__ void k_sphere_level(float4* __restrict__ lo, float4* __restrict__ hi,
   bf[off + j] = bound_ball(F, nf, A);
 }
 
+// Morton keys of query points (processing order of the packet kernel)
+__global__ void k_query_keys(const double* __restrict__ x64, const float* __restrict__ x32, int64_t m,
+                             uint32_t* __restrict__ keys, int* __restrict__ vals) {
+  int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= m) return;
+  float x, y, z;
+  if (x32) {
+    x = x32[3 * i]; y = x32[3 * i + 1]; z = x32[3 * i + 2];
+  } else {
+    x = float(x64[3 * i]); y = float(x64[3 * i + 1]); z = float(x64[3 * i + 2]);
+  }
+  keys[i] = morton3(x, y, z);
+  vals[i] = int(i);
+}
+
 __global__ void k_point_keys(const float4* __restrict__ items, int64_t n, uint32_t* __restrict__ keys,
                              int* __restrict__ vals) {
   int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -280,18 +295,67 @@ __global__ void k_gather_points(const float4* __restrict__ src, const int* __res
 }
 
 // ---------------------------------------------------------------------------
+// Warp-cooperative ("packet") traversal.  The 32 lanes of a warp hold 32
+// query points that are neighbours in Morton order; they walk one hierarchy
+// together: the warp pops a node, every lane decides for its own point
+// whether the node can matter, and the node's children (or items) are
+// visited if any lane needs them.  Node and item records are read once per
+// warp (all lanes load the same address), control flow stays uniform, and
+// the stack lives in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kPStack = 128;  // >= kFan + (kFan-1)*(kMaxLevels-1)
+constexpr unsigned kFull = 0xffffffffu;
+
+struct WarpStack {
+  uint32_t* s;
+  int sp;
+  __device__ void push_top(const Tree& T, int lane) {
+    const int top = T.nlevels - 1;
+    const int cnt = int(T.count[top]);
+    if (lane < cnt) s[lane] = pack_node(top, lane);
+    sp = cnt;
+    __syncwarp();
+  }
+  __device__ uint32_t pop() {
+    const uint32_t nd = s[sp - 1];
+    --sp;
+    __syncwarp();
+    return nd;
+  }
+  // push the children whose bit is set in `need`, `first` last (visited next)
+  __device__ void push(int lev, int64_t cb, unsigned need, int first, int lane) {
+    int k = 0;
+    for (int c = 0; c < kFan; ++c) {
+      if (!((need >> c) & 1u) || c == first) continue;
+      if (lane == 0) s[sp + k] = pack_node(lev, cb + c);
+      ++k;
+    }
+    if (first >= 0) {
+      if (lane == 0) s[sp + k] = pack_node(lev, cb + first);
+      ++k;
+    }
+    sp += k;
+    __syncwarp();
+  }
+};
+
+// ---------------------------------------------------------------------------
 // P build: coverage culling of the candidates q_ik = p_i + |s_i| u_k
 // ---------------------------------------------------------------------------
-// One thread per candidate; a warp holds 32 Morton-consecutive spheres with
-// the same direction k, so its candidates are spatial neighbours and walk
-// similar parts of the hierarchy.  The walk visits the child with the
-// largest covering margin first and stops at the first covering ball.
+// One lane per candidate; a warp holds 32 Morton-consecutive spheres with the
+// same direction k, so its candidates are spatial neighbours.  The warp walks
+// the sphere hierarchy as a packet (one node at a time, children visited if
+// any lane still needs them); a lane drops out at the first ball that covers
+// its candidate, and the warp stops when every lane is settled.
 __global__ void __launch_bounds__(128) k_cull(CullArgs a) {
+  __shared__ uint32_t s_stack[4][kPStack];
+  const int lane = threadIdx.x & 31;
+  WarpStack W{s_stack[threadIdx.x >> 5], 0};
   const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   const int k = blockIdx.y;
-  if (i >= a.n) return;
+  const bool active = i < a.n;
   const BuildConsts bc = *a.bc;
-  const float4 S = a.sph[i];
+  const float4 S = active ? a.sph[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   const float r = fabsf(S.w);
   const float ux = a.U32[3 * k], uy = a.U32[3 * k + 1], uz = a.U32[3 * k + 2];
   const float qx = fmaf(r, ux, S.x), qy = fmaf(r, uy, S.y), qz = fmaf(r, uz, S.z);
@@ -305,80 +369,77 @@ __global__ void __launch_bounds__(128) k_cull(CullArgs a) {
       have64 = true;
     }
   };
-  if (a.box_cull) {
-    float mq = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
-    float eb = 2.f * bc.eq;
-    if (mq > 1.f + eb) return;
-    if (mq >= 1.f - eb) {
+  bool open = active;  // still looking for a covering ball
+  if (open && a.box_cull) {
+    const float mq = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
+    const float eb = 2.f * bc.eq;
+    if (mq > 1.f + eb) {
+      open = false;
+    } else if (mq >= 1.f - eb) {
       load64();
       ++rechecks;
-      if (!ex_inbox(qx64, qy64, qz64)) {
-        atomicAdd(&a.cnt->cull_rechecks, rechecks);
-        return;
-      }
+      if (!ex_inbox(qx64, qy64, qz64)) open = false;
     }
   }
+  const bool inbox = open;
   const Tree& T = a.tree;
-  uint32_t stack[kStack];
-  int sp = 0;
-  const int top = T.nlevels - 1;
-  for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
-  bool covered = false;
   const float grow = 1.f + 8.f * kU;
-  while (sp > 0 && !covered) {
-    const uint32_t nd = stack[--sp];
-    const int lev = node_level(nd);
-    const int64_t idx = node_index(nd);
-    if (lev == 0) {
-      const int64_t b = idx * kLeaf, e = min(b + kLeaf, a.n);
-      for (int64_t j = b; j < e; ++j) {
-        if (j == i) continue;
-        const float4 P = a.sph[j];
-        const float dx = qx - P.x, dy = qy - P.y, dz = qz - P.z;
-        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float4 Th = a.thr[j];
-        if (d2 < Th.x) { covered = true; break; }
-        if (d2 <= Th.y) {
-          load64();
-          ++rechecks;
-          if (ex_cov(qx64, qy64, qz64, a.sph64[a.sid[j]], a.tol)) { covered = true; break; }
-        }
-      }
-    } else {
-      const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
-      const int64_t off = T.offset[lev - 1];
-      int best = -1;
-      float bestm = -INFINITY;
-      uint32_t pend[kFan];
-      int np = 0;
-      for (int64_t c = cb; c < ce; ++c) {
-        // the node can hold a covering ball only if q lies in one of its
-        // bounding balls shrunk by tol
-        float margin = -INFINITY;
-        const float4 Bs[2] = {T.bp[off + c], T.bn[off + c]};
-        for (int cl = 0; cl < 2; ++cl) {
-          const float t = fmaf(Bs[cl].w - a.tol32, grow, bc.pad);
-          if (!(t > 0.f)) continue;
-          const float dx = qx - Bs[cl].x, dy = qy - Bs[cl].y, dz = qz - Bs[cl].z;
+  if (__any_sync(kFull, open)) {
+    W.push_top(T, lane);
+    while (W.sp > 0 && __any_sync(kFull, open)) {
+      const uint32_t nd = W.pop();
+      const int lev = node_level(nd);
+      const int64_t idx = node_index(nd);
+      if (lev == 0) {
+        const int64_t b = idx * kLeaf, e = min(b + kLeaf, a.n);
+        for (int64_t j = b; j < e; ++j) {
+          const float4 P = a.sph[j];
+          const float4 Th = a.thr[j];
+          if (!open || j == i) continue;
+          const float dx = qx - P.x, dy = qy - P.y, dz = qz - P.z;
           const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          if (d2 < t * t) margin = fmaxf(margin, t * t - d2);
-        }
-        if (margin > -INFINITY) {
-          if (margin > bestm) {
-            if (best >= 0) pend[np++] = pack_node(lev - 1, best);
-            best = int(c);
-            bestm = margin;
-          } else {
-            pend[np++] = pack_node(lev - 1, c);
+          if (d2 < Th.x) {
+            open = false;
+          } else if (d2 <= Th.y) {
+            load64();
+            ++rechecks;
+            if (ex_cov(qx64, qy64, qz64, a.sph64[a.sid[j]], a.tol)) open = false;
           }
         }
+      } else {
+        const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
+        const int64_t off = T.offset[lev - 1];
+        unsigned need = 0;
+        int first = -1, firstn = 0;
+        for (int64_t c = cb; c < ce; ++c) {
+          // the node can hold a covering ball only if q lies in one of its
+          // bounding balls shrunk by tol
+          bool nd_c = false;
+          if (open) {
+            const float4 Bs[2] = {T.bp[off + c], T.bn[off + c]};
+            for (int cl = 0; cl < 2; ++cl) {
+              const float t = fmaf(Bs[cl].w - a.tol32, grow, bc.pad);
+              if (!(t > 0.f)) continue;
+              const float dx = qx - Bs[cl].x, dy = qy - Bs[cl].y, dz = qz - Bs[cl].z;
+              if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < t * t) nd_c = true;
+            }
+          }
+          const unsigned votes = __ballot_sync(kFull, nd_c);
+          if (votes) {
+            need |= 1u << unsigned(c - cb);
+            const int nv = __popc(votes);
+            if (nv > firstn) {
+              firstn = nv;
+              first = int(c - cb);
+            }
+          }
+        }
+        W.push(lev - 1, cb, need, first, lane);
       }
-      for (int q = 0; q < np; ++q) stack[sp++] = pend[q];
-      if (best >= 0) stack[sp++] = pack_node(lev - 1, best);
     }
   }
   if (rechecks) atomicAdd(&a.cnt->cull_rechecks, rechecks);
-  if (covered) return;
+  if (!(inbox && open)) return;
   // survivor: append to the list of its sign class (zero spheres: both)
   const uint32_t g = uint32_t(a.sid[i]) * uint32_t(a.KS) + uint32_t(k);
   const float4 item = make_float4(qx, qy, qz, __uint_as_float(g));
@@ -456,30 +517,29 @@ __device__ __forceinline__ void warp_count(unsigned long long* dst, unsigned lon
   if ((threadIdx.x & 31) == __ffs(mask) - 1 && v) atomicAdd(dst, v);
 }
 
-// FP64 band pass over the sphere hierarchy.  Finds, among the spheres whose
-// FP32 value lies at or below thr, the exact FP64 minimum and its input index
-// (ties to the lowest index).  mode 0: value |x-p| - r over sign class c;
-// mode 1: value |x-p| + r over all spheres.  The FP32 threshold is chosen so
-// that the exact minimiser always lies in the band.
-__device__ double band_sphere(const QueryArgs& a, const BuildConsts& bc, double x64, double y64, double z64, float x,
-                              float y, float z, int mode, int c, float thr, int& arg) {
-  const Tree& T = a.st;
-  const float grow = 1.f + 8.f * 5.9604644775390625e-8f;
+// Packet FP64 band pass over the sphere hierarchy.  A lane with band = true
+// finds, among the spheres whose FP32 value lies at or below its threshold
+// thr, the exact FP64 minimum and its input index (ties to the lowest index).
+// mode 0: |x-p| - r over sign class cls; mode 1: |x-p| + r over all spheres.
+__device__ double packet_band_sphere(const QueryArgs& a, const BuildConsts& bc, WarpStack& W, int lane, bool band,
+                                     double x64, double y64, double z64, float x, float y, float z, int mode,
+                                     int cls, float thr, int& arg) {
   double best = INFINITY;
   arg = INT_MAX;
-  uint32_t stack[kStack];
-  int sp = 0;
-  const int top = T.nlevels - 1;
-  for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
-  while (sp > 0) {
-    const uint32_t nd = stack[--sp];
+  if (!__any_sync(kFull, band)) return best;
+  const Tree& T = a.st;
+  const float grow = 1.f + 8.f * kU;
+  W.push_top(T, lane);
+  while (W.sp > 0) {
+    const uint32_t nd = W.pop();
     const int lev = node_level(nd);
     const int64_t idx = node_index(nd);
     if (lev == 0) {
       const int64_t b = idx * kLeaf, e = min(b + kLeaf, a.n);
       for (int64_t j = b; j < e; ++j) {
         const float4 P = a.sph[j];
-        if (mode == 0 && (P.w == 0.f || int(P.w < 0.f) != c)) continue;
+        if (!band) continue;
+        if (mode == 0 && (P.w == 0.f || int(P.w < 0.f) != cls)) continue;
         const float dx = x - P.x, dy = y - P.y, dz = z - P.z;
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float r = fabsf(P.w);
@@ -497,39 +557,44 @@ __device__ double band_sphere(const QueryArgs& a, const BuildConsts& bc, double 
     } else {
       const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
       const int64_t off = T.offset[lev - 1];
-      for (int64_t cc = cb; cc < ce; ++cc) {
-        const float4 B = mode == 1 ? T.bf[off + cc] : (c == 0 ? T.bp[off + cc] : T.bn[off + cc]);
-        if (!(B.w > -INFINITY)) continue;
-        const float t = fmaf(thr + B.w, grow, bc.eprune);
-        if (t > 0.f && ball_d2(x, y, z, B) < t * t) stack[sp++] = pack_node(lev - 1, cc);
+      unsigned need = 0;
+      for (int64_t c = cb; c < ce; ++c) {
+        bool nd_c = false;
+        if (band) {
+          const float4 B = mode == 1 ? T.bf[off + c] : (cls == 0 ? T.bp[off + c] : T.bn[off + c]);
+          const float t = fmaf(thr + B.w, grow, bc.eprune);
+          nd_c = t > 0.f && ball_d2(x, y, z, B) < t * t;
+        }
+        if (__any_sync(kFull, nd_c)) need |= 1u << unsigned(c - cb);
       }
+      W.push(lev - 1, cb, need, -1, lane);
     }
   }
   return best;
 }
 
-// FP64 band pass over a survivor hierarchy: exact nearest survivor among
-// those whose FP32 distance^2 is at most thr (ties to the lowest id).
-__device__ double band_surv(const QueryArgs& a, const BuildConsts& bc, int cls, double x64, double y64, double z64,
-                            float x, float y, float z, float thr, uint32_t& gbest) {
-  const Tree& T = a.vt[cls];
-  const float4* items = a.surv[cls];
-  const float grow = 1.f + 8.f * 5.9604644775390625e-8f;
-  const float thn = thr * grow + bc.ed_lin * __fsqrt_rn(thr) + 1e-30f;
+// Packet FP64 band pass over the survivor hierarchy of class cls: exact
+// nearest survivor among those whose FP32 distance^2 is at most thr.
+__device__ double packet_band_surv(const QueryArgs& a, const BuildConsts& bc, WarpStack& W, int lane, bool band,
+                                   int cls, double x64, double y64, double z64, float x, float y, float z, float thr,
+                                   uint32_t& gbest) {
   double best = INFINITY;
   gbest = 0xffffffffu;
-  uint32_t stack[kStack];
-  int sp = 0;
-  const int top = T.nlevels - 1;
-  for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
-  while (sp > 0) {
-    const uint32_t nd = stack[--sp];
+  if (!__any_sync(kFull, band)) return best;
+  const Tree& T = a.vt[cls];
+  const float4* items = a.surv[cls];
+  const float grow = 1.f + 8.f * kU;
+  const float thn = band ? thr * grow + bc.ed_lin * __fsqrt_rn(thr) + 1e-30f : -1.f;
+  W.push_top(T, lane);
+  while (W.sp > 0) {
+    const uint32_t nd = W.pop();
     const int lev = node_level(nd);
     const int64_t idx = node_index(nd);
     if (lev == 0) {
       const int64_t b = idx * kLeaf, e = min(b + kLeaf, T.nitems);
       for (int64_t j = b; j < e; ++j) {
         const float4 P = items[j];
+        if (!band) continue;
         const float dx = x - P.x, dy = y - P.y, dz = z - P.z;
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (!(d2 <= thr)) continue;
@@ -545,25 +610,48 @@ __device__ double band_surv(const QueryArgs& a, const BuildConsts& bc, int cls, 
     } else {
       const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
       const int64_t off = T.offset[lev - 1];
-      for (int64_t cc = cb; cc < ce; ++cc)
-        if (box_d2(x, y, z, T.lo[off + cc], T.hi[off + cc]) < thn) stack[sp++] = pack_node(lev - 1, cc);
+      unsigned need = 0;
+      for (int64_t c = cb; c < ce; ++c) {
+        const bool nd_c = box_d2(x, y, z, T.lo[off + c], T.hi[off + c]) < thn;
+        if (__any_sync(kFull, nd_c)) need |= 1u << unsigned(c - cb);
+      }
+      W.push(lev - 1, cb, need, -1, lane);
     }
   }
   return best;
 }
 
 __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
-  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (q >= a.m) return;
+  __shared__ uint32_t s_stack[4][kPStack];
+  const int lane = threadIdx.x & 31;
+  WarpStack W{s_stack[threadIdx.x >> 5], 0};
+  const int64_t slot = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const bool active = slot < a.m;
+  const int64_t q = active ? int64_t(a.perm ? a.perm[slot] : uint32_t(slot)) : 0;
   const BuildConsts bc = *a.bc;
-  double x64, y64, z64;
-  load_query(a, q, x64, y64, z64);
+  double x64 = 0.0, y64 = 0.0, z64 = 0.0;
+  if (active) load_query(a, q, x64, y64, z64);
   const float x = float(x64), y = float(y64), z = float(z64);
   unsigned long long rechecks = 0, n_nodes = 0, n_items = 0, n_snodes = 0, n_sitems = 0, n_band = 0;
-  bool defer = !(fabs(x64) <= bc.A && fabs(y64) <= bc.A && fabs(z64) <= bc.A);
+  bool defer = active && !(fabs(x64) <= bc.A && fabs(y64) <= bc.A && fabs(z64) <= bc.A);
+  bool live = active && !defer;
   const float grow = 1.f + 8.f * kU;
   const float ea2 = 2.f * bc.ea;
   const float negtol = -a.tol32 + ea2;
+  // warp centre, used to order children (nearest first)
+  float cx = live ? x : 0.f, cy = live ? y : 0.f, cz = live ? z : 0.f;
+  float cnt = live ? 1.f : 0.f;
+  for (int o = 16; o > 0; o >>= 1) {
+    cx += __shfl_xor_sync(kFull, cx, o);
+    cy += __shfl_xor_sync(kFull, cy, o);
+    cz += __shfl_xor_sync(kFull, cz, o);
+    cnt += __shfl_xor_sync(kFull, cnt, o);
+  }
+  if (cnt > 0.f) {
+    cx /= cnt;
+    cy /= cnt;
+    cz /= cnt;
+  }
   // ---- pass over the spheres -------------------------------------------
   bool cov[2] = {false, false};
   Top2 A[2], F;
@@ -571,22 +659,20 @@ __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
   top2_init(A[1]);
   top2_init(F);
   int sample = INT_MAX;
-  if (!defer) {
+  if (__any_sync(kFull, live)) {
     const Tree& T = a.st;
-    uint32_t stack[kStack];
-    int sp = 0;
-    const int top = T.nlevels - 1;
-    for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
-    while (sp > 0) {
-      const uint32_t nd = stack[--sp];
+    W.push_top(T, lane);
+    while (W.sp > 0) {
+      const uint32_t nd = W.pop();
       const int lev = node_level(nd);
       const int64_t idx = node_index(nd);
-      ++n_nodes;
+      n_nodes += live;
       if (lev == 0) {
         const int64_t b = idx * kLeaf, e = min(b + kLeaf, a.n);
-        n_items += uint64_t(e - b);
+        n_items += live ? uint64_t(e - b) : 0;
         for (int64_t j = b; j < e; ++j) {
           const float4 P = a.sph[j];
+          if (!live) continue;
           const float dx = x - P.x, dy = y - P.y, dz = z - P.z;
           const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           if (d2 == 0.f) {
@@ -619,40 +705,40 @@ __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
         if (!cov[0]) th0 = fmaxf(th0, negtol);
         if (!cov[1]) th1 = fmaxf(th1, negtol);
         const float thf = top2_th(F, ea2);
-        int best = -1;
-        float bestd = INFINITY;
-        uint32_t pend[kFan];
-        int np = 0;
+        unsigned need = 0;
+        int first = -1;
+        float firstd = INFINITY;
         for (int64_t c = cb; c < ce; ++c) {
           const float4 L = T.lo[off + c], H = T.hi[off + c];
-          const float d2 = box_d2(x, y, z, L, H);
-          bool need = inside_box(x, y, z, L, H);
-          if (!need) {
-            const float4 B = T.bp[off + c];
-            const float t = fmaf(th0 + B.w, grow, bc.eprune);
-            need = t > 0.f && ball_d2(x, y, z, B) < t * t;
+          bool nd_c = false;
+          if (live) {
+            nd_c = inside_box(x, y, z, L, H);
+            if (!nd_c) {
+              const float4 B = T.bp[off + c];
+              const float t = fmaf(th0 + B.w, grow, bc.eprune);
+              nd_c = t > 0.f && ball_d2(x, y, z, B) < t * t;
+            }
+            if (!nd_c) {
+              const float4 B = T.bn[off + c];
+              const float t = fmaf(th1 + B.w, grow, bc.eprune);
+              nd_c = t > 0.f && ball_d2(x, y, z, B) < t * t;
+            }
+            if (!nd_c) {
+              const float4 B = T.bf[off + c];
+              const float t = fmaf(thf + B.w, grow, bc.eprune);
+              nd_c = t > 0.f && ball_d2(x, y, z, B) < t * t;
+            }
           }
-          if (!need) {
-            const float4 B = T.bn[off + c];
-            const float t = fmaf(th1 + B.w, grow, bc.eprune);
-            need = t > 0.f && ball_d2(x, y, z, B) < t * t;
-          }
-          if (!need) {
-            const float4 B = T.bf[off + c];
-            const float t = fmaf(thf + B.w, grow, bc.eprune);
-            need = t > 0.f && ball_d2(x, y, z, B) < t * t;
-          }
-          if (!need) continue;
-          if (d2 < bestd) {
-            if (best >= 0) pend[np++] = pack_node(lev - 1, best);
-            best = int(c);
-            bestd = d2;
-          } else {
-            pend[np++] = pack_node(lev - 1, c);
+          if (__any_sync(kFull, nd_c)) {
+            need |= 1u << unsigned(c - cb);
+            const float dc = box_d2(cx, cy, cz, L, H);
+            if (dc < firstd) {
+              firstd = dc;
+              first = int(c - cb);
+            }
           }
         }
-        for (int t = 0; t < np; ++t) stack[sp++] = pend[t];
-        if (best >= 0) stack[sp++] = pack_node(lev - 1, best);
+        W.push(lev - 1, cb, need, first, lane);
       }
     }
   }
@@ -660,7 +746,7 @@ __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
   double value = 0.0;
   int64_t arg = -1;
   int flags = 0;
-  if (!defer) {
+  if (live) {
     if (sample != INT_MAX) {
       code = GFS_CODE_SAMPLE;
       value = a.sph64[sample].w;
@@ -673,111 +759,110 @@ __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
     }
     if (code >= 0) flags = code;
   }
-  if (!defer && code < 0) {
-    const int cs = cov[0] ? 0 : 1, co = 1 - cs;
-    // ---- pass over the survivors of x's sign -----------------------------
-    float bd = INFINITY, sd = INFINITY;
-    uint32_t gbest = 0xffffffffu;
-    auto band = [&](float D) { return bc.ed_lin * __fsqrt_rn(D) + bc.ed_quad * D + 1e-30f; };
-    if (a.vt[cs].nlevels > 0) {
-      const Tree& T = a.vt[cs];
-      const float4* items = a.surv[cs];
-      float th = INFINITY, thn = INFINITY;  // threshold on d^2, and widened for nodes
-      uint32_t stack[kStack];
-      int sp = 0;
-      const int top = T.nlevels - 1;
-      for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
-      while (sp > 0) {
-        const uint32_t nd = stack[--sp];
-        const int lev = node_level(nd);
-        const int64_t idx = node_index(nd);
-        ++n_snodes;
-        if (lev == 0) {
-          const int64_t b = idx * kLeaf, e = min(b + kLeaf, T.nitems);
-          n_sitems += uint64_t(e - b);
-          for (int64_t j = b; j < e; ++j) {
-            const float4 P = items[j];
-            const float dx = x - P.x, dy = y - P.y, dz = z - P.z;
-            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (d2 < th) {
-              if (d2 < bd) {
-                sd = bd;
-                bd = d2;
-                gbest = __float_as_uint(P.w);
-              } else {
-                sd = d2;
-              }
-              th = fminf(sd, bd + 2.f * band(bd));
-              thn = th * grow + bc.ed_lin * __fsqrt_rn(th) + 1e-30f;
-            }
-          }
-        } else {
-          const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
-          const int64_t off = T.offset[lev - 1];
-          int best = -1;
-          float bestd = INFINITY;
-          uint32_t pend[kFan];
-          int np = 0;
-          for (int64_t c = cb; c < ce; ++c) {
-            const float d2 = box_d2(x, y, z, T.lo[off + c], T.hi[off + c]);
-            if (!(d2 < thn)) continue;
-            if (d2 < bestd) {
-              if (best >= 0) pend[np++] = pack_node(lev - 1, best);
-              best = int(c);
-              bestd = d2;
+  const bool open = live && code < 0;
+  const int cs = cov[0] ? 0 : 1, co = 1 - cs;
+  // ---- pass over the survivors of each lane's sign ------------------------
+  float bd = INFINITY, sd = INFINITY;
+  uint32_t gbest = 0xffffffffu;
+  auto band = [&](float D) { return bc.ed_lin * __fsqrt_rn(D) + bc.ed_quad * D + 1e-30f; };
+  for (int cl = 0; cl < 2; ++cl) {
+    const bool mine = open && cs == cl;
+    if (!__any_sync(kFull, mine) || a.vt[cl].nlevels == 0) continue;
+    const Tree& T = a.vt[cl];
+    const float4* items = a.surv[cl];
+    float th = mine ? INFINITY : -1.f;   // threshold on d^2
+    float thn = th;                      // widened for node tests
+    W.push_top(T, lane);
+    while (W.sp > 0) {
+      const uint32_t nd = W.pop();
+      const int lev = node_level(nd);
+      const int64_t idx = node_index(nd);
+      n_snodes += mine;
+      if (lev == 0) {
+        const int64_t b = idx * kLeaf, e = min(b + kLeaf, T.nitems);
+        n_sitems += mine ? uint64_t(e - b) : 0;
+        for (int64_t j = b; j < e; ++j) {
+          const float4 P = items[j];
+          const float dx = x - P.x, dy = y - P.y, dz = z - P.z;
+          const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (d2 < th) {
+            if (d2 < bd) {
+              sd = bd;
+              bd = d2;
+              gbest = __float_as_uint(P.w);
             } else {
-              pend[np++] = pack_node(lev - 1, c);
+              sd = d2;
+            }
+            th = fminf(sd, bd + 2.f * band(bd));
+            thn = th * grow + bc.ed_lin * __fsqrt_rn(th) + 1e-30f;
+          }
+        }
+      } else {
+        const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
+        const int64_t off = T.offset[lev - 1];
+        unsigned need = 0;
+        int first = -1;
+        float firstd = INFINITY;
+        for (int64_t c = cb; c < ce; ++c) {
+          const float4 L = T.lo[off + c], H = T.hi[off + c];
+          const bool nd_c = box_d2(x, y, z, L, H) < thn;
+          if (__any_sync(kFull, nd_c)) {
+            need |= 1u << unsigned(c - cb);
+            const float dc = box_d2(cx, cy, cz, L, H);
+            if (dc < firstd) {
+              firstd = dc;
+              first = int(c - cb);
             }
           }
-          for (int t = 0; t < np; ++t) stack[sp++] = pend[t];
-          if (best >= 0) stack[sp++] = pack_node(lev - 1, best);
         }
+        W.push(lev - 1, cb, need, first, lane);
       }
     }
-    const bool have_s = gbest != 0xffffffffu, have_u = A[co].idx >= 0;
-    // exact nearest survivor: direct when no other survivor lies in the
-    // error band, else an FP64 pass over the band
-    double ds = INFINITY;
-    if (have_s) {
-      if (sd >= bd + 2.f * band(bd)) {
-        double qx, qy, qz;
-        surv_pos64(a, gbest, qx, qy, qz);
-        ds = __dsqrt_rn(ex_d2(x64, y64, z64, qx, qy, qz));
-      } else {
-        ++n_band;
-        ds = __dsqrt_rn(band_surv(a, bc, cs, x64, y64, z64, x, y, z, bd + 2.f * band(bd), gbest));
-      }
+  }
+  const bool have_s = open && gbest != 0xffffffffu, have_u = open && A[co].idx >= 0;
+  // exact nearest survivor: direct when no other survivor lies in the error
+  // band, else an FP64 pass over the band
+  double ds = INFINITY;
+  bool sband = have_s && !(sd >= bd + 2.f * band(bd));
+  if (have_s && !sband) {
+    double qx, qy, qz;
+    surv_pos64(a, gbest, qx, qy, qz);
+    ds = __dsqrt_rn(ex_d2(x64, y64, z64, qx, qy, qz));
+  }
+  for (int cl = 0; cl < 2; ++cl) {
+    uint32_t g2;
+    const bool mine = sband && cs == cl;
+    const double e2 = packet_band_surv(a, bc, W, lane, mine, cl, x64, y64, z64, x, y, z,
+                                       mine ? bd + 2.f * band(bd) : -1.f, g2);
+    if (mine) {
+      ++n_band;
+      ds = __dsqrt_rn(e2);
+      gbest = g2;
     }
-    // exact nearest opposite tangent point
-    double ub = INFINITY;
-    int uj = -1;
-    if (have_u) {
-      if (A[co].sec >= A[co].best + ea2) {
-        uj = a.sid[A[co].idx];
-        const D4 pj = a.sph64[uj];
-        ub = __dsub_rn(__dsqrt_rn(ex_d2(x64, y64, z64, pj.x, pj.y, pj.z)), fabs(pj.w));
-      } else {
-        ++n_band;
-        ub = band_sphere(a, bc, x64, y64, z64, x, y, z, 0, co, A[co].best + ea2, uj);
-      }
+  }
+  // exact nearest opposite tangent point
+  double ub = INFINITY;
+  int uj = -1;
+  const bool uband = have_u && !(A[co].sec >= A[co].best + ea2);
+  if (have_u && !uband) {
+    uj = a.sid[A[co].idx];
+    const D4 pj = a.sph64[uj];
+    ub = __dsub_rn(__dsqrt_rn(ex_d2(x64, y64, z64, pj.x, pj.y, pj.z)), fabs(pj.w));
+  }
+  {
+    int j2;
+    const double v = packet_band_sphere(a, bc, W, lane, uband, x64, y64, z64, x, y, z, 0, co,
+                                        uband ? A[co].best + ea2 : -1.f, j2);
+    if (uband) {
+      ++n_band;
+      ub = v;
+      uj = j2;
     }
-    // exact lower bound LB (max over x's class of r - |x-p|) on demand
-    double lb = 0.0;
-    int lj = -1;
-    bool have_lb = false;
-    auto exact_lb = [&]() {
-      if (have_lb) return;
-      have_lb = true;
-      if (A[cs].sec >= A[cs].best + ea2) {
-        lj = a.sid[A[cs].idx];
-        const D4 pl = a.sph64[lj];
-        lb = __dsub_rn(fabs(pl.w), __dsqrt_rn(ex_d2(x64, y64, z64, pl.x, pl.y, pl.z)));
-      } else {
-        ++n_band;
-        lb = -band_sphere(a, bc, x64, y64, z64, x, y, z, 0, cs, A[cs].best + ea2, lj);
-      }
-    };
-    double m;
+  }
+  // value and the result code
+  double m = 0.0;
+  bool need_lb = false;
+  if (open) {
     if (have_s && (!a.clamp_opp || ds <= ub)) {
       code = GFS_CODE_SURVIVOR;
       m = ds;
@@ -787,38 +872,64 @@ __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
       m = ub;
       arg = uj;
     } else {
-      exact_lb();
       code = GFS_CODE_LOWER;
-      m = lb;
-      arg = lj;
+      need_lb = true;
     }
-    if (m < 0.0) m = 0.0;
+  }
+  const double E = double(bc.ea) * 1.01 + 1e-15;
+  const double lbt = -double(A[cs].best) - a.tol;
+  const double ft = double(F.best) + a.tol;
+  if (open && code != GFS_CODE_LOWER) {
+    const double mm = m < 0.0 ? 0.0 : m;
+    need_lb = !(mm < lbt - E) && !(mm > lbt + E);
+  }
+  // exact lower bound LB (max over the lane's class of r - |x-p|) if needed
+  double lb = 0.0;
+  int lj = -1;
+  const bool lband = need_lb && !(A[cs].sec >= A[cs].best + ea2);
+  if (need_lb && !lband) {
+    lj = a.sid[A[cs].idx];
+    const D4 pl = a.sph64[lj];
+    lb = __dsub_rn(fabs(pl.w), __dsqrt_rn(ex_d2(x64, y64, z64, pl.x, pl.y, pl.z)));
+  }
+  {
+    int j2;
+    const double v = packet_band_sphere(a, bc, W, lane, lband, x64, y64, z64, x, y, z, 0, cs,
+                                        lband ? A[cs].best + ea2 : -1.f, j2);
+    if (lband) {
+      ++n_band;
+      lb = -v;
+      lj = j2;
+    }
+  }
+  if (open && code == GFS_CODE_LOWER) {
+    m = lb;
+    arg = lj;
+  }
+  if (m < 0.0) m = 0.0;
+  // exact far bound if the FP32 margin does not decide FAR_VIOL
+  const bool need_far = open && !(m > ft + E) && !(m < ft - E);
+  const bool fband = need_far && !(F.sec >= F.best + ea2);
+  double far = INFINITY;
+  if (need_far && !fband) {
+    const D4 pf = a.sph64[a.sid[F.idx]];
+    far = __dadd_rn(__dsqrt_rn(ex_d2(x64, y64, z64, pf.x, pf.y, pf.z)), fabs(pf.w));
+  }
+  {
+    int j2;
+    const double v = packet_band_sphere(a, bc, W, lane, fband, x64, y64, z64, x, y, z, 1, 0,
+                                        fband ? F.best + ea2 : -1.f, j2);
+    if (fband) {
+      ++n_band;
+      far = v;
+    }
+  }
+  if (open) {
     flags = code;
-    const double E = double(bc.ea) * 1.01 + 1e-15;
-    // LB_VIOL: m < LB - tol
-    const double lbt = -double(A[cs].best) - a.tol;
-    if (m < lbt - E) {
-      flags |= GFS_FLAG_LB_VIOL;
-    } else if (!(m > lbt + E)) {
-      exact_lb();
-      if (m < __dsub_rn(lb, a.tol)) flags |= GFS_FLAG_LB_VIOL;
-    }
-    // FAR_VIOL: m > FAR + tol
-    const double ft = double(F.best) + a.tol;
-    if (m > ft + E) {
-      flags |= GFS_FLAG_FAR_VIOL;
-    } else if (!(m < ft - E)) {
-      double far;
-      if (F.sec >= F.best + ea2) {
-        const D4 pf = a.sph64[a.sid[F.idx]];
-        far = __dadd_rn(__dsqrt_rn(ex_d2(x64, y64, z64, pf.x, pf.y, pf.z)), fabs(pf.w));
-      } else {
-        ++n_band;
-        int fj;
-        far = band_sphere(a, bc, x64, y64, z64, x, y, z, 1, 0, F.best + ea2, fj);
-      }
-      if (m > __dadd_rn(far, a.tol)) flags |= GFS_FLAG_FAR_VIOL;
-    }
+    if (m < lbt - E) flags |= GFS_FLAG_LB_VIOL;
+    else if (need_lb && m < __dsub_rn(lb, a.tol)) flags |= GFS_FLAG_LB_VIOL;
+    if (m > ft + E) flags |= GFS_FLAG_FAR_VIOL;
+    else if (need_far && m > __dadd_rn(far, a.tol)) flags |= GFS_FLAG_FAR_VIOL;
     if (have_u && ub < __dsub_rn(m, a.tol)) flags |= GFS_FLAG_OPP_VIOL;
     value = cs == 0 ? m : -m;
   }
@@ -828,13 +939,13 @@ __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
   warp_count(&a.cnt->q_surv_nodes, n_snodes);
   warp_count(&a.cnt->q_band_passes, n_band);
   warp_count(&a.cnt->q_surv_items, n_sitems);
-  if (!defer) {
+  if (live) {
     write_result(a, q, value, arg, flags);
-    return;
+  } else if (defer) {
+    // outside the coordinate range the error bounds assume: FP64 path
+    const unsigned int s2 = atomicAdd(&a.cnt->ndefer, 1u);
+    if (s2 < a.defer_cap) a.defer[s2] = uint32_t(q);
   }
-  // outside the coordinate range the error bounds assume: FP64 path
-  const unsigned int slot = atomicAdd(&a.cnt->ndefer, 1u);
-  if (slot < a.defer_cap) a.defer[slot] = uint32_t(q);
 }
 
 // ---------------------------------------------------------------------------
@@ -1170,6 +1281,14 @@ cudaError_t launch_build_tree(const float4* items, int is_sphere, float A, Tree&
       ++g_launches;
     }
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_query_keys(const double* x64, const float* x32, int64_t m, uint32_t* keys, int* vals,
+                              cudaStream_t st) {
+  if (m == 0) return cudaSuccess;
+  k_query_keys<<<nblk(m, 256), 256, 0, st>>>(x64, x32, m, keys, vals);
+  ++g_launches;
   return cudaGetLastError();
 }
 

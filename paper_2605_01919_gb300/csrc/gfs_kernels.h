@@ -47,6 +47,7 @@ struct QueryArgs {
   const double* x64;
   const float* x32;
   int64_t m;
+  const uint32_t* perm;     // processing order of the query points (Morton), or null
   float* s_out;
   double* s64_out;
   int64_t* arg_out;
@@ -55,6 +56,50 @@ struct QueryArgs {
   unsigned int defer_cap;
   Counters* cnt;
 };
+
+struct InsertArgs {
+  // spheres: [0, n_static) in the hierarchy, [n_static, *n_total) since the last rebuild
+  const float4* sph;
+  const int* sid;
+  Tree st;
+  int n_static;
+  D4* sph64;            // every sphere, global index order
+  double* witness64;    // witness point per sphere (inserted spheres)
+  int* counts;          // live survivors per sphere
+  int* n_total;         // device counter
+  // survivors: hierarchies with tombstone bits, plus lists added since the rebuild
+  const float4* surv[2];
+  Tree vt[2];
+  uint32_t* tomb[2];
+  float4* dsurv[2];
+  uint32_t* dtomb[2];
+  unsigned* dcount;        // entries per dynamic list
+  unsigned* dcount_start;  // entries at the start of the current step
+  unsigned dcap;
+  const double* U64;
+  int K, KS;
+  double tol;
+  int box_cull, clamp_opp;
+  const BuildConsts* bc;
+  const double* y;
+  double* s_out;
+  int64_t* arg_out;
+  uint16_t* fl_out;
+  struct StepRec* rec;
+  unsigned* lost;
+  unsigned* err;  // bit 0: walk stack overflow, bit 1: dynamic list overflow
+};
+
+struct StepRec {
+  int insert;
+  int pad;
+};
+
+cudaError_t launch_ins_step(const InsertArgs& a, int64_t t, cudaStream_t st);
+cudaError_t launch_ins_counts(const float4* s0, unsigned n0, const float4* s1, unsigned n1, const D4* sph64, int KS,
+                              int* counts, cudaStream_t st);
+cudaError_t launch_ins_compact(const float4* ssurv, const uint32_t* tomb, unsigned ns, const float4* dsurv,
+                               const uint32_t* dtomb, unsigned nd, float4* out, unsigned* count, cudaStream_t st);
 
 struct GradArgs {
   const double* x64;
@@ -83,6 +128,8 @@ cudaError_t sort_keys_u32(void* temp, size_t& temp_bytes, const uint32_t* kin, u
 cudaError_t launch_gather_spheres(const D4* sph64, const int* order, int64_t n, const BuildConsts* bc, float tol32,
                                   double tol, float4* sph, float4* thr, int* sid, cudaStream_t st);
 cudaError_t launch_build_tree(const float4* items, int is_sphere, float A, Tree& T, cudaStream_t st);
+cudaError_t launch_query_keys(const double* x64, const float* x32, int64_t m, uint32_t* keys, int* vals,
+                              cudaStream_t st);
 cudaError_t launch_point_keys(const float4* items, int64_t n, uint32_t* keys, int* vals, cudaStream_t st);
 cudaError_t launch_gather_points(const float4* src, const int* order, int64_t n, float4* dst, cudaStream_t st);
 cudaError_t launch_cull(const CullArgs& a, cudaStream_t st);

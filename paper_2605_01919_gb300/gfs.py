@@ -18,8 +18,8 @@ CODE_SURVIVOR, CODE_OPPOSITE, CODE_SAMPLE, CODE_OUTSIDE, CODE_INVALID, CODE_LOWE
 FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 0x10, 0x20, 0x40, 0x80
 
 EXPORTED = ["gfs_default_options", "gfs_create", "gfs_set_stream", "gfs_build", "gfs_query",
-            "gfs_query_backward", "gfs_survivors", "gfs_stats", "gfs_solve_host", "gfs_icosphere",
-            "gfs_strerror", "gfs_destroy"]
+            "gfs_query_backward", "gfs_insert", "gfs_survivors", "gfs_stats", "gfs_solve_host",
+            "gfs_icosphere", "gfs_strerror", "gfs_destroy"]
 
 
 class Options(ctypes.Structure):
@@ -73,6 +73,8 @@ def load(build_if_missing: bool = True):
     L.gfs_query.restype = i32
     L.gfs_query_backward.argtypes = [P, P, i32, i64, P, P, P, P, P, P, P]
     L.gfs_query_backward.restype = i32
+    L.gfs_insert.argtypes = [P, P, i64, P, P, P]
+    L.gfs_insert.restype = i32
     L.gfs_survivors.argtypes = [P, P, i64, ctypes.POINTER(i64)]
     L.gfs_survivors.restype = i32
     L.gfs_stats.argtypes = [P, ctypes.POINTER(Stats)]
@@ -195,6 +197,21 @@ class Context:
                                          _ptr(flags.contiguous()), _ptr(grad_s.contiguous().float()),
                                          _ptr(gx), _ptr(gp), _ptr(gs)))
         return gx, gp, gs
+
+    # -- greedy sequential insertion -------------------------------------------
+    def insert(self, y: torch.Tensor):
+        """Insert the rows of y in order (Sec. 4 greedy loop); returns the
+        per-step FP64 value, argmin and result word."""
+        assert y.is_cuda and y.dtype == torch.float64 and y.shape[-1] == 3
+        y = y.contiguous()
+        T = y.shape[0]
+        out = {"s64": torch.empty(T, dtype=torch.float64, device=y.device),
+               "argmin": torch.empty(T, dtype=torch.int64, device=y.device),
+               "flags": torch.empty(T, dtype=torch.int16, device=y.device)}
+        self._sync_stream()
+        _check(load().gfs_insert(self._h, _ptr(y), T, _ptr(out["s64"]), _ptr(out["argmin"]), _ptr(out["flags"])))
+        self.n = self.stats()["n_spheres"]
+        return out
 
     def survivors(self) -> torch.Tensor:
         cnt = ctypes.c_int64(0)

@@ -1,0 +1,80 @@
+"""Greedy sequential insertion on the GPU against the oracle's sequential
+loop: every step's value (FP64, bitwise), argmin and result word
+(including LOST_WITNESS), the final survivor set, and queries against the
+final state."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2605_01919_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2605_01919_gb300 import gfs
+    gfs.load()
+    return gfs
+
+
+def _compare(G, orc, p, s, tau, y, xq):
+    U = orc.icosphere(tau)
+    val, arg, fl, st = orc.insert(p, s, U, y)
+    ctx = G.Context(tau=tau)
+    ctx.build(torch.from_numpy(p).cuda(), torch.from_numpy(s).cuda())
+    out = ctx.insert(torch.from_numpy(y).cuda())
+    torch.cuda.synchronize()
+    gv = out["s64"].cpu().numpy()
+    ga = out["argmin"].cpu().numpy()
+    gf = out["flags"].cpu().numpy().astype(np.int32) & 0xFFFF
+    bad = np.nonzero((gf != fl) | (ga != arg))[0]
+    assert bad.size == 0, f"steps differ: {bad[:10]} gpu {gf[bad[:5]]} {ga[bad[:5]]} oracle {fl[bad[:5]]} {arg[bad[:5]]}"
+    assert np.array_equal(gv, val, equal_nan=True)
+    surv = ctx.survivors().cpu().numpy()
+    assert np.array_equal(surv, st["g"])
+    # queries against the final state use the inserted samples and witnesses
+    res = ctx.query(torch.from_numpy(xq).cuda())
+    ov, oa, of, _ = orc.query(st["p"], st["s"], (st["g"], st["sph"], st["q"]), xq)
+    assert np.array_equal(res["flags"].cpu().numpy().astype(np.int32) & 0xFFFF, of)
+    assert np.array_equal(res["argmin"].cpu().numpy(), oa)
+    assert np.array_equal(res["s64"].cpu().numpy(), ov, equal_nan=True)
+    ctx.close()
+    return fl
+
+
+def test_insert_refinement_sphere_grid(G, orc):
+    """Refinement: new points in random order inside the 10^3 sphere grid."""
+    w = W.sphere_grid(N=10, up=2, tau=2)
+    rng = np.random.default_rng(21)
+    y = rng.uniform(-0.9, 0.9, size=(300, 3))
+    xq = rng.uniform(-1, 1, size=(500, 3))
+    fl = _compare(G, orc, w.p, w.s, w.tau, y, xq)
+    assert np.any((fl & 15) == 0)
+
+
+def test_insert_with_rebuilds_and_repeats(G, orc):
+    """More steps than the rebuild interval (256), repeated points (SAMPLE
+    steps) and points outside every ball (OUTSIDE steps)."""
+    w = W.union_grid(N=10, up=2, tau=1)
+    rng = np.random.default_rng(22)
+    y = rng.uniform(-1, 1, size=(600, 3))
+    y[100:110] = y[0:10]                          # re-inserting a point: SAMPLE
+    xq = rng.uniform(-1, 1, size=(300, 3))
+    fl = _compare(G, orc, w.p, w.s, w.tau, y, xq)
+    assert np.sum((fl[100:110] & 15) == 2) == 10
+
+
+def test_insert_pseudo_sdf_repair(G, orc):
+    """Repair: samples fully covered at tau are removed and re-inserted in
+    index order with the greedy loop (noisy pseudo-SDF, small grid)."""
+    w = W.csg_pseudo_grid(N=10, tau=1)
+    U = orc.icosphere(w.tau)
+    keep = orc.keep_all(w.p, w.s, U)
+    covered = keep.sum(axis=1) == 0
+    p2, s2 = w.p[~covered], w.s[~covered]
+    y = w.p[covered][:200]
+    xq = np.random.default_rng(3).uniform(-1, 1, size=(300, 3))
+    _compare(G, orc, p2, s2, w.tau, y, xq)
