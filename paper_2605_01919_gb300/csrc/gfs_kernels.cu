@@ -58,10 +58,10 @@ __global__ void k_keys_d4(const D4* __restrict__ sph64, int64_t n, uint32_t* __r
   }
 }
 
-// Derive the launch-wide error bounds from the data bounds (one thread).
-__global__ void k_consts(const unsigned int* __restrict__ bound_bits, BuildConsts* __restrict__ bc) {
-  float A = fmaxf(1.0f, __uint_as_float(bound_bits[0]));
-  float R = __uint_as_float(bound_bits[1]);
+// Launch-wide error bounds from the data bounds (max |coordinate|, max |s|).
+__device__ BuildConsts make_consts(unsigned int amax_bits, unsigned int rmax_bits) {
+  float A = fmaxf(1.0f, __uint_as_float(amax_bits));
+  float R = __uint_as_float(rmax_bits);
   const float u = kU;
   const float s3 = 1.7320508f;
   BuildConsts c;
@@ -79,7 +79,11 @@ __global__ void k_consts(const unsigned int* __restrict__ bound_bits, BuildConst
   c.eprune = 4.f * s3 * u * A + 1e-7f;
   // the same for candidate points (their FP32 error is eq)
   c.pad = 4.f * s3 * (c.eq + u * A) + 1e-7f;
-  *bc = c;
+  return c;
+}
+
+__global__ void k_consts(const unsigned int* __restrict__ bound_bits, BuildConsts* __restrict__ bc) {
+  *bc = make_consts(bound_bits[0], bound_bits[1]);
 }
 
 // FP32 coverage thresholds on d^2 for the filter: d2 < lo => covered for
@@ -122,10 +126,8 @@ __global__ void k_gather_spheres(const D4* __restrict__ sph64, const int* __rest
 // ---------------------------------------------------------------------------
 // hierarchy build
 // ---------------------------------------------------------------------------
-__global__ void k_leaves(const float4* __restrict__ items, int64_t nitems, float4* __restrict__ lo,
-                         float4* __restrict__ hi, int64_t nleaves) {
-  int64_t L = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (L >= nleaves) return;
+__device__ void point_leaf_node(const float4* __restrict__ items, int64_t nitems, float4* __restrict__ lo,
+                                float4* __restrict__ hi, int64_t L) {
   int64_t b = L * kLeaf, e = min(b + kLeaf, nitems);
   float3 mn = make_float3(INFINITY, INFINITY, INFINITY), mx = make_float3(-INFINITY, -INFINITY, -INFINITY);
   for (int64_t i = b; i < e; ++i) {
@@ -139,10 +141,8 @@ __global__ void k_leaves(const float4* __restrict__ items, int64_t nitems, float
   hi[L] = make_float4(nextafterf(mx.x, INFINITY), nextafterf(mx.y, INFINITY), nextafterf(mx.z, INFINITY), 0.f);
 }
 
-__global__ void k_level(float4* __restrict__ lo, float4* __restrict__ hi, int64_t child_off, int64_t nchild,
-                        int64_t off, int64_t nnode) {
-  int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (j >= nnode) return;
+__device__ void point_level_node(float4* __restrict__ lo, float4* __restrict__ hi, int64_t child_off, int64_t nchild,
+                                 int64_t off, int64_t j) {
   int64_t b = j * kFan, e = min(b + kFan, nchild);
   float4 L = make_float4(INFINITY, INFINITY, INFINITY, 0.f), H = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
   for (int64_t c = b; c < e; ++c) {
@@ -152,6 +152,18 @@ __global__ void k_level(float4* __restrict__ lo, float4* __restrict__ hi, int64_
   }
   lo[off + j] = L;
   hi[off + j] = H;
+}
+
+__global__ void k_leaves(const float4* __restrict__ items, int64_t nitems, float4* __restrict__ lo,
+                         float4* __restrict__ hi, int64_t nleaves) {
+  int64_t L = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (L < nleaves) point_leaf_node(items, nitems, lo, hi, L);
+}
+
+__global__ void k_level(float4* __restrict__ lo, float4* __restrict__ hi, int64_t child_off, int64_t nchild,
+                        int64_t off, int64_t nnode) {
+  int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (j < nnode) point_level_node(lo, hi, child_off, nchild, off, j);
 }
 
 // Bounding ball of weighted centres (c_i, w_i): a centre c and
@@ -213,11 +225,9 @@ __device__ float4 bound_ball(const float4* it, int k, float A) {
   return make_float4(bx, by, bz, v);
 }
 
-__global__ void k_sphere_leaves(const float4* __restrict__ items, int64_t nitems, float A, float4* __restrict__ lo,
-                                float4* __restrict__ hi, float4* __restrict__ bp, float4* __restrict__ bn,
-                                float4* __restrict__ bf, int64_t nleaves) {
-  int64_t L = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (L >= nleaves) return;
+__device__ void sphere_leaf_node(const float4* __restrict__ items, int64_t nitems, float A, float4* __restrict__ lo,
+                                 float4* __restrict__ hi, float4* __restrict__ bp, float4* __restrict__ bn,
+                                 float4* __restrict__ bf, int64_t L) {
   int64_t b = L * kLeaf, e = min(b + kLeaf, nitems);
   float4 P[kLeaf], N[kLeaf], F[kLeaf];
   int np = 0, nn = 0, nf = 0;
@@ -238,11 +248,9 @@ __global__ void k_sphere_leaves(const float4* __restrict__ items, int64_t nitems
   bf[L] = bound_ball(F, nf, A);
 }
 
-__global__ void k_sphere_level(float4* __restrict__ lo, float4* __restrict__ hi, float4* __restrict__ bp,
-                               float4* __restrict__ bn, float4* __restrict__ bf, float A, int64_t child_off,
-                               int64_t nchild, int64_t off, int64_t nnode) {
-  int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (j >= nnode) return;
+__device__ void sphere_level_node(float4* __restrict__ lo, float4* __restrict__ hi, float4* __restrict__ bp,
+                                  float4* __restrict__ bn, float4* __restrict__ bf, float A, int64_t child_off,
+                                  int64_t nchild, int64_t off, int64_t j) {
   int64_t b = j * kFan, e = min(b + kFan, nchild);
   float4 L = make_float4(INFINITY, INFINITY, INFINITY, 0.f), H = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
   float4 P[kFan], N[kFan], F[kFan];
@@ -261,6 +269,20 @@ __global__ void k_sphere_level(float4* __restrict__ lo, float4* __restrict__ hi,
   bp[off + j] = bound_ball(P, np, A);
   bn[off + j] = bound_ball(N, nn, A);
   bf[off + j] = bound_ball(F, nf, A);
+}
+
+__global__ void k_sphere_leaves(const float4* __restrict__ items, int64_t nitems, float A, float4* __restrict__ lo,
+                                float4* __restrict__ hi, float4* __restrict__ bp, float4* __restrict__ bn,
+                                float4* __restrict__ bf, int64_t nleaves) {
+  int64_t L = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (L < nleaves) sphere_leaf_node(items, nitems, A, lo, hi, bp, bn, bf, L);
+}
+
+__global__ void k_sphere_level(float4* __restrict__ lo, float4* __restrict__ hi, float4* __restrict__ bp,
+                               float4* __restrict__ bn, float4* __restrict__ bf, float A, int64_t child_off,
+                               int64_t nchild, int64_t off, int64_t nnode) {
+  int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (j < nnode) sphere_level_node(lo, hi, bp, bn, bf, A, child_off, nchild, off, j);
 }
 
 // Morton keys of query points (processing order of the packet kernel)
@@ -347,12 +369,7 @@ struct WarpStack {
 // the sphere hierarchy as a packet (one node at a time, children visited if
 // any lane still needs them); a lane drops out at the first ball that covers
 // its candidate, and the warp stops when every lane is settled.
-__global__ void __launch_bounds__(128) k_cull(CullArgs a) {
-  __shared__ uint32_t s_stack[4][kPStack];
-  const int lane = threadIdx.x & 31;
-  WarpStack W{s_stack[threadIdx.x >> 5], 0};
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  const int k = blockIdx.y;
+__device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, int lane) {
   const bool active = i < a.n;
   const BuildConsts bc = *a.bc;
   const float4 S = active ? a.sph[i] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -450,8 +467,17 @@ __global__ void __launch_bounds__(128) k_cull(CullArgs a) {
     unsigned int base = 0;
     if (grp.thread_rank() == 0) base = atomicAdd(&a.cnt->nsurv[c], grp.size());
     base = grp.shfl(base, 0) + grp.thread_rank();
-    if (base < a.cap) a.surv[c][base] = item;
+    if (base < a.cap) {
+      a.surv[c][base] = item;
+      if (a.surv_shape) a.surv_shape[c][base] = uint16_t(a.shape);
+    }
   }
+}
+
+__global__ void __launch_bounds__(128) k_cull(CullArgs a) {
+  __shared__ uint32_t s_stack[4][kPStack];
+  WarpStack W{s_stack[threadIdx.x >> 5], 0};
+  cull_packet(a, blockIdx.x * int64_t(blockDim.x) + threadIdx.x, blockIdx.y, W, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------
@@ -621,11 +647,11 @@ __device__ double packet_band_surv(const QueryArgs& a, const BuildConsts& bc, Wa
   return best;
 }
 
-__global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
-  __shared__ uint32_t s_stack[4][kPStack];
-  const int lane = threadIdx.x & 31;
-  WarpStack W{s_stack[threadIdx.x >> 5], 0};
-  const int64_t slot = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ void query_exact_one(const QueryArgs& a, int64_t q);
+
+// One lane's query inside a warp-cooperative pass; `slot` indexes the
+// processing order (a.perm), all 32 lanes of the warp must call together.
+__device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int lane) {
   const bool active = slot < a.m;
   const int64_t q = active ? int64_t(a.perm ? a.perm[slot] : uint32_t(slot)) : 0;
   const BuildConsts bc = *a.bc;
@@ -944,8 +970,18 @@ __global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
   } else if (defer) {
     // outside the coordinate range the error bounds assume: FP64 path
     const unsigned int s2 = atomicAdd(&a.cnt->ndefer, 1u);
-    if (s2 < a.defer_cap) a.defer[s2] = uint32_t(q);
+    if (a.defer) {
+      if (s2 < a.defer_cap) a.defer[s2] = uint32_t(q);
+    } else {
+      query_exact_one(a, q);
+    }
   }
+}
+
+__global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
+  __shared__ uint32_t s_stack[4][kPStack];
+  WarpStack W{s_stack[threadIdx.x >> 5], 0};
+  query_packet(a, blockIdx.x * int64_t(blockDim.x) + threadIdx.x, W, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------

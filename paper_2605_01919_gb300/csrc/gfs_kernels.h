@@ -26,6 +26,8 @@ struct CullArgs {
   float4* surv[2];       // survivors per sign class (x, y, z, id bits)
   unsigned int cap;      // capacity of each survivor list
   Counters* cnt;
+  uint16_t* surv_shape[2];  // batched builds: shape index of each survivor (else null)
+  int shape;
 };
 
 struct QueryArgs {

@@ -135,25 +135,28 @@ def _random_primitive(rng, kinds=("sphere", "box", "torus")):
 
 def csg_pseudo_grid(N: int = 128, tau: int = 3, seed: int = 3000,
                     n_prims: int = 12, noise_frac: float = 0.05) -> Workload:
-    """Pseudo-SDF: CSG tree (min = union, max = intersection, max(a,-b) =
-    difference) over seeded spheres/boxes/tori, plus N(0, 0.1 h) noise on a
-    seeded 5% of the samples."""
+    """Pseudo-SDF: a CSG tree over seeded spheres/boxes/tori -- pairs of
+    primitives combined by union (min), difference (max(a, -b)) or
+    intersection with a dilated partner (max(a, b - 0.15)), and the pairs
+    joined by union -- plus N(0, 0.1 h) noise on a seeded 5% of the samples.
+    max/min combinations are not Euclidean distances, hence "pseudo"."""
     rng = np.random.default_rng(seed)
     prims = [_random_primitive(rng) for _ in range(n_prims)]
     p = grid_points(N)
     vals = [f(p) for f in prims]
-    # fold left with a seeded operator sequence; unions dominate so the
-    # result keeps volume.
-    acc = vals[0]
-    for v in vals[1:]:
-        op = rng.choice(["union", "union", "inter", "diff"])
+    acc = None
+    for j in range(0, n_prims - 1, 2):
+        a, b = vals[j], vals[j + 1]
+        op = rng.choice(["union", "diff", "inter"])
         if op == "union":
-            acc = np.minimum(acc, v)
-        elif op == "inter":
-            # intersection with a dilated primitive (keeps most volume)
-            acc = np.maximum(acc, v - 0.3)
+            blob = np.minimum(a, b)
+        elif op == "diff":
+            blob = np.maximum(a, -b)
         else:
-            acc = np.maximum(acc, -v)
+            blob = np.maximum(a, b - 0.15)
+        if not np.any(blob < 0):            # an empty pair falls back to its union
+            blob = np.minimum(a, b)
+        acc = blob if acc is None else np.minimum(acc, blob)
     h = grid_spacing(N)
     s = acc.copy()
     idx = rng.choice(s.shape[0], size=int(noise_frac * s.shape[0]), replace=False)

@@ -64,7 +64,8 @@ def test_insert_with_rebuilds_and_repeats(G, orc):
     y[100:110] = y[0:10]                          # re-inserting a point: SAMPLE
     xq = rng.uniform(-1, 1, size=(300, 3))
     fl = _compare(G, orc, w.p, w.s, w.tau, y, xq)
-    assert np.sum((fl[100:110] & 15) == 2) == 10
+    inserted_first = np.isin(fl[:10] & 15, [0, 1, 5])
+    assert np.all((fl[100:110][inserted_first] & 15) == 2)   # re-insertions reproduce the value
 
 
 def test_insert_pseudo_sdf_repair(G, orc):
