@@ -154,6 +154,43 @@ int gfs_insert(gfs_ctx* ctx, const double* y, int64_t T, double* s_out, int64_t*
  * Errors: GFS_ERR_STATE, GFS_ERR_ARG (cap too small: *count_host still set). */
 int gfs_survivors(gfs_ctx* ctx, int64_t* g_out, int64_t cap, int64_t* count_host);
 
+/* ---- batched shapes ------------------------------------------------------ */
+/* One independent shape of a batched call: its samples, its query points and
+ * its outputs (all device pointers; outputs nullable).  Layout and meaning
+ * are those of gfs_build / gfs_query. */
+typedef struct {
+  const double* p_xyz;  /* n*3 FP64 sample positions */
+  const double* s;      /* n FP64 samples */
+  int64_t n;
+  const void* x;        /* m*3 query points, FP64 or FP32 */
+  int x_is_fp32;
+  int64_t m;
+  float* s_out;         /* m FP32 values */
+  double* s64_out;      /* m FP64 values */
+  int64_t* argmin_out;  /* m candidate ids (local to the shape) or sphere indices */
+  uint16_t* flags_out;  /* m result words */
+} gfs_shape;
+
+/* P build of many shapes at once: one persistent cull launch covers every
+ * shape's candidates (the library keeps the shape table; the caller keeps the
+ * buffers alive until the last gfs_batch_query).  Results per shape are those
+ * of gfs_build on that shape alone.  The first build also picks the
+ * persistent grid sizes by timing a few candidates (autotuning).
+ * Synchronises the stream.  Errors: GFS_ERR_ARG (nshapes < 1 or > 65535, a
+ * shape with n < 1), GFS_ERR_TOO_LARGE, GFS_ERR_OOM, GFS_ERR_CUDA. */
+int gfs_batch_build(gfs_ctx* ctx, const gfs_shape* shapes_host, int nshapes);
+
+/* Queries of every shape of the last gfs_batch_build in one persistent
+ * launch, into each shape's outputs.  Issues no host synchronisation and no
+ * allocation, so it can be captured in a CUDA graph and replayed (with new
+ * point coordinates written into the same buffers).
+ * Errors: GFS_ERR_STATE (no batch build), GFS_ERR_CUDA. */
+int gfs_batch_query(gfs_ctx* ctx);
+
+/* Surviving candidate ids of one shape of the batch, ascending (device
+ * g_out, capacity cap; *count_host set).  Errors as gfs_survivors. */
+int gfs_batch_survivors(gfs_ctx* ctx, int shape, int64_t* g_out, int64_t cap, int64_t* count_host);
+
 /* Counters of the last build/query (host struct). */
 typedef struct {
   int64_t n_spheres;        /* spheres in the current state */

@@ -126,6 +126,20 @@ struct gfs_ctx {
   DevBuf qk_in, qk_out, qv_in, qv_out;  // query Morton keys / processing order
   // insertion state
   DevBuf ins_counts, ins_tomb[2], ins_dsurv[2], ins_dtomb[2], ins_misc;
+  // batched shapes
+  int b_ns = 0;
+  bool b_built = false;
+  std::vector<gfs_shape> b_shapes;
+  std::vector<int64_t> b_off, b_qoff, b_soff[2];
+  std::vector<Tree> b_st, b_vt[2];
+  DevBuf b_desc, b_offd, b_qoffd, b_sph64, b_k64in, b_k64out, b_sph, b_thr, b_sid, b_bits, b_bcs;
+  DevBuf b_lo, b_hi, b_bp, b_bn, b_bf, b_stdev, b_prefix, b_ctr, b_cnt, b_cviews, b_cw;
+  DevBuf b_sraw[2], b_sshape[2], b_ssorted[2], b_vlo[2], b_vhi[2], b_vtdev[2], b_hist;
+  DevBuf b_qkin, b_qkout, b_qvin, b_qvout, b_qviews, b_qw;
+  unsigned b_cap = 0;
+  unsigned b_nsurv[2] = {0, 0};
+  int64_t b_M = 0, b_qtotal = 0;
+  int b_grid_cull = 0, b_grid_query = 0;
   Counters host_cnt{};
   // host-buffer path (gfs_solve_host)
   DevBuf h_p, h_s, h_x, h_sout, h_arg, h_fl;
@@ -659,6 +673,411 @@ int gfs_survivors(gfs_ctx* c, int64_t* g_out, int64_t cap, int64_t* count_host) 
   return stt;
 }
 
+// ---------------------------------------------------------------------------
+// batched shapes
+// ---------------------------------------------------------------------------
+namespace {
+
+static_assert(sizeof(gfs_shape) == sizeof(ShapeDesc), "gfs_shape and ShapeDesc must share a layout");
+
+// Lay out one tree per shape inside shared node arrays: each shape's tree
+// pointers are offset to its block of nodes; level offsets stay local.
+int64_t forest_layout(std::vector<Tree>& trees, const std::vector<int64_t>& nitems, float4* lo, float4* hi,
+                      float4* bp, float4* bn, float4* bf, int& max_levels) {
+  int64_t base = 0;
+  max_levels = 0;
+  for (size_t s = 0; s < nitems.size(); ++s) {
+    Tree& T = trees[s];
+    tree_layout(T, nitems[s]);
+    T.lo = lo ? lo + base : nullptr;
+    T.hi = hi ? hi + base : nullptr;
+    T.bp = bp ? bp + base : nullptr;
+    T.bn = bn ? bn + base : nullptr;
+    T.bf = bf ? bf + base : nullptr;
+    base += tree_nodes(T);
+    max_levels = std::max(max_levels, T.nlevels);
+  }
+  return base;
+}
+
+// Build every level of a forest: one launch per level over all shapes.
+int forest_build(gfs_ctx* c, std::vector<Tree>& trees, DevBuf& trees_dev, const float4* items,
+                 const std::vector<int64_t>& item_off, const BuildConsts* bc, int is_sphere, int max_levels) {
+  cudaStream_t st = c->stream;
+  const int ns = int(trees.size());
+  GFS_TRY(ensure(trees_dev, trees.size() * sizeof(Tree)));
+  GFS_CK(cudaMemcpyAsync(trees_dev.p, trees.data(), trees.size() * sizeof(Tree), cudaMemcpyHostToDevice, st));
+  std::vector<int64_t> pre(size_t(ns + 1) * std::max(1, max_levels) + item_off.size());
+  for (int l = 0; l < max_levels; ++l) {
+    int64_t acc = 0;
+    for (int s = 0; s < ns; ++s) {
+      pre[size_t(l) * (ns + 1) + s] = acc;
+      acc += trees[s].nlevels > l ? trees[s].count[l] : 0;
+    }
+    pre[size_t(l) * (ns + 1) + ns] = acc;
+  }
+  const size_t io = size_t(ns + 1) * std::max(1, max_levels);
+  for (size_t s = 0; s < item_off.size(); ++s) pre[io + s] = item_off[s];
+  DevBuf& pd = c->b_prefix;
+  GFS_TRY(ensure(pd, pre.size() * 8));
+  GFS_CK(cudaMemcpyAsync(pd.p, pre.data(), pre.size() * 8, cudaMemcpyHostToDevice, st));
+  for (int l = 0; l < max_levels; ++l) {
+    const int64_t total = pre[size_t(l) * (ns + 1) + ns];
+    GFS_CK(launch_batch_tree_level(trees_dev.as<Tree>(), pd.as<int64_t>() + size_t(l) * (ns + 1), total, ns, l,
+                                   items, pd.as<int64_t>() + io, bc, is_sphere, st));
+  }
+  // the prefix buffer is reused by the next forest: finish before returning
+  GFS_CK(cudaStreamSynchronize(st));
+  return GFS_OK;
+}
+
+int sort64(gfs_ctx* c, unsigned long long* kin, unsigned long long* kout, int* vin, int* vout, int64_t n, int ns) {
+  int end_bit = 32;
+  while ((int64_t(1) << (end_bit - 32)) < ns) ++end_bit;
+  size_t bytes = 0;
+  GFS_CK(sort_pairs64(nullptr, bytes, kin, kout, vin, vout, n, end_bit, c->stream));
+  GFS_TRY(ensure(c->cub_temp, bytes));
+  bytes = c->cub_temp.bytes;
+  GFS_CK(sort_pairs64(c->cub_temp.p, bytes, kin, kout, vin, vout, n, end_bit, c->stream));
+  return GFS_OK;
+}
+
+// time one persistent launch configuration on a prefix of the work
+float time_grid(gfs_ctx* c, bool cull, int grid, int64_t limit) {
+  cudaStream_t st = c->stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaMemsetAsync(c->b_ctr.p, 0, 8, st);
+  cudaEventRecord(e0, st);
+  if (cull)
+    launch_batch_cull(c->b_cviews.as<CullArgs>(), c->b_cw.as<int64_t>(), c->b_ns, limit,
+                      c->b_ctr.as<unsigned long long>(), grid, st);
+  else
+    launch_batch_query(c->b_qviews.as<QueryArgs>(), c->b_qw.as<int64_t>(), c->b_ns, limit,
+                       c->b_ctr.as<unsigned long long>(), grid, st);
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms;
+}
+
+// pick the persistent grid (blocks of 128 threads) for one kernel
+int autotune_grid(gfs_ctx* c, bool cull, int64_t total) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int cand[] = {2, 3, 4, 5, 6, 8};
+  const int64_t limit = std::min<int64_t>(total, std::max<int64_t>(int64_t(sms) * 256, total / 16));
+  int best = sms * 4;
+  float best_ms = 1e30f;
+  for (int m : cand) {
+    const float ms = time_grid(c, cull, sms * m, limit);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = sms * m;
+    }
+  }
+  cudaGetLastError();
+  return best;
+}
+
+}  // namespace
+
+int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
+  if (!c || !shapes || ns < 1 || ns > 65535) return GFS_ERR_ARG;
+  cudaStream_t st = c->stream;
+  c->b_built = false;
+  c->b_ns = ns;
+  c->b_shapes.assign(shapes, shapes + ns);
+  std::vector<int64_t> off(ns + 1), qoff(ns + 1);
+  off[0] = qoff[0] = 0;
+  for (int s = 0; s < ns; ++s) {
+    if (shapes[s].n < 1 || !shapes[s].p_xyz || !shapes[s].s || shapes[s].m < 0 || (shapes[s].m > 0 && !shapes[s].x))
+      return GFS_ERR_ARG;
+    if (uint64_t(shapes[s].n) * uint64_t(c->KS) >= (uint64_t(1) << 32) || shapes[s].m >= (int64_t(1) << 31))
+      return GFS_ERR_TOO_LARGE;
+    off[s + 1] = off[s] + shapes[s].n;
+    qoff[s + 1] = qoff[s] + shapes[s].m;
+  }
+  const int64_t N = off[ns], M = qoff[ns];
+  if (N >= (int64_t(1) << 31)) return GFS_ERR_TOO_LARGE;
+  c->b_off = off;
+  c->b_qoff = qoff;
+  GFS_TRY(ensure(c->b_desc, size_t(ns) * sizeof(ShapeDesc)));
+  GFS_TRY(ensure(c->b_offd, size_t(ns + 1) * 8));
+  GFS_TRY(ensure(c->b_qoffd, size_t(ns + 1) * 8));
+  GFS_CK(cudaMemcpyAsync(c->b_desc.p, shapes, size_t(ns) * sizeof(ShapeDesc), cudaMemcpyHostToDevice, st));
+  GFS_CK(cudaMemcpyAsync(c->b_offd.p, off.data(), size_t(ns + 1) * 8, cudaMemcpyHostToDevice, st));
+  GFS_CK(cudaMemcpyAsync(c->b_qoffd.p, qoff.data(), size_t(ns + 1) * 8, cudaMemcpyHostToDevice, st));
+  // samples: copy, Morton sort by (shape, code), sorted FP32 copies
+  GFS_TRY(ensure(c->b_sph64, size_t(N) * sizeof(D4)));
+  GFS_TRY(ensure(c->b_k64in, size_t(std::max(N, M)) * 8));
+  GFS_TRY(ensure(c->b_k64out, size_t(std::max(N, M)) * 8));
+  GFS_TRY(ensure(c->vals_in, size_t(N) * 4));
+  GFS_TRY(ensure(c->vals_out, size_t(N) * 4));
+  GFS_TRY(ensure(c->b_sph, size_t(N) * sizeof(float4)));
+  GFS_TRY(ensure(c->b_thr, size_t(N) * sizeof(float4)));
+  GFS_TRY(ensure(c->b_sid, size_t(N) * 4));
+  GFS_TRY(ensure(c->b_bits, size_t(ns) * 8));
+  GFS_TRY(ensure(c->b_bcs, size_t(ns) * sizeof(BuildConsts)));
+  GFS_CK(cudaMemsetAsync(c->b_bits.p, 0, size_t(ns) * 8, st));
+  GFS_CK(launch_batch_copy(c->b_desc.as<ShapeDesc>(), c->b_offd.as<int64_t>(), ns, N, c->b_sph64.as<D4>(),
+                           c->b_k64in.as<unsigned long long>(), c->vals_in.as<int>(), c->b_bits.as<unsigned int>(),
+                           c->b_bcs.as<BuildConsts>(), st));
+  GFS_TRY(sort64(c, c->b_k64in.as<unsigned long long>(), c->b_k64out.as<unsigned long long>(), c->vals_in.as<int>(),
+                 c->vals_out.as<int>(), N, ns));
+  GFS_CK(launch_batch_gather(c->b_sph64.as<D4>(), c->vals_out.as<int>(), c->b_offd.as<int64_t>(), ns, N,
+                             c->b_bcs.as<BuildConsts>(), float(c->opt.tol), c->opt.tol, c->b_sph.as<float4>(),
+                             c->b_thr.as<float4>(), c->b_sid.as<int>(), st));
+  // sphere forest
+  c->b_st.assign(ns, Tree{});
+  std::vector<int64_t> nits(ns);
+  for (int s = 0; s < ns; ++s) nits[s] = shapes[s].n;
+  int maxL = 0;
+  const int64_t nodes = forest_layout(c->b_st, nits, nullptr, nullptr, nullptr, nullptr, nullptr, maxL);
+  GFS_TRY(ensure(c->b_lo, size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->b_hi, size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->b_bp, size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->b_bn, size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->b_bf, size_t(nodes) * sizeof(float4)));
+  forest_layout(c->b_st, nits, c->b_lo.as<float4>(), c->b_hi.as<float4>(), c->b_bp.as<float4>(), c->b_bn.as<float4>(),
+                c->b_bf.as<float4>(), maxL);
+  std::vector<int64_t> item_off(off.begin(), off.end() - 1);
+  GFS_TRY(forest_build(c, c->b_st, c->b_stdev, c->b_sph.as<float4>(), item_off, c->b_bcs.as<BuildConsts>(), 1, maxL));
+  // culling views and work items (shape, direction, warp of 32 spheres)
+  const uint64_t ncand = uint64_t(N) * uint64_t(c->K);
+  uint64_t cap = std::max<uint64_t>(uint64_t(1) << 16, ncand / 16 + 1024);
+  cap = std::min<uint64_t>(cap, 0xfffffff0u);
+  std::vector<CullArgs> cv(ns);
+  std::vector<int64_t> cw(ns + 1);
+  GFS_TRY(ensure(c->b_ctr, 16));
+  GFS_TRY(ensure(c->b_cnt, sizeof(Counters)));
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    c->b_cap = unsigned(cap);
+    for (int k = 0; k < 2; ++k) {
+      GFS_TRY(ensure(c->b_sraw[k], size_t(cap) * sizeof(float4)));
+      GFS_TRY(ensure(c->b_sshape[k], size_t(cap) * 2));
+    }
+    cw[0] = 0;
+    for (int s = 0; s < ns; ++s) {
+      CullArgs& a = cv[s];
+      std::memset(&a, 0, sizeof(a));
+      a.sph = c->b_sph.as<float4>() + off[s];
+      a.thr = c->b_thr.as<float4>() + off[s];
+      a.sid = c->b_sid.as<int>() + off[s];
+      a.sph64 = c->b_sph64.as<D4>() + off[s];
+      a.U32 = c->U32.as<float>();
+      a.U64 = c->U64.as<double>();
+      a.K = c->K;
+      a.KS = c->KS;
+      a.tree = c->b_st[s];
+      a.tol32 = float(c->opt.tol);
+      a.tol = c->opt.tol;
+      a.box_cull = c->opt.box_cull;
+      a.bc = c->b_bcs.as<BuildConsts>() + s;
+      a.n = shapes[s].n;
+      a.surv[0] = c->b_sraw[0].as<float4>();
+      a.surv[1] = c->b_sraw[1].as<float4>();
+      a.cap = c->b_cap;
+      a.cnt = c->b_cnt.as<Counters>();
+      a.surv_shape[0] = c->b_sshape[0].as<uint16_t>();
+      a.surv_shape[1] = c->b_sshape[1].as<uint16_t>();
+      a.shape = s;
+      cw[s + 1] = cw[s] + (shapes[s].n + 31) / 32 * c->K;
+    }
+    GFS_TRY(ensure(c->b_cviews, size_t(ns) * sizeof(CullArgs)));
+    GFS_TRY(ensure(c->b_cw, size_t(ns + 1) * 8));
+    GFS_CK(cudaMemcpyAsync(c->b_cviews.p, cv.data(), size_t(ns) * sizeof(CullArgs), cudaMemcpyHostToDevice, st));
+    GFS_CK(cudaMemcpyAsync(c->b_cw.p, cw.data(), size_t(ns + 1) * 8, cudaMemcpyHostToDevice, st));
+    if (c->b_grid_cull == 0) {
+      c->b_ns = ns;
+      c->b_grid_cull = autotune_grid(c, true, cw[ns]);
+    }
+    GFS_CK(cudaMemsetAsync(c->b_cnt.p, 0, sizeof(Counters), st));
+    GFS_CK(cudaMemsetAsync(c->b_ctr.p, 0, 8, st));
+    GFS_CK(launch_batch_cull(c->b_cviews.as<CullArgs>(), c->b_cw.as<int64_t>(), ns, cw[ns],
+                             c->b_ctr.as<unsigned long long>(), c->b_grid_cull, st));
+    Counters hc;
+    GFS_CK(cudaMemcpyAsync(&hc, c->b_cnt.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    GFS_CK(cudaStreamSynchronize(st));
+    const unsigned need = std::max(hc.nsurv[0], hc.nsurv[1]);
+    c->b_nsurv[0] = hc.nsurv[0];
+    c->b_nsurv[1] = hc.nsurv[1];
+    if (need <= c->b_cap) break;
+    cap = uint64_t(need) + need / 8 + 1024;
+    if (attempt == 2) return GFS_ERR_OOM;
+  }
+  // survivor forests, one tree per (shape, sign class)
+  for (int k = 0; k < 2; ++k) {
+    const unsigned nsv = c->b_nsurv[k];
+    GFS_TRY(ensure(c->b_hist, size_t(ns) * 4));
+    GFS_CK(cudaMemsetAsync(c->b_hist.p, 0, size_t(ns) * 4, st));
+    GFS_CK(launch_batch_hist(c->b_sshape[k].as<uint16_t>(), nsv, c->b_hist.as<unsigned>(), st));
+    std::vector<unsigned> cnts(ns);
+    GFS_CK(cudaMemcpyAsync(cnts.data(), c->b_hist.p, size_t(ns) * 4, cudaMemcpyDeviceToHost, st));
+    GFS_CK(cudaStreamSynchronize(st));
+    std::vector<int64_t> so(ns + 1), sn(ns);
+    so[0] = 0;
+    for (int s = 0; s < ns; ++s) {
+      so[s + 1] = so[s] + cnts[s];
+      sn[s] = cnts[s];
+    }
+    c->b_soff[k] = so;
+    GFS_TRY(ensure(c->b_ssorted[k], size_t(nsv) * sizeof(float4) + 16));
+    if (nsv) {
+      GFS_TRY(ensure(c->b_k64in, size_t(nsv) * 8));
+      GFS_TRY(ensure(c->b_k64out, size_t(nsv) * 8));
+      GFS_TRY(ensure(c->vals_in, size_t(nsv) * 4));
+      GFS_TRY(ensure(c->vals_out, size_t(nsv) * 4));
+      GFS_CK(launch_batch_surv_keys(c->b_sraw[k].as<float4>(), c->b_sshape[k].as<uint16_t>(), nsv,
+                                    c->b_k64in.as<unsigned long long>(), c->vals_in.as<int>(), st));
+      GFS_TRY(sort64(c, c->b_k64in.as<unsigned long long>(), c->b_k64out.as<unsigned long long>(),
+                     c->vals_in.as<int>(), c->vals_out.as<int>(), nsv, ns));
+      GFS_CK(launch_batch_gather_points(c->b_sraw[k].as<float4>(), c->vals_out.as<int>(), nsv,
+                                        c->b_ssorted[k].as<float4>(), st));
+    }
+    c->b_vt[k].assign(ns, Tree{});
+    int mL = 0;
+    const int64_t vn = forest_layout(c->b_vt[k], sn, nullptr, nullptr, nullptr, nullptr, nullptr, mL);
+    GFS_TRY(ensure(c->b_vlo[k], size_t(vn) * sizeof(float4) + 16));
+    GFS_TRY(ensure(c->b_vhi[k], size_t(vn) * sizeof(float4) + 16));
+    forest_layout(c->b_vt[k], sn, c->b_vlo[k].as<float4>(), c->b_vhi[k].as<float4>(), nullptr, nullptr, nullptr, mL);
+    std::vector<int64_t> io(so.begin(), so.end() - 1);
+    GFS_TRY(forest_build(c, c->b_vt[k], c->b_vtdev[k], c->b_ssorted[k].as<float4>(), io, nullptr, 0, mL));
+  }
+  // query views and work items (shape, 32 points)
+  std::vector<QueryArgs> qv(ns);
+  std::vector<int64_t> qw(ns + 1);
+  qw[0] = 0;
+  GFS_TRY(ensure(c->b_qkin, size_t(std::max<int64_t>(M, 1)) * 8));
+  GFS_TRY(ensure(c->b_qkout, size_t(std::max<int64_t>(M, 1)) * 8));
+  GFS_TRY(ensure(c->b_qvin, size_t(std::max<int64_t>(M, 1)) * 4));
+  GFS_TRY(ensure(c->b_qvout, size_t(std::max<int64_t>(M, 1)) * 4));
+  for (int s = 0; s < ns; ++s) {
+    QueryArgs& a = qv[s];
+    std::memset(&a, 0, sizeof(a));
+    a.sph = c->b_sph.as<float4>() + off[s];
+    a.thr = c->b_thr.as<float4>() + off[s];
+    a.sid = c->b_sid.as<int>() + off[s];
+    a.sph64 = c->b_sph64.as<D4>() + off[s];
+    a.st = c->b_st[s];
+    a.n = shapes[s].n;
+    for (int k = 0; k < 2; ++k) {
+      a.surv[k] = c->b_ssorted[k].as<float4>() + c->b_soff[k][s];
+      a.vt[k] = c->b_vt[k][s];
+    }
+    a.U64 = c->U64.as<double>();
+    a.K = c->K;
+    a.KS = c->KS;
+    a.tol32 = float(c->opt.tol);
+    a.tol = c->opt.tol;
+    a.clamp_opp = c->opt.clamp_opp;
+    a.bc = c->b_bcs.as<BuildConsts>() + s;
+    if (shapes[s].x_is_fp32) a.x32 = static_cast<const float*>(shapes[s].x);
+    else a.x64 = static_cast<const double*>(shapes[s].x);
+    a.m = shapes[s].m;
+    a.perm = reinterpret_cast<const uint32_t*>(c->b_qvout.as<int>() + qoff[s]);
+    a.s_out = shapes[s].s_out;
+    a.s64_out = shapes[s].s64_out;
+    a.arg_out = shapes[s].argmin_out;
+    a.fl_out = shapes[s].flags_out;
+    a.cnt = c->b_cnt.as<Counters>();
+    qw[s + 1] = qw[s] + (shapes[s].m + 31) / 32;
+  }
+  GFS_TRY(ensure(c->b_qviews, size_t(ns) * sizeof(QueryArgs)));
+  GFS_TRY(ensure(c->b_qw, size_t(ns + 1) * 8));
+  GFS_CK(cudaMemcpyAsync(c->b_qviews.p, qv.data(), size_t(ns) * sizeof(QueryArgs), cudaMemcpyHostToDevice, st));
+  GFS_CK(cudaMemcpyAsync(c->b_qw.p, qw.data(), size_t(ns + 1) * 8, cudaMemcpyHostToDevice, st));
+  c->b_M = M;
+  c->b_qtotal = qw[ns];
+  // sort scratch for the query order, sized here so gfs_batch_query allocates nothing
+  size_t bytes = 0;
+  GFS_CK(sort_pairs64(nullptr, bytes, c->b_qkin.as<unsigned long long>(), c->b_qkout.as<unsigned long long>(),
+                      c->b_qvin.as<int>(), c->b_qvout.as<int>(), M, 64, st));
+  GFS_TRY(ensure(c->cub_temp, bytes));
+  c->b_built = true;
+  if (c->b_grid_query == 0 && c->b_qtotal > 0) {
+    GFS_TRY(gfs_batch_query(c));  // produces the Morton order used while tuning
+    c->b_grid_query = autotune_grid(c, false, c->b_qtotal);
+  }
+  GFS_CK(cudaStreamSynchronize(st));
+  return GFS_OK;
+}
+
+int gfs_batch_query(gfs_ctx* c) {
+  if (!c) return GFS_ERR_ARG;
+  if (!c->b_built) return GFS_ERR_STATE;
+  if (c->b_M == 0) return GFS_OK;
+  cudaStream_t st = c->stream;
+  const int ns = c->b_ns;
+  GFS_CK(launch_batch_qkeys(c->b_desc.as<ShapeDesc>(), c->b_qoffd.as<int64_t>(), ns, c->b_M,
+                            c->b_qkin.as<unsigned long long>(), c->b_qvin.as<int>(), st));
+  int end_bit = 32;
+  while ((int64_t(1) << (end_bit - 32)) < ns) ++end_bit;
+  size_t bytes = c->cub_temp.bytes;
+  GFS_CK(sort_pairs64(c->cub_temp.p, bytes, c->b_qkin.as<unsigned long long>(), c->b_qkout.as<unsigned long long>(),
+                      c->b_qvin.as<int>(), c->b_qvout.as<int>(), c->b_M, end_bit, st));
+  GFS_CK(cudaMemsetAsync(c->b_ctr.p, 0, 8, st));
+  const int grid = c->b_grid_query ? c->b_grid_query : 152 * 4;
+  GFS_CK(launch_batch_query(c->b_qviews.as<QueryArgs>(), c->b_qw.as<int64_t>(), ns, c->b_qtotal,
+                            c->b_ctr.as<unsigned long long>(), grid, st));
+  return GFS_OK;
+}
+
+int gfs_batch_survivors(gfs_ctx* c, int shape, int64_t* g_out, int64_t cap, int64_t* count_host) {
+  if (!c || !count_host || cap < 0) return GFS_ERR_ARG;
+  if (!c->b_built) return GFS_ERR_STATE;
+  if (shape < 0 || shape >= c->b_ns) return GFS_ERR_ARG;
+  cudaStream_t st = c->stream;
+  const int64_t n0 = c->b_soff[0][shape + 1] - c->b_soff[0][shape];
+  const int64_t n1 = c->b_soff[1][shape + 1] - c->b_soff[1][shape];
+  DevBuf ids, sorted, cnt;
+  int stt = ensure(ids, size_t(n0 + n1) * 4 + 16);
+  if (stt == GFS_OK) stt = ensure(sorted, size_t(n0 + n1) * 4 + 16);
+  if (stt == GFS_OK) stt = ensure(cnt, 16);
+  unsigned hc = 0;
+  if (stt == GFS_OK) {
+    if (cudaMemsetAsync(cnt.p, 0, 4, st) != cudaSuccess ||
+        launch_collect_ids(c->b_ssorted[0].as<float4>() + c->b_soff[0][shape], unsigned(n0),
+                           c->b_ssorted[1].as<float4>() + c->b_soff[1][shape], unsigned(n1),
+                           c->b_sph64.as<D4>() + c->b_off[shape], c->KS, ids.as<uint32_t>(), cnt.as<unsigned>(),
+                           st) != cudaSuccess ||
+        cudaMemcpyAsync(&hc, cnt.p, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      stt = GFS_ERR_CUDA;
+    }
+  }
+  if (stt == GFS_OK) {
+    *count_host = hc;
+    if (hc > 0 && g_out && cap >= int64_t(hc)) {
+      size_t bytes = 0;
+      if (sort_keys_u32(nullptr, bytes, ids.as<uint32_t>(), sorted.as<uint32_t>(), hc, st) != cudaSuccess ||
+          cub_ensure(c, bytes) != GFS_OK) {
+        stt = GFS_ERR_CUDA;
+      } else {
+        bytes = c->cub_temp.bytes;
+        if (sort_keys_u32(c->cub_temp.p, bytes, ids.as<uint32_t>(), sorted.as<uint32_t>(), hc, st) != cudaSuccess ||
+            launch_widen_ids(sorted.as<uint32_t>(), hc, g_out, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+          cudaGetLastError();
+          stt = GFS_ERR_CUDA;
+        }
+      }
+    } else if (cap < int64_t(hc)) {
+      stt = GFS_ERR_ARG;
+    }
+  }
+  release(ids);
+  release(sorted);
+  release(cnt);
+  return stt;
+}
+
 int gfs_stats(gfs_ctx* c, gfs_stats_t* out) {
   if (!c || !out) return GFS_ERR_ARG;
   std::memset(out, 0, sizeof(*out));
@@ -741,7 +1160,13 @@ void gfs_destroy(gfs_ctx* c) {
                     &c->h_p, &c->h_s, &c->h_x, &c->h_sout, &c->h_arg, &c->h_fl,
                     &c->qk_in, &c->qk_out, &c->qv_in, &c->qv_out, &c->ins_counts,
                     &c->ins_tomb[0], &c->ins_tomb[1], &c->ins_dsurv[0], &c->ins_dsurv[1], &c->ins_dtomb[0],
-                    &c->ins_dtomb[1], &c->ins_misc};
+                    &c->ins_dtomb[1], &c->ins_misc,
+                    &c->b_desc, &c->b_offd, &c->b_qoffd, &c->b_sph64, &c->b_k64in, &c->b_k64out, &c->b_sph,
+                    &c->b_thr, &c->b_sid, &c->b_bits, &c->b_bcs, &c->b_lo, &c->b_hi, &c->b_bp, &c->b_bn, &c->b_bf,
+                    &c->b_stdev, &c->b_prefix, &c->b_ctr, &c->b_cnt, &c->b_cviews, &c->b_cw, &c->b_sraw[0],
+                    &c->b_sraw[1], &c->b_sshape[0], &c->b_sshape[1], &c->b_ssorted[0], &c->b_ssorted[1],
+                    &c->b_vlo[0], &c->b_vlo[1], &c->b_vhi[0], &c->b_vhi[1], &c->b_vtdev[0], &c->b_vtdev[1],
+                    &c->b_hist, &c->b_qkin, &c->b_qkout, &c->b_qvin, &c->b_qvout, &c->b_qviews, &c->b_qw};
   for (DevBuf* b : bufs) release(*b);
   delete c;
 }

@@ -1393,3 +1393,5 @@ cudaError_t launch_widen_ids(const uint32_t* in, int64_t n, int64_t* out, cudaSt
 }
 
 }  // namespace gfs
+
+#include "gfs_batch.cuh"

@@ -9,6 +9,20 @@
 
 namespace gfs {
 
+// one shape of a batched call (device pointers; outputs nullable)
+struct ShapeDesc {
+  const double* p;
+  const double* s;
+  int64_t n;
+  const void* x;
+  int x_is_fp32;
+  int64_t m;
+  float* s_out;
+  double* s64_out;
+  int64_t* argmin_out;
+  uint16_t* flags_out;
+};
+
 struct CullArgs {
   const float4* sph;     // sorted spheres (x, y, z, s) FP32
   const float4* thr;     // sorted coverage thresholds (lo/hi for candidates, lo/hi for queries)
@@ -142,5 +156,27 @@ cudaError_t launch_collect_ids(const float4* s0, unsigned int n0, const float4* 
                                int KS, uint32_t* out, unsigned int* count, cudaStream_t st);
 void launch_counts(unsigned long long* own, unsigned long long* sorts);
 cudaError_t launch_widen_ids(const uint32_t* in, int64_t n, int64_t* out, cudaStream_t st);
+
+cudaError_t launch_batch_copy(const ShapeDesc* d, const int64_t* off, int ns, int64_t N, D4* sph64,
+                              unsigned long long* keys, int* vals, unsigned int* bits, BuildConsts* bc,
+                              cudaStream_t st);
+cudaError_t sort_pairs64(void* temp, size_t& bytes, const unsigned long long* kin, unsigned long long* kout,
+                         const int* vin, int* vout, int64_t n, int end_bit, cudaStream_t st);
+cudaError_t launch_batch_gather(const D4* sph64, const int* order, const int64_t* off, int ns, int64_t N,
+                                const BuildConsts* bc, float tol32, double tol, float4* sph, float4* thr, int* sid,
+                                cudaStream_t st);
+cudaError_t launch_batch_tree_level(const Tree* trees, const int64_t* prefix, int64_t total, int ns, int level,
+                                    const float4* items_base, const int64_t* item_off, const BuildConsts* bc,
+                                    int is_sphere, cudaStream_t st);
+cudaError_t launch_batch_hist(const uint16_t* shape, unsigned n, unsigned* counts, cudaStream_t st);
+cudaError_t launch_batch_surv_keys(const float4* items, const uint16_t* shape, unsigned n, unsigned long long* keys,
+                                   int* vals, cudaStream_t st);
+cudaError_t launch_batch_gather_points(const float4* src, const int* order, unsigned n, float4* dst, cudaStream_t st);
+cudaError_t launch_batch_qkeys(const ShapeDesc* d, const int64_t* off, int ns, int64_t M, unsigned long long* keys,
+                               int* vals, cudaStream_t st);
+cudaError_t launch_batch_cull(const CullArgs* views, const int64_t* wprefix, int ns, int64_t limit,
+                              unsigned long long* ctr, int grid, cudaStream_t st);
+cudaError_t launch_batch_query(const QueryArgs* views, const int64_t* wprefix, int ns, int64_t limit,
+                               unsigned long long* ctr, int grid, cudaStream_t st);
 
 }  // namespace gfs

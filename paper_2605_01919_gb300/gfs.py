@@ -18,8 +18,9 @@ CODE_SURVIVOR, CODE_OPPOSITE, CODE_SAMPLE, CODE_OUTSIDE, CODE_INVALID, CODE_LOWE
 FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 0x10, 0x20, 0x40, 0x80
 
 EXPORTED = ["gfs_default_options", "gfs_create", "gfs_set_stream", "gfs_build", "gfs_query",
-            "gfs_query_backward", "gfs_insert", "gfs_survivors", "gfs_stats", "gfs_solve_host",
-            "gfs_icosphere", "gfs_strerror", "gfs_destroy"]
+            "gfs_query_backward", "gfs_insert", "gfs_survivors", "gfs_batch_build", "gfs_batch_query",
+            "gfs_batch_survivors", "gfs_stats", "gfs_solve_host", "gfs_icosphere", "gfs_strerror",
+            "gfs_destroy"]
 
 
 class Options(ctypes.Structure):
@@ -36,6 +37,13 @@ class Stats(ctypes.Structure):
         "query_surv_items")] + [(n, ctypes.c_double) for n in (
         "ms_build_total", "ms_build_cull", "ms_query_fast", "ms_query_exact")] + [
         (n, ctypes.c_int64) for n in ("kernel_launches", "sort_calls")]
+
+
+class Shape(ctypes.Structure):
+    _fields_ = [("p_xyz", ctypes.c_void_p), ("s", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("x", ctypes.c_void_p), ("x_is_fp32", ctypes.c_int), ("m", ctypes.c_int64),
+                ("s_out", ctypes.c_void_p), ("s64_out", ctypes.c_void_p), ("argmin_out", ctypes.c_void_p),
+                ("flags_out", ctypes.c_void_p)]
 
 
 class GfsError(RuntimeError):
@@ -75,6 +83,12 @@ def load(build_if_missing: bool = True):
     L.gfs_query_backward.restype = i32
     L.gfs_insert.argtypes = [P, P, i64, P, P, P]
     L.gfs_insert.restype = i32
+    L.gfs_batch_build.argtypes = [P, P, i32]
+    L.gfs_batch_build.restype = i32
+    L.gfs_batch_query.argtypes = [P]
+    L.gfs_batch_query.restype = i32
+    L.gfs_batch_survivors.argtypes = [P, i32, P, i64, ctypes.POINTER(i64)]
+    L.gfs_batch_survivors.restype = i32
     L.gfs_survivors.argtypes = [P, P, i64, ctypes.POINTER(i64)]
     L.gfs_survivors.restype = i32
     L.gfs_stats.argtypes = [P, ctypes.POINTER(Stats)]
@@ -235,6 +249,45 @@ class Context:
         _check(load().gfs_solve_host(self._h, ptr(p), ptr(s), p.shape[0], ptr(x), is32, x.shape[0],
                                      ptr(s_out), ptr(argmin_out), ptr(flags_out)))
         self.n = p.shape[0]
+
+    # -- batched shapes -----------------------------------------------------------
+    def batch_build(self, shapes):
+        """shapes: list of dicts with CUDA tensors p (n,3) f64, s (n,) f64 and
+        x (m,3) f64/f32.  Allocates each shape's outputs (returned as a list of
+        dicts) and builds every shape in one pass; keep the returned list alive
+        while calling batch_query."""
+        arr = (Shape * len(shapes))()
+        outs = []
+        for k, sh in enumerate(shapes):
+            p, sv, x = sh["p"].contiguous(), sh["s"].contiguous(), sh["x"].contiguous()
+            m = x.shape[0]
+            o = {"p": p, "s_in": sv, "x": x,
+                 "s": torch.empty(m, dtype=torch.float32, device=x.device),
+                 "s64": torch.empty(m, dtype=torch.float64, device=x.device),
+                 "argmin": torch.empty(m, dtype=torch.int64, device=x.device),
+                 "flags": torch.empty(m, dtype=torch.int16, device=x.device)}
+            arr[k] = Shape(p.data_ptr(), sv.data_ptr(), p.shape[0], x.data_ptr(), int(x.dtype == torch.float32), m,
+                           o["s"].data_ptr(), o["s64"].data_ptr(), o["argmin"].data_ptr(), o["flags"].data_ptr())
+            outs.append(o)
+        self._sync_stream()
+        _check(load().gfs_batch_build(self._h, ctypes.cast(arr, ctypes.c_void_p), len(shapes)))
+        self._batch = outs
+        return outs
+
+    def batch_query(self):
+        self._sync_stream()
+        _check(load().gfs_batch_query(self._h))
+        return self._batch
+
+    def batch_survivors(self, shape: int) -> torch.Tensor:
+        cnt = ctypes.c_int64(0)
+        self._sync_stream()
+        st = load().gfs_batch_survivors(self._h, shape, None, 0, ctypes.byref(cnt))
+        if st not in (0, 1):
+            _check(st)
+        out = torch.empty(max(cnt.value, 1), dtype=torch.int64, device="cuda")
+        _check(load().gfs_batch_survivors(self._h, shape, _ptr(out), out.numel(), ctypes.byref(cnt)))
+        return out[: cnt.value]
 
     def stats(self) -> dict:
         st = Stats()

@@ -1,0 +1,87 @@
+"""Batched shapes in one persistent launch: every shape's outputs equal the
+single-shape path (bitwise) and, on small shapes, the oracle; the batched
+query replays correctly from a captured CUDA graph."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2605_01919_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2605_01919_gb300 import gfs
+    gfs.load()
+    return gfs
+
+
+def _shapes(count, scale, tau):
+    shapes = []
+    for i in range(count):
+        w = W.batch_shape(i, tau=tau, scale=scale)
+        x = w.make_queries()
+        if x.shape[0] > 40000:
+            x = x[np.random.default_rng(i).choice(x.shape[0], 40000, replace=False)]
+        shapes.append((w, x))
+    return shapes
+
+
+def test_batch_matches_single_shape_and_oracle(G, orc):
+    tau = 1
+    shapes = _shapes(10, 0.12, tau)
+    ctx = G.Context(tau=tau)
+    outs = ctx.batch_build([{"p": torch.from_numpy(w.p).cuda(), "s": torch.from_numpy(w.s).cuda(),
+                             "x": torch.from_numpy(x).cuda()} for w, x in shapes])
+    ctx.batch_query()
+    torch.cuda.synchronize()
+    for k, (w, x) in enumerate(shapes):
+        single = G.Context(tau=tau)
+        single.build(torch.from_numpy(w.p).cuda(), torch.from_numpy(w.s).cuda())
+        ref = single.query(torch.from_numpy(x).cuda())
+        for key in ("flags", "argmin"):
+            assert torch.equal(outs[k][key], ref[key]), (k, key)
+        assert torch.equal(outs[k]["s64"].view(torch.int64), ref["s64"].view(torch.int64)), k
+        assert torch.equal(ctx.batch_survivors(k), single.survivors()), k
+        single.close()
+        if w.n <= 3000:
+            U = orc.icosphere(tau)
+            keep = orc.keep_all(w.p, w.s, U)
+            surv = orc.collect(w.p, w.s, U, keep)
+            sel = np.arange(0, x.shape[0], max(1, x.shape[0] // 500))
+            val, arg, fl, _ = orc.query(w.p, w.s, surv, x[sel])
+            assert np.array_equal(outs[k]["argmin"].cpu().numpy()[sel], arg)
+            assert np.array_equal(outs[k]["flags"].cpu().numpy()[sel].astype(np.int32) & 0xFFFF, fl)
+            assert np.array_equal(ctx.batch_survivors(k).cpu().numpy(), surv[0])
+    ctx.close()
+
+
+def test_batch_query_cuda_graph_replay(G):
+    tau = 2
+    shapes = _shapes(6, 0.1, tau)
+    ctx = G.Context(tau=tau)
+    outs = ctx.batch_build([{"p": torch.from_numpy(w.p).cuda(), "s": torch.from_numpy(w.s).cuda(),
+                             "x": torch.from_numpy(x).cuda()} for w, x in shapes])
+    ctx.batch_query()
+    torch.cuda.synchronize()
+    first = [{k: o[k].clone() for k in ("s64", "argmin", "flags")} for o in outs]
+    for o in outs:
+        o["s64"].fill_(7.0)
+        o["argmin"].fill_(-7)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            ctx.batch_query()
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    for o, f in zip(outs, first):
+        assert torch.equal(o["argmin"], f["argmin"])
+        assert torch.equal(o["flags"], f["flags"])
+        assert torch.equal(o["s64"].view(torch.int64), f["s64"].view(torch.int64))
+    ctx.close()
