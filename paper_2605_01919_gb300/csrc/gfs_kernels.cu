@@ -469,7 +469,7 @@ __device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, i
     base = grp.shfl(base, 0) + grp.thread_rank();
     if (base < a.cap) {
       a.surv[c][base] = item;
-      if (a.surv_shape) a.surv_shape[c][base] = uint16_t(a.shape);
+      if (a.surv_shape[c]) a.surv_shape[c][base] = uint16_t(a.shape);
     }
   }
 }
