@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", default="gfs", choices=["gfs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the sub-benchmarks of the backward, insertion and batched paths")
     ap.add_argument("--query-subsample", type=int, default=1,
                     help="use every k-th query point (small cases for profiler captures)")
     return ap.parse_args()
@@ -202,6 +204,124 @@ def recorded_traffic(kernel: str):
     return None
 
 
+
+# ----------------------------------------------------------------------------
+# sub-benchmarks of the other rows of the hot path (rank 0, one GPU)
+# ----------------------------------------------------------------------------
+def _ev_time(fn, reps=3):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def extra_backward():
+    """128^3 torus grid, tau 3, 2^22 uniform FP32 points: forward, and
+    forward + hand-written backward (d/dx, d/dp_i, d/ds_i)."""
+    import torch
+    from paper_2605_01919_gb300 import gfs
+    from paper_2605_01919_gb300 import workloads as W
+    w = W.torus_grid()
+    x = torch.from_numpy(w.make_queries()).cuda()
+    p, s = torch.from_numpy(w.p).cuda(), torch.from_numpy(w.s).cuda()
+    ctx = gfs.Context(tau=w.tau)
+    t_build = _ev_time(lambda: ctx.build(p, s), reps=2)
+    out = ctx.query(x, want_f64=False)
+    g = torch.ones(x.shape[0], device="cuda")
+    t_fwd = _ev_time(lambda: ctx.query(x, want_f64=False))
+    t_bwd = _ev_time(lambda: ctx.backward(x, out["s"], out["argmin"], out["flags"], g))
+    m = x.shape[0]
+    ctx.close()
+    return {"workload": "torus128_tau3_2^22_fp32_points", "build_ms": t_build, "forward_ms": t_fwd,
+            "backward_ms": t_bwd, "forward_queries_per_s": m / (t_fwd / 1e3),
+            "forward_backward_queries_per_s": m / ((t_fwd + t_bwd) / 1e3),
+            "queries_per_s_incl_build": m / ((t_build + t_fwd) / 1e3)}
+
+
+def extra_insert(T=2048):
+    """128^3 CSG pseudo-SDF with 5% noisy samples, tau 3: samples left with no
+    surviving candidate are removed and the first T re-inserted in index
+    order with the greedy sequential loop."""
+    import torch
+    from paper_2605_01919_gb300 import gfs
+    from paper_2605_01919_gb300 import workloads as W
+    w = W.csg_pseudo_grid()
+    p, s = torch.from_numpy(w.p).cuda(), torch.from_numpy(w.s).cuda()
+    ctx = gfs.Context(tau=w.tau)
+    ctx.build(p, s)
+    sph = torch.unique(ctx.survivors() // (ctx.K + 1))
+    covered = torch.ones(w.n, dtype=torch.bool, device="cuda")
+    covered[sph] = False
+    keep = ~covered
+    ctx.close()
+    ctx2 = gfs.Context(tau=w.tau)
+    t_build = _ev_time(lambda: ctx2.build(p[keep].contiguous(), s[keep].contiguous()), reps=1)
+    y = p[covered][:T].contiguous()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = ctx2.insert(y)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    fl = out["flags"].cpu().numpy().astype(np.int32) & 0xFFFF
+    ctx2.close()
+    return {"workload": "csg128_tau3_repair", "samples_fully_covered": int(covered.sum()),
+            "inserted": int(y.shape[0]), "build_ms": t_build, "insert_s": dt,
+            "insertions_per_s": y.shape[0] / dt,
+            "codes": np.bincount(fl & 15, minlength=6).tolist(),
+            "lost_witness_steps": int(np.sum((fl & 0x80) != 0))}
+
+
+def extra_batch(count=64, scale=0.5):
+    """Shapes of the 256-shape batch (unions of 1-8 primitives; even index =
+    grid with 2x upsampled queries, odd = scattered samples with 8n uniform
+    queries), sizes scaled by `scale`: one batched build + persistent query
+    launch vs. the same shapes one by one; batched query replayed from a
+    captured CUDA graph."""
+    import torch
+    from paper_2605_01919_gb300 import gfs
+    from paper_2605_01919_gb300 import workloads as W
+    shapes = []
+    for i in range(count):
+        w = W.batch_shape(i, scale=scale)
+        shapes.append({"p": torch.from_numpy(w.p).cuda(), "s": torch.from_numpy(w.s).cuda(),
+                       "x": torch.from_numpy(w.make_queries()).cuda()})
+    M = sum(int(sh["x"].shape[0]) for sh in shapes)
+    Nn = sum(int(sh["p"].shape[0]) for sh in shapes)
+    ctx = gfs.Context(tau=3)
+    ctx.batch_build(shapes)            # first build also autotunes the persistent grids
+    t_build = _ev_time(lambda: ctx.batch_build(shapes), reps=1)
+    t_query = _ev_time(lambda: ctx.batch_query())
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            ctx.batch_query()
+    torch.cuda.synchronize()
+    t_graph = _ev_time(lambda: g.replay())
+    single = gfs.Context(tau=3)
+
+    def one_by_one():
+        for sh in shapes:
+            single.build(sh["p"], sh["s"])
+            single.query(sh["x"], want_f64=False)
+    t_single = _ev_time(one_by_one, reps=1)
+    ctx.close()
+    single.close()
+    return {"workload": f"batch{count}_scale{scale}_tau3", "shapes": count, "samples": Nn, "queries": M,
+            "batched_build_ms": t_build, "batched_query_ms": t_query, "graph_replay_query_ms": t_graph,
+            "batched_queries_per_s_incl_build": M / ((t_build + t_query) / 1e3),
+            "one_by_one_ms": t_single, "one_by_one_queries_per_s_incl_build": M / (t_single / 1e3)}
+
+
 def run_gfs(args):
     import torch
     import torch.distributed as dist
@@ -324,6 +444,16 @@ def run_gfs(args):
         "gpu_launches": own_launches,
         "gpu_launches_note": f"own kernels in the timed region; plus {sort_calls} radix-sort calls",
     }
+    if rank == 0 and world == 1 and not args.no_extras:
+        del p, s, x, s_out, arg_out, fl_out, flush
+        torch.cuda.empty_cache()
+        line["extras"] = {}
+        for name, fn in (("backward", extra_backward), ("insert", extra_insert), ("batch", extra_batch)):
+            try:
+                line["extras"][name] = fn()
+            except Exception as e:  # a failing sub-benchmark must not hide the headline line
+                line["extras"][name] = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(w, xh, steps=2, n_keep=400, n_query=6)
     ctx.close()
