@@ -149,6 +149,29 @@ int gfs_query_backward(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, co
 int gfs_insert(gfs_ctx* ctx, const double* y, int64_t T, double* s_out, int64_t* argmin_out,
                uint16_t* flags_out);
 
+/* Same computation and outputs as gfs_query_backward, for callers that must
+ * not allocate device memory: code running while a CUDA graph is captured
+ * (allocation is not allowed during capture), and runtimes that reserve all
+ * device memory at start-up and forbid later allocation.  gfs_query_backward
+ * grows a context-owned accumulator buffer on demand; this variant instead
+ * uses one library-wide array in static device memory of
+ * 4 * GFS_NOALLOC_MAX_SPHERES 64-bit words (8 MiB), which every GPU that
+ * loads the library holds until the process exits.  The paper has no
+ * counterpart of this call.
+ *  - Limit: the context's sphere count n must be <= GFS_NOALLOC_MAX_SPHERES,
+ *    else GFS_ERR_TOO_LARGE (nothing is launched).
+ *  - The array is shared by every call on a device and keeps the last call's
+ *    contents; each call clears the part it uses first.  Calls whose work
+ *    overlaps on the GPU (different streams, or different contexts on the
+ *    same device) race on it and must be ordered by the caller.
+ *  - The first call on a device looks up the array's device address (no
+ *    allocation); make that first call before any stream capture.
+ * Arguments and other errors: as gfs_query_backward. */
+#define GFS_NOALLOC_MAX_SPHERES 262144
+int gfs_query_backward_noalloc(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, const float* s,
+                               const int64_t* argmin, const uint16_t* flags, const float* grad_s, float* grad_x,
+                               float* grad_p, float* grad_sv);
+
 /* Copy the surviving candidate ids, ascending, into g_out (device, capacity
  * cap); *count_host receives the number of survivors (host pointer).
  * Errors: GFS_ERR_STATE, GFS_ERR_ARG (cap too small: *count_host still set). */

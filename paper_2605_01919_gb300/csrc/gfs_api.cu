@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstddef>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "gfs.h"
@@ -1171,4 +1172,69 @@ void gfs_destroy(gfs_ctx* c) {
   delete c;
 }
 
+// ---------------------------------------------------------------------------
+// backward without device allocation
+// ---------------------------------------------------------------------------
+// Callers inside CUDA graph capture, or runtimes that forbid allocation after
+// start-up, cannot let the library grow buffers.  This entry point keeps the
+// backward pass's per-sample fixed-point accumulators in one static device
+// array instead (held by every GPU that loads the library until exit).
 }  // extern "C"
+
+namespace {
+
+__device__ __align__(256) long long g_noalloc_acc[4 * GFS_NOALLOC_MAX_SPHERES];
+
+constexpr int kMaxDevices = 64;
+long long* g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+// device address of the static array on the current device (looked up once
+// per device; the host-side symbol is only a stand-in, never a device pointer)
+int noalloc_scratch(long long** out) {
+  int dev = 0;
+  GFS_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return GFS_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    GFS_CK(cudaGetSymbolAddress(&p, g_noalloc_acc));
+    g_noalloc_ptr[dev] = static_cast<long long*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return GFS_OK;
+}
+
+}  // namespace
+
+extern "C" int gfs_query_backward_noalloc(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, const float* s,
+                                          const int64_t* argmin, const uint16_t* flags, const float* grad_s,
+                                          float* grad_x, float* grad_p, float* grad_sv) {
+  if (!c || m < 0 || (m > 0 && (!x || !s || !argmin || !flags || !grad_s))) return GFS_ERR_ARG;
+  if (!c->built) return GFS_ERR_STATE;
+  const int64_t n = c->n;
+  if (n > GFS_NOALLOC_MAX_SPHERES) return GFS_ERR_TOO_LARGE;
+  long long* acc = nullptr;
+  GFS_TRY(noalloc_scratch(&acc));
+  // the array keeps the previous call's sums: clear the part used here
+  GFS_CK(cudaMemsetAsync(acc, 0, size_t(4 * n) * sizeof(long long), c->stream));
+  GradArgs a;
+  std::memset(&a, 0, sizeof(a));
+  if (x_is_fp32) a.x32 = static_cast<const float*>(x);
+  else a.x64 = static_cast<const double*>(x);
+  a.m = m;
+  a.s = s;
+  a.arg = argmin;
+  a.flags = flags;
+  a.grad_s = grad_s;
+  a.grad_x = grad_x;
+  a.sph64 = c->sph64.as<D4>();
+  a.U64 = c->U64.as<double>();
+  a.witness64 = c->witness64.as<double>();
+  a.K = c->K;
+  a.KS = c->KS;
+  a.acc_p = acc;
+  a.acc_s = acc + 3 * n;
+  GFS_CK(launch_grad(a, n, grad_p, grad_sv, c->stream));
+  return GFS_OK;
+}
