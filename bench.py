@@ -247,36 +247,40 @@ def extra_backward():
 
 
 def extra_insert(T=2048):
-    """128^3 CSG pseudo-SDF with 5% noisy samples, tau 3: samples left with no
-    surviving candidate are removed and the first T re-inserted in index
-    order with the greedy sequential loop."""
+    """Greedy sequential refinement on the 128^3 CSG pseudo-SDF (tau 3): new
+    points at the centres of the cells whose eight corner samples do not all
+    exceed half the cell diagonal (the cells that may contain the surface),
+    inserted in index order, each against the inputs and every earlier
+    insertion."""
     import torch
     from paper_2605_01919_gb300 import gfs
     from paper_2605_01919_gb300 import workloads as W
     w = W.csg_pseudo_grid()
+    N = round(w.n ** (1 / 3))
+    S = w.s.reshape(N, N, N)
+    near = np.abs(S) < 0.5 * np.sqrt(3) * w.h
+    cell = near[:-1, :-1, :-1] | near[1:, :-1, :-1] | near[:-1, 1:, :-1] | near[:-1, :-1, 1:] | \
+        near[1:, 1:, :-1] | near[1:, :-1, 1:] | near[:-1, 1:, 1:] | near[1:, 1:, 1:]
+    g = np.linspace(-1, 1, N)
+    c = 0.5 * (g[:-1] + g[1:])
+    ix, iy, iz = np.nonzero(cell)
+    y = np.stack([c[ix], c[iy], c[iz]], axis=1)[:T]
     p, s = torch.from_numpy(w.p).cuda(), torch.from_numpy(w.s).cuda()
     ctx = gfs.Context(tau=w.tau)
-    ctx.build(p, s)
-    sph = torch.unique(ctx.survivors() // (ctx.K + 1))
-    covered = torch.ones(w.n, dtype=torch.bool, device="cuda")
-    covered[sph] = False
-    keep = ~covered
-    ctx.close()
-    ctx2 = gfs.Context(tau=w.tau)
-    t_build = _ev_time(lambda: ctx2.build(p[keep].contiguous(), s[keep].contiguous()), reps=1)
-    y = p[covered][:T].contiguous()
+    t_build = _ev_time(lambda: ctx.build(p, s), reps=1)
+    yt = torch.from_numpy(np.ascontiguousarray(y)).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    out = ctx2.insert(y)
+    out = ctx.insert(yt)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     fl = out["flags"].cpu().numpy().astype(np.int32) & 0xFFFF
-    ctx2.close()
-    return {"workload": "csg128_tau3_repair", "samples_fully_covered": int(covered.sum()),
+    ctx.close()
+    return {"workload": "csg128_tau3_refine_surface_cells", "candidate_cells": int(cell.sum()),
             "inserted": int(y.shape[0]), "build_ms": t_build, "insert_s": dt,
-            "insertions_per_s": y.shape[0] / dt,
-            "codes": np.bincount(fl & 15, minlength=6).tolist(),
-            "lost_witness_steps": int(np.sum((fl & 0x80) != 0))}
+            "insertions_per_s": y.shape[0] / dt, "codes": np.bincount(fl & 15, minlength=6).tolist(),
+            "lost_witness_steps": int(np.sum((fl & 0x80) != 0)),
+            "far_violations": int(np.sum((fl & 0x20) != 0))}
 
 
 def extra_batch(count=64, scale=0.5):

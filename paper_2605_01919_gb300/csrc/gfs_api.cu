@@ -494,6 +494,7 @@ struct InsMisc {
   StepRec rec;
   unsigned lost;
   unsigned err;
+  unsigned done;
 };
 
 // Rebuild the hierarchies from the current state: live survivors compacted
@@ -614,6 +615,7 @@ int gfs_insert(gfs_ctx* c, const double* y, int64_t T, double* s_out, int64_t* a
     a.rec = &dm->rec;
     a.lost = &dm->lost;
     a.err = &dm->err;
+    a.done = &dm->done;
     GFS_CK(launch_ins_step(a, t, st));
     ++since;
   }

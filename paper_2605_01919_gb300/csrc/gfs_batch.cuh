@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(128) k_batch_query(const QueryArgs* __restrict
     if (int64_t(w) >= limit) break;
     const int s = find_seg(wprefix, ns, int64_t(w));
     const int64_t wl = int64_t(w) - wprefix[s];
-    query_packet(views[s], wl * 32 + lane, W, lane);
+    query_packet<true>(views[s], wl * 32 + lane, W, lane);
   }
 }
 

@@ -122,6 +122,35 @@ __device__ void warp_walk(const Tree& T, uint32_t* stk, int lane, unsigned* err,
   }
 }
 
+// Greedy descent to the leaf whose box is nearest to (x, y, z) (uniform
+// across the warp); used to seed the pruning thresholds of a walk.
+__device__ int64_t nearest_leaf(const Tree& T, double x, double y, double z) {
+  int lev = T.nlevels - 1;
+  int64_t best = 0;
+  double bd = INFINITY;
+  for (int64_t j = 0; j < T.count[lev]; ++j) {
+    const double d = box_d2_64(x, y, z, T.lo[T.offset[lev] + j], T.hi[T.offset[lev] + j]);
+    if (d < bd) {
+      bd = d;
+      best = j;
+    }
+  }
+  while (lev > 0) {
+    const int64_t cb = best * kFan, ce = min(cb + kFan, T.count[lev - 1]);
+    const int64_t off = T.offset[lev - 1];
+    bd = INFINITY;
+    for (int64_t c = cb; c < ce; ++c) {
+      const double d = box_d2_64(x, y, z, T.lo[off + c], T.hi[off + c]);
+      if (d < bd) {
+        bd = d;
+        best = c;
+      }
+    }
+    --lev;
+  }
+  return best;
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(32) k_ins_query(InsertArgs a, int64_t t) {
@@ -159,6 +188,12 @@ __global__ void __launch_bounds__(32) k_ins_query(InsertArgs a, int64_t t) {
     const double f = __dadd_rn(dl, r);
     if (f < bestF) bestF = f;
   };
+  // seed the thresholds with the spheres of the nearest leaf
+  if (a.st.nlevels > 0) {
+    const int64_t nl = nearest_leaf(a.st, x, y, z);
+    const int64_t j = nl * kLeaf + lane;
+    if (lane < kLeaf && j < a.st.nitems) sphere_item(a.sid[j]);
+  }
   warp_walk(
       a.st, stk, lane, a.err,
       [&]() {
@@ -238,6 +273,12 @@ __global__ void __launch_bounds__(32) k_ins_query(InsertArgs a, int64_t t) {
     const Tree& T = a.vt[cs];
     const float4* items = a.surv[cs];
     const uint32_t* tomb = a.tomb[cs];
+    // seed with the live survivors of the nearest leaf
+    if (T.nlevels > 0) {
+      const int64_t nl = nearest_leaf(T, x, y, z);
+      const int64_t j = nl * kLeaf + lane;
+      if (lane < kLeaf && j < T.nitems && !tombed(tomb, j)) surv_item(items[j]);
+    }
     warp_walk(
         T, stk, lane, a.err, [&]() { thd = warp_min_d(bd); },
         [&](int64_t node) {
@@ -307,124 +348,181 @@ __global__ void __launch_bounds__(32) k_ins_query(InsertArgs a, int64_t t) {
 }
 
 // Cull the new sphere's candidates and witness; tombstone covered survivors.
-__global__ void __launch_bounds__(128) k_ins_update(InsertArgs a, int64_t t) {
-  if (!a.rec->insert) return;
-  const int jn = *a.n_total - 1;
-  const D4 nw = a.sph64[jn];
-  const double rn = fabs(nw.w);
-  const double tol = a.tol;
-  const int KS = a.KS;
-  const int64_t nl0 = a.vt[0].nlevels ? a.vt[0].count[0] : 0;
-  const int64_t nl1 = a.vt[1].nlevels ? a.vt[1].count[0] : 0;
-  const unsigned dc0 = a.dcount_start[0], dc1 = a.dcount_start[1];
-  const int64_t total = int64_t(KS) + nl0 + nl1 + dc0 + dc1;
-  const float x32 = float(nw.x), y32 = float(nw.y), z32 = float(nw.z);
-  const float reach = float(rn) + 1e-4f;
-  for (int64_t w = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; w < total; w += int64_t(gridDim.x) * blockDim.x) {
-    if (w < KS) {
-      // candidate k of the new sphere (k = K: its witness)
-      const int k = int(w);
-      double qx, qy, qz;
-      if (k < a.K) {
-        ex_cand(nw, a.U64[3 * k], a.U64[3 * k + 1], a.U64[3 * k + 2], qx, qy, qz);
+// Blocks [0, nc) hold one warp per candidate (k = 0..K, k = K the witness):
+// a warp-parallel exact walk of the sphere hierarchy that stops at the first
+// covering ball.  The last block walks both survivor hierarchies with the new
+// ball (warps 0, 1) and scans the lists added since the rebuild (warps 2, 3).
+// The block that finishes last sets LOST_WITNESS and opens the next step.
+constexpr int kUStack = 2048;
+
+template <class Refresh, class NeedChild, class Leaf>
+__device__ void warp_walk_until(const Tree& T, uint32_t* stk, int cap, int lane, unsigned* err, Refresh refresh,
+                                NeedChild need_child, Leaf leaf) {
+  if (T.nlevels == 0) return;
+  const int top = T.nlevels - 1;
+  int sp = int(T.count[top]);
+  if (lane < sp) stk[lane] = pack_node(top, lane);
+  __syncwarp();
+  while (sp > 0) {
+    if (!refresh()) return;
+    const int take = min(sp, 32);
+    const uint32_t nd = lane < take ? stk[sp - 1 - lane] : 0xffffffffu;
+    sp -= take;
+    __syncwarp();
+    unsigned mask = 0;
+    int64_t cb = 0;
+    int lev = -1;
+    if (nd != 0xffffffffu) {
+      lev = node_level(nd);
+      const int64_t idx = node_index(nd);
+      if (lev == 0) {
+        leaf(idx);
       } else {
-        qx = a.witness64[3 * int64_t(jn)];
-        qy = a.witness64[3 * int64_t(jn) + 1];
-        qz = a.witness64[3 * int64_t(jn) + 2];
+        cb = idx * kFan;
+        const int64_t ce = min(cb + kFan, T.count[lev - 1]);
+        const int64_t off = T.offset[lev - 1];
+        for (int64_t c = cb; c < ce; ++c)
+          if (need_child(off + c)) mask |= 1u << unsigned(c - cb);
       }
-      if (a.box_cull && !ex_inbox(qx, qy, qz)) continue;
-      bool covered = false;
-      // spheres in the hierarchy (per-thread walk, exact FP64 tests)
-      {
-        const Tree& T = a.st;
-        uint32_t stack[kStack];
-        int sp = 0;
-        const int top = T.nlevels - 1;
-        for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
-        while (sp > 0 && !covered) {
-          const uint32_t nd = stack[--sp];
-          const int lev = node_level(nd);
-          const int64_t idx = node_index(nd);
-          if (lev == 0) {
-            const int64_t b = idx * kLeaf, e = min(b + kLeaf, T.nitems);
-            for (int64_t j = b; j < e && !covered; ++j) {
-              const int o = a.sid[j];
-              if (o != jn && ex_cov(qx, qy, qz, a.sph64[o], tol)) covered = true;
-            }
-          } else {
-            const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
-            const int64_t off = T.offset[lev - 1];
-            for (int64_t c = cb; c < ce; ++c) {
-              const float4 Bs[2] = {T.bp[off + c], T.bn[off + c]};
-              bool need = false;
-              for (int cl = 0; cl < 2 && !need; ++cl) {
-                const double rr = (double(Bs[cl].w) - tol) * (1.0 + 1e-12) + 1e-12;
-                need = rr > 0.0 && ball_d2_64(qx, qy, qz, Bs[cl]) < rr * rr;
+    }
+    const int cnt = __popc(mask);
+    int pre = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(kAll, pre, o);
+      if (lane >= o) pre += v;
+    }
+    const int total = __shfl_sync(kAll, pre, 31);
+    pre -= cnt;
+    if (sp + total > cap) {
+      if (lane == 0) atomicOr(err, 1u);
+      return;
+    }
+    int w = sp + pre;
+    for (int c = 0; c < kFan; ++c)
+      if ((mask >> c) & 1u) stk[w++] = pack_node(lev - 1, cb + c);
+    sp += total;
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(128) k_ins_update(InsertArgs a, int64_t t) {
+  __shared__ uint32_t s_stk[4][kUStack];
+  __shared__ bool s_last;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint32_t* stk = s_stk[wib];
+  const bool active = a.rec->insert != 0;
+  const int jn = *a.n_total - 1;
+  const int KS = a.KS;
+  const int ncand_blocks = (KS + 3) / 4;
+  if (active) {
+    const D4 nw = a.sph64[jn];
+    const double tol = a.tol;
+    if (int(blockIdx.x) < ncand_blocks) {
+      const int k = int(blockIdx.x) * 4 + wib;
+      if (k < KS) {
+        double qx, qy, qz;
+        if (k < a.K) {
+          ex_cand(nw, a.U64[3 * k], a.U64[3 * k + 1], a.U64[3 * k + 2], qx, qy, qz);
+        } else {
+          qx = a.witness64[3 * int64_t(jn)];
+          qy = a.witness64[3 * int64_t(jn) + 1];
+          qz = a.witness64[3 * int64_t(jn) + 2];
+        }
+        if (!a.box_cull || ex_inbox(qx, qy, qz)) {
+          bool covered = false;
+          for (int o = a.n_static + lane; o < jn && !covered; o += 32)
+            if (ex_cov(qx, qy, qz, a.sph64[o], tol)) covered = true;
+          warp_walk_until(
+              a.st, stk, kUStack, lane, a.err, [&]() { return !__any_sync(kAll, covered); },
+              [&](int64_t node) {
+                const float4 Bs[2] = {a.st.bp[node], a.st.bn[node]};
+                for (int cl = 0; cl < 2; ++cl) {
+                  const double rr = (double(Bs[cl].w) - tol) * (1.0 + 1e-12) + 1e-12;
+                  if (rr > 0.0 && ball_d2_64(qx, qy, qz, Bs[cl]) < rr * rr) return true;
+                }
+                return false;
+              },
+              [&](int64_t leaf) {
+                const int64_t b = leaf * kLeaf, e = min(b + kLeaf, a.st.nitems);
+                for (int64_t j = b; j < e && !covered; ++j)
+                  if (ex_cov(qx, qy, qz, a.sph64[a.sid[j]], tol)) covered = true;
+              });
+          covered = __any_sync(kAll, covered);
+          if (!covered && lane == 0) {
+            const uint32_t g = uint32_t(jn) * uint32_t(KS) + uint32_t(k);
+            const float4 item = make_float4(float(qx), float(qy), float(qz), __uint_as_float(g));
+            for (int c = 0; c < 2; ++c) {
+              const bool mine = c == 0 ? !(nw.w < 0.0) : !(nw.w > 0.0);
+              if (!mine) continue;
+              const unsigned slot = atomicAdd(a.dcount + c, 1u);
+              if (slot < a.dcap) {
+                a.dsurv[c][slot] = item;
+                a.dtomb[c][slot] = 0;
+              } else {
+                atomicOr(a.err, 2u);
               }
-              if (need) stack[sp++] = pack_node(lev - 1, c);
             }
+            atomicAdd(a.counts + jn, 1);
           }
         }
       }
-      for (int o = a.n_static; o < jn && !covered; ++o)
-        if (ex_cov(qx, qy, qz, a.sph64[o], tol)) covered = true;
-      if (covered) continue;
-      const uint32_t g = uint32_t(jn) * uint32_t(KS) + uint32_t(k);
-      const float4 item = make_float4(float(qx), float(qy), float(qz), __uint_as_float(g));
-      for (int c = 0; c < 2; ++c) {
-        const bool mine = c == 0 ? !(nw.w < 0.0) : !(nw.w > 0.0);
-        if (!mine) continue;
-        const unsigned slot = atomicAdd(a.dcount + c, 1u);
-        if (slot < a.dcap) {
-          a.dsurv[c][slot] = item;
-          a.dtomb[c][slot] = 0;
-        } else {
-          atomicOr(a.err, 2u);
-        }
-      }
-      atomicAdd(a.counts + jn, 1);
-      continue;
-    }
-    // survivors covered by the new ball
-    int cls;
-    int64_t lo_j, hi_j;
-    bool dyn;
-    int64_t u = w - KS;
-    if (u < nl0) {
-      cls = 0, dyn = false, lo_j = u * kLeaf, hi_j = min(lo_j + kLeaf, a.vt[0].nitems);
-      const float4 L = a.vt[0].lo[u], H = a.vt[0].hi[u];
-      if (box_d2(x32, y32, z32, L, H) > reach * reach) continue;
-    } else if ((u -= nl0) < nl1) {
-      cls = 1, dyn = false, lo_j = u * kLeaf, hi_j = min(lo_j + kLeaf, a.vt[1].nitems);
-      const float4 L = a.vt[1].lo[u], H = a.vt[1].hi[u];
-      if (box_d2(x32, y32, z32, L, H) > reach * reach) continue;
-    } else if ((u -= nl1) < dc0) {
-      cls = 0, dyn = true, lo_j = u, hi_j = u + 1;
     } else {
-      u -= dc0;
-      cls = 1, dyn = true, lo_j = u, hi_j = u + 1;
-    }
-    for (int64_t j = lo_j; j < hi_j; ++j) {
-      const float4 P = dyn ? a.dsurv[cls][j] : a.surv[cls][j];
-      const float dx = P.x - x32, dy = P.y - y32, dz = P.z - z32;
-      if (dx * dx + dy * dy + dz * dz > reach * reach) continue;
-      const uint32_t g = __float_as_uint(P.w);
-      double qx, qy, qz;
-      surv64(a, g, qx, qy, qz);
-      if (!ex_cov(qx, qy, qz, nw, tol)) continue;
-      bool fresh;
-      if (dyn) {
-        fresh = atomicExch(a.dtomb[cls] + j, 1u) == 0u;
+      // survivors the new ball covers
+      const double rn = fabs(nw.w);
+      const double reach = rn + 2.0 * 1.7320508075688772 * double(a.bc->eq) + 1e-9;
+      auto kill = [&](int cls, const float4& P, bool dyn, int64_t j) {
+        const uint32_t g = __float_as_uint(P.w);
+        double qx, qy, qz;
+        surv64(a, g, qx, qy, qz);
+        if (!ex_cov(qx, qy, qz, nw, tol)) return;
+        bool fresh;
+        if (dyn) {
+          fresh = atomicExch(a.dtomb[cls] + j, 1u) == 0u;
+        } else {
+          const uint32_t bit = 1u << unsigned(j & 31);
+          fresh = !(atomicOr(a.tomb[cls] + (j >> 5), bit) & bit);
+        }
+        if (!fresh) return;
+        // count each survivor once (a zero sample's survivors are in both lists)
+        const int sph = int(g / uint32_t(KS));
+        if (cls == 1 && a.sph64[sph].w == 0.0) return;
+        if (atomicSub(a.counts + sph, 1) == 1) atomicOr(a.lost, 1u);
+      };
+      if (wib < 2) {
+        const int cls = wib;
+        const Tree& T = a.vt[cls];
+        warp_walk_until(
+            T, stk, kUStack, lane, a.err, [&]() { return true; },
+            [&](int64_t node) {
+              const double rr = reach * (1.0 + 1e-12);
+              return box_d2_64(nw.x, nw.y, nw.z, T.lo[node], T.hi[node]) < rr * rr;
+            },
+            [&](int64_t leaf) {
+              const int64_t b = leaf * kLeaf, e = min(b + kLeaf, T.nitems);
+              for (int64_t j = b; j < e; ++j) kill(cls, a.surv[cls][j], false, j);
+            });
       } else {
-        const uint32_t bit = 1u << unsigned(j & 31);
-        fresh = !(atomicOr(a.tomb[cls] + (j >> 5), bit) & bit);
+        const int cls = wib - 2;
+        const unsigned nd = a.dcount_start[cls];
+        for (unsigned j = lane; j < nd; j += 32) kill(cls, a.dsurv[cls][j], true, j);
       }
-      if (!fresh) continue;
-      // count each survivor once (a zero sample's survivors are in both lists)
-      const int sph = int(g / uint32_t(KS));
-      if (cls == 1 && a.sph64[sph].w == 0.0) continue;
-      if (atomicSub(a.counts + sph, 1) == 1) atomicOr(a.lost, 1u);
     }
+  }
+  // the last block to finish closes the step
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(a.done, 1u);
+    s_last = done == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    if (active && *a.lost && a.fl_out) a.fl_out[t] = uint16_t(a.fl_out[t] | GFS_FLAG_LOST_WITNESS);
+    *a.lost = 0;
+    a.dcount_start[0] = a.dcount[0];
+    a.dcount_start[1] = a.dcount[1];
+    *a.done = 0;
   }
 }
 
@@ -459,18 +557,9 @@ __global__ void k_ins_compact(const float4* __restrict__ ssurv, const uint32_t* 
   if (live) out[atomicAdd(count, 1u)] = v;
 }
 
-// the LOST_WITNESS bit of step t
-__global__ void k_ins_flag(InsertArgs a, int64_t t) {
-  if (*a.lost && a.fl_out) a.fl_out[t] = uint16_t(a.fl_out[t] | GFS_FLAG_LOST_WITNESS);
-  *a.lost = 0;
-  a.dcount_start[0] = a.dcount[0];
-  a.dcount_start[1] = a.dcount[1];
-}
-
 cudaError_t launch_ins_step(const InsertArgs& a, int64_t t, cudaStream_t st) {
   k_ins_query<<<1, 32, 0, st>>>(a, t);
-  k_ins_update<<<64, 128, 0, st>>>(a, t);
-  k_ins_flag<<<1, 1, 0, st>>>(a, t);
+  k_ins_update<<<(a.KS + 3) / 4 + 1, 128, 0, st>>>(a, t);
   return cudaGetLastError();
 }
 

@@ -651,6 +651,9 @@ __device__ void query_exact_one(const QueryArgs& a, int64_t q);
 
 // One lane's query inside a warp-cooperative pass; `slot` indexes the
 // processing order (a.perm), all 32 lanes of the warp must call together.
+// Points outside the coordinate range of the FP32 error model go to the
+// FP64 kernel through a.defer, or (kInlineExact) are evaluated in place.
+template <bool kInlineExact>
 __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int lane) {
   const bool active = slot < a.m;
   const int64_t q = active ? int64_t(a.perm ? a.perm[slot] : uint32_t(slot)) : 0;
@@ -970,18 +973,18 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
   } else if (defer) {
     // outside the coordinate range the error bounds assume: FP64 path
     const unsigned int s2 = atomicAdd(&a.cnt->ndefer, 1u);
-    if (a.defer) {
-      if (s2 < a.defer_cap) a.defer[s2] = uint32_t(q);
-    } else {
+    if constexpr (kInlineExact) {
       query_exact_one(a, q);
+    } else {
+      if (s2 < a.defer_cap) a.defer[s2] = uint32_t(q);
     }
   }
 }
 
-__global__ void __launch_bounds__(128) k_query_fast(QueryArgs a) {
+__global__ void __launch_bounds__(128, 6) k_query_fast(QueryArgs a) {
   __shared__ uint32_t s_stack[4][kPStack];
   WarpStack W{s_stack[threadIdx.x >> 5], 0};
-  query_packet(a, blockIdx.x * int64_t(blockDim.x) + threadIdx.x, W, threadIdx.x & 31);
+  query_packet<false>(a, blockIdx.x * int64_t(blockDim.x) + threadIdx.x, W, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------

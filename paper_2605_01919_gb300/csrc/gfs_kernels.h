@@ -103,7 +103,8 @@ struct InsertArgs {
   uint16_t* fl_out;
   struct StepRec* rec;
   unsigned* lost;
-  unsigned* err;  // bit 0: walk stack overflow, bit 1: dynamic list overflow
+  unsigned* err;   // bit 0: walk stack overflow, bit 1: dynamic list overflow
+  unsigned* done;  // blocks of the update kernel that have finished (reset by the last)
 };
 
 struct StepRec {
