@@ -52,9 +52,26 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sub-benchmarks of the backward, insertion and batched paths")
+    ap.add_argument("--only", choices=["backward", "insert", "batch"], default=None,
+                    help="run one sub-benchmark alone and print its JSON (profiling)")
+    ap.add_argument("--insert-steps", type=int, default=2048)
     ap.add_argument("--query-subsample", type=int, default=1,
                     help="use every k-th query point (small cases for profiler captures)")
     return ap.parse_args()
+
+
+def aggregate(total_ms: float, units_per_rank: int, steps: int, world: int, device=None):
+    """Whole-job throughput of `world` replicas: every rank processed
+    units_per_rank units per step; the job time is the slowest rank's.
+    Returns (value, ms_per_step).  Uses torch.distributed when world > 1."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / steps
+    return world * units_per_rank / (ms_per_step / 1e3), ms_per_step
 
 
 def dist_env():
@@ -382,13 +399,7 @@ def run_gfs(args):
     # own kernels, plus the radix-sort calls (each runs a handful of sort kernels)
     own_launches = launches1["kernel_launches"] - launches0["kernel_launches"]
     sort_calls = launches1["sort_calls"] - launches0["sort_calls"]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * m / (ms_per_step / 1e3)
+    value, ms_per_step = aggregate(float(sum(step_ms)), m, args.steps, world, device=dev)
 
     # ---- end to end through the host-buffer entry point ----------------------
     e2e = None
@@ -452,7 +463,8 @@ def run_gfs(args):
         del p, s, x, s_out, arg_out, fl_out, flush
         torch.cuda.empty_cache()
         line["extras"] = {}
-        for name, fn in (("backward", extra_backward), ("insert", extra_insert), ("batch", extra_batch)):
+        for name, fn in (("backward", extra_backward), ("insert", lambda: extra_insert(args.insert_steps)),
+                         ("batch", extra_batch)):
             try:
                 line["extras"][name] = fn()
             except Exception as e:  # a failing sub-benchmark must not hide the headline line
@@ -469,7 +481,11 @@ def run_gfs(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.only:
+        fn = {"backward": extra_backward, "insert": lambda: extra_insert(a.insert_steps),
+              "batch": extra_batch}[a.only]
+        print(json.dumps({a.only: fn()}), flush=True)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_gfs(a)

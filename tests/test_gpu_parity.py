@@ -203,3 +203,57 @@ def test_union_grid_full_size_fp32_equals_fp64_path(G, orc):
         fp32_ok = np.array_equal(a["argmin"].numpy()[sel], arg)
         fp64_ok = np.array_equal(b["argmin"].numpy()[sel], arg)
         pytest.fail(f"{bad.size} queries differ; FP32 path matches oracle: {fp32_ok}, FP64 path: {fp64_ok}")
+
+
+# ---------------------------------------------------------------------------
+# full-size 128^3 workloads: sampled outputs against the lazy oracle
+# ---------------------------------------------------------------------------
+
+def _sampled_check(G, orc, w, x, n_keep=400, n_query=32, x32=False, seed=91):
+    ctx = G.Context(tau=w.tau)
+    ctx.build(torch.from_numpy(w.p).cuda(), torch.from_numpy(w.s).cuda())
+    out = ctx.query(torch.from_numpy(np.ascontiguousarray(x)).cuda())
+    surv = ctx.survivors().cpu().numpy()
+    s64 = out["s64"].cpu().numpy()
+    arg = out["argmin"].cpu().numpy()
+    fl = out["flags"].cpu().numpy().astype(np.int32) & 0xFFFF
+    ctx.close()
+    rng = np.random.default_rng(seed)
+    U = orc.icosphere(w.tau)
+    K = U.shape[0]
+    survset = set(int(g) for g in surv)
+    for i, k in zip(rng.integers(0, w.n, n_keep), rng.integers(0, K, n_keep)):
+        assert orc.keep_one(w.p, w.s, U, int(i), int(k)) == ((int(i) * (K + 1) + int(k)) in survset)
+    for g in rng.choice(surv, min(100, surv.size), replace=False):
+        assert orc.keep_one(w.p, w.s, U, int(g) // (K + 1), int(g) % (K + 1))
+    sel = rng.choice(x.shape[0], n_query, replace=False)
+    xs = x[sel].astype(np.float64)
+    chunks = np.array_split(np.arange(n_query), 16)
+    ctxm = mp.get_context("spawn")
+    with ctxm.Pool(min(16, mp.cpu_count())) as pool:
+        outs = pool.map(_lazy_worker, [(w.p, w.s, w.tau, xs[c]) for c in chunks])
+    val = np.concatenate([o[0] for o in outs])
+    oarg = np.concatenate([o[1] for o in outs])
+    ofl = np.concatenate([o[2] for o in outs])
+    assert np.array_equal(fl[sel], ofl)
+    assert np.array_equal(arg[sel], oarg)
+    assert np.array_equal(s64[sel], val, equal_nan=True)
+    return fl
+
+
+def test_csg_pseudo_grid_full_size_sampled(G, orc):
+    """128^3 CSG pseudo-SDF with 5% noisy samples (balls of both signs may
+    overlap: INVALID points occur)."""
+    w = W.csg_pseudo_grid()
+    rng = np.random.default_rng(12)
+    x = rng.uniform(-1, 1, size=(1 << 20, 3))
+    fl = _sampled_check(G, orc, w, x)
+    assert np.any((fl & 15) <= 1)
+
+
+def test_torus_grid_full_size_sampled(G, orc):
+    """128^3 torus grid, 2^22 uniform FP32 points (the differentiable-query
+    workload)."""
+    w = W.torus_grid()
+    x = w.make_queries()
+    _sampled_check(G, orc, w, x, x32=True)
