@@ -117,6 +117,7 @@ struct gfs_ctx {
   DevBuf sph64, keys_in, keys_out, vals_in, vals_out, sph, thr, sid, bound_bits, consts, cnt, cub_temp;
   Tree st{};
   DevBuf st_lo, st_hi, st_bp, st_bn, st_bf;
+  DevBuf st_tight;  // scratch of the internal-ball tightening
   // survivors
   DevBuf surv_raw[2], surv_sorted[2], vt_lo[2], vt_hi[2];
   Tree vt[2]{};
@@ -186,7 +187,7 @@ int build_point_tree(gfs_ctx* c, int cls) {
   T.lo = c->vt_lo[cls].as<float4>();
   T.hi = c->vt_hi[cls].as<float4>();
   T.bp = T.bn = T.bf = nullptr;
-  GFS_CK(launch_build_tree(c->surv_sorted[cls].as<float4>(), 0, 0.f, T, c->stream));
+  GFS_CK(launch_build_tree(c->surv_sorted[cls].as<float4>(), 0, 0.f, T, nullptr, c->stream));
   return GFS_OK;
 }
 
@@ -252,7 +253,8 @@ int build_sphere_hierarchy(gfs_ctx* c, int64_t n) {
   float Ahost;
   std::memcpy(&Ahost, &bits[0], 4);
   Ahost = std::max(1.0f, Ahost);
-  GFS_CK(launch_build_tree(c->sph.as<float4>(), 1, Ahost, c->st, st));
+  GFS_TRY(ensure(c->st_tight, size_t(std::max<int64_t>(nodes - c->st.count[0], 1)) * 3 * sizeof(unsigned)));
+  GFS_CK(launch_build_tree(c->sph.as<float4>(), 1, Ahost, c->st, c->st_tight.as<unsigned>(), st));
   return GFS_OK;
 }
 
@@ -1158,7 +1160,7 @@ void gfs_destroy(gfs_ctx* c) {
       if (e) cudaEventDestroy(e);
   DevBuf* bufs[] = {&c->U32, &c->U64, &c->sph64, &c->keys_in, &c->keys_out, &c->vals_in, &c->vals_out, &c->sph,
                     &c->thr, &c->sid, &c->bound_bits, &c->consts, &c->cnt, &c->cub_temp, &c->st_lo, &c->st_hi,
-                    &c->st_bp, &c->st_bn, &c->st_bf, &c->surv_raw[0], &c->surv_raw[1], &c->surv_sorted[0], &c->surv_sorted[1],
+                    &c->st_bp, &c->st_bn, &c->st_bf, &c->st_tight, &c->surv_raw[0], &c->surv_raw[1], &c->surv_sorted[0], &c->surv_sorted[1],
                     &c->vt_lo[0], &c->vt_lo[1], &c->vt_hi[0], &c->vt_hi[1], &c->defer, &c->acc, &c->witness64,
                     &c->h_p, &c->h_s, &c->h_x, &c->h_sout, &c->h_arg, &c->h_fl,
                     &c->qk_in, &c->qk_out, &c->qv_in, &c->qv_out, &c->ins_counts,

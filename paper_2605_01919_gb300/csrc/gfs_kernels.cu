@@ -221,7 +221,11 @@ __device__ float4 bound_ball(const float4* it, int k, float A) {
   }
   int j;
   float v = eval(bx, by, bz, j);
-  v = v + (fabsf(v) + A) * 4.8e-7f;
+  // rounding of the evaluation and of the items' FP32 copies (|p| <= A, and
+  // radii up to rmax)
+  float rmax = 0.f;
+  for (int i = 0; i < k; ++i) rmax = fmaxf(rmax, fabsf(it[i].w));
+  v = v + (fabsf(v) + A + rmax) * 4.8e-7f;
   return make_float4(bx, by, bz, v);
 }
 
@@ -278,11 +282,85 @@ __global__ void k_sphere_leaves(const float4* __restrict__ items, int64_t nitems
   if (L < nleaves) sphere_leaf_node(items, nitems, A, lo, hi, bp, bn, bf, L);
 }
 
+// items of node j at `level`: [j * span, (j + 1) * span), span = kLeaf * kFan^level
+__host__ __device__ inline int64_t level_span(int level) {
+  int64_t span = kLeaf;
+  for (int l = 0; l < level; ++l) span *= kFan;
+  return span;
+}
+
 __global__ void k_sphere_level(float4* __restrict__ lo, float4* __restrict__ hi, float4* __restrict__ bp,
                                float4* __restrict__ bn, float4* __restrict__ bf, float A, int64_t child_off,
                                int64_t nchild, int64_t off, int64_t nnode) {
   int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (j < nnode) sphere_level_node(lo, hi, bp, bn, bf, A, child_off, nchild, off, j);
+}
+
+// order-preserving map of floats onto unsigned integers (for atomicMax)
+__device__ __forceinline__ unsigned ord_key(float v) {
+  const unsigned b = __float_as_uint(v);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ord_val(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Tightening of the internal bounding balls, pass 1: one thread per sphere;
+// at every level >= 1 it evaluates its sphere against the node's balls (the
+// node's spheres are a contiguous range of the Morton order) and raises the
+// node's per-ball maximum.  Each value carries its own rounding bound: the
+// FP32 distance (<= 3.6 ulp relative), the sum (1 ulp) and the FP32 copy of
+// the FP64 sphere (sqrt3 ulp of |p|, 1 ulp of r), covered with ~10 ulp each.
+__global__ void k_tighten_items(const float4* __restrict__ items, Tree T, unsigned* __restrict__ keys) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const bool live = i < T.nitems;
+  const int lane = threadIdx.x & 31;
+  const float4 v = live ? items[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float r = fabsf(v.w);
+  const float pm = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fabsf(v.z));
+  for (int l = 1; l < T.nlevels; ++l) {
+    // a level-l node spans >= 64 consecutive spheres, so the 32 threads of a
+    // warp (32 aligned consecutive spheres) share it
+    const int64_t node = T.offset[l] + (live ? i / level_span(l) : 0);
+    float m[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (live) {
+      for (int q = 0; q < 3; ++q) {
+        if ((q == 0 && !(v.w > 0.f)) || (q == 1 && !(v.w < 0.f))) continue;
+        const float4 B = q == 0 ? T.bp[node] : q == 1 ? T.bn[node] : T.bf[node];
+        const float dx = v.x - B.x, dy = v.y - B.y, dz = v.z - B.z;
+        const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+        const float d = dist + (q == 2 ? -r : r);
+        m[q] = d + (dist + 2.f * r + fabsf(d) + pm) * 6e-7f;
+      }
+    }
+    for (int q = 0; q < 3; ++q)
+      for (int o = 16; o > 0; o >>= 1) m[q] = fmaxf(m[q], __shfl_xor_sync(0xffffffffu, m[q], o));
+    if (lane == 0 && live) {
+      const int64_t slot = 3 * (node - T.offset[1]);
+      for (int q = 0; q < 3; ++q)
+        if (m[q] > -INFINITY) atomicMax(keys + slot + q, ord_key(m[q]));
+    }
+  }
+}
+
+// pass 2: every internal ball takes the smaller of its radius through the
+// children and the exact maximum over its own spheres (same centre)
+__global__ void k_tighten_nodes(Tree T, const unsigned* __restrict__ keys, float A, int64_t nupper) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= nupper) return;
+  const int64_t node = T.offset[1] + t;
+  float4* balls[3] = {T.bp, T.bn, T.bf};
+  for (int q = 0; q < 3; ++q) {
+    const unsigned k = keys[3 * t + q];
+    if (k == 0u) continue;
+    const float vmax = ord_val(k);
+    const float v = vmax + (fabsf(vmax) + A) * 4.8e-7f;
+    float4 B = balls[q][node];
+    if (v < B.w) {
+      B.w = v;
+      balls[q][node] = B;
+    }
+  }
 }
 
 // Morton keys of query points (processing order of the packet kernel)
@@ -682,10 +760,13 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
     cz /= cnt;
   }
   // ---- pass over the spheres -------------------------------------------
-  bool cov[2] = {false, false};
-  Top2 A[2], F;
-  top2_init(A[0]);
-  top2_init(A[1]);
+  // per-class state as scalars (the class of an item is uniform across the
+  // warp, so branching on it costs nothing; indexing a register array with
+  // it would push the array to local memory)
+  bool cov0 = false, cov1 = false;
+  Top2 A0, A1, F;
+  top2_init(A0);
+  top2_init(A1);
   top2_init(F);
   int sample = INT_MAX;
   if (__any_sync(kFull, live)) {
@@ -710,29 +791,30 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
             if (pj.x == x64 && pj.y == y64 && pj.z == z64 && o < sample) sample = o;
           }
           const float r = fabsf(P.w);
-          if (P.w != 0.f) {
-            const int c = P.w < 0.f;
-            if (!cov[c]) {
+          auto class_item = [&](bool& cv, Top2& Ac) {
+            if (!cv) {
               const float4 Th = a.thr[j];
               if (d2 < Th.z) {
-                cov[c] = true;
+                cv = true;
               } else if (d2 <= Th.w) {
                 ++rechecks;
-                cov[c] = ex_cov(x64, y64, z64, a.sph64[a.sid[j]], a.tol);
+                cv = ex_cov(x64, y64, z64, a.sph64[a.sid[j]], a.tol);
               }
             }
-            const float t = r + top2_th(A[c], ea2);
-            if (t > 0.f && d2 < t * t * grow) top2_push(A[c], __fsqrt_rn(d2) - r, int(j));
-          }
+            const float t = r + top2_th(Ac, ea2);
+            if (t > 0.f && d2 < t * t * grow) top2_push(Ac, __fsqrt_rn(d2) - r, int(j));
+          };
+          if (P.w > 0.f) class_item(cov0, A0);
+          else if (P.w < 0.f) class_item(cov1, A1);
           const float t2 = top2_th(F, ea2) - r;
           if (t2 > 0.f && d2 < t2 * t2 * grow) top2_push(F, __fsqrt_rn(d2) + r, int(j));
         }
       } else {
         const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
         const int64_t off = T.offset[lev - 1];
-        float th0 = top2_th(A[0], ea2), th1 = top2_th(A[1], ea2);
-        if (!cov[0]) th0 = fmaxf(th0, negtol);
-        if (!cov[1]) th1 = fmaxf(th1, negtol);
+        float th0 = top2_th(A0, ea2), th1 = top2_th(A1, ea2);
+        if (!cov0) th0 = fmaxf(th0, negtol);
+        if (!cov1) th1 = fmaxf(th1, negtol);
         const float thf = top2_th(F, ea2);
         unsigned need = 0;
         int first = -1;
@@ -780,16 +862,18 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
       code = GFS_CODE_SAMPLE;
       value = a.sph64[sample].w;
       arg = sample;
-    } else if (cov[0] && cov[1]) {
+    } else if (cov0 && cov1) {
       code = GFS_CODE_INVALID;
       value = __longlong_as_double(0x7ff8000000000000LL);
-    } else if (!cov[0] && !cov[1]) {
+    } else if (!cov0 && !cov1) {
       code = GFS_CODE_OUTSIDE;
     }
     if (code >= 0) flags = code;
   }
   const bool open = live && code < 0;
-  const int cs = cov[0] ? 0 : 1, co = 1 - cs;
+  const int cs = cov0 ? 0 : 1, co = 1 - cs;
+  const Top2 As = cs == 0 ? A0 : A1;   // x's own class
+  const Top2 Ao = cs == 0 ? A1 : A0;   // the opposite class
   // ---- pass over the survivors of each lane's sign ------------------------
   float bd = INFINITY, sd = INFINITY;
   uint32_t gbest = 0xffffffffu;
@@ -848,7 +932,7 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
       }
     }
   }
-  const bool have_s = open && gbest != 0xffffffffu, have_u = open && A[co].idx >= 0;
+  const bool have_s = open && gbest != 0xffffffffu, have_u = open && Ao.idx >= 0;
   // exact nearest survivor: direct when no other survivor lies in the error
   // band, else an FP64 pass over the band
   double ds = INFINITY;
@@ -872,16 +956,16 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
   // exact nearest opposite tangent point
   double ub = INFINITY;
   int uj = -1;
-  const bool uband = have_u && !(A[co].sec >= A[co].best + ea2);
+  const bool uband = have_u && !(Ao.sec >= Ao.best + ea2);
   if (have_u && !uband) {
-    uj = a.sid[A[co].idx];
+    uj = a.sid[Ao.idx];
     const D4 pj = a.sph64[uj];
     ub = __dsub_rn(__dsqrt_rn(ex_d2(x64, y64, z64, pj.x, pj.y, pj.z)), fabs(pj.w));
   }
   {
     int j2;
     const double v = packet_band_sphere(a, bc, W, lane, uband, x64, y64, z64, x, y, z, 0, co,
-                                        uband ? A[co].best + ea2 : -1.f, j2);
+                                        uband ? Ao.best + ea2 : -1.f, j2);
     if (uband) {
       ++n_band;
       ub = v;
@@ -906,7 +990,7 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
     }
   }
   const double E = double(bc.ea) * 1.01 + 1e-15;
-  const double lbt = -double(A[cs].best) - a.tol;
+  const double lbt = -double(As.best) - a.tol;
   const double ft = double(F.best) + a.tol;
   if (open && code != GFS_CODE_LOWER) {
     const double mm = m < 0.0 ? 0.0 : m;
@@ -915,16 +999,16 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
   // exact lower bound LB (max over the lane's class of r - |x-p|) if needed
   double lb = 0.0;
   int lj = -1;
-  const bool lband = need_lb && !(A[cs].sec >= A[cs].best + ea2);
+  const bool lband = need_lb && !(As.sec >= As.best + ea2);
   if (need_lb && !lband) {
-    lj = a.sid[A[cs].idx];
+    lj = a.sid[As.idx];
     const D4 pl = a.sph64[lj];
     lb = __dsub_rn(fabs(pl.w), __dsqrt_rn(ex_d2(x64, y64, z64, pl.x, pl.y, pl.z)));
   }
   {
     int j2;
     const double v = packet_band_sphere(a, bc, W, lane, lband, x64, y64, z64, x, y, z, 0, cs,
-                                        lband ? A[cs].best + ea2 : -1.f, j2);
+                                        lband ? As.best + ea2 : -1.f, j2);
     if (lband) {
       ++n_band;
       lb = -v;
@@ -1300,7 +1384,8 @@ cudaError_t launch_gather_spheres(const D4* sph64, const int* order, int64_t n, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_tree(const float4* items, int is_sphere, float A, Tree& T, cudaStream_t st) {
+cudaError_t launch_build_tree(const float4* items, int is_sphere, float A, Tree& T, unsigned* scratch,
+                              cudaStream_t st) {
   if (T.nlevels == 0) return cudaSuccess;
   if (is_sphere) {
     k_sphere_leaves<<<nblk(T.count[0], 128), 128, 0, st>>>(items, T.nitems, A, T.lo, T.hi, T.bp, T.bn, T.bf,
@@ -1310,6 +1395,14 @@ cudaError_t launch_build_tree(const float4* items, int is_sphere, float A, Tree&
       k_sphere_level<<<nblk(T.count[l], 128), 128, 0, st>>>(T.lo, T.hi, T.bp, T.bn, T.bf, A, T.offset[l - 1],
                                                             T.count[l - 1], T.offset[l], T.count[l]);
       ++g_launches;
+    }
+    if (scratch && T.nlevels > 1) {
+      const int64_t nupper = T.offset[T.nlevels - 1] + T.count[T.nlevels - 1] - T.offset[1];
+      const cudaError_t e = cudaMemsetAsync(scratch, 0, size_t(nupper) * 3 * sizeof(unsigned), st);
+      if (e != cudaSuccess) return e;
+      k_tighten_items<<<nblk(T.nitems, 256), 256, 0, st>>>(items, T, scratch);
+      k_tighten_nodes<<<nblk(nupper, 128), 128, 0, st>>>(T, scratch, A, nupper);
+      g_launches += 2;
     }
   } else {
     k_leaves<<<nblk(T.count[0], 128), 128, 0, st>>>(items, T.nitems, T.lo, T.hi, T.count[0]);

@@ -144,7 +144,10 @@ cudaError_t sort_keys_u32(void* temp, size_t& temp_bytes, const uint32_t* kin, u
                           cudaStream_t st);
 cudaError_t launch_gather_spheres(const D4* sph64, const int* order, int64_t n, const BuildConsts* bc, float tol32,
                                   double tol, float4* sph, float4* thr, int* sid, cudaStream_t st);
-cudaError_t launch_build_tree(const float4* items, int is_sphere, float A, Tree& T, cudaStream_t st);
+// scratch (spheres only, may be null): 3 * (nodes above the leaves) unsigned
+// words for tightening the internal bounding balls; null skips it
+cudaError_t launch_build_tree(const float4* items, int is_sphere, float A, Tree& T, unsigned* scratch,
+                              cudaStream_t st);
 cudaError_t launch_query_keys(const double* x64, const float* x32, int64_t m, uint32_t* keys, int* vals,
                               cudaStream_t st);
 cudaError_t launch_point_keys(const float4* items, int64_t n, uint32_t* keys, int* vals, cudaStream_t st);
