@@ -247,6 +247,10 @@ int gfs_stats(gfs_ctx* ctx, gfs_stats_t* out);
  * gfs_build and gfs_query, and copies the FP32 values, argmins and result
  * words back into s_out_host / argmin_out_host / flags_out_host (each
  * nullable).  Host buffers should be page-locked for asynchronous copies.
+ * The upload of x overlaps the build and the query runs in up to four
+ * chunks whose results go down while the next chunk runs (on a second stream
+ * the context owns); results are identical to one gfs_query call.  Phase
+ * timings then describe the last chunk.
  * Returns after the results are in host memory (synchronises the stream).
  * Errors: as gfs_build / gfs_query. */
 int gfs_solve_host(gfs_ctx* ctx, const double* p_host, const double* s_host, int64_t n, const void* x_host,

@@ -145,6 +145,8 @@ struct gfs_ctx {
   Counters host_cnt{};
   // host-buffer path (gfs_solve_host)
   DevBuf h_p, h_s, h_x, h_sout, h_arg, h_fl;
+  cudaStream_t side = nullptr;  // copies that overlap the build and the query
+  cudaEvent_t sev = nullptr;
   // phase events (timing = 1): build start, cull start, cull end, build end,
   // query start, fast end, query end
   cudaEvent_t ev[7] = {};
@@ -1130,25 +1132,51 @@ int gfs_solve_host(gfs_ctx* c, const double* p_host, const double* s_host, int64
                    uint16_t* flags_out_host) {
   if (!c || !p_host || !s_host || n < 1 || m < 0 || (m > 0 && !x_host)) return GFS_ERR_ARG;
   cudaStream_t st = c->stream;
-  const size_t xb = size_t(m) * 3 * (x_is_fp32 ? 4 : 8);
+  const size_t xrow = size_t(3) * (x_is_fp32 ? 4 : 8);
+  const size_t xb = size_t(m) * xrow;
   GFS_TRY(ensure(c->h_p, size_t(n) * 24));
   GFS_TRY(ensure(c->h_s, size_t(n) * 8));
   GFS_TRY(ensure(c->h_x, xb));
   GFS_TRY(ensure(c->h_sout, size_t(m) * 4));
   GFS_TRY(ensure(c->h_arg, size_t(m) * 8));
   GFS_TRY(ensure(c->h_fl, size_t(m) * 2));
+  if (!c->side) {
+    GFS_CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    GFS_CK(cudaEventCreateWithFlags(&c->sev, cudaEventDisableTiming));
+  }
+  // the query points go up on the side stream while the build runs
+  GFS_CK(cudaEventRecord(c->sev, st));
+  GFS_CK(cudaStreamWaitEvent(c->side, c->sev, 0));
+  if (m > 0) GFS_CK(cudaMemcpyAsync(c->h_x.p, x_host, xb, cudaMemcpyHostToDevice, c->side));
   GFS_CK(cudaMemcpyAsync(c->h_p.p, p_host, size_t(n) * 24, cudaMemcpyHostToDevice, st));
   GFS_CK(cudaMemcpyAsync(c->h_s.p, s_host, size_t(n) * 8, cudaMemcpyHostToDevice, st));
-  if (m > 0) GFS_CK(cudaMemcpyAsync(c->h_x.p, x_host, xb, cudaMemcpyHostToDevice, st));
   GFS_TRY(gfs_build(c, c->h_p.as<double>(), c->h_s.as<double>(), n));
-  GFS_TRY(gfs_query(c, c->h_x.p, x_is_fp32, m, s_out_host ? c->h_sout.as<float>() : nullptr, nullptr,
-                    argmin_out_host ? c->h_arg.as<int64_t>() : nullptr,
-                    flags_out_host ? c->h_fl.as<uint16_t>() : nullptr));
-  if (m > 0 && s_out_host) GFS_CK(cudaMemcpyAsync(s_out_host, c->h_sout.p, size_t(m) * 4, cudaMemcpyDeviceToHost, st));
-  if (m > 0 && argmin_out_host)
-    GFS_CK(cudaMemcpyAsync(argmin_out_host, c->h_arg.p, size_t(m) * 8, cudaMemcpyDeviceToHost, st));
-  if (m > 0 && flags_out_host)
-    GFS_CK(cudaMemcpyAsync(flags_out_host, c->h_fl.p, size_t(m) * 2, cudaMemcpyDeviceToHost, st));
+  GFS_CK(cudaEventRecord(c->sev, c->side));
+  GFS_CK(cudaStreamWaitEvent(st, c->sev, 0));
+  // the query in four chunks: each chunk's results go down on the side
+  // stream while the next chunk runs (every query point is independent)
+  const int64_t chunk = std::max<int64_t>((m + 3) / 4, int64_t(1) << 20);
+  for (int64_t b = 0; b < m; b += chunk) {
+    const int64_t e = std::min(m, b + chunk), k = e - b;
+    GFS_TRY(gfs_query(c, static_cast<const char*>(c->h_x.p) + size_t(b) * xrow, x_is_fp32, k,
+                      s_out_host ? c->h_sout.as<float>() + b : nullptr, nullptr,
+                      argmin_out_host ? c->h_arg.as<int64_t>() + b : nullptr,
+                      flags_out_host ? c->h_fl.as<uint16_t>() + b : nullptr));
+    GFS_CK(cudaEventRecord(c->sev, st));
+    GFS_CK(cudaStreamWaitEvent(c->side, c->sev, 0));
+    if (s_out_host)
+      GFS_CK(cudaMemcpyAsync(s_out_host + b, c->h_sout.as<float>() + b, size_t(k) * 4, cudaMemcpyDeviceToHost,
+                             c->side));
+    if (argmin_out_host)
+      GFS_CK(cudaMemcpyAsync(argmin_out_host + b, c->h_arg.as<int64_t>() + b, size_t(k) * 8,
+                             cudaMemcpyDeviceToHost, c->side));
+    if (flags_out_host)
+      GFS_CK(cudaMemcpyAsync(flags_out_host + b, c->h_fl.as<uint16_t>() + b, size_t(k) * 2,
+                             cudaMemcpyDeviceToHost, c->side));
+  }
+  // later work on the context's stream stays ordered after the copies
+  GFS_CK(cudaEventRecord(c->sev, c->side));
+  GFS_CK(cudaStreamWaitEvent(st, c->sev, 0));
   GFS_CK(cudaStreamSynchronize(st));
   return GFS_OK;
 }
@@ -1158,6 +1186,8 @@ void gfs_destroy(gfs_ctx* c) {
   if (c->have_ev)
     for (cudaEvent_t e : c->ev)
       if (e) cudaEventDestroy(e);
+  if (c->sev) cudaEventDestroy(c->sev);
+  if (c->side) cudaStreamDestroy(c->side);
   DevBuf* bufs[] = {&c->U32, &c->U64, &c->sph64, &c->keys_in, &c->keys_out, &c->vals_in, &c->vals_out, &c->sph,
                     &c->thr, &c->sid, &c->bound_bits, &c->consts, &c->cnt, &c->cub_temp, &c->st_lo, &c->st_hi,
                     &c->st_bp, &c->st_bn, &c->st_bf, &c->st_tight, &c->surv_raw[0], &c->surv_raw[1], &c->surv_sorted[0], &c->surv_sorted[1],
