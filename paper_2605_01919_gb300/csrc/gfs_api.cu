@@ -116,7 +116,7 @@ struct gfs_ctx {
   bool built = false;
   DevBuf sph64, keys_in, keys_out, vals_in, vals_out, sph, thr, sid, bound_bits, consts, cnt, cub_temp;
   Tree st{};
-  DevBuf st_lo, st_hi, st_bp, st_bn, st_bf;
+  DevBuf st_lo, st_hi, st_na, st_nb, st_nf;
   DevBuf st_tight;  // scratch of the internal-ball tightening
   // survivors
   DevBuf surv_raw[2], surv_sorted[2], vt_lo[2], vt_hi[2];
@@ -135,7 +135,7 @@ struct gfs_ctx {
   std::vector<int64_t> b_off, b_qoff, b_soff[2];
   std::vector<Tree> b_st, b_vt[2];
   DevBuf b_desc, b_offd, b_qoffd, b_sph64, b_k64in, b_k64out, b_sph, b_thr, b_sid, b_bits, b_bcs;
-  DevBuf b_lo, b_hi, b_bp, b_bn, b_bf, b_stdev, b_prefix, b_ctr, b_cnt, b_cviews, b_cw;
+  DevBuf b_lo, b_hi, b_na, b_nb, b_nf, b_stdev, b_prefix, b_ctr, b_cnt, b_cviews, b_cw;
   DevBuf b_sraw[2], b_sshape[2], b_ssorted[2], b_vlo[2], b_vhi[2], b_vtdev[2], b_hist;
   DevBuf b_qkin, b_qkout, b_qvin, b_qvout, b_qviews, b_qw;
   unsigned b_cap = 0;
@@ -188,7 +188,7 @@ int build_point_tree(gfs_ctx* c, int cls) {
   GFS_TRY(ensure(c->vt_hi[cls], size_t(nodes) * sizeof(float4)));
   T.lo = c->vt_lo[cls].as<float4>();
   T.hi = c->vt_hi[cls].as<float4>();
-  T.bp = T.bn = T.bf = nullptr;
+  T.na = T.nb = T.nf = nullptr;
   GFS_CK(launch_build_tree(c->surv_sorted[cls].as<float4>(), 0, 0.f, T, nullptr, c->stream));
   return GFS_OK;
 }
@@ -240,14 +240,14 @@ int build_sphere_hierarchy(gfs_ctx* c, int64_t n) {
   const int64_t nodes = tree_nodes(c->st);
   GFS_TRY(ensure(c->st_lo, size_t(nodes) * sizeof(float4)));
   GFS_TRY(ensure(c->st_hi, size_t(nodes) * sizeof(float4)));
-  GFS_TRY(ensure(c->st_bp, size_t(nodes) * sizeof(float4)));
-  GFS_TRY(ensure(c->st_bn, size_t(nodes) * sizeof(float4)));
-  GFS_TRY(ensure(c->st_bf, size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->st_na, size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->st_nb, size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->st_nf, size_t(nodes) * sizeof(float4)));
   c->st.lo = c->st_lo.as<float4>();
   c->st.hi = c->st_hi.as<float4>();
-  c->st.bp = c->st_bp.as<float4>();
-  c->st.bn = c->st_bn.as<float4>();
-  c->st.bf = c->st_bf.as<float4>();
+  c->st.na = c->st_na.as<float4>();
+  c->st.nb = c->st_nb.as<float4>();
+  c->st.nf = c->st_nf.as<float4>();
   // the coordinate bound A is needed on the host for the hierarchy's rounding slack
   unsigned int bits[2] = {0, 0};
   GFS_CK(cudaMemcpyAsync(bits, c->bound_bits.p, 8, cudaMemcpyDeviceToHost, st));
@@ -255,7 +255,7 @@ int build_sphere_hierarchy(gfs_ctx* c, int64_t n) {
   float Ahost;
   std::memcpy(&Ahost, &bits[0], 4);
   Ahost = std::max(1.0f, Ahost);
-  GFS_TRY(ensure(c->st_tight, size_t(std::max<int64_t>(nodes - c->st.count[0], 1)) * 3 * sizeof(unsigned)));
+  GFS_TRY(ensure(c->st_tight, size_t(std::max<int64_t>(nodes - c->st.count[0], 1)) * 4 * sizeof(unsigned)));
   GFS_CK(launch_build_tree(c->sph.as<float4>(), 1, Ahost, c->st, c->st_tight.as<unsigned>(), st));
   return GFS_OK;
 }
@@ -690,7 +690,7 @@ static_assert(sizeof(gfs_shape) == sizeof(ShapeDesc), "gfs_shape and ShapeDesc m
 // Lay out one tree per shape inside shared node arrays: each shape's tree
 // pointers are offset to its block of nodes; level offsets stay local.
 int64_t forest_layout(std::vector<Tree>& trees, const std::vector<int64_t>& nitems, float4* lo, float4* hi,
-                      float4* bp, float4* bn, float4* bf, int& max_levels) {
+                      float4* na, float4* nb, float4* nf, int& max_levels) {
   int64_t base = 0;
   max_levels = 0;
   for (size_t s = 0; s < nitems.size(); ++s) {
@@ -698,9 +698,9 @@ int64_t forest_layout(std::vector<Tree>& trees, const std::vector<int64_t>& nite
     tree_layout(T, nitems[s]);
     T.lo = lo ? lo + base : nullptr;
     T.hi = hi ? hi + base : nullptr;
-    T.bp = bp ? bp + base : nullptr;
-    T.bn = bn ? bn + base : nullptr;
-    T.bf = bf ? bf + base : nullptr;
+    T.na = na ? na + base : nullptr;
+    T.nb = nb ? nb + base : nullptr;
+    T.nf = nf ? nf + base : nullptr;
     base += tree_nodes(T);
     max_levels = std::max(max_levels, T.nlevels);
   }
@@ -848,11 +848,11 @@ int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
   const int64_t nodes = forest_layout(c->b_st, nits, nullptr, nullptr, nullptr, nullptr, nullptr, maxL);
   GFS_TRY(ensure(c->b_lo, size_t(nodes) * sizeof(float4)));
   GFS_TRY(ensure(c->b_hi, size_t(nodes) * sizeof(float4)));
-  GFS_TRY(ensure(c->b_bp, size_t(nodes) * sizeof(float4)));
-  GFS_TRY(ensure(c->b_bn, size_t(nodes) * sizeof(float4)));
-  GFS_TRY(ensure(c->b_bf, size_t(nodes) * sizeof(float4)));
-  forest_layout(c->b_st, nits, c->b_lo.as<float4>(), c->b_hi.as<float4>(), c->b_bp.as<float4>(), c->b_bn.as<float4>(),
-                c->b_bf.as<float4>(), maxL);
+  GFS_TRY(ensure(c->b_na, size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->b_nb, size_t(nodes) * sizeof(float4)));
+  GFS_TRY(ensure(c->b_nf, size_t(nodes) * sizeof(float4)));
+  forest_layout(c->b_st, nits, c->b_lo.as<float4>(), c->b_hi.as<float4>(), c->b_na.as<float4>(), c->b_nb.as<float4>(),
+                c->b_nf.as<float4>(), maxL);
   std::vector<int64_t> item_off(off.begin(), off.end() - 1);
   GFS_TRY(forest_build(c, c->b_st, c->b_stdev, c->b_sph.as<float4>(), item_off, c->b_bcs.as<BuildConsts>(), 1, maxL));
   // culling views and work items (shape, direction, warp of 32 spheres)
@@ -1190,14 +1190,14 @@ void gfs_destroy(gfs_ctx* c) {
   if (c->side) cudaStreamDestroy(c->side);
   DevBuf* bufs[] = {&c->U32, &c->U64, &c->sph64, &c->keys_in, &c->keys_out, &c->vals_in, &c->vals_out, &c->sph,
                     &c->thr, &c->sid, &c->bound_bits, &c->consts, &c->cnt, &c->cub_temp, &c->st_lo, &c->st_hi,
-                    &c->st_bp, &c->st_bn, &c->st_bf, &c->st_tight, &c->surv_raw[0], &c->surv_raw[1], &c->surv_sorted[0], &c->surv_sorted[1],
+                    &c->st_na, &c->st_nb, &c->st_nf, &c->st_tight, &c->surv_raw[0], &c->surv_raw[1], &c->surv_sorted[0], &c->surv_sorted[1],
                     &c->vt_lo[0], &c->vt_lo[1], &c->vt_hi[0], &c->vt_hi[1], &c->defer, &c->acc, &c->witness64,
                     &c->h_p, &c->h_s, &c->h_x, &c->h_sout, &c->h_arg, &c->h_fl,
                     &c->qk_in, &c->qk_out, &c->qv_in, &c->qv_out, &c->ins_counts,
                     &c->ins_tomb[0], &c->ins_tomb[1], &c->ins_dsurv[0], &c->ins_dsurv[1], &c->ins_dtomb[0],
                     &c->ins_dtomb[1], &c->ins_misc,
                     &c->b_desc, &c->b_offd, &c->b_qoffd, &c->b_sph64, &c->b_k64in, &c->b_k64out, &c->b_sph,
-                    &c->b_thr, &c->b_sid, &c->b_bits, &c->b_bcs, &c->b_lo, &c->b_hi, &c->b_bp, &c->b_bn, &c->b_bf,
+                    &c->b_thr, &c->b_sid, &c->b_bits, &c->b_bcs, &c->b_lo, &c->b_hi, &c->b_na, &c->b_nb, &c->b_nf,
                     &c->b_stdev, &c->b_prefix, &c->b_ctr, &c->b_cnt, &c->b_cviews, &c->b_cw, &c->b_sraw[0],
                     &c->b_sraw[1], &c->b_sshape[0], &c->b_sshape[1], &c->b_ssorted[0], &c->b_ssorted[1],
                     &c->b_vlo[0], &c->b_vlo[1], &c->b_vhi[0], &c->b_vhi[1], &c->b_vtdev[0], &c->b_vtdev[1],

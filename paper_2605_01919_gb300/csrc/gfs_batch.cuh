@@ -88,11 +88,11 @@ __global__ void k_batch_tree_level(const Tree* __restrict__ trees, const int64_t
   const int64_t j = g - prefix[s];
   if (level == 0) {
     const float4* items = items_base + item_off[s];
-    if (is_sphere) sphere_leaf_node(items, T.nitems, bc[s].A, T.lo, T.hi, T.bp, T.bn, T.bf, j);
+    if (is_sphere) sphere_leaf_node(items, T.nitems, bc[s].A, T.lo, T.hi, T.na, T.nb, T.nf, j);
     else point_leaf_node(items, T.nitems, T.lo, T.hi, j);
   } else {
     if (is_sphere)
-      sphere_level_node(T.lo, T.hi, T.bp, T.bn, T.bf, bc[s].A, T.offset[level - 1], T.count[level - 1],
+      sphere_level_node(T.lo, T.hi, T.na, T.nb, T.nf, bc[s].A, T.offset[level - 1], T.count[level - 1],
                         T.offset[level], j);
     else
       point_level_node(T.lo, T.hi, T.offset[level - 1], T.count[level - 1], T.offset[level], j);

@@ -293,9 +293,14 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
     const int grp = lane >> 3, sub = lane & 7;
     const int64_t nl = group_descend(a.st, sub, [&](int64_t node) {
       if (grp == 0) return box_d2(xf, yf, zf, a.st.lo[node], a.st.hi[node]);
-      const float4 b = grp == 1 ? a.st.bp[node] : grp == 2 ? a.st.bn[node] : a.st.bf[node];
-      if (!(b.w > -INFINITY)) return INFINITY;
-      return sqrtf(ball_d2(xf, yf, zf, b)) - b.w;
+      if (grp == 3) {
+        const float4 Fb = a.st.nf[node];
+        return sqrtf(ball_d2(xf, yf, zf, Fb)) - Fb.w;
+      }
+      const float4 R = a.st.nb[node];
+      const float w = grp == 1 ? R.x : R.y;
+      if (!(w > -INFINITY)) return INFINITY;
+      return sqrtf(ball_d2(xf, yf, zf, a.st.na[node])) - w;
     });
     const int64_t j = nl * kLeaf + sub;
     if (j < a.st.nitems) sphere_filtered(a.sph[j], a.sid[j]);
@@ -303,20 +308,20 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
   block_walk(
       a.st, S, a.err, refresh_spheres,
       [&](int64_t node) {
-        const float4 L = a.st.lo[node], H = a.st.hi[node];
-        if (inside_box(xf, yf, zf, L, H)) return true;
-        const float4 Bp = a.st.bp[node], Bn = a.st.bn[node], Bf = a.st.bf[node];
-        // lower bound over the node's spheres of |x-p| - r (per class) and
-        // |x-p| + r (far): |x-c| - w, evaluated in FP32 with margin
-        auto below = [&](const float4& B, double th) {
-          if (!(B.w > -INFINITY)) return false;
-          const float dc = sqrtf(ball_d2(xf, yf, zf, B));
-          const float E = kRel * (dc + fabsf(B.w) + Ax) + 1e-30f;
-          return double(dc - B.w - E) <= th;
+        // lower bounds over the node's spheres of |x-p| - r (per class),
+        // |x-p| + r (far) and |x-p| (a sample at x): |x-C| - w, evaluated in
+        // FP32 with margin
+        const float4 R = a.st.nb[node], Fb = a.st.nf[node];
+        const float dc = sqrtf(ball_d2(xf, yf, zf, a.st.na[node]));
+        const float df = sqrtf(ball_d2(xf, yf, zf, Fb));
+        auto below = [&](float d, float w, double th) {
+          if (!(w > -INFINITY)) return false;
+          const float E = kRel * (d + fabsf(w) + Ax) + 1e-30f;
+          return double(d - w - E) <= th;
         };
         const double th0 = cw0 ? tA0 : fmax(tA0, -tol);
         const double th1 = cw1 ? tA1 : fmax(tA1, -tol);
-        return below(Bp, th0) || below(Bn, th1) || below(Bf, tF);
+        return below(dc, R.z, 0.0) || below(dc, R.x, th0) || below(dc, R.y, th1) || below(df, Fb.w, tF);
       },
       [&](int64_t leaf) {
         const int64_t b = leaf * kLeaf, e = min(b + kLeaf, a.st.nitems);
@@ -586,15 +591,12 @@ __global__ void __launch_bounds__(128) k_ins_update(InsertArgs a, int64_t t) {
               a.st, stk, kUStack, lane, a.err, [&]() { return !__any_sync(kAll, covered); },
               [&](int64_t node) {
                 // some sphere of the node has |q-p| - r < -tol only if
-                // |q-c| - w < -tol for its class's bounding ball (c, w)
-                const float4 Bs[2] = {a.st.bp[node], a.st.bn[node]};
-                for (int cl = 0; cl < 2; ++cl) {
-                  if (!(Bs[cl].w > -INFINITY)) continue;
-                  const float dc = sqrtf(ball_d2(qxf, qyf, qzf, Bs[cl]));
-                  const float E = kRel * (dc + fabsf(Bs[cl].w) + Aq) + 1e-30f;
-                  if (double(dc - Bs[cl].w - E) < -tol) return true;
-                }
-                return false;
+                // |q-C| - max(wp, wn) < -tol
+                const float4 B = a.st.na[node];
+                if (!(B.w > -INFINITY)) return false;
+                const float dc = sqrtf(ball_d2(qxf, qyf, qzf, B));
+                const float E = kRel * (dc + fabsf(B.w) + Aq) + 1e-30f;
+                return double(dc - B.w - E) < -tol;
               },
               [&](int64_t leaf) {
                 const int64_t b = leaf * kLeaf, e = min(b + kLeaf, a.st.nitems);

@@ -13,14 +13,20 @@ namespace gfs {
 // item positions and widened by one ulp, so they also contain the FP64
 // positions the FP32 ones were rounded from.
 //
-// Sphere nodes also carry three bounding balls (centre, radius):
-//   bp, bn -- a ball that contains every ball of sign + (resp. -) in the
-//             node: for any x, |x - p_j| - r_j >= |x - c| - R;
-//   bf     -- a centre c and Q >= max_j (|p_j - c| - r_j) over all spheres:
-//             for any x, |x - p_j| + r_j >= |x - c| - Q.
-// Exact SDF samples are close to nested along the gradient (a deeper ball
-// contains a shallower one), which these balls exploit; an axis box with the
-// largest radius cannot.  Empty classes have R = -inf.
+// Sphere nodes also carry two centres and four radii, each radius an upper
+// bound over the node's spheres (p_j, r_j):
+//   wp, wn -- max over spheres of sign + (resp. -) of |p_j - C| + r_j: their
+//             balls lie in B(C, w), so |x - p_j| - r_j >= |x - C| - w;
+//   w0     -- max over all spheres of |p_j - C| (their centres lie in
+//             B(C, w0): a query point equal to a sample lies in it);
+//   wf     -- max over all spheres of |p_j - F| - r_j about a second centre
+//             F, so that |x - p_j| + r_j >= |x - F| - wf.
+// Stored as na = (C, max(wp, wn)) -- all a coverage test reads --,
+// nb = (wp, wn, w0, 0) and nf = (F, wf).  C is the centre of a small ball
+// enclosing the node's balls; F is chosen for the far bound alone (it leans
+// towards the small spheres, C towards the large ones).  Exact SDF samples
+// are close to nested along the gradient (a deeper ball contains a shallower
+// one), which balls exploit and an axis box cannot.  Empty classes have -inf.
 // ---------------------------------------------------------------------------
 constexpr int kLeaf = 8;
 constexpr int kFan = 8;
@@ -34,9 +40,9 @@ struct Tree {
   int64_t offset[kMaxLevels];     // first node of each level in the node arrays
   float4* lo;                     // (min x, min y, min z, -)
   float4* hi;                     // (max x, max y, max z, -)
-  float4* bp;                     // sphere trees: ball enclosing the + balls
-  float4* bn;                     // sphere trees: ball enclosing the - balls
-  float4* bf;                     // sphere trees: far bound (centre, Q)
+  float4* na;                     // sphere trees: (C, max(wp, wn))
+  float4* nb;                     // sphere trees: (wp, wn, w0, 0)
+  float4* nf;                     // sphere trees: (F, wf)
 };
 
 __host__ __device__ inline uint32_t pack_node(int level, int64_t idx) {

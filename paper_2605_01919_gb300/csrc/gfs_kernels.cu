@@ -229,57 +229,106 @@ __device__ float4 bound_ball(const float4* it, int k, float A) {
   return make_float4(bx, by, bz, v);
 }
 
+// Upper bound of a node radius term d = dist (+-) r computed in FP32: the
+// rounding of dist (<= 3.6 ulp relative) and of the sum (1 ulp), and the FP32
+// copy of an FP64 sphere (sqrt3 ulp of |p| = pm, 1 ulp of r), each covered
+// with ~10 ulp.
+__device__ __forceinline__ float radius_up(float dist, float d, float r, float pm) {
+  return d + (dist + 2.f * r + fabsf(d) + pm) * 6e-7f;
+}
+// final widening of a stored radius (absolute slack in the coordinate bound A)
+__device__ __forceinline__ float radius_fin(float v, float A) {
+  return v > -INFINITY ? v + (fabsf(v) + A) * 4.8e-7f : v;
+}
+
+__device__ __forceinline__ void store_sphere_node(float4* __restrict__ na, float4* __restrict__ nb,
+                                                  float4* __restrict__ nf, int64_t node, float4 C, float4 Fc,
+                                                  float wp, float wn, float w0, float wf, float A) {
+  wp = radius_fin(wp, A);
+  wn = radius_fin(wn, A);
+  w0 = radius_fin(w0, A);
+  wf = radius_fin(wf, A);
+  na[node] = make_float4(C.x, C.y, C.z, fmaxf(wp, wn));
+  nb[node] = make_float4(wp, wn, w0, 0.f);
+  nf[node] = make_float4(Fc.x, Fc.y, Fc.z, wf);
+}
+
 __device__ void sphere_leaf_node(const float4* __restrict__ items, int64_t nitems, float A, float4* __restrict__ lo,
-                                 float4* __restrict__ hi, float4* __restrict__ bp, float4* __restrict__ bn,
-                                 float4* __restrict__ bf, int64_t L) {
+                                 float4* __restrict__ hi, float4* __restrict__ na, float4* __restrict__ nb,
+                                 float4* __restrict__ nf, int64_t L) {
   int64_t b = L * kLeaf, e = min(b + kLeaf, nitems);
-  float4 P[kLeaf], N[kLeaf], F[kLeaf];
-  int np = 0, nn = 0, nf = 0;
+  float4 Ab[kLeaf], Fb[kLeaf];
+  int k = 0;
   float3 mn = make_float3(INFINITY, INFINITY, INFINITY), mx = make_float3(-INFINITY, -INFINITY, -INFINITY);
   for (int64_t i = b; i < e; ++i) {
     const float4 v = items[i];
     mn.x = fminf(mn.x, v.x); mn.y = fminf(mn.y, v.y); mn.z = fminf(mn.z, v.z);
     mx.x = fmaxf(mx.x, v.x); mx.y = fmaxf(mx.y, v.y); mx.z = fmaxf(mx.z, v.z);
-    const float r = fabsf(v.w);
-    if (v.w > 0.f) P[np++] = make_float4(v.x, v.y, v.z, r);
-    if (v.w < 0.f) N[nn++] = make_float4(v.x, v.y, v.z, r);
-    F[nf++] = make_float4(v.x, v.y, v.z, -r);
+    Ab[k] = make_float4(v.x, v.y, v.z, fabsf(v.w));
+    Fb[k++] = make_float4(v.x, v.y, v.z, -fabsf(v.w));
   }
   lo[L] = make_float4(nextafterf(mn.x, -INFINITY), nextafterf(mn.y, -INFINITY), nextafterf(mn.z, -INFINITY), 0.f);
   hi[L] = make_float4(nextafterf(mx.x, INFINITY), nextafterf(mx.y, INFINITY), nextafterf(mx.z, INFINITY), 0.f);
-  bp[L] = bound_ball(P, np, A);
-  bn[L] = bound_ball(N, nn, A);
-  bf[L] = bound_ball(F, nf, A);
+  const float4 C = bound_ball(Ab, k, A);   // small ball enclosing the balls
+  const float4 Fc = bound_ball(Fb, k, A);  // centre for the far bound
+  float wp = -INFINITY, wn = -INFINITY, w0 = -INFINITY, wf = -INFINITY;
+  for (int64_t i = b; i < e; ++i) {
+    const float4 v = items[i];
+    const float r = fabsf(v.w);
+    const float pm = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fabsf(v.z));
+    float dx = v.x - C.x, dy = v.y - C.y, dz = v.z - C.z;
+    const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+    w0 = fmaxf(w0, radius_up(dist, dist, r, pm));
+    if (v.w > 0.f) wp = fmaxf(wp, radius_up(dist, dist + r, r, pm));
+    if (v.w < 0.f) wn = fmaxf(wn, radius_up(dist, dist + r, r, pm));
+    dx = v.x - Fc.x, dy = v.y - Fc.y, dz = v.z - Fc.z;
+    const float df = sqrtf(dx * dx + dy * dy + dz * dz);
+    wf = fmaxf(wf, radius_up(df, df - r, r, pm));
+  }
+  store_sphere_node(na, nb, nf, L, C, Fc, wp, wn, w0, wf, A);
 }
 
-__device__ void sphere_level_node(float4* __restrict__ lo, float4* __restrict__ hi, float4* __restrict__ bp,
-                                  float4* __restrict__ bn, float4* __restrict__ bf, float A, int64_t child_off,
+__device__ void sphere_level_node(float4* __restrict__ lo, float4* __restrict__ hi, float4* __restrict__ na,
+                                  float4* __restrict__ nb, float4* __restrict__ nf, float A, int64_t child_off,
                                   int64_t nchild, int64_t off, int64_t j) {
   int64_t b = j * kFan, e = min(b + kFan, nchild);
   float4 L = make_float4(INFINITY, INFINITY, INFINITY, 0.f), H = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
-  float4 P[kFan], N[kFan], F[kFan];
-  int np = 0, nn = 0, nf = 0;
+  float4 Ab[kFan], Fb[kFan];
+  int k = 0;
   for (int64_t c = b; c < e; ++c) {
     const float4 a = lo[child_off + c], z = hi[child_off + c];
     L.x = fminf(L.x, a.x); L.y = fminf(L.y, a.y); L.z = fminf(L.z, a.z);
     H.x = fmaxf(H.x, z.x); H.y = fmaxf(H.y, z.y); H.z = fmaxf(H.z, z.z);
-    const float4 u = bp[child_off + c], v = bn[child_off + c], w = bf[child_off + c];
-    if (u.w > -INFINITY) P[np++] = u;
-    if (v.w > -INFINITY) N[nn++] = v;
-    if (w.w > -INFINITY) F[nf++] = w;
+    const float4 ca = na[child_off + c], cb = nb[child_off + c];
+    // a ball around the child that holds all its spheres
+    Ab[k] = make_float4(ca.x, ca.y, ca.z, fmaxf(ca.w, cb.z));
+    Fb[k++] = nf[child_off + c];
   }
   lo[off + j] = L;
   hi[off + j] = H;
-  bp[off + j] = bound_ball(P, np, A);
-  bn[off + j] = bound_ball(N, nn, A);
-  bf[off + j] = bound_ball(F, nf, A);
+  const float4 C = bound_ball(Ab, k, A);
+  const float4 Fc = bound_ball(Fb, k, A);
+  // radii through the children (|p - C| <= |p - C_c| + |C_c - C|)
+  float wp = -INFINITY, wn = -INFINITY, w0 = -INFINITY, wf = -INFINITY;
+  for (int64_t c = b; c < e; ++c) {
+    const float4 ca = na[child_off + c], cb = nb[child_off + c], cf = nf[child_off + c];
+    float dx = ca.x - C.x, dy = ca.y - C.y, dz = ca.z - C.z;
+    const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+    if (cb.x > -INFINITY) wp = fmaxf(wp, radius_up(dist, dist + cb.x, 0.f, 0.f));
+    if (cb.y > -INFINITY) wn = fmaxf(wn, radius_up(dist, dist + cb.y, 0.f, 0.f));
+    w0 = fmaxf(w0, radius_up(dist, dist + cb.z, 0.f, 0.f));
+    dx = cf.x - Fc.x, dy = cf.y - Fc.y, dz = cf.z - Fc.z;
+    const float df = sqrtf(dx * dx + dy * dy + dz * dz);
+    wf = fmaxf(wf, radius_up(df, df + cf.w, 0.f, 0.f));
+  }
+  store_sphere_node(na, nb, nf, off + j, C, Fc, wp, wn, w0, wf, A);
 }
 
 __global__ void k_sphere_leaves(const float4* __restrict__ items, int64_t nitems, float A, float4* __restrict__ lo,
-                                float4* __restrict__ hi, float4* __restrict__ bp, float4* __restrict__ bn,
-                                float4* __restrict__ bf, int64_t nleaves) {
+                                float4* __restrict__ hi, float4* __restrict__ na, float4* __restrict__ nb,
+                                float4* __restrict__ nf, int64_t nleaves) {
   int64_t L = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (L < nleaves) sphere_leaf_node(items, nitems, A, lo, hi, bp, bn, bf, L);
+  if (L < nleaves) sphere_leaf_node(items, nitems, A, lo, hi, na, nb, nf, L);
 }
 
 // items of node j at `level`: [j * span, (j + 1) * span), span = kLeaf * kFan^level
@@ -289,11 +338,11 @@ __host__ __device__ inline int64_t level_span(int level) {
   return span;
 }
 
-__global__ void k_sphere_level(float4* __restrict__ lo, float4* __restrict__ hi, float4* __restrict__ bp,
-                               float4* __restrict__ bn, float4* __restrict__ bf, float A, int64_t child_off,
+__global__ void k_sphere_level(float4* __restrict__ lo, float4* __restrict__ hi, float4* __restrict__ na,
+                               float4* __restrict__ nb, float4* __restrict__ nf, float A, int64_t child_off,
                                int64_t nchild, int64_t off, int64_t nnode) {
   int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (j < nnode) sphere_level_node(lo, hi, bp, bn, bf, A, child_off, nchild, off, j);
+  if (j < nnode) sphere_level_node(lo, hi, na, nb, nf, A, child_off, nchild, off, j);
 }
 
 // order-preserving map of floats onto unsigned integers (for atomicMax)
@@ -305,12 +354,10 @@ __device__ __forceinline__ float ord_val(unsigned k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// Tightening of the internal bounding balls, pass 1: one thread per sphere;
-// at every level >= 1 it evaluates its sphere against the node's balls (the
-// node's spheres are a contiguous range of the Morton order) and raises the
-// node's per-ball maximum.  Each value carries its own rounding bound: the
-// FP32 distance (<= 3.6 ulp relative), the sum (1 ulp) and the FP32 copy of
-// the FP64 sphere (sqrt3 ulp of |p|, 1 ulp of r), covered with ~10 ulp each.
+// Tightening of the internal radii, pass 1: one thread per sphere; at every
+// level >= 1 it evaluates its sphere against the node's centre (a node's
+// spheres are a contiguous range of the Morton order) and raises the node's
+// per-radius maximum (same rounding bounds as the leaves).
 __global__ void k_tighten_items(const float4* __restrict__ items, Tree T, unsigned* __restrict__ keys) {
   const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   const bool live = i < T.nitems;
@@ -322,45 +369,47 @@ __global__ void k_tighten_items(const float4* __restrict__ items, Tree T, unsign
     // a level-l node spans >= 64 consecutive spheres, so the 32 threads of a
     // warp (32 aligned consecutive spheres) share it
     const int64_t node = T.offset[l] + (live ? i / level_span(l) : 0);
-    float m[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float m[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
     if (live) {
-      for (int q = 0; q < 3; ++q) {
-        if ((q == 0 && !(v.w > 0.f)) || (q == 1 && !(v.w < 0.f))) continue;
-        const float4 B = q == 0 ? T.bp[node] : q == 1 ? T.bn[node] : T.bf[node];
-        const float dx = v.x - B.x, dy = v.y - B.y, dz = v.z - B.z;
-        const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
-        const float d = dist + (q == 2 ? -r : r);
-        m[q] = d + (dist + 2.f * r + fabsf(d) + pm) * 6e-7f;
-      }
+      const float4 C = T.na[node], Fc = T.nf[node];
+      float dx = v.x - C.x, dy = v.y - C.y, dz = v.z - C.z;
+      const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+      if (v.w > 0.f) m[0] = radius_up(dist, dist + r, r, pm);
+      if (v.w < 0.f) m[1] = radius_up(dist, dist + r, r, pm);
+      m[2] = radius_up(dist, dist, r, pm);
+      dx = v.x - Fc.x, dy = v.y - Fc.y, dz = v.z - Fc.z;
+      const float df = sqrtf(dx * dx + dy * dy + dz * dz);
+      m[3] = radius_up(df, df - r, r, pm);
     }
-    for (int q = 0; q < 3; ++q)
+    for (int q = 0; q < 4; ++q)
       for (int o = 16; o > 0; o >>= 1) m[q] = fmaxf(m[q], __shfl_xor_sync(0xffffffffu, m[q], o));
     if (lane == 0 && live) {
-      const int64_t slot = 3 * (node - T.offset[1]);
-      for (int q = 0; q < 3; ++q)
+      const int64_t slot = 4 * (node - T.offset[1]);
+      for (int q = 0; q < 4; ++q)
         if (m[q] > -INFINITY) atomicMax(keys + slot + q, ord_key(m[q]));
     }
   }
 }
 
-// pass 2: every internal ball takes the smaller of its radius through the
+// pass 2: each internal radius becomes the smaller of its bound through the
 // children and the exact maximum over its own spheres (same centre)
 __global__ void k_tighten_nodes(Tree T, const unsigned* __restrict__ keys, float A, int64_t nupper) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (t >= nupper) return;
   const int64_t node = T.offset[1] + t;
-  float4* balls[3] = {T.bp, T.bn, T.bf};
-  for (int q = 0; q < 3; ++q) {
-    const unsigned k = keys[3 * t + q];
-    if (k == 0u) continue;
-    const float vmax = ord_val(k);
-    const float v = vmax + (fabsf(vmax) + A) * 4.8e-7f;
-    float4 B = balls[q][node];
-    if (v < B.w) {
-      B.w = v;
-      balls[q][node] = B;
-    }
+  const float4 B = T.nb[node];
+  float4 Fc = T.nf[node];
+  float w[4] = {B.x, B.y, B.z, Fc.w};
+  for (int q = 0; q < 4; ++q) {
+    const unsigned k = keys[4 * t + q];
+    if (k != 0u) w[q] = fminf(w[q], radius_fin(ord_val(k), A));
   }
+  T.nb[node] = make_float4(w[0], w[1], w[2], 0.f);
+  Fc.w = w[3];
+  T.nf[node] = Fc;
+  float4 Ca = T.na[node];
+  Ca.w = fmaxf(w[0], w[1]);
+  T.na[node] = Ca;
 }
 
 // Morton keys of query points (processing order of the packet kernel)
@@ -507,17 +556,13 @@ __device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, i
         unsigned need = 0;
         int first = -1, firstn = 0;
         for (int64_t c = cb; c < ce; ++c) {
-          // the node can hold a covering ball only if q lies in one of its
-          // bounding balls shrunk by tol
+          // the node can hold a covering ball only if q lies in the ball
+          // B(C, max(wp, wn)) shrunk by tol
           bool nd_c = false;
           if (open) {
-            const float4 Bs[2] = {T.bp[off + c], T.bn[off + c]};
-            for (int cl = 0; cl < 2; ++cl) {
-              const float t = fmaf(Bs[cl].w - a.tol32, grow, bc.pad);
-              if (!(t > 0.f)) continue;
-              const float dx = qx - Bs[cl].x, dy = qy - Bs[cl].y, dz = qz - Bs[cl].z;
-              if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < t * t) nd_c = true;
-            }
+            const float4 B = T.na[off + c];
+            const float t = fmaf(B.w - a.tol32, grow, bc.pad);
+            nd_c = t > 0.f && ball_d2(qx, qy, qz, B) < t * t;
           }
           const unsigned votes = __ballot_sync(kFull, nd_c);
           if (votes) {
@@ -665,8 +710,17 @@ __device__ double packet_band_sphere(const QueryArgs& a, const BuildConsts& bc, 
       for (int64_t c = cb; c < ce; ++c) {
         bool nd_c = false;
         if (band) {
-          const float4 B = mode == 1 ? T.bf[off + c] : (cls == 0 ? T.bp[off + c] : T.bn[off + c]);
-          const float t = fmaf(thr + B.w, grow, bc.eprune);
+          float4 B;
+          float w;
+          if (mode == 1) {
+            B = T.nf[off + c];
+            w = B.w;
+          } else {
+            B = T.na[off + c];
+            const float4 R = T.nb[off + c];
+            w = cls == 0 ? R.x : R.y;
+          }
+          const float t = fmaf(thr + w, grow, bc.eprune);
           nd_c = t > 0.f && ball_d2(x, y, z, B) < t * t;
         }
         if (__any_sync(kFull, nd_c)) need |= 1u << unsigned(c - cb);
@@ -820,29 +874,27 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
         int first = -1;
         float firstd = INFINITY;
         for (int64_t c = cb; c < ce; ++c) {
-          const float4 L = T.lo[off + c], H = T.hi[off + c];
+          const float4 B = T.na[off + c];
           bool nd_c = false;
           if (live) {
-            nd_c = inside_box(x, y, z, L, H);
+            // one distance to the node centre C against the larger of each
+            // class's tangent threshold and the centres ball (a sample equal
+            // to x), then the far bound about its own centre
+            const float4 R = T.nb[off + c];
+            float v = R.z;
+            if (R.x > -INFINITY) v = fmaxf(v, th0 + R.x);
+            if (R.y > -INFINITY) v = fmaxf(v, th1 + R.y);
+            const float t = fmaf(v, grow, bc.eprune);
+            nd_c = t > 0.f && ball_d2(x, y, z, B) < t * t;
             if (!nd_c) {
-              const float4 B = T.bp[off + c];
-              const float t = fmaf(th0 + B.w, grow, bc.eprune);
-              nd_c = t > 0.f && ball_d2(x, y, z, B) < t * t;
-            }
-            if (!nd_c) {
-              const float4 B = T.bn[off + c];
-              const float t = fmaf(th1 + B.w, grow, bc.eprune);
-              nd_c = t > 0.f && ball_d2(x, y, z, B) < t * t;
-            }
-            if (!nd_c) {
-              const float4 B = T.bf[off + c];
-              const float t = fmaf(thf + B.w, grow, bc.eprune);
-              nd_c = t > 0.f && ball_d2(x, y, z, B) < t * t;
+              const float4 Fb = T.nf[off + c];
+              const float tf = fmaf(thf + Fb.w, grow, bc.eprune);
+              nd_c = tf > 0.f && ball_d2(x, y, z, Fb) < tf * tf;
             }
           }
           if (__any_sync(kFull, nd_c)) {
             need |= 1u << unsigned(c - cb);
-            const float dc = box_d2(cx, cy, cz, L, H);
+            const float dc = ball_d2(cx, cy, cz, B);
             if (dc < firstd) {
               firstd = dc;
               first = int(c - cb);
@@ -1124,18 +1176,20 @@ __device__ void query_exact_one(const QueryArgs& a, int64_t q) {
           const float4 L = T.lo[off + c], H = T.hi[off + c];
           bool need = x >= double(L.x) && x <= double(H.x) && y >= double(L.y) && y <= double(H.y) &&
                       z >= double(L.z) && z <= double(H.z);
-          const float4 Bs[2] = {T.bp[off + c], T.bn[off + c]};
-          for (int cl = 0; cl < 2 && !need; ++cl) {
-            if (!(Bs[cl].w > -INFINITY)) continue;
-            double th = bestA[cl];
-            if (!cov[cl]) th = fmax(th, -tol);
-            const double t = (th + double(Bs[cl].w)) * (1.0 + 1e-12) + 1e-12;
-            need = t > 0.0 && ball_d2_64(x, y, z, Bs[cl]) <= t * t;
-          }
           if (!need) {
-            const float4 B = T.bf[off + c];
-            const double t = (bestF + double(B.w)) * (1.0 + 1e-12) + 1e-12;
-            need = t > 0.0 && ball_d2_64(x, y, z, B) <= t * t;
+            const float4 B = T.na[off + c], R = T.nb[off + c], Fb = T.nf[off + c];
+            const double tf = (bestF + double(Fb.w)) * (1.0 + 1e-12) + 1e-12;
+            need = tf > 0.0 && ball_d2_64(x, y, z, Fb) <= tf * tf;
+            double v = -INFINITY;
+            for (int cl = 0; cl < 2; ++cl) {
+              const float w = cl == 0 ? R.x : R.y;
+              if (!(w > -INFINITY)) continue;
+              double th = bestA[cl];
+              if (!cov[cl]) th = fmax(th, -tol);
+              v = fmax(v, th + double(w));
+            }
+            const double t = v * (1.0 + 1e-12) + 1e-12;
+            need = need || (t > 0.0 && ball_d2_64(x, y, z, B) <= t * t);
           }
           if (need) stack[sp++] = pack_node(lev - 1, c);
         }
@@ -1388,17 +1442,17 @@ cudaError_t launch_build_tree(const float4* items, int is_sphere, float A, Tree&
                               cudaStream_t st) {
   if (T.nlevels == 0) return cudaSuccess;
   if (is_sphere) {
-    k_sphere_leaves<<<nblk(T.count[0], 128), 128, 0, st>>>(items, T.nitems, A, T.lo, T.hi, T.bp, T.bn, T.bf,
+    k_sphere_leaves<<<nblk(T.count[0], 128), 128, 0, st>>>(items, T.nitems, A, T.lo, T.hi, T.na, T.nb, T.nf,
                                                            T.count[0]);
     ++g_launches;
     for (int l = 1; l < T.nlevels; ++l) {
-      k_sphere_level<<<nblk(T.count[l], 128), 128, 0, st>>>(T.lo, T.hi, T.bp, T.bn, T.bf, A, T.offset[l - 1],
+      k_sphere_level<<<nblk(T.count[l], 128), 128, 0, st>>>(T.lo, T.hi, T.na, T.nb, T.nf, A, T.offset[l - 1],
                                                             T.count[l - 1], T.offset[l], T.count[l]);
       ++g_launches;
     }
     if (scratch && T.nlevels > 1) {
       const int64_t nupper = T.offset[T.nlevels - 1] + T.count[T.nlevels - 1] - T.offset[1];
-      const cudaError_t e = cudaMemsetAsync(scratch, 0, size_t(nupper) * 3 * sizeof(unsigned), st);
+      const cudaError_t e = cudaMemsetAsync(scratch, 0, size_t(nupper) * 4 * sizeof(unsigned), st);
       if (e != cudaSuccess) return e;
       k_tighten_items<<<nblk(T.nitems, 256), 256, 0, st>>>(items, T, scratch);
       k_tighten_nodes<<<nblk(nupper, 128), 128, 0, st>>>(T, scratch, A, nupper);
