@@ -471,19 +471,15 @@ struct WarpStack {
     __syncwarp();
     return nd;
   }
-  // push the children whose bit is set in `need`, `first` last (visited next)
+  // push the children whose bit is set in `need` (lane c writes child c),
+  // `first` last (visited next)
   __device__ void push(int lev, int64_t cb, unsigned need, int first, int lane) {
-    int k = 0;
-    for (int c = 0; c < kFan; ++c) {
-      if (!((need >> c) & 1u) || c == first) continue;
-      if (lane == 0) s[sp + k] = pack_node(lev, cb + c);
-      ++k;
-    }
-    if (first >= 0) {
-      if (lane == 0) s[sp + k] = pack_node(lev, cb + first);
-      ++k;
-    }
-    sp += k;
+    const unsigned rest = first >= 0 ? need & ~(1u << unsigned(first)) : need;
+    const int nrest = __popc(rest);
+    if (lane < kFan && ((rest >> lane) & 1u))
+      s[sp + __popc(rest & ((1u << lane) - 1u))] = pack_node(lev, cb + lane);
+    if (first >= 0 && lane == 0) s[sp + nrest] = pack_node(lev, cb + first);
+    sp += nrest + (first >= 0 ? 1 : 0);
     __syncwarp();
   }
 };
@@ -555,22 +551,26 @@ __device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, i
         const int64_t off = T.offset[lev - 1];
         unsigned need = 0;
         int first = -1, firstn = 0;
-        for (int64_t c = cb; c < ce; ++c) {
+        const int nc = int(ce - cb);
+#pragma unroll
+        for (int c = 0; c < kFan; ++c) {
+          if (c >= nc) break;
           // the node can hold a covering ball only if q lies in the ball
           // B(C, max(wp, wn)) shrunk by tol
           bool nd_c = false;
           if (open) {
-            const float4 B = T.na[off + c];
+            const float4 B = T.na[off + cb + c];
             const float t = fmaf(B.w - a.tol32, grow, bc.pad);
             nd_c = t > 0.f && ball_d2(qx, qy, qz, B) < t * t;
           }
+          // visit first the child most lanes need
           const unsigned votes = __ballot_sync(kFull, nd_c);
           if (votes) {
-            need |= 1u << unsigned(c - cb);
+            need |= 1u << unsigned(c);
             const int nv = __popc(votes);
             if (nv > firstn) {
               firstn = nv;
-              first = int(c - cb);
+              first = c;
             }
           }
         }
@@ -793,7 +793,7 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
   double x64 = 0.0, y64 = 0.0, z64 = 0.0;
   if (active) load_query(a, q, x64, y64, z64);
   const float x = float(x64), y = float(y64), z = float(z64);
-  unsigned long long rechecks = 0, n_nodes = 0, n_items = 0, n_snodes = 0, n_sitems = 0, n_band = 0;
+  unsigned rechecks = 0, n_nodes = 0, n_items = 0, n_snodes = 0, n_sitems = 0, n_band = 0;
   bool defer = active && !(fabs(x64) <= bc.A && fabs(y64) <= bc.A && fabs(z64) <= bc.A);
   bool live = active && !defer;
   const float grow = 1.f + 8.f * kU;
@@ -833,7 +833,7 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
       n_nodes += live;
       if (lev == 0) {
         const int64_t b = idx * kLeaf, e = min(b + kLeaf, a.n);
-        n_items += live ? uint64_t(e - b) : 0;
+        n_items += live ? unsigned(e - b) : 0u;
         for (int64_t j = b; j < e; ++j) {
           const float4 P = a.sph[j];
           if (!live) continue;
@@ -870,37 +870,38 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
         if (!cov0) th0 = fmaxf(th0, negtol);
         if (!cov1) th1 = fmaxf(th1, negtol);
         const float thf = top2_th(F, ea2);
-        unsigned need = 0;
-        int first = -1;
-        float firstd = INFINITY;
-        for (int64_t c = cb; c < ce; ++c) {
-          const float4 B = T.na[off + c];
-          bool nd_c = false;
-          if (live) {
+        // every child is tested by every lane (unrolled, so the loads of
+        // all children issue together); one warp OR gives the children to
+        // visit and one warp MIN the child nearest the packet centre (its
+        // squared distance with the child number in the low 3 bits)
+        const int nc = int(ce - cb);
+        unsigned mine = 0, key = 0xffffffffu;
+#pragma unroll
+        for (int c = 0; c < kFan; ++c) {
+          if (c < nc && live) {
+            const float4 B = T.na[off + cb + c];
             // one distance to the node centre C against the larger of each
             // class's tangent threshold and the centres ball (a sample equal
             // to x), then the far bound about its own centre
-            const float4 R = T.nb[off + c];
+            const float4 R = T.nb[off + cb + c];
             float v = R.z;
             if (R.x > -INFINITY) v = fmaxf(v, th0 + R.x);
             if (R.y > -INFINITY) v = fmaxf(v, th1 + R.y);
             const float t = fmaf(v, grow, bc.eprune);
-            nd_c = t > 0.f && ball_d2(x, y, z, B) < t * t;
+            bool nd_c = t > 0.f && ball_d2(x, y, z, B) < t * t;
             if (!nd_c) {
-              const float4 Fb = T.nf[off + c];
+              const float4 Fb = T.nf[off + cb + c];
               const float tf = fmaf(thf + Fb.w, grow, bc.eprune);
               nd_c = tf > 0.f && ball_d2(x, y, z, Fb) < tf * tf;
             }
-          }
-          if (__any_sync(kFull, nd_c)) {
-            need |= 1u << unsigned(c - cb);
-            const float dc = ball_d2(cx, cy, cz, B);
-            if (dc < firstd) {
-              firstd = dc;
-              first = int(c - cb);
+            if (nd_c) {
+              mine |= 1u << c;
+              key = min(key, (__float_as_uint(ball_d2(cx, cy, cz, B)) & ~7u) | unsigned(c));
             }
           }
         }
+        const unsigned need = __reduce_or_sync(kFull, mine);
+        const int first = need ? int(__reduce_min_sync(kFull, key) & 7u) : -1;
         W.push(lev - 1, cb, need, first, lane);
       }
     }
@@ -945,7 +946,7 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
       n_snodes += mine;
       if (lev == 0) {
         const int64_t b = idx * kLeaf, e = min(b + kLeaf, T.nitems);
-        n_sitems += mine ? uint64_t(e - b) : 0;
+        n_sitems += mine ? unsigned(e - b) : 0u;
         for (int64_t j = b; j < e; ++j) {
           const float4 P = items[j];
           const float dx = x - P.x, dy = y - P.y, dz = z - P.z;
@@ -965,21 +966,20 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
       } else {
         const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
         const int64_t off = T.offset[lev - 1];
-        unsigned need = 0;
-        int first = -1;
-        float firstd = INFINITY;
-        for (int64_t c = cb; c < ce; ++c) {
-          const float4 L = T.lo[off + c], H = T.hi[off + c];
-          const bool nd_c = box_d2(x, y, z, L, H) < thn;
-          if (__any_sync(kFull, nd_c)) {
-            need |= 1u << unsigned(c - cb);
-            const float dc = box_d2(cx, cy, cz, L, H);
-            if (dc < firstd) {
-              firstd = dc;
-              first = int(c - cb);
+        const int nc = int(ce - cb);
+        unsigned mine_c = 0, key = 0xffffffffu;
+#pragma unroll
+        for (int c = 0; c < kFan; ++c) {
+          if (c < nc && mine) {
+            const float4 L = T.lo[off + cb + c], H = T.hi[off + cb + c];
+            if (box_d2(x, y, z, L, H) < thn) {
+              mine_c |= 1u << c;
+              key = min(key, (__float_as_uint(box_d2(cx, cy, cz, L, H)) & ~7u) | unsigned(c));
             }
           }
         }
+        const unsigned need = __reduce_or_sync(kFull, mine_c);
+        const int first = need ? int(__reduce_min_sync(kFull, key) & 7u) : -1;
         W.push(lev - 1, cb, need, first, lane);
       }
     }
