@@ -431,8 +431,12 @@ def run_gfs(args):
     q_exact = float(np.mean([ph_["ms_query_exact"] for ph_ in phases]))
     cull = float(np.mean([ph_["ms_build_cull"] for ph_ in phases]))
     build = float(np.mean([ph_["ms_build_total"] for ph_ in phases]))
-    pair_tests = last["query_sphere_items"] + last["query_surv_items"]
-    flops = 8.0 * pair_tests                       # 8 flops per (point, sphere|survivor) pair test
+    # distance evaluations of the query: (point, sphere) and (point,
+    # survivor) pairs plus (point, child node) bound tests, 8 flops each
+    # (3 differences, 3 multiply-adds)
+    pair_tests = (last["query_sphere_items"] + last["query_surv_items"] + last["query_sphere_node_tests"]
+                  + last["query_surv_node_tests"])
+    flops = 8.0 * pair_tests
     clock_mhz = 2070.0
     peak = SM_COUNT * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
     achieved = flops / (q_fast / 1e3) / 1e12 if q_fast > 0 else 0.0
@@ -450,9 +454,9 @@ def run_gfs(args):
         "roofline": roofline,
         "phases_ms": {"build_total": build, "cull": cull, "query_fast": q_fast, "query_exact": q_exact},
         "counters": {k: last[k] for k in ("n_survivors_pos", "n_survivors_neg", "cull_fp64_rechecks",
-                                          "query_fp64_rechecks", "query_deferred", "query_sphere_nodes",
-                                          "query_sphere_items", "query_surv_nodes", "query_surv_items",
-                                          "query_band_passes", "tree_levels")},
+                                          "query_fp64_rechecks", "query_deferred", "query_sphere_node_tests",
+                                          "query_sphere_items", "query_surv_node_tests", "query_surv_items",
+                                          "query_band_passes", "tree_levels", "cull_node_tests", "cull_items")},
         "step_ms": step_ms,
         "clocks": clk,
         "e2e": e2e,

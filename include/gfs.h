@@ -225,9 +225,9 @@ typedef struct {
   int64_t query_fp64_rechecks; /* predicates re-decided in FP64 by the last query */
   int64_t query_deferred;      /* queries finished by the FP64 path in the last query */
   int64_t tree_levels;         /* levels of the sphere hierarchy */
-  int64_t query_sphere_nodes;  /* sphere-hierarchy nodes expanded by the last query (sum over points) */
+  int64_t query_sphere_node_tests; /* child-node bound tests of the last query's sphere pass (sum over points) */
   int64_t query_sphere_items;  /* spheres tested by the last query */
-  int64_t query_surv_nodes;    /* survivor-hierarchy nodes expanded by the last query */
+  int64_t query_surv_node_tests;   /* child-node bound tests of the last query's survivor pass */
   int64_t query_band_passes;   /* FP64 passes over an error band that settled near-ties */
   int64_t query_surv_items;    /* survivors tested by the last query */
   /* phase times of the last build / query in ms (timing = 1 only, else 0) */
@@ -237,6 +237,8 @@ typedef struct {
   double ms_query_exact;       /* FP64 kernel for queries outside the FP32 error model */
   int64_t kernel_launches;     /* kernels this library has launched in this process (cumulative) */
   int64_t sort_calls;          /* radix-sort calls (each launches a few library-sort kernels) */
+  int64_t cull_node_tests;     /* child-node coverage tests of the last build (sum over open candidates) */
+  int64_t cull_items;          /* sphere coverage tests of the last build (sum over open candidates) */
 } gfs_stats_t;
 
 /* Synchronises the stream and fills *out (host). */
@@ -247,10 +249,8 @@ int gfs_stats(gfs_ctx* ctx, gfs_stats_t* out);
  * gfs_build and gfs_query, and copies the FP32 values, argmins and result
  * words back into s_out_host / argmin_out_host / flags_out_host (each
  * nullable).  Host buffers should be page-locked for asynchronous copies.
- * The upload of x overlaps the build and the query runs in up to four
- * chunks whose results go down while the next chunk runs (on a second stream
- * the context owns); results are identical to one gfs_query call.  Phase
- * timings then describe the last chunk.
+ * The upload of x runs on a second stream the context owns and overlaps
+ * the build.
  * Returns after the results are in host memory (synchronises the stream).
  * Errors: as gfs_build / gfs_query. */
 int gfs_solve_host(gfs_ctx* ctx, const double* p_host, const double* s_host, int64_t n, const void* x_host,

@@ -445,7 +445,7 @@ int gfs_query(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, float* s_out,
   }
   GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, query_rechecks), 0,
                          sizeof(unsigned long long), c->stream));
-  GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, q_sphere_nodes), 0,
+  GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, q_sphere_ntests), 0,
                          5 * sizeof(unsigned long long), c->stream));
   GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, ndefer), 0, sizeof(unsigned int),
                          c->stream));
@@ -1098,11 +1098,13 @@ int gfs_stats(gfs_ctx* c, gfs_stats_t* out) {
   out->query_fp64_rechecks = int64_t(c->host_cnt.query_rechecks);
   out->query_deferred = c->opt.precision == 0 ? int64_t(c->host_cnt.ndefer) : 0;
   out->tree_levels = c->st.nlevels;
-  out->query_sphere_nodes = int64_t(c->host_cnt.q_sphere_nodes);
+  out->query_sphere_node_tests = int64_t(c->host_cnt.q_sphere_ntests);
   out->query_sphere_items = int64_t(c->host_cnt.q_sphere_items);
-  out->query_surv_nodes = int64_t(c->host_cnt.q_surv_nodes);
+  out->query_surv_node_tests = int64_t(c->host_cnt.q_surv_ntests);
   out->query_band_passes = int64_t(c->host_cnt.q_band_passes);
   out->query_surv_items = int64_t(c->host_cnt.q_surv_items);
+  out->cull_node_tests = int64_t(c->host_cnt.c_ntests);
+  out->cull_items = int64_t(c->host_cnt.c_items);
   auto ms = [&](int a, int b) {
     float t = 0.f;
     if (cudaEventElapsedTime(&t, c->ev[a], c->ev[b]) != cudaSuccess) {
@@ -1153,30 +1155,14 @@ int gfs_solve_host(gfs_ctx* c, const double* p_host, const double* s_host, int64
   GFS_TRY(gfs_build(c, c->h_p.as<double>(), c->h_s.as<double>(), n));
   GFS_CK(cudaEventRecord(c->sev, c->side));
   GFS_CK(cudaStreamWaitEvent(st, c->sev, 0));
-  // the query in four chunks: each chunk's results go down on the side
-  // stream while the next chunk runs (every query point is independent)
-  const int64_t chunk = std::max<int64_t>((m + 3) / 4, int64_t(1) << 20);
-  for (int64_t b = 0; b < m; b += chunk) {
-    const int64_t e = std::min(m, b + chunk), k = e - b;
-    GFS_TRY(gfs_query(c, static_cast<const char*>(c->h_x.p) + size_t(b) * xrow, x_is_fp32, k,
-                      s_out_host ? c->h_sout.as<float>() + b : nullptr, nullptr,
-                      argmin_out_host ? c->h_arg.as<int64_t>() + b : nullptr,
-                      flags_out_host ? c->h_fl.as<uint16_t>() + b : nullptr));
-    GFS_CK(cudaEventRecord(c->sev, st));
-    GFS_CK(cudaStreamWaitEvent(c->side, c->sev, 0));
-    if (s_out_host)
-      GFS_CK(cudaMemcpyAsync(s_out_host + b, c->h_sout.as<float>() + b, size_t(k) * 4, cudaMemcpyDeviceToHost,
-                             c->side));
-    if (argmin_out_host)
-      GFS_CK(cudaMemcpyAsync(argmin_out_host + b, c->h_arg.as<int64_t>() + b, size_t(k) * 8,
-                             cudaMemcpyDeviceToHost, c->side));
-    if (flags_out_host)
-      GFS_CK(cudaMemcpyAsync(flags_out_host + b, c->h_fl.as<uint16_t>() + b, size_t(k) * 2,
-                             cudaMemcpyDeviceToHost, c->side));
-  }
-  // later work on the context's stream stays ordered after the copies
-  GFS_CK(cudaEventRecord(c->sev, c->side));
-  GFS_CK(cudaStreamWaitEvent(st, c->sev, 0));
+  GFS_TRY(gfs_query(c, c->h_x.p, x_is_fp32, m, s_out_host ? c->h_sout.as<float>() : nullptr, nullptr,
+                    argmin_out_host ? c->h_arg.as<int64_t>() : nullptr,
+                    flags_out_host ? c->h_fl.as<uint16_t>() : nullptr));
+  if (m > 0 && s_out_host) GFS_CK(cudaMemcpyAsync(s_out_host, c->h_sout.p, size_t(m) * 4, cudaMemcpyDeviceToHost, st));
+  if (m > 0 && argmin_out_host)
+    GFS_CK(cudaMemcpyAsync(argmin_out_host, c->h_arg.p, size_t(m) * 8, cudaMemcpyDeviceToHost, st));
+  if (m > 0 && flags_out_host)
+    GFS_CK(cudaMemcpyAsync(flags_out_host, c->h_fl.p, size_t(m) * 2, cudaMemcpyDeviceToHost, st));
   GFS_CK(cudaStreamSynchronize(st));
   return GFS_OK;
 }

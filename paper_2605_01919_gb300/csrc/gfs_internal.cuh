@@ -154,11 +154,13 @@ struct Counters {
   unsigned int nsurv[2];
   unsigned int ndefer;
   unsigned int pad;
-  unsigned long long q_sphere_nodes;   // hierarchy nodes expanded by the query sphere pass
+  unsigned long long q_sphere_ntests;  // child-node bound tests of the query sphere pass
   unsigned long long q_sphere_items;   // spheres tested by the query sphere pass
-  unsigned long long q_surv_nodes;     // nodes expanded by the survivor pass
+  unsigned long long q_surv_ntests;    // child-node bound tests of the survivor pass
   unsigned long long q_band_passes;    // FP64 band passes run to settle near-ties
   unsigned long long q_surv_items;     // survivors tested by the survivor pass
+  unsigned long long c_ntests;         // child-node coverage tests of the cull (open lanes)
+  unsigned long long c_items;          // sphere coverage tests of the cull (open lanes)
 };
 
 }  // namespace gfs

@@ -455,6 +455,13 @@ __global__ void k_gather_points(const float4* __restrict__ src, const int* __res
 constexpr int kPStack = 128;  // >= kFan + (kFan-1)*(kMaxLevels-1)
 constexpr unsigned kFull = 0xffffffffu;
 
+// sum of v over the active lanes of the warp, added once to *dst
+__device__ __forceinline__ void warp_count(unsigned long long* dst, unsigned long long v) {
+  const unsigned mask = __activemask();
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  if ((threadIdx.x & 31) == __ffs(mask) - 1 && v) atomicAdd(dst, v);
+}
+
 struct WarpStack {
   uint32_t* s;
   int sp;
@@ -502,6 +509,7 @@ __device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, i
   bool have64 = false;
   double qx64 = 0, qy64 = 0, qz64 = 0;
   unsigned long long rechecks = 0;
+  unsigned n_ntests = 0, n_items = 0;  // tests made for this lane while it is open
   auto load64 = [&]() {
     if (!have64) {
       D4 pi = a.sph64[a.sid[i]];
@@ -522,6 +530,30 @@ __device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, i
     }
   }
   const bool inbox = open;
+  // the warp's 32 spheres are Morton-consecutive: the spheres of lanes
+  // lane^1, ^2, ^4, ^8, ^16 are near neighbours, the balls most likely to
+  // cover this lane's candidate; a lane they settle skips the walk
+  {
+    const float4 Tho = active ? a.thr[i] : make_float4(-1.f, -1.f, -1.f, -1.f);
+    const int64_t base = i - lane;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int src = lane ^ o;
+      const float4 P = make_float4(__shfl_sync(kFull, S.x, src), __shfl_sync(kFull, S.y, src),
+                                   __shfl_sync(kFull, S.z, src), __shfl_sync(kFull, S.w, src));
+      const float th_lo = __shfl_sync(kFull, Tho.x, src), th_hi = __shfl_sync(kFull, Tho.y, src);
+      const int64_t j = base + src;
+      if (!open || j >= a.n) continue;
+      const float dx = qx - P.x, dy = qy - P.y, dz = qz - P.z;
+      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      if (d2 < th_lo) {
+        open = false;
+      } else if (d2 <= th_hi) {
+        load64();
+        ++rechecks;
+        if (ex_cov(qx64, qy64, qz64, a.sph64[a.sid[j]], a.tol)) open = false;
+      }
+    }
+  }
   const Tree& T = a.tree;
   const float grow = 1.f + 8.f * kU;
   if (__any_sync(kFull, open)) {
@@ -532,7 +564,11 @@ __device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, i
       const int64_t idx = node_index(nd);
       if (lev == 0) {
         const int64_t b = idx * kLeaf, e = min(b + kLeaf, a.n);
-        for (int64_t j = b; j < e; ++j) {
+        n_items += open ? unsigned(e - b) : 0u;
+#pragma unroll
+        for (int jj = 0; jj < kLeaf; ++jj) {
+          const int64_t j = b + jj;
+          if (j >= e) break;
           const float4 P = a.sph[j];
           const float4 Th = a.thr[j];
           if (!open || j == i) continue;
@@ -552,6 +588,7 @@ __device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, i
         unsigned need = 0;
         int first = -1, firstn = 0;
         const int nc = int(ce - cb);
+        n_ntests += open ? unsigned(nc) : 0u;
 #pragma unroll
         for (int c = 0; c < kFan; ++c) {
           if (c >= nc) break;
@@ -579,6 +616,8 @@ __device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, i
     }
   }
   if (rechecks) atomicAdd(&a.cnt->cull_rechecks, rechecks);
+  warp_count(&a.cnt->c_ntests, n_ntests);
+  warp_count(&a.cnt->c_items, n_items);
   if (!(inbox && open)) return;
   // survivor: append to the list of its sign class (zero spheres: both)
   const uint32_t g = uint32_t(a.sid[i]) * uint32_t(a.KS) + uint32_t(k);
@@ -660,11 +699,6 @@ __device__ __forceinline__ void surv_pos64(const QueryArgs& a, uint32_t g, doubl
 }
 
 // Warp-aggregated counter update (one atomic per warp)
-__device__ __forceinline__ void warp_count(unsigned long long* dst, unsigned long long v) {
-  const unsigned mask = __activemask();
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
-  if ((threadIdx.x & 31) == __ffs(mask) - 1 && v) atomicAdd(dst, v);
-}
 
 // Packet FP64 band pass over the sphere hierarchy.  A lane with band = true
 // finds, among the spheres whose FP32 value lies at or below its threshold
@@ -830,7 +864,6 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
       const uint32_t nd = W.pop();
       const int lev = node_level(nd);
       const int64_t idx = node_index(nd);
-      n_nodes += live;
       if (lev == 0) {
         const int64_t b = idx * kLeaf, e = min(b + kLeaf, a.n);
         n_items += live ? unsigned(e - b) : 0u;
@@ -875,6 +908,7 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
         // visit and one warp MIN the child nearest the packet centre (its
         // squared distance with the child number in the low 3 bits)
         const int nc = int(ce - cb);
+        n_nodes += live ? unsigned(nc) : 0u;
         unsigned mine = 0, key = 0xffffffffu;
 #pragma unroll
         for (int c = 0; c < kFan; ++c) {
@@ -943,7 +977,6 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
       const uint32_t nd = W.pop();
       const int lev = node_level(nd);
       const int64_t idx = node_index(nd);
-      n_snodes += mine;
       if (lev == 0) {
         const int64_t b = idx * kLeaf, e = min(b + kLeaf, T.nitems);
         n_sitems += mine ? unsigned(e - b) : 0u;
@@ -967,6 +1000,7 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
         const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
         const int64_t off = T.offset[lev - 1];
         const int nc = int(ce - cb);
+        n_snodes += mine ? unsigned(nc) : 0u;
         unsigned mine_c = 0, key = 0xffffffffu;
 #pragma unroll
         for (int c = 0; c < kFan; ++c) {
@@ -1099,9 +1133,9 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
     value = cs == 0 ? m : -m;
   }
   warp_count(&a.cnt->query_rechecks, rechecks);
-  warp_count(&a.cnt->q_sphere_nodes, n_nodes);
+  warp_count(&a.cnt->q_sphere_ntests, n_nodes);
   warp_count(&a.cnt->q_sphere_items, n_items);
-  warp_count(&a.cnt->q_surv_nodes, n_snodes);
+  warp_count(&a.cnt->q_surv_ntests, n_snodes);
   warp_count(&a.cnt->q_band_passes, n_band);
   warp_count(&a.cnt->q_surv_items, n_sitems);
   if (live) {
@@ -1117,7 +1151,7 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
   }
 }
 
-__global__ void __launch_bounds__(128, 6) k_query_fast(QueryArgs a) {
+__global__ void __launch_bounds__(128, 7) k_query_fast(QueryArgs a) {
   __shared__ uint32_t s_stack[4][kPStack];
   WarpStack W{s_stack[threadIdx.x >> 5], 0};
   query_packet<false>(a, blockIdx.x * int64_t(blockDim.x) + threadIdx.x, W, threadIdx.x & 31);

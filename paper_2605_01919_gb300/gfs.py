@@ -33,10 +33,10 @@ class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "n_spheres", "n_candidates", "n_survivors", "n_survivors_pos", "n_survivors_neg",
         "cull_fp64_rechecks", "query_fp64_rechecks", "query_deferred", "tree_levels",
-        "query_sphere_nodes", "query_sphere_items", "query_surv_nodes", "query_band_passes",
+        "query_sphere_node_tests", "query_sphere_items", "query_surv_node_tests", "query_band_passes",
         "query_surv_items")] + [(n, ctypes.c_double) for n in (
         "ms_build_total", "ms_build_cull", "ms_query_fast", "ms_query_exact")] + [
-        (n, ctypes.c_int64) for n in ("kernel_launches", "sort_calls")]
+        (n, ctypes.c_int64) for n in ("kernel_launches", "sort_calls", "cull_node_tests", "cull_items")]
 
 
 class Shape(ctypes.Structure):
