@@ -819,6 +819,26 @@ __device__ void query_exact_one(const QueryArgs& a, int64_t q);
 // processing order (a.perm), all 32 lanes of the warp must call together.
 // Points outside the coordinate range of the FP32 error model go to the
 // FP64 kernel through a.defer, or (kInlineExact) are evaluated in place.
+// Greedy descent of a whole warp to one leaf: at every level lanes 0-7
+// score the 8 children (score(node) >= 0), the lowest score (lowest child on
+// ties) is followed.  The score must be uniform across the warp.
+template <class Score>
+__device__ int64_t warp_descend(const Tree& T, int lane, Score score) {
+  int lev = T.nlevels - 1;
+  int64_t cb = 0, ce = T.count[lev];
+  for (;;) {
+    const int c = lane & 7;
+    const float v = cb + c < ce ? score(T.offset[lev] + cb + c) : INFINITY;
+    const unsigned key = __reduce_min_sync(kFull, (__float_as_uint(v) & ~7u) | unsigned(c));
+    const int64_t best = cb + (key & 7u);
+    if (lev == 0) return best;
+    cb = best * kFan;
+    ce = min(cb + kFan, T.count[lev - 1]);
+    --lev;
+  }
+}
+
+
 template <bool kInlineExact>
 __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int lane) {
   const bool active = slot < a.m;
@@ -859,12 +879,7 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
   int sample = INT_MAX;
   if (__any_sync(kFull, live)) {
     const Tree& T = a.st;
-    W.push_top(T, lane);
-    while (W.sp > 0) {
-      const uint32_t nd = W.pop();
-      const int lev = node_level(nd);
-      const int64_t idx = node_index(nd);
-      if (lev == 0) {
+    auto leaf_items = [&](int64_t idx) {
         const int64_t b = idx * kLeaf, e = min(b + kLeaf, a.n);
         n_items += live ? unsigned(e - b) : 0u;
         for (int64_t j = b; j < e; ++j) {
@@ -896,6 +911,19 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
           const float t2 = top2_th(F, ea2) - r;
           if (t2 > 0.f && d2 < t2 * t2 * grow) top2_push(F, __fsqrt_rn(d2) + r, int(j));
         }
+    };
+    // seed the thresholds with the leaf nearest the packet centre: a greedy
+    // descent (lanes 0-7 score the 8 children by centre distance) and the
+    // leaf's spheres evaluated by every lane; the walk then skips that leaf
+    const int64_t seeded = warp_descend(T, lane, [&](int64_t node) { return ball_d2(cx, cy, cz, T.na[node]); });
+    leaf_items(seeded);
+    W.push_top(T, lane);
+    while (W.sp > 0) {
+      const uint32_t nd = W.pop();
+      const int lev = node_level(nd);
+      const int64_t idx = node_index(nd);
+      if (lev == 0) {
+        if (idx != seeded) leaf_items(idx);
       } else {
         const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
         const int64_t off = T.offset[lev - 1];
@@ -972,12 +1000,7 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
     const float4* items = a.surv[cl];
     float th = mine ? INFINITY : -1.f;   // threshold on d^2
     float thn = th;                      // widened for node tests
-    W.push_top(T, lane);
-    while (W.sp > 0) {
-      const uint32_t nd = W.pop();
-      const int lev = node_level(nd);
-      const int64_t idx = node_index(nd);
-      if (lev == 0) {
+    auto surv_leaf = [&](int64_t idx) {
         const int64_t b = idx * kLeaf, e = min(b + kLeaf, T.nitems);
         n_sitems += mine ? unsigned(e - b) : 0u;
         for (int64_t j = b; j < e; ++j) {
@@ -996,6 +1019,19 @@ __device__ void query_packet(const QueryArgs& a, int64_t slot, WarpStack& W, int
             thn = th * grow + bc.ed_lin * __fsqrt_rn(th) + 1e-30f;
           }
         }
+    };
+    // seed the threshold with the leaf nearest the packet centre (the walk
+    // skips it)
+    const int64_t seeded =
+        warp_descend(T, lane, [&](int64_t node) { return box_d2(cx, cy, cz, T.lo[node], T.hi[node]); });
+    surv_leaf(seeded);
+    W.push_top(T, lane);
+    while (W.sp > 0) {
+      const uint32_t nd = W.pop();
+      const int lev = node_level(nd);
+      const int64_t idx = node_index(nd);
+      if (lev == 0) {
+        if (idx != seeded) surv_leaf(idx);
       } else {
         const int64_t cb = idx * kFan, ce = min(cb + kFan, T.count[lev - 1]);
         const int64_t off = T.offset[lev - 1];
