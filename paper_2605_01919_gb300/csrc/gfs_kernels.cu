@@ -820,8 +820,9 @@ __device__ void query_exact_one(const QueryArgs& a, int64_t q);
 // Points outside the coordinate range of the FP32 error model go to the
 // FP64 kernel through a.defer, or (kInlineExact) are evaluated in place.
 // Greedy descent of a whole warp to one leaf: at every level lanes 0-7
-// score the 8 children (score(node) >= 0), the lowest score (lowest child on
-// ties) is followed.  The score must be uniform across the warp.
+// score the 8 children, the lowest score (lowest child on ties, up to the
+// score's last 3 bits) is followed.  The score must be uniform across the
+// warp.
 template <class Score>
 __device__ int64_t warp_descend(const Tree& T, int lane, Score score) {
   int lev = T.nlevels - 1;
@@ -829,7 +830,7 @@ __device__ int64_t warp_descend(const Tree& T, int lane, Score score) {
   for (;;) {
     const int c = lane & 7;
     const float v = cb + c < ce ? score(T.offset[lev] + cb + c) : INFINITY;
-    const unsigned key = __reduce_min_sync(kFull, (__float_as_uint(v) & ~7u) | unsigned(c));
+    const unsigned key = __reduce_min_sync(kFull, (ord_key(v) & ~7u) | unsigned(c));
     const int64_t best = cb + (key & 7u);
     if (lev == 0) return best;
     cb = best * kFan;
