@@ -200,23 +200,28 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 # the CUDA path
 # ----------------------------------------------------------------------------
+KERNEL_TU = ("gfs_kernels.cu", "gfs_batch.cuh", "gfs_internal.cuh", "gfs_kernels.h")
+
+
 def kernel_hash() -> str:
+    """Hash of the translation unit that holds the query and cull kernels."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2605_01919_gb300", "csrc"))):
+    for f in KERNEL_TU:
         h.update(open(os.path.join(ROOT, "paper_2605_01919_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+    """DRAM bytes per launch from the committed ncu summary of the kernel
+    (profiles/<kernel>_union64.md, line "dram_bytes_per_launch: N
+    source_hash: H"), if it was taken on the current kernel sources."""
+    import re
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            t = json.load(f)
-        e = t.get(kernel)
-        if e and e.get("source_hash") == kernel_hash():
-            return e["dram_bytes_per_launch"]
-    except (OSError, ValueError):
+        with open(os.path.join(ROOT, "profiles", f"{kernel}_union64.md")) as f:
+            m = re.search(r"dram_bytes_per_launch:\s*(\d+)\s+source_hash:\s*([0-9a-f]+)", f.read())
+        if m and m.group(2) == kernel_hash():
+            return int(m.group(1))
+    except OSError:
         pass
     return None
 

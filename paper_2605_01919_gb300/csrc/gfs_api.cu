@@ -28,6 +28,9 @@ struct DevBuf {
 
 int ensure(DevBuf& b, size_t bytes) {
   if (b.bytes >= bytes && b.p) return GFS_OK;
+  // a buffer that has to grow gets 1/8 headroom, so that slowly growing
+  // sizes (hierarchy rebuilds during insertion) do not reallocate each time
+  if (b.p) bytes += bytes / 8;
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;

@@ -204,6 +204,14 @@ __device__ int64_t group_descend(const Tree& T, int sub, Score score) {
 
 __device__ __forceinline__ float absmax3(float a, float b, float c) { return fmaxf(fmaxf(fabsf(a), fabsf(b)), fabsf(c)); }
 
+// FP32 upper / lower bounds of an FP64 threshold: the filters compare FP32
+// values against these, so no FP64 instruction runs per tested item or node
+__device__ __forceinline__ float f_up(double v) { return __double2float_ru(v); }
+__device__ __forceinline__ float f_dn(double v) { return __double2float_rd(v); }
+// upper bound of sqrt(v) in FP32 (v >= 0; the FP64 root is correctly
+// rounded, the factor covers its half ulp)
+__device__ __forceinline__ float f_up_sqrt(double v) { return f_up(__dsqrt_rn(v) * (1.0 + 1e-15)); }
+
 }  // namespace
 
 __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
@@ -223,6 +231,9 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
   // block-wide thresholds of the last refresh
   double tA0 = INFINITY, tA1 = INFINITY, tF = INFINITY;
   bool cw0 = false, cw1 = false;
+  // FP32 upper bounds of min(block threshold, own best), for the filters
+  float fA0 = INFINITY, fA1 = INFINITY, fF = INFINITY;
+  const float ntol_up = f_up(-tol);
   auto sphere_exact = [&](int o) {
     const D4 P = a.sph64[o];
     if (P.x == x && P.y == y && P.z == z && o < sample) sample = o;
@@ -242,10 +253,15 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
       if (av < bA || (av == bA && uint32_t(o) < iA)) {
         bA = av;
         iA = uint32_t(o);
+        float& fA = neg ? fA1 : fA0;
+        fA = fminf(fA, f_up(av));
       }
     }
     const double f = __dadd_rn(dl, r);
-    if (f < bF) bF = f;
+    if (f < bF) {
+      bF = f;
+      fF = fminf(fF, f_up(f));
+    }
   };
   // FP32 filter of one sphere (float copy Pf of sphere o): evaluates it
   // exactly unless it provably cannot be the sample, a covering ball, a
@@ -261,12 +277,11 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
     if (Pf.w != 0.f) {
       const bool neg = Pf.w < 0.f;
       const bool cv = neg ? (cov1 || cw1) : (cov0 || cw0);
-      const double th = neg ? fmin(tA1, bA1) : fmin(tA0, bA0);
       const float lo = df - r - E;
-      if (!cv && double(lo) < -tol) need = true;
-      if (double(lo) <= th) need = true;
+      if (!cv && lo < ntol_up) need = true;
+      if (lo <= (neg ? fA1 : fA0)) need = true;
     }
-    if (double(df + r - E) <= fmin(tF, bF)) need = true;
+    if (df + r - E <= fF) need = true;
     if (need) sphere_exact(o);
   };
   auto refresh_spheres = [&]() {
@@ -276,6 +291,9 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
     tA0 = v[0];
     tA1 = v[1];
     tF = v[2];
+    fA0 = fminf(fA0, f_up(tA0));
+    fA1 = fminf(fA1, f_up(tA1));
+    fF = fminf(fF, f_up(tF));
     cw0 = __syncthreads_or(cov0) != 0;
     cw1 = __syncthreads_or(cov1) != 0;
   };
@@ -314,14 +332,14 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
         const float4 R = a.st.nb[node], Fb = a.st.nf[node];
         const float dc = sqrtf(ball_d2(xf, yf, zf, a.st.na[node]));
         const float df = sqrtf(ball_d2(xf, yf, zf, Fb));
-        auto below = [&](float d, float w, double th) {
+        auto below = [&](float d, float w, float th) {
           if (!(w > -INFINITY)) return false;
           const float E = kRel * (d + fabsf(w) + Ax) + 1e-30f;
-          return double(d - w - E) <= th;
+          return d - w - E <= th;
         };
-        const double th0 = cw0 ? tA0 : fmax(tA0, -tol);
-        const double th1 = cw1 ? tA1 : fmax(tA1, -tol);
-        return below(dc, R.z, 0.0) || below(dc, R.x, th0) || below(dc, R.y, th1) || below(df, Fb.w, tF);
+        const float th0 = cw0 ? fA0 : fmaxf(fA0, ntol_up);
+        const float th1 = cw1 ? fA1 : fmaxf(fA1, ntol_up);
+        return below(dc, R.z, 0.f) || below(dc, R.x, th0) || below(dc, R.y, th1) || below(df, Fb.w, fF);
       },
       [&](int64_t leaf) {
         const int64_t b = leaf * kLeaf, e = min(b + kLeaf, a.st.nitems);
@@ -366,6 +384,7 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
   const uint32_t iAs = cs == 0 ? iA0 : iA1, iAo = cs == 0 ? iA1 : iA0;
   // ---- nearest live survivor of x's class ----------------------------------
   double bd = INFINITY, td = INFINITY;  // squared distances: own best, block threshold
+  float fd = INFINITY;                   // FP32 upper bound of sqrt(min(td, bd))
   uint32_t gbest = 0xffffffffu;
   const float eqt = float(a.bc->eq);
   auto surv_exact = [&](uint32_t g) {
@@ -375,6 +394,7 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
     if (d2 < bd || (d2 == bd && g < gbest)) {
       bd = d2;
       gbest = g;
+      fd = fminf(fd, f_up_sqrt(d2));
     }
   };
   // FP32 filter of one survivor: its FP32 position is within eq of the exact
@@ -384,15 +404,15 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
     const float dx = xf - P.x, dy = yf - P.y, dz = zf - P.z;
     const float df = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
     const float eqi = fmaxf(eqt, 1.2e-7f * absmax3(P.x, P.y, P.z));
-    const double lo = double(df) - (1.7320508 * double(eqi) + double(kRel * (df + Ax) + 1e-30f));
-    const double th = fmin(td, bd);
-    if (lo <= 0.0 || lo * lo <= th * (1.0 + 1e-12)) surv_exact(__float_as_uint(P.w));
+    const float lo = df - (1.7320508f * eqi * 1.01f + kRel * (df + Ax) + 1e-30f);
+    if (lo <= fd) surv_exact(__float_as_uint(P.w));
   };
   auto refresh_surv = [&]() {
     double v[1] = {bd};
     uint32_t id[1] = {0};
     block_argmin<1>(v, id, S);
     td = v[0];
+    if (td < INFINITY) fd = fminf(fd, f_up_sqrt(td));
   };
   {
     const Tree& T = a.vt[cs];
@@ -410,13 +430,12 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
       const int64_t j = (nl + grp) * kLeaf + sub;
       if (j < T.nitems && !tombed(tomb, j)) surv_filtered(items[j]);
     }
-    const double slack = 2.0 * 1.7320508075688772 * double(a.bc->eq) + 1e-12;
+    const float slack = f_up(2.0 * 1.7320508075688772 * double(a.bc->eq) + 1e-12);
     block_walk(
         T, S, a.err, refresh_surv,
         [&](int64_t node) {
           const float db = sqrtf(box_d2(xf, yf, zf, T.lo[node], T.hi[node]));
-          const double lo = double(db) - double(kRel * (db + Ax) + 1e-30f) - slack;
-          return lo <= 0.0 || lo * lo <= td * (1.0 + 1e-12);
+          return db - kRel * (db + Ax) - 1e-30f - slack <= fd;
         },
         [&](int64_t leaf) {
           const int64_t b = leaf * kLeaf, e = min(b + kLeaf, T.nitems);
@@ -555,6 +574,7 @@ __global__ void __launch_bounds__(128) k_ins_update(InsertArgs a, int64_t t) {
   if (active) {
     const D4 nw = a.sph64[jn];
     const double tol = a.tol;
+    const float ntol_up = f_up(-tol), ntol_dn = f_dn(-tol);
     if (int(blockIdx.x) < ncand_blocks) {
       const int k = int(blockIdx.x) * 4 + wib;
       if (k < KS) {
@@ -578,8 +598,8 @@ __global__ void __launch_bounds__(128) k_ins_update(InsertArgs a, int64_t t) {
             const float df = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
             const float r = fabsf(Pf.w);
             const float E = kRel * (df + r + Aq + absmax3(Pf.x, Pf.y, Pf.z)) + 1e-30f;
-            if (double(df - r - E) >= -tol) return false;
-            if (double(df - r + E) < -tol) return true;
+            if (df - r - E >= ntol_up) return false;
+            if (df - r + E < ntol_dn) return true;
             return ex_cov(qx, qy, qz, a.sph64[o], tol);
           };
           bool covered = false;
@@ -596,7 +616,7 @@ __global__ void __launch_bounds__(128) k_ins_update(InsertArgs a, int64_t t) {
                 if (!(B.w > -INFINITY)) return false;
                 const float dc = sqrtf(ball_d2(qxf, qyf, qzf, B));
                 const float E = kRel * (dc + fabsf(B.w) + Aq) + 1e-30f;
-                return double(dc - B.w - E) < -tol;
+                return dc - B.w - E < ntol_up;
               },
               [&](int64_t leaf) {
                 const int64_t b = leaf * kLeaf, e = min(b + kLeaf, a.st.nitems);
@@ -628,14 +648,15 @@ __global__ void __launch_bounds__(128) k_ins_update(InsertArgs a, int64_t t) {
       const float nxf = float(nw.x), nyf = float(nw.y), nzf = float(nw.z);
       const float An = absmax3(nxf, nyf, nzf);
       const float eqt = float(a.bc->eq);
-      const double reach = rn - tol + 2.0 * 1.7320508075688772 * double(eqt) + 1e-9;
+      const float reach = f_up(rn - tol + 2.0 * 1.7320508075688772 * double(eqt) + 1e-9);
+      const float rkill = f_up(rn - tol);
       auto kill = [&](int cls, const float4& P, bool dyn, int64_t j) {
         // FP32 filter: the exact survivor lies within sqrt3 eqi of P
         const float dx = P.x - nxf, dy = P.y - nyf, dz = P.z - nzf;
         const float df = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         const float eqi = fmaxf(eqt, 1.2e-7f * absmax3(P.x, P.y, P.z));
         const float E = kRel * (df + An + absmax3(P.x, P.y, P.z)) + 1.7320508f * eqi * 1.01f + 1e-30f;
-        if (double(df - E) >= rn - tol) return;
+        if (df - E >= rkill) return;
         const uint32_t g = __float_as_uint(P.w);
         double qx, qy, qz;
         surv64(a, g, qx, qy, qz);
@@ -661,7 +682,7 @@ __global__ void __launch_bounds__(128) k_ins_update(InsertArgs a, int64_t t) {
               T, stk, kUStack, lane, a.err, [&]() { return true; },
               [&](int64_t node) {
                 const float db = sqrtf(box_d2(nxf, nyf, nzf, T.lo[node], T.hi[node]));
-                return double(db - kRel * (db + An) - 1e-30f) < reach;
+                return db - kRel * (db + An) - 1e-30f < reach;
               },
               [&](int64_t leaf) {
                 const int64_t b = leaf * kLeaf, e = min(b + kLeaf, T.nitems);
