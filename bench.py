@@ -52,9 +52,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sub-benchmarks of the backward, insertion and batched paths")
-    ap.add_argument("--only", choices=["backward", "insert", "batch"], default=None,
+    ap.add_argument("--only", choices=["backward", "repair", "insert", "batch"], default=None,
                     help="run one sub-benchmark alone and print its JSON (profiling)")
-    ap.add_argument("--insert-steps", type=int, default=2048)
+    ap.add_argument("--insert-steps", type=int, default=1024)
+    ap.add_argument("--repair-steps", type=int, default=8192)
     ap.add_argument("--query-subsample", type=int, default=1,
                     help="use every k-th query point (small cases for profiler captures)")
     return ap.parse_args()
@@ -268,7 +269,7 @@ def extra_backward():
             "queries_per_s_incl_build": m / ((t_build + t_fwd) / 1e3)}
 
 
-def extra_insert(T=2048):
+def extra_insert(T=1024):
     """Greedy sequential refinement on the 128^3 CSG pseudo-SDF (tau 3): new
     points at the centres of the cells whose eight corner samples do not all
     exceed half the cell diagonal (the cells that may contain the surface),
@@ -301,6 +302,43 @@ def extra_insert(T=2048):
     return {"workload": "csg128_tau3_refine_surface_cells", "candidate_cells": int(cell.sum()),
             "inserted": int(y.shape[0]), "build_ms": t_build, "insert_s": dt,
             "insertions_per_s": y.shape[0] / dt, "codes": np.bincount(fl & 15, minlength=6).tolist(),
+            "lost_witness_steps": int(np.sum((fl & 0x80) != 0)),
+            "far_violations": int(np.sum((fl & 0x20) != 0))}
+
+
+def extra_repair(T=8192):
+    """Repair of the 128^3 CSG pseudo-SDF (tau 3, Sec. 6): build on all
+    samples; the samples left with no surviving candidate are removed; rebuild
+    on the rest; re-insert the removed samples in index order with their own
+    values known (their signs fix the classes, NONCONSERVATIVE counts values
+    below them).  Times the first T insertions."""
+    import torch
+    from paper_2605_01919_gb300 import gfs
+    from paper_2605_01919_gb300 import workloads as W
+    w = W.csg_pseudo_grid()
+    p, s = torch.from_numpy(w.p).cuda(), torch.from_numpy(w.s).cuda()
+    ctx = gfs.Context(tau=w.tau)
+    ctx.build(p, s)
+    surv = ctx.survivors().cpu().numpy()
+    cnt = np.bincount(surv // (ctx.K + 1), minlength=w.n)
+    removed = np.nonzero(cnt == 0)[0]
+    kept = torch.from_numpy(cnt > 0).cuda()
+    p2, s2 = p[kept].contiguous(), s[kept].contiguous()
+    t_build = _ev_time(lambda: ctx.build(p2, s2), reps=1)
+    sel = removed[:T]
+    yt = torch.from_numpy(np.ascontiguousarray(w.p[sel])).cuda()
+    kn = torch.from_numpy(np.ascontiguousarray(w.s[sel])).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = ctx.insert(yt, known=kn)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    fl = out["flags"].cpu().numpy().astype(np.int32) & 0xFFFF
+    ctx.close()
+    return {"workload": "csg128_tau3_repair_known_values", "samples": int(w.n), "removed": int(removed.size),
+            "inserted": int(sel.size), "rebuild_ms": t_build, "insert_s": dt,
+            "insertions_per_s": sel.size / dt, "codes": np.bincount(fl & 15, minlength=6).tolist(),
+            "nonconservative": int(np.sum((fl & 0x100) != 0)),
             "lost_witness_steps": int(np.sum((fl & 0x80) != 0)),
             "far_violations": int(np.sum((fl & 0x20) != 0))}
 
@@ -472,8 +510,8 @@ def run_gfs(args):
         del p, s, x, s_out, arg_out, fl_out, flush
         torch.cuda.empty_cache()
         line["extras"] = {}
-        for name, fn in (("backward", extra_backward), ("insert", lambda: extra_insert(args.insert_steps)),
-                         ("batch", extra_batch)):
+        for name, fn in (("backward", extra_backward), ("repair", lambda: extra_repair(args.repair_steps)),
+                         ("insert", lambda: extra_insert(args.insert_steps)), ("batch", extra_batch)):
             try:
                 line["extras"][name] = fn()
             except Exception as e:  # a failing sub-benchmark must not hide the headline line
@@ -491,8 +529,8 @@ def run_gfs(args):
 if __name__ == "__main__":
     a = parse()
     if a.only:
-        fn = {"backward": extra_backward, "insert": lambda: extra_insert(a.insert_steps),
-              "batch": extra_batch}[a.only]
+        fn = {"backward": extra_backward, "repair": lambda: extra_repair(a.repair_steps),
+              "insert": lambda: extra_insert(a.insert_steps), "batch": extra_batch}[a.only]
         print(json.dumps({a.only: fn()}), flush=True)
     elif a.impl == "reference":
         run_reference(a)

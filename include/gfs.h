@@ -70,6 +70,7 @@ extern "C" {
 #define GFS_FLAG_FAR_VIOL 0x20    /* |s| > FAR + tol (FAR: nearest far tangent point of any sphere) */
 #define GFS_FLAG_OPP_VIOL 0x40    /* |s| > UB_opp + tol (only possible with clamp_opp = 0) */
 #define GFS_FLAG_LOST_WITNESS 0x80 /* insertion: some sphere lost its last surviving candidate */
+#define GFS_FLAG_NONCONSERVATIVE 0x100 /* insertion with known values: |value| < |known| - tol */
 
 /* ---- options ------------------------------------------------------------ */
 typedef struct {
@@ -146,6 +147,17 @@ int gfs_query_backward(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, co
  * the inserted samples.  Synchronises the stream periodically (hierarchy
  * rebuilds).  Errors: GFS_ERR_STATE (no build), GFS_ERR_ARG,
  * GFS_ERR_TOO_LARGE ((n+T+1)*(K+1) >= 2^32), GFS_ERR_OOM, GFS_ERR_CUDA. */
+/* As gfs_insert, with a known value per point (Sec. 6 repair: the removed
+ * samples are re-inserted knowing their own sample values).
+ * known: device, T FP64 values (nullable: then this is gfs_insert).  The sign
+ * of known[t] fixes y_t's sign class instead of containment (0 or NaN: the
+ * class is inferred as in gfs_query), so a known step is never OUTSIDE or
+ * INVALID; LOWER with no sphere of that class has value 0, argmin -1.
+ * GFS_FLAG_NONCONSERVATIVE marks an inserted step whose |value| is below
+ * |known[t]| - tol.  Errors: as gfs_insert. */
+int gfs_insert_known(gfs_ctx* ctx, const double* y, const double* known, int64_t T, double* s_out,
+                     int64_t* argmin_out, uint16_t* flags_out);
+
 int gfs_insert(gfs_ctx* ctx, const double* y, int64_t T, double* s_out, int64_t* argmin_out,
                uint16_t* flags_out);
 

@@ -51,6 +51,7 @@
 #define FLAG_FAR_VIOL (1 << 5)
 #define FLAG_OPP_VIOL (1 << 6)
 #define FLAG_LOST_WITNESS (1 << 7)
+#define FLAG_NONCONSERVATIVE (1 << 8) /* repair: |value| < |known value| - tol */
 
 /* ------------------------------------------------------------------------ */
 /* elementary FP64 pieces, each written in the one order the device repeats */
@@ -329,8 +330,11 @@ static int64_t sample_index(const double* p, int64_t n, const double* x) {
   return -1;
 }
 
+/* known: 0 = infer the sign from containment; +1 / -1 = the sign is given
+ * (Sec. 6 min_valid_radius_for_known_sign: the repair knows each removed
+ * sample's sign), so no OUTSIDE / INVALID outcome */
 static orc_result query_one(const double* p, const double* s, int64_t n, const int64_t* sg, const int64_t* ssph,
-                            const double* sq, int64_t ns, double tol, int clamp_opp, const double* x) {
+                            const double* sq, int64_t ns, double tol, int clamp_opp, const double* x, int known) {
   orc_result R;
   R.gap = ORC_INF;
   int64_t si = sample_index(p, n, x);
@@ -340,8 +344,8 @@ static orc_result query_one(const double* p, const double* s, int64_t n, const i
     R.flags = CODE_SAMPLE;
     return R;
   }
-  int sigma = 0;
-  int code = classify(p, s, n, tol, x, &sigma);
+  int sigma = known;
+  int code = known ? -1 : classify(p, s, n, tol, x, &sigma);
   if (code >= 0) {
     R.value = code == CODE_OUTSIDE ? 0.0 : (0.0 / 0.0);
     R.argmin = -1;
@@ -371,7 +375,7 @@ void orc_query(const double* p, const double* s, int64_t n, const int64_t* sg, c
                const double* sq, int64_t ns, double tol, int clamp_opp, const double* x, int64_t m,
                double* value, int64_t* argmin, int32_t* flags, double* gap) {
   for (int64_t t = 0; t < m; ++t) {
-    orc_result R = query_one(p, s, n, sg, ssph, sq, ns, tol, clamp_opp, x + 3 * t);
+    orc_result R = query_one(p, s, n, sg, ssph, sq, ns, tol, clamp_opp, x + 3 * t, 0);
     value[t] = R.value;
     argmin[t] = R.argmin;
     flags[t] = R.flags;
@@ -597,7 +601,8 @@ static int uncovered_except(const double* q, int64_t self, double tol) {
 }
 
 int64_t orc_insert(const double* p, const double* s, int64_t n, const double* U, int K, double tol, int box_cull,
-                   int clamp_opp, const double* y, int64_t T, double* value, int64_t* argmin, int32_t* flags) {
+                   int clamp_opp, const double* y, const double* known, int64_t T, double* value, int64_t* argmin,
+                   int32_t* flags) {
   st_free();
   g_state.cap_sph = n + T;
   g_state.p = (double*)malloc(sizeof(double) * 3 * (g_state.cap_sph + 1));
@@ -619,20 +624,28 @@ int64_t orc_insert(const double* p, const double* s, int64_t n, const double* U,
   int64_t inserted = 0;
   for (int64_t t = 0; t < T; ++t) {
     const double* x = y + 3 * t;
+    const int ks = known ? sgn(known[t]) : 0;
     orc_result R = query_one(g_state.p, g_state.s, g_state.nsph, g_state.g, g_state.sph, g_state.q, g_state.ns, tol,
-                             clamp_opp, x);
+                             clamp_opp, x, ks);
     int code = R.flags & 15;
+    /* repair (Sec. 6): a value below the removed sample's own by more than
+     * tol is flagged (the inserted ball is smaller than the input's) */
+    if (ks && (code == CODE_SURVIVOR || code == CODE_OPPOSITE || code == CODE_LOWER) &&
+        fabs(R.value) < fabs(known[t]) - tol)
+      R.flags |= FLAG_NONCONSERVATIVE;
     value[t] = R.value;
     argmin[t] = R.argmin;
     flags[t] = R.flags;
     if (!(code == CODE_SURVIVOR || code == CODE_OPPOSITE || code == CODE_LOWER)) continue;
-    /* witness point */
+    /* witness point (x itself when no sphere sets the value) */
     double wq[3];
     if (code == CODE_SURVIVOR) {
       int64_t at = -1;
       for (int64_t u = 0; u < g_state.ns; ++u)
         if (g_state.g[u] == R.argmin) { at = u; break; }
       memcpy(wq, g_state.q + 3 * at, sizeof(wq));
+    } else if (R.argmin < 0) {
+      memcpy(wq, x, sizeof(wq));
     } else {
       const double* pj = g_state.p + 3 * R.argmin;
       double rj = fabs(g_state.s[R.argmin]);

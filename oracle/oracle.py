@@ -24,6 +24,7 @@ TOL = 1e-6  # App. B: "all other tolerances are 1e-6"
 
 CODE_SURVIVOR, CODE_OPPOSITE, CODE_SAMPLE, CODE_OUTSIDE, CODE_INVALID, CODE_LOWER = range(6)
 FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 16, 32, 64, 128
+FLAG_NONCONSERVATIVE = 256
 
 
 def build(force: bool = False) -> str:
@@ -60,7 +61,7 @@ def lib():
         L.orc_query_lazy.restype = None
         L.orc_grad.argtypes = [P, P, i64, P, i32, P, i64, P, P, P, P, P, P, P]
         L.orc_grad.restype = None
-        L.orc_insert.argtypes = [P, P, i64, P, i32, f64, i32, i32, P, i64, P, P, P]
+        L.orc_insert.argtypes = [P, P, i64, P, i32, f64, i32, i32, P, P, i64, P, P, P]
         L.orc_insert.restype = i64
         L.orc_insert_state.argtypes = [P, P, P, P, P, P]
         L.orc_insert_state.restype = i64
@@ -162,17 +163,21 @@ def grad(p, s, U, x, value, argmin, flags, gup):
     return gx, gp, gs
 
 
-def insert(p, s, U, y, tol=TOL, box_cull=True, clamp_opp=True):
-    """Sequential greedy insertion of the rows of y.  Returns (value, argmin,
-    flags) per insertion and the final state dict."""
+def insert(p, s, U, y, tol=TOL, box_cull=True, clamp_opp=True, known=None):
+    """Sequential greedy insertion of the rows of y.  known (optional, T
+    values): the sign of known[t] fixes y_t's sign class (0: inferred from
+    containment), and NONCONSERVATIVE marks |value| < |known[t]| - tol (the
+    Sec. 6 repair of removed samples).  Returns (value, argmin, flags) per
+    insertion and the final state dict."""
     p, s, U, y = _c(p, np.float64), _c(s, np.float64), _c(U, np.float64), _c(y, np.float64)
     T = y.shape[0]
     val = np.zeros(T, np.float64)
     arg = np.zeros(T, np.int64)
     fl = np.zeros(T, np.int32)
+    kn = None if known is None else _c(known, np.float64)
     L = lib()
     L.orc_insert(_ptr(p), _ptr(s), s.shape[0], _ptr(U), U.shape[0], tol, int(box_cull), int(clamp_opp),
-                 _ptr(y), T, _ptr(val), _ptr(arg), _ptr(fl))
+                 _ptr(y), _ptr(kn) if kn is not None else None, T, _ptr(val), _ptr(arg), _ptr(fl))
     nsph = ctypes.c_int64(0)
     ns = L.orc_insert_state(None, None, None, None, None, ctypes.byref(nsph))
     P = np.zeros((nsph.value, 3))

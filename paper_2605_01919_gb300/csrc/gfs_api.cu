@@ -548,6 +548,11 @@ int ins_rebuild(gfs_ctx* c, int64_t n_total) {
 }  // namespace
 
 int gfs_insert(gfs_ctx* c, const double* y, int64_t T, double* s_out, int64_t* argmin_out, uint16_t* flags_out) {
+  return gfs_insert_known(c, y, nullptr, T, s_out, argmin_out, flags_out);
+}
+
+int gfs_insert_known(gfs_ctx* c, const double* y, const double* known, int64_t T, double* s_out,
+                     int64_t* argmin_out, uint16_t* flags_out) {
   if (!c || T < 0 || (T > 0 && !y)) return GFS_ERR_ARG;
   if (!c->built) return GFS_ERR_STATE;
   if (T == 0) return GFS_OK;
@@ -616,6 +621,7 @@ int gfs_insert(gfs_ctx* c, const double* y, int64_t T, double* s_out, int64_t* a
     a.clamp_opp = c->opt.clamp_opp;
     a.bc = c->consts.as<BuildConsts>();
     a.y = y;
+    a.known = known;
     a.s_out = s_out;
     a.arg_out = argmin_out;
     a.fl_out = flags_out;

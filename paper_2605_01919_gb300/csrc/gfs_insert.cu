@@ -357,6 +357,9 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
     iA1 = id[1];
     sample = v[3] < double(INT_MAX) ? int(v[3]) : INT_MAX;
   }
+  // a known value's sign fixes the class (Sec. 6 repair), else containment
+  const double sk = a.known ? a.known[t] : 0.0;
+  const int ks = sk > 0.0 ? 0 : (sk < 0.0 ? 1 : -1);
   int code = -1;
   double value = 0.0;
   int64_t arg = -1;
@@ -364,6 +367,8 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
     code = GFS_CODE_SAMPLE;
     value = a.sph64[sample].w;
     arg = sample;
+  } else if (ks >= 0) {
+    // class given: no OUTSIDE / INVALID outcome
   } else if (c0 && c1) {
     code = GFS_CODE_INVALID;
     value = __longlong_as_double(0x7ff8000000000000LL);
@@ -379,7 +384,7 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
     }
     return;
   }
-  const int cs = c0 ? 0 : 1;
+  const int cs = ks >= 0 ? ks : (c0 ? 0 : 1);
   const double bAs = cs == 0 ? bA0 : bA1, bAo = cs == 0 ? bA1 : bA0;
   const uint32_t iAs = cs == 0 ? iA0 : iA1, iAo = cs == 0 ? iA1 : iA0;
   // ---- nearest live survivor of x's class ----------------------------------
@@ -467,7 +472,7 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
   } else {
     code = GFS_CODE_LOWER;
     m = lb;
-    arg = int64_t(iAs);
+    arg = iAs == 0xffffffffu ? int64_t(-1) : int64_t(iAs);
   }
   if (m < 0.0) m = 0.0;
   int flags = code;
@@ -475,6 +480,7 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
   if (m > __dadd_rn(bF, tol)) flags |= GFS_FLAG_FAR_VIOL;
   if (have_u && ub < __dsub_rn(m, tol)) flags |= GFS_FLAG_OPP_VIOL;
   value = cs == 0 ? m : -m;
+  if (ks >= 0 && fabs(value) < __dsub_rn(fabs(sk), tol)) flags |= GFS_FLAG_NONCONSERVATIVE;
   if (a.s_out) a.s_out[t] = value;
   if (a.arg_out) a.arg_out[t] = arg;
   if (a.fl_out) a.fl_out[t] = uint16_t(flags);
@@ -482,6 +488,10 @@ __global__ void __launch_bounds__(kQT) k_ins_query(InsertArgs a, int64_t t) {
   double wx, wy, wz;
   if (code == GFS_CODE_SURVIVOR) {
     surv64(a, gbest, wx, wy, wz);
+  } else if (arg < 0) {  // no sphere sets the value (value 0): the point itself
+    wx = x;
+    wy = y;
+    wz = z;
   } else {
     const D4 pj = a.sph64[arg];
     const double rj = fabs(pj.w);

@@ -98,6 +98,7 @@ struct InsertArgs {
   int box_cull, clamp_opp;
   const BuildConsts* bc;
   const double* y;
+  const double* known;  // nullable: per-point known value (its sign fixes the class)
   double* s_out;
   int64_t* arg_out;
   uint16_t* fl_out;

@@ -18,7 +18,7 @@ CODE_SURVIVOR, CODE_OPPOSITE, CODE_SAMPLE, CODE_OUTSIDE, CODE_INVALID, CODE_LOWE
 FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 0x10, 0x20, 0x40, 0x80
 
 EXPORTED = ["gfs_default_options", "gfs_create", "gfs_set_stream", "gfs_build", "gfs_query",
-            "gfs_query_backward", "gfs_insert", "gfs_survivors", "gfs_batch_build", "gfs_batch_query",
+            "gfs_query_backward", "gfs_insert", "gfs_insert_known", "gfs_survivors", "gfs_batch_build", "gfs_batch_query",
             "gfs_batch_survivors", "gfs_stats", "gfs_solve_host", "gfs_icosphere", "gfs_strerror",
             "gfs_destroy"]
 
@@ -83,6 +83,8 @@ def load(build_if_missing: bool = True):
     L.gfs_query_backward.restype = i32
     L.gfs_insert.argtypes = [P, P, i64, P, P, P]
     L.gfs_insert.restype = i32
+    L.gfs_insert_known.argtypes = [P, P, P, i64, P, P, P]
+    L.gfs_insert_known.restype = i32
     L.gfs_batch_build.argtypes = [P, P, i32]
     L.gfs_batch_build.restype = i32
     L.gfs_batch_query.argtypes = [P]
@@ -213,17 +215,23 @@ class Context:
         return gx, gp, gs
 
     # -- greedy sequential insertion -------------------------------------------
-    def insert(self, y: torch.Tensor):
+    def insert(self, y: torch.Tensor, known: torch.Tensor | None = None):
         """Insert the rows of y in order (Sec. 4 greedy loop); returns the
-        per-step FP64 value, argmin and result word."""
+        per-step FP64 value, argmin and result word.  known (optional, T FP64
+        values on the device): their signs fix the points' classes and
+        NONCONSERVATIVE marks values below them (Sec. 6 repair)."""
         assert y.is_cuda and y.dtype == torch.float64 and y.shape[-1] == 3
         y = y.contiguous()
         T = y.shape[0]
+        if known is not None:
+            assert known.is_cuda and known.dtype == torch.float64 and known.shape == (T,)
+            known = known.contiguous()
         out = {"s64": torch.empty(T, dtype=torch.float64, device=y.device),
                "argmin": torch.empty(T, dtype=torch.int64, device=y.device),
                "flags": torch.empty(T, dtype=torch.int16, device=y.device)}
         self._sync_stream()
-        _check(load().gfs_insert(self._h, _ptr(y), T, _ptr(out["s64"]), _ptr(out["argmin"]), _ptr(out["flags"])))
+        _check(load().gfs_insert_known(self._h, _ptr(y), _ptr(known), T, _ptr(out["s64"]), _ptr(out["argmin"]),
+                                       _ptr(out["flags"])))
         self.n = self.stats()["n_spheres"]
         return out
 

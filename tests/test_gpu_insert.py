@@ -79,3 +79,28 @@ def test_insert_pseudo_sdf_repair(G, orc):
     y = w.p[covered][:200]
     xq = np.random.default_rng(3).uniform(-1, 1, size=(300, 3))
     _compare(G, orc, p2, s2, w.tau, y, xq)
+
+
+def test_insert_known_values_repair(G, orc):
+    """Repair with known values (Sec. 6): samples fully covered at tau are
+    removed and re-inserted in index order with their own values known (their
+    signs fix the classes; NONCONSERVATIVE marks values below them)."""
+    w = W.csg_pseudo_grid(N=10, tau=1)
+    U = orc.icosphere(w.tau)
+    keep = orc.keep_all(w.p, w.s, U)
+    covered = keep.sum(axis=1) == 0
+    p2, s2 = w.p[~covered], w.s[~covered]
+    y, known = w.p[covered][:300], w.s[covered][:300]
+    val, arg, fl, st = orc.insert(p2, s2, U, y, known=known)
+    ctx = G.Context(tau=w.tau)
+    ctx.build(torch.from_numpy(p2).cuda(), torch.from_numpy(s2).cuda())
+    out = ctx.insert(torch.from_numpy(y).cuda(), known=torch.from_numpy(known).cuda())
+    torch.cuda.synchronize()
+    gf = out["flags"].cpu().numpy().astype(np.int32) & 0xFFFF
+    ga = out["argmin"].cpu().numpy()
+    bad = np.nonzero((gf != fl) | (ga != arg))[0]
+    assert bad.size == 0, f"steps differ: {bad[:10]} gpu {gf[bad[:5]]} {ga[bad[:5]]} oracle {fl[bad[:5]]} {arg[bad[:5]]}"
+    assert np.array_equal(out["s64"].cpu().numpy(), val, equal_nan=True)
+    assert np.array_equal(ctx.survivors().cpu().numpy(), st["g"])
+    assert np.any(fl & orc.FLAG_NONCONSERVATIVE) and not np.any(np.isin(fl & 15, [3, 4]))
+    ctx.close()

@@ -394,3 +394,56 @@ def test_insert_first_value_equals_query(orc):
     val, arg, fl, _ = orc.insert(w.p, w.s, U, y[:1])
     q = orc.solve(w.p, w.s, 2, y[:1])[2]
     assert val[0] == q[0][0] and arg[0] == q[1][0] and fl[0] == q[2][0]
+
+
+# ----------------------------------------------------------------------------
+# insertion with known values (Sec. 6 repair of removed samples)
+# ----------------------------------------------------------------------------
+
+def test_insert_known_sign_equals_inferred_where_they_agree(orc):
+    """Where containment gives the same class as the known value's sign, the
+    known-value loop takes the same decisions (only NONCONSERVATIVE may be
+    added)."""
+    w = W.sphere_grid(N=7, up=2)
+    U = orc.icosphere(1)
+    y = np.random.default_rng(12).uniform(-0.8, 0.8, size=(30, 3))
+    v0, a0, f0, _ = orc.insert(w.p, w.s, U, y)
+    ok = np.isin(f0 & 15, [0, 1, 5])
+    # the loops only stay in step while every earlier decision agrees
+    first_bad = np.argmin(ok) if not ok.all() else y.shape[0]
+    yk = y[:first_bad]
+    known = np.where(v0[:first_bad] >= 0, 1.0, -1.0) * 1e-9     # sign only, tiny magnitude
+    v1, a1, f1, _ = orc.insert(w.p, w.s, U, yk, known=known)
+    assert first_bad >= 5
+    assert np.array_equal(v1, v0[:first_bad]) and np.array_equal(a1, a0[:first_bad])
+    assert np.array_equal(f1 & ~orc.FLAG_NONCONSERVATIVE, f0[:first_bad])
+    assert not np.any(f1 & orc.FLAG_NONCONSERVATIVE)   # |value| >= 1e-9 - tol always
+
+
+def test_insert_known_sign_single_sphere_closed_forms(orc):
+    """One positive sphere (p, r), a point y outside its ball: with known sign
+    + the value is the distance to the nearest in-box candidate of the sphere
+    (brute force over the icosphere); with known sign - the sphere is the
+    opposite class and the value is -(|y - p| - r) (its tangent point)."""
+    p = np.array([[0.1, -0.05, 0.02]])
+    s = np.array([0.3])
+    U = orc.icosphere(2)
+    y = np.array([[0.62, 0.31, -0.2]])
+    v, a, f, _ = orc.insert(p, s, U, y, known=np.array([0.5]))
+    q = p[0] + s[0] * U
+    q = q[np.all(np.abs(q) <= 1.0, axis=1)]
+    d = np.sqrt(((y[0] - q) ** 2).sum(axis=1))
+    assert f[0] & 15 == orc.CODE_SURVIVOR and abs(v[0] - d.min()) < 1e-15
+    assert f[0] & orc.FLAG_NONCONSERVATIVE        # |v| < 0.5 - tol
+    v, a, f, _ = orc.insert(p, s, U, y, known=np.array([-0.01]))
+    assert f[0] & 15 == orc.CODE_OPPOSITE and a[0] == 0
+    assert abs(v[0] + (np.sqrt(((y[0] - p[0]) ** 2).sum()) - s[0])) < 1e-15
+    assert not f[0] & orc.FLAG_NONCONSERVATIVE
+    # no survivor and no sphere of either class (one zero sample outside the
+    # box, its only candidate box-culled): LOWER, value 0, argmin -1, and the
+    # point itself becomes the new sphere's witness
+    v, a, f, st = orc.insert(np.array([[1.5, 0.0, 0.0]]), np.array([0.0]), U, y, known=np.array([0.2]))
+    assert f[0] & 15 == orc.CODE_LOWER and v[0] == 0.0 and a[0] == -1
+    K = U.shape[0]
+    assert np.array_equal(st["g"], [1 * (K + 1) + k for k in range(K + 1)])   # zero sphere at y: all survive
+    assert np.allclose(st["q"], y[0])
