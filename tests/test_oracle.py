@@ -148,8 +148,8 @@ def test_keep_zero_radius_covers_nothing(orc):
 
 def test_sphere_grid_survivor_count_matches_independent_probe(orc):
     """5,449 of 663,552 candidates survive on the 16^3 sphere grid at tau=2
-    with box culling, the count an independent numpy probe of the same rule
-    reported when the workloads were surveyed."""
+    with box culling, the count an independent numpy evaluation of the same
+    rule gives."""
     w = W.sphere_grid()
     keep = orc.keep_all(w.p, w.s, orc.icosphere(w.tau))
     assert keep.size == 663_552 and int(keep.sum()) == 5449
