@@ -251,6 +251,8 @@ typedef struct {
   int64_t sort_calls;          /* radix-sort calls (each launches a few library-sort kernels) */
   int64_t cull_node_tests;     /* child-node coverage tests of the last build (sum over open candidates) */
   int64_t cull_items;          /* sphere coverage tests of the last build (sum over open candidates) */
+  double ms_query_spheres;     /* first of the query's two FP32 kernels (the pass over the spheres); part of
+                                  ms_query_fast (timing = 1 only) */
 } gfs_stats_t;
 
 /* Synchronises the stream and fills *out (host). */

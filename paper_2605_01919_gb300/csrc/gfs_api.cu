@@ -148,11 +148,12 @@ struct gfs_ctx {
   Counters host_cnt{};
   // host-buffer path (gfs_solve_host)
   DevBuf h_p, h_s, h_x, h_sout, h_arg, h_fl;
-  cudaStream_t side = nullptr;  // copies that overlap the build and the query
-  cudaEvent_t sev = nullptr;
+  cudaStream_t side = nullptr;  // the query points' upload, overlapping the build
+  cudaEvent_t sev = nullptr, sev2 = nullptr;  // main -> side, side -> main
+  DevBuf qstate;                // per-slot state between the query's two kernels
   // phase events (timing = 1): build start, cull start, cull end, build end,
   // query start, fast end, query end
-  cudaEvent_t ev[7] = {};
+  cudaEvent_t ev[8] = {};  // + end of the query's sphere pass
   bool have_ev = false;
   bool built_timed = false, query_timed = false;
 };
@@ -353,19 +354,36 @@ int gfs_set_stream(gfs_ctx* c, void* cuda_stream) {
   return GFS_OK;
 }
 
-int gfs_build(gfs_ctx* c, const double* p, const double* s, int64_t n) {
+namespace {
+
+// the cull's counters (before a rerun of the cull)
+int reset_cull_counters(gfs_ctx* c, cudaStream_t st) {
+  char* base = reinterpret_cast<char*>(c->cnt.p);
+  GFS_CK(cudaMemsetAsync(base + offsetof(Counters, cull_rechecks), 0, sizeof(unsigned long long), st));
+  GFS_CK(cudaMemsetAsync(base + offsetof(Counters, nsurv), 0, 2 * sizeof(unsigned int), st));
+  GFS_CK(cudaMemsetAsync(base + offsetof(Counters, c_ntests), 0, 2 * sizeof(unsigned long long), st));
+  return GFS_OK;
+}
+
+// a2: inputs copied, counters cleared, sphere hierarchy built
+int build_begin(gfs_ctx* c, const double* p, const double* s, int64_t n) {
   if (!c || !p || !s || n < 1) return GFS_ERR_ARG;
   if (uint64_t(n) * uint64_t(c->KS) >= (uint64_t(1) << 32) || n >= (int64_t(1) << 30)) return GFS_ERR_TOO_LARGE;
   c->built = false;
   c->built_timed = false;
+  c->query_timed = false;
   cudaStream_t st = c->stream;
   if (c->have_ev) GFS_CK(cudaEventRecord(c->ev[0], st));
   GFS_TRY(ensure(c->sph64, size_t(n) * sizeof(D4)));
   GFS_CK(cudaMemsetAsync(c->cnt.p, 0, sizeof(Counters), st));
   GFS_CK(launch_copy_inputs(p, s, n, c->sph64.as<D4>(), st));
-  // a2: sphere hierarchy
-  GFS_TRY(build_sphere_hierarchy(c, n));
-  // a3: candidate generation and coverage culling
+  return build_sphere_hierarchy(c, n);
+}
+
+// a3, a4: candidate generation and coverage culling, survivor hierarchies
+int build_finish(gfs_ctx* c) {
+  cudaStream_t st = c->stream;
+  const int64_t n = c->n;
   const uint64_t ncand = uint64_t(n) * uint64_t(c->K);
   uint64_t cap = std::max<uint64_t>(uint64_t(1) << 16, ncand / 16 + 1024);
   cap = std::min<uint64_t>(cap, ncand + 16);
@@ -373,7 +391,7 @@ int gfs_build(gfs_ctx* c, const double* p, const double* s, int64_t n) {
     c->cap = unsigned(std::min<uint64_t>(cap, 0xffffffffu));
     GFS_TRY(ensure(c->surv_raw[0], size_t(c->cap) * sizeof(float4)));
     GFS_TRY(ensure(c->surv_raw[1], size_t(c->cap) * sizeof(float4)));
-    GFS_CK(cudaMemsetAsync(c->cnt.p, 0, sizeof(Counters), st));
+    if (attempt > 0) GFS_TRY(reset_cull_counters(c, st));
     CullArgs a;
     std::memset(&a, 0, sizeof(a));
     a.sph = c->sph.as<float4>();
@@ -397,16 +415,19 @@ int gfs_build(gfs_ctx* c, const double* p, const double* s, int64_t n) {
     if (c->have_ev) GFS_CK(cudaEventRecord(c->ev[1], st));
     GFS_CK(launch_cull(a, st));
     if (c->have_ev) GFS_CK(cudaEventRecord(c->ev[2], st));
-    GFS_CK(cudaMemcpyAsync(&c->host_cnt, c->cnt.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    unsigned int ns[2] = {0, 0};
+    GFS_CK(cudaMemcpyAsync(ns, reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, nsurv), sizeof(ns),
+                           cudaMemcpyDeviceToHost, st));
     GFS_CK(cudaStreamSynchronize(st));
-    const unsigned int need = std::max(c->host_cnt.nsurv[0], c->host_cnt.nsurv[1]);
+    c->host_cnt.nsurv[0] = ns[0];
+    c->host_cnt.nsurv[1] = ns[1];
+    const unsigned int need = std::max(ns[0], ns[1]);
     if (need <= c->cap) break;
     cap = uint64_t(need) + need / 8 + 1024;
     if (attempt == 2) return GFS_ERR_OOM;
   }
   c->nsurv[0] = c->host_cnt.nsurv[0];
   c->nsurv[1] = c->host_cnt.nsurv[1];
-  // a4: survivor hierarchies, one per sign class
   GFS_TRY(build_point_tree(c, 0));
   GFS_TRY(build_point_tree(c, 1));
   if (c->have_ev) {
@@ -415,6 +436,21 @@ int gfs_build(gfs_ctx* c, const double* p, const double* s, int64_t n) {
   }
   c->built = true;
   return GFS_OK;
+}
+
+int ensure_side(gfs_ctx* c) {
+  if (c->side) return GFS_OK;
+  GFS_CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  GFS_CK(cudaEventCreateWithFlags(&c->sev, cudaEventDisableTiming));
+  GFS_CK(cudaEventCreateWithFlags(&c->sev2, cudaEventDisableTiming));
+  return GFS_OK;
+}
+
+}  // namespace
+
+int gfs_build(gfs_ctx* c, const double* p, const double* s, int64_t n) {
+  GFS_TRY(build_begin(c, p, s, n));
+  return build_finish(c);
 }
 
 int gfs_query(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, float* s_out, double* s64_out,
@@ -445,6 +481,8 @@ int gfs_query(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, float* s_out,
     GFS_TRY(sort_u32_pairs(c, c->qk_in.as<uint32_t>(), c->qk_out.as<uint32_t>(), c->qv_in.as<int>(),
                            c->qv_out.as<int>(), m));
     a.perm = reinterpret_cast<const uint32_t*>(c->qv_out.p);
+    GFS_TRY(ensure(c->qstate, size_t(m) * 3 * sizeof(uint4)));
+    a.state = reinterpret_cast<uint4*>(c->qstate.p);
   }
   GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, query_rechecks), 0,
                          sizeof(unsigned long long), c->stream));
@@ -453,7 +491,13 @@ int gfs_query(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, float* s_out,
   GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->cnt.p) + offsetof(Counters, ndefer), 0, sizeof(unsigned int),
                          c->stream));
   if (c->have_ev) GFS_CK(cudaEventRecord(c->ev[4], c->stream));
-  if (c->opt.precision == 0) GFS_CK(launch_query_fast(a, c->stream));
+  if (c->opt.precision == 0) {
+    GFS_CK(launch_query_spheres(a, c->stream));
+    if (c->have_ev) GFS_CK(cudaEventRecord(c->ev[7], c->stream));
+    GFS_CK(launch_query_finish(a, c->stream));
+  } else if (c->have_ev) {
+    GFS_CK(cudaEventRecord(c->ev[7], c->stream));
+  }
   if (c->have_ev) GFS_CK(cudaEventRecord(c->ev[5], c->stream));
   GFS_CK(launch_query_exact(a, c->opt.precision == 1, c->stream));
   if (c->have_ev) {
@@ -1133,6 +1177,7 @@ int gfs_stats(gfs_ctx* c, gfs_stats_t* out) {
   if (c->have_ev && c->query_timed) {
     out->ms_query_fast = ms(4, 5);
     out->ms_query_exact = ms(5, 6);
+    out->ms_query_spheres = ms(4, 7);
   }
   out->n_survivors = -1;  // unique count is available through gfs_survivors
   return GFS_OK;
@@ -1151,10 +1196,7 @@ int gfs_solve_host(gfs_ctx* c, const double* p_host, const double* s_host, int64
   GFS_TRY(ensure(c->h_sout, size_t(m) * 4));
   GFS_TRY(ensure(c->h_arg, size_t(m) * 8));
   GFS_TRY(ensure(c->h_fl, size_t(m) * 2));
-  if (!c->side) {
-    GFS_CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
-    GFS_CK(cudaEventCreateWithFlags(&c->sev, cudaEventDisableTiming));
-  }
+  GFS_TRY(ensure_side(c));
   // the query points go up on the side stream while the build runs
   GFS_CK(cudaEventRecord(c->sev, st));
   GFS_CK(cudaStreamWaitEvent(c->side, c->sev, 0));
@@ -1162,8 +1204,8 @@ int gfs_solve_host(gfs_ctx* c, const double* p_host, const double* s_host, int64
   GFS_CK(cudaMemcpyAsync(c->h_p.p, p_host, size_t(n) * 24, cudaMemcpyHostToDevice, st));
   GFS_CK(cudaMemcpyAsync(c->h_s.p, s_host, size_t(n) * 8, cudaMemcpyHostToDevice, st));
   GFS_TRY(gfs_build(c, c->h_p.as<double>(), c->h_s.as<double>(), n));
-  GFS_CK(cudaEventRecord(c->sev, c->side));
-  GFS_CK(cudaStreamWaitEvent(st, c->sev, 0));
+  GFS_CK(cudaEventRecord(c->sev2, c->side));
+  GFS_CK(cudaStreamWaitEvent(st, c->sev2, 0));
   GFS_TRY(gfs_query(c, c->h_x.p, x_is_fp32, m, s_out_host ? c->h_sout.as<float>() : nullptr, nullptr,
                     argmin_out_host ? c->h_arg.as<int64_t>() : nullptr,
                     flags_out_host ? c->h_fl.as<uint16_t>() : nullptr));
@@ -1182,10 +1224,11 @@ void gfs_destroy(gfs_ctx* c) {
     for (cudaEvent_t e : c->ev)
       if (e) cudaEventDestroy(e);
   if (c->sev) cudaEventDestroy(c->sev);
+  if (c->sev2) cudaEventDestroy(c->sev2);
   if (c->side) cudaStreamDestroy(c->side);
   DevBuf* bufs[] = {&c->U32, &c->U64, &c->sph64, &c->keys_in, &c->keys_out, &c->vals_in, &c->vals_out, &c->sph,
                     &c->thr, &c->sid, &c->bound_bits, &c->consts, &c->cnt, &c->cub_temp, &c->st_lo, &c->st_hi,
-                    &c->st_na, &c->st_nb, &c->st_nf, &c->st_tight, &c->surv_raw[0], &c->surv_raw[1], &c->surv_sorted[0], &c->surv_sorted[1],
+                    &c->st_na, &c->st_nb, &c->st_nf, &c->st_tight, &c->qstate, &c->surv_raw[0], &c->surv_raw[1], &c->surv_sorted[0], &c->surv_sorted[1],
                     &c->vt_lo[0], &c->vt_lo[1], &c->vt_hi[0], &c->vt_hi[1], &c->defer, &c->acc, &c->witness64,
                     &c->h_p, &c->h_s, &c->h_x, &c->h_sout, &c->h_arg, &c->h_fl,
                     &c->qk_in, &c->qk_out, &c->qv_in, &c->qv_out, &c->ins_counts,

@@ -71,6 +71,7 @@ struct QueryArgs {
   uint32_t* defer;
   unsigned int defer_cap;
   Counters* cnt;
+  uint4* state;             // 3 x uint4 per processing slot, between the query's two kernels
 };
 
 struct InsertArgs {
@@ -154,7 +155,10 @@ cudaError_t launch_query_keys(const double* x64, const float* x32, int64_t m, ui
 cudaError_t launch_point_keys(const float4* items, int64_t n, uint32_t* keys, int* vals, cudaStream_t st);
 cudaError_t launch_gather_points(const float4* src, const int* order, int64_t n, float4* dst, cudaStream_t st);
 cudaError_t launch_cull(const CullArgs& a, cudaStream_t st);
-cudaError_t launch_query_fast(const QueryArgs& a, cudaStream_t st);
+// the query in two kernels: phase 1 (sphere pass, state to a.state), phase 2
+// (survivor pass, exact re-evaluation, flags, outputs)
+cudaError_t launch_query_spheres(const QueryArgs& a, cudaStream_t st);
+cudaError_t launch_query_finish(const QueryArgs& a, cudaStream_t st);
 cudaError_t launch_query_exact(const QueryArgs& a, int all, cudaStream_t st);
 cudaError_t launch_grad(const GradArgs& a, int64_t n, float* grad_p, float* grad_sv, cudaStream_t st);
 cudaError_t launch_collect_ids(const float4* s0, unsigned int n0, const float4* s1, unsigned int n1, const D4* sph64,

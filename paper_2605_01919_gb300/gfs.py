@@ -36,7 +36,8 @@ class Stats(ctypes.Structure):
         "query_sphere_node_tests", "query_sphere_items", "query_surv_node_tests", "query_band_passes",
         "query_surv_items")] + [(n, ctypes.c_double) for n in (
         "ms_build_total", "ms_build_cull", "ms_query_fast", "ms_query_exact")] + [
-        (n, ctypes.c_int64) for n in ("kernel_launches", "sort_calls", "cull_node_tests", "cull_items")]
+        (n, ctypes.c_int64) for n in ("kernel_launches", "sort_calls", "cull_node_tests", "cull_items")] + [
+        ("ms_query_spheres", ctypes.c_double)]
 
 
 class Shape(ctypes.Structure):
