@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(128) k_batch_cull(const CullArgs* __restrict__
     const int64_t nw = (a.n + 31) / 32;
     const int k = int(local / nw);
     const int64_t wl = local - int64_t(k) * nw;
-    cull_packet(a, wl * 32 + lane, k, W, lane);
+    cull_packet<false>(a, wl * 32 + lane, k, W, lane, nullptr, nullptr);
   }
 }
 

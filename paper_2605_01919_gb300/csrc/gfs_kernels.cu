@@ -502,13 +502,20 @@ struct WarpStack {
 // the sphere hierarchy as a packet (one node at a time, children visited if
 // any lane still needs them); a lane drops out at the first ball that covers
 // its candidate, and the warp stops when every lane is settled.
-__device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, int lane) {
-  const bool active = i < a.n;
+// kCompact (single-shape launch, blocks of 128 threads with one direction k):
+// after the neighbour pre-test the candidates still open in the block are
+// packed, in Morton order, into its first warps, so the walks run with full
+// warps (s_idx: 128 ints, s_wcnt: 4 ints of shared memory).  Without it each
+// warp walks for its own lanes (the batched launch, where warps take
+// independent work items).
+template <bool kCompact>
+__device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, int lane, int* s_idx, int* s_wcnt) {
+  bool active = i < a.n;
   const BuildConsts bc = *a.bc;
-  const float4 S = active ? a.sph[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const float r = fabsf(S.w);
+  float4 S = active ? a.sph[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  float r = fabsf(S.w);
   const float ux = a.U32[3 * k], uy = a.U32[3 * k + 1], uz = a.U32[3 * k + 2];
-  const float qx = fmaf(r, ux, S.x), qy = fmaf(r, uy, S.y), qz = fmaf(r, uz, S.z);
+  float qx = fmaf(r, ux, S.x), qy = fmaf(r, uy, S.y), qz = fmaf(r, uz, S.z);
   bool have64 = false;
   double qx64 = 0, qy64 = 0, qz64 = 0;
   unsigned long long rechecks = 0;
@@ -532,7 +539,6 @@ __device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, i
       if (!ex_inbox(qx64, qy64, qz64)) open = false;
     }
   }
-  const bool inbox = open;
   // the warp's 32 spheres are Morton-consecutive: the spheres of lanes
   // lane^1, ^2, ^4, ^8, ^16 are near neighbours, the balls most likely to
   // cover this lane's candidate; a lane they settle skips the walk
@@ -557,6 +563,35 @@ __device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, i
       }
     }
   }
+  // (a candidate that is still open here is in the box)
+  if constexpr (kCompact) {
+    const int wid = threadIdx.x >> 5;
+    const unsigned ballot = __ballot_sync(kFull, open);
+    if (lane == 0) s_wcnt[wid] = __popc(ballot);
+    __syncthreads();
+    int off = 0, total = 0;
+    for (int w = 0; w < 4; ++w) {
+      const int c = s_wcnt[w];
+      if (w < wid) off += c;
+      total += c;
+    }
+    if (open) s_idx[off + __popc(ballot & ((1u << lane) - 1u))] = int(threadIdx.x);
+    __syncthreads();
+    // this thread now walks for entry threadIdx.x of the packed list
+    if (rechecks) atomicAdd(&a.cnt->cull_rechecks, rechecks);
+    rechecks = 0;
+    if (wid * 32 >= total) return;  // warp-uniform: no entries left for this warp
+    open = int(threadIdx.x) < total;
+    i = open ? blockIdx.x * int64_t(blockDim.x) + s_idx[threadIdx.x] : a.n;
+    active = open;
+    S = open ? a.sph[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    r = fabsf(S.w);
+    qx = fmaf(r, ux, S.x);
+    qy = fmaf(r, uy, S.y);
+    qz = fmaf(r, uz, S.z);
+    have64 = false;
+  }
+  const bool inbox = open;
   const Tree& T = a.tree;
   const float grow = 1.f + 8.f * kU;
   if (__any_sync(kFull, open)) {
@@ -639,10 +674,13 @@ __device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, i
   }
 }
 
+constexpr bool kCullCompact = true;
 __global__ void __launch_bounds__(128) k_cull(CullArgs a) {
   __shared__ uint32_t s_stack[4][kPStack];
+  __shared__ int s_idx[128], s_wcnt[4];
   WarpStack W{s_stack[threadIdx.x >> 5], 0};
-  cull_packet(a, blockIdx.x * int64_t(blockDim.x) + threadIdx.x, blockIdx.y, W, threadIdx.x & 31);
+  cull_packet<kCullCompact>(a, blockIdx.x * int64_t(blockDim.x) + threadIdx.x, blockIdx.y, W, threadIdx.x & 31,
+                            s_idx, s_wcnt);
 }
 
 // ---------------------------------------------------------------------------
