@@ -140,7 +140,7 @@ struct gfs_ctx {
   DevBuf b_desc, b_offd, b_qoffd, b_sph64, b_k64in, b_k64out, b_sph, b_thr, b_sid, b_bits, b_bcs;
   DevBuf b_lo, b_hi, b_na, b_nb, b_nf, b_stdev, b_prefix, b_ctr, b_cnt, b_cviews, b_cw;
   DevBuf b_sraw[2], b_sshape[2], b_ssorted[2], b_vlo[2], b_vhi[2], b_vtdev[2], b_hist;
-  DevBuf b_qkin, b_qkout, b_qvin, b_qvout, b_qviews, b_qw;
+  DevBuf b_qkin, b_qkout, b_qvin, b_qvout, b_qviews, b_qw, b_qstate;
   unsigned b_cap = 0;
   unsigned b_nsurv[2] = {0, 0};
   int64_t b_M = 0, b_qtotal = 0;
@@ -810,12 +810,16 @@ float time_grid(gfs_ctx* c, bool cull, int grid, int64_t limit) {
   cudaEventCreate(&e1);
   cudaMemsetAsync(c->b_ctr.p, 0, 8, st);
   cudaEventRecord(e0, st);
-  if (cull)
+  if (cull) {
     launch_batch_cull(c->b_cviews.as<CullArgs>(), c->b_cw.as<int64_t>(), c->b_ns, limit,
                       c->b_ctr.as<unsigned long long>(), grid, st);
-  else
-    launch_batch_query(c->b_qviews.as<QueryArgs>(), c->b_qw.as<int64_t>(), c->b_ns, limit,
-                       c->b_ctr.as<unsigned long long>(), grid, st);
+  } else {
+    for (int phase = 1; phase <= 2; ++phase) {
+      cudaMemsetAsync(c->b_ctr.p, 0, 8, st);
+      launch_batch_query(c->b_qviews.as<QueryArgs>(), c->b_qw.as<int64_t>(), c->b_ns, limit,
+                         c->b_ctr.as<unsigned long long>(), grid, phase, st);
+    }
+  }
   cudaEventRecord(e1, st);
   cudaEventSynchronize(e1);
   float ms = 0.f;
@@ -1017,6 +1021,7 @@ int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
   GFS_TRY(ensure(c->b_qkout, size_t(std::max<int64_t>(M, 1)) * 8));
   GFS_TRY(ensure(c->b_qvin, size_t(std::max<int64_t>(M, 1)) * 4));
   GFS_TRY(ensure(c->b_qvout, size_t(std::max<int64_t>(M, 1)) * 4));
+  GFS_TRY(ensure(c->b_qstate, size_t(std::max<int64_t>(M, 1)) * 3 * sizeof(uint4)));
   for (int s = 0; s < ns; ++s) {
     QueryArgs& a = qv[s];
     std::memset(&a, 0, sizeof(a));
@@ -1041,6 +1046,7 @@ int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
     else a.x64 = static_cast<const double*>(shapes[s].x);
     a.m = shapes[s].m;
     a.perm = reinterpret_cast<const uint32_t*>(c->b_qvout.as<int>() + qoff[s]);
+    a.state = reinterpret_cast<uint4*>(c->b_qstate.p) + 3 * qoff[s];
     a.s_out = shapes[s].s_out;
     a.s64_out = shapes[s].s64_out;
     a.arg_out = shapes[s].argmin_out;
@@ -1081,10 +1087,12 @@ int gfs_batch_query(gfs_ctx* c) {
   size_t bytes = c->cub_temp.bytes;
   GFS_CK(sort_pairs64(c->cub_temp.p, bytes, c->b_qkin.as<unsigned long long>(), c->b_qkout.as<unsigned long long>(),
                       c->b_qvin.as<int>(), c->b_qvout.as<int>(), c->b_M, end_bit, st));
-  GFS_CK(cudaMemsetAsync(c->b_ctr.p, 0, 8, st));
   const int grid = c->b_grid_query ? c->b_grid_query : 152 * 4;
-  GFS_CK(launch_batch_query(c->b_qviews.as<QueryArgs>(), c->b_qw.as<int64_t>(), ns, c->b_qtotal,
-                            c->b_ctr.as<unsigned long long>(), grid, st));
+  for (int phase = 1; phase <= 2; ++phase) {
+    GFS_CK(cudaMemsetAsync(c->b_ctr.p, 0, 8, st));
+    GFS_CK(launch_batch_query(c->b_qviews.as<QueryArgs>(), c->b_qw.as<int64_t>(), ns, c->b_qtotal,
+                              c->b_ctr.as<unsigned long long>(), grid, phase, st));
+  }
   return GFS_OK;
 }
 
@@ -1239,7 +1247,7 @@ void gfs_destroy(gfs_ctx* c) {
                     &c->b_stdev, &c->b_prefix, &c->b_ctr, &c->b_cnt, &c->b_cviews, &c->b_cw, &c->b_sraw[0],
                     &c->b_sraw[1], &c->b_sshape[0], &c->b_sshape[1], &c->b_ssorted[0], &c->b_ssorted[1],
                     &c->b_vlo[0], &c->b_vlo[1], &c->b_vhi[0], &c->b_vhi[1], &c->b_vtdev[0], &c->b_vtdev[1],
-                    &c->b_hist, &c->b_qkin, &c->b_qkout, &c->b_qvin, &c->b_qvout, &c->b_qviews, &c->b_qw};
+                    &c->b_hist, &c->b_qkin, &c->b_qkout, &c->b_qvin, &c->b_qvout, &c->b_qviews, &c->b_qw, &c->b_qstate};
   for (DevBuf* b : bufs) release(*b);
   delete c;
 }

@@ -165,6 +165,9 @@ __global__ void __launch_bounds__(128) k_batch_cull(const CullArgs* __restrict__
 
 // Persistent query over all shapes: work item = (shape, 32 consecutive
 // points of the shape's Morton order).
+// kPhase 1: the sphere pass (state per point to the view's state array);
+// kPhase 2: the rest of the query (as the single-shape query's two kernels)
+template <int kPhase>
 __global__ void __launch_bounds__(128) k_batch_query(const QueryArgs* __restrict__ views,
                                                      const int64_t* __restrict__ wprefix, int ns, int64_t limit,
                                                      unsigned long long* __restrict__ ctr) {
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(128) k_batch_query(const QueryArgs* __restrict
     if (int64_t(w) >= limit) break;
     const int s = find_seg(wprefix, ns, int64_t(w));
     const int64_t wl = int64_t(w) - wprefix[s];
-    query_packet<true>(views[s], wl * 32 + lane, W, lane);
+    query_packet<true, kPhase>(views[s], wl * 32 + lane, W, lane);
   }
 }
 
@@ -250,8 +253,9 @@ cudaError_t launch_batch_cull(const CullArgs* views, const int64_t* wprefix, int
 }
 
 cudaError_t launch_batch_query(const QueryArgs* views, const int64_t* wprefix, int ns, int64_t limit,
-                               unsigned long long* ctr, int grid, cudaStream_t st) {
-  k_batch_query<<<grid, 128, 0, st>>>(views, wprefix, ns, limit, ctr);
+                               unsigned long long* ctr, int grid, int phase, cudaStream_t st) {
+  if (phase == 1) k_batch_query<1><<<grid, 128, 0, st>>>(views, wprefix, ns, limit, ctr);
+  else k_batch_query<2><<<grid, 128, 0, st>>>(views, wprefix, ns, limit, ctr);
   return cudaGetLastError();
 }
 

@@ -502,10 +502,11 @@ struct WarpStack {
 // the sphere hierarchy as a packet (one node at a time, children visited if
 // any lane still needs them); a lane drops out at the first ball that covers
 // its candidate, and the warp stops when every lane is settled.
-// kCompact (single-shape launch, blocks of 128 threads with one direction k):
-// after the neighbour pre-test the candidates still open in the block are
-// packed, in Morton order, into its first warps, so the walks run with full
-// warps (s_idx: 128 ints, s_wcnt: 4 ints of shared memory).  Without it each
+// kCompact (single-shape launch, blocks of kCullBlock threads with one
+// direction k): after the neighbour pre-test the candidates still open in
+// the block are packed, in Morton order, into its first warps, so the walks
+// run with full warps (s_idx: one int per thread, s_wcnt: one per warp, in
+// shared memory).  Without it each
 // warp walks for its own lanes (the batched launch, where warps take
 // independent work items).
 template <bool kCompact>
@@ -570,7 +571,7 @@ __device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, i
     if (lane == 0) s_wcnt[wid] = __popc(ballot);
     __syncthreads();
     int off = 0, total = 0;
-    for (int w = 0; w < 4; ++w) {
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
       const int c = s_wcnt[w];
       if (w < wid) off += c;
       total += c;
@@ -675,9 +676,10 @@ __device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, i
 }
 
 constexpr bool kCullCompact = true;
-__global__ void __launch_bounds__(128) k_cull(CullArgs a) {
-  __shared__ uint32_t s_stack[4][kPStack];
-  __shared__ int s_idx[128], s_wcnt[4];
+constexpr int kCullBlock = 128;
+__global__ void __launch_bounds__(kCullBlock) k_cull(CullArgs a) {
+  __shared__ uint32_t s_stack[kCullBlock / 32][kPStack];
+  __shared__ int s_idx[kCullBlock], s_wcnt[kCullBlock / 32];
   WarpStack W{s_stack[threadIdx.x >> 5], 0};
   cull_packet<kCullCompact>(a, blockIdx.x * int64_t(blockDim.x) + threadIdx.x, blockIdx.y, W, threadIdx.x & 31,
                             s_idx, s_wcnt);
@@ -1654,8 +1656,8 @@ cudaError_t launch_gather_points(const float4* src, const int* order, int64_t n,
 }
 
 cudaError_t launch_cull(const CullArgs& a, cudaStream_t st) {
-  dim3 grid(nblk(a.n, 128), unsigned(a.K));
-  k_cull<<<grid, 128, 0, st>>>(a);
+  dim3 grid(nblk(a.n, kCullBlock), unsigned(a.K));
+  k_cull<<<grid, kCullBlock, 0, st>>>(a);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -185,7 +185,9 @@ cudaError_t launch_batch_qkeys(const ShapeDesc* d, const int64_t* off, int ns, i
                                int* vals, cudaStream_t st);
 cudaError_t launch_batch_cull(const CullArgs* views, const int64_t* wprefix, int ns, int64_t limit,
                               unsigned long long* ctr, int grid, cudaStream_t st);
+// phase 1: the sphere pass of every (shape, 32 points) item, phase 2: the rest
+// (reset ctr between the two launches)
 cudaError_t launch_batch_query(const QueryArgs* views, const int64_t* wprefix, int ns, int64_t limit,
-                               unsigned long long* ctr, int grid, cudaStream_t st);
+                               unsigned long long* ctr, int grid, int phase, cudaStream_t st);
 
 }  // namespace gfs
