@@ -582,8 +582,9 @@ __device__ void cull_packet(const CullArgs& a, int64_t i, int k, WarpStack& W, i
     if (rechecks) atomicAdd(&a.cnt->cull_rechecks, rechecks);
     rechecks = 0;
     if (wid * 32 >= total) return;  // warp-uniform: no entries left for this warp
+    const int64_t blk_base = i - int64_t(threadIdx.x);  // the block's first sphere
     open = int(threadIdx.x) < total;
-    i = open ? blockIdx.x * int64_t(blockDim.x) + s_idx[threadIdx.x] : a.n;
+    i = open ? blk_base + s_idx[threadIdx.x] : a.n;
     active = open;
     S = open ? a.sph[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     r = fabsf(S.w);
