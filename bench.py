@@ -56,6 +56,10 @@ def parse():
                     help="run one sub-benchmark alone and print its JSON (profiling)")
     ap.add_argument("--insert-steps", type=int, default=1024)
     ap.add_argument("--repair-steps", type=int, default=8192)
+    ap.add_argument("--batch-shapes", type=int, default=256)
+    ap.add_argument("--batch-scale", type=float, default=0.5,
+                    help="scale of the batch shapes' grid sides and sample counts (1 = the full workload, "
+                         "~4 min of sub-benchmark)")
     ap.add_argument("--query-subsample", type=int, default=1,
                     help="use every k-th query point (small cases for profiler captures)")
     return ap.parse_args()
@@ -343,20 +347,22 @@ def extra_repair(T=8192):
             "far_violations": int(np.sum((fl & 0x20) != 0))}
 
 
-def extra_batch(count=64, scale=0.5):
-    """Shapes of the 256-shape batch (unions of 1-8 primitives; even index =
-    grid with 2x upsampled queries, odd = scattered samples with 8n uniform
-    queries), sizes scaled by `scale`: one batched build + persistent query
-    launch vs. the same shapes one by one; batched query replayed from a
-    captured CUDA graph."""
+def extra_batch(count=256, scale=0.5):
+    """The first `count` shapes of the 256-shape batch (unions of 1-8
+    primitives; even index = grid with 2x upsampled queries, odd = scattered
+    samples with 8n uniform queries), sizes scaled by `scale`: one batched
+    build + persistent query launches vs. the same shapes one by one; the
+    batched query is also replayed from a captured CUDA graph."""
     import torch
     from paper_2605_01919_gb300 import gfs
     from paper_2605_01919_gb300 import workloads as W
     shapes = []
+    t_gen = time.perf_counter()
     for i in range(count):
         w = W.batch_shape(i, scale=scale)
         shapes.append({"p": torch.from_numpy(w.p).cuda(), "s": torch.from_numpy(w.s).cuda(),
                        "x": torch.from_numpy(w.make_queries()).cuda()})
+    t_gen = time.perf_counter() - t_gen
     M = sum(int(sh["x"].shape[0]) for sh in shapes)
     Nn = sum(int(sh["p"].shape[0]) for sh in shapes)
     ctx = gfs.Context(tau=3)
@@ -383,7 +389,8 @@ def extra_batch(count=64, scale=0.5):
     return {"workload": f"batch{count}_scale{scale}_tau3", "shapes": count, "samples": Nn, "queries": M,
             "batched_build_ms": t_build, "batched_query_ms": t_query, "graph_replay_query_ms": t_graph,
             "batched_queries_per_s_incl_build": M / ((t_build + t_query) / 1e3),
-            "one_by_one_ms": t_single, "one_by_one_queries_per_s_incl_build": M / (t_single / 1e3)}
+            "one_by_one_ms": t_single, "one_by_one_queries_per_s_incl_build": M / (t_single / 1e3),
+            "input_generation_s": t_gen}
 
 
 def run_gfs(args):
@@ -515,7 +522,8 @@ def run_gfs(args):
         torch.cuda.empty_cache()
         line["extras"] = {}
         for name, fn in (("backward", extra_backward), ("repair", lambda: extra_repair(args.repair_steps)),
-                         ("insert", lambda: extra_insert(args.insert_steps)), ("batch", extra_batch)):
+                         ("insert", lambda: extra_insert(args.insert_steps)),
+                         ("batch", lambda: extra_batch(args.batch_shapes, args.batch_scale))):
             try:
                 line["extras"][name] = fn()
             except Exception as e:  # a failing sub-benchmark must not hide the headline line
@@ -534,7 +542,8 @@ if __name__ == "__main__":
     a = parse()
     if a.only:
         fn = {"backward": extra_backward, "repair": lambda: extra_repair(a.repair_steps),
-              "insert": lambda: extra_insert(a.insert_steps), "batch": extra_batch}[a.only]
+              "insert": lambda: extra_insert(a.insert_steps),
+              "batch": lambda: extra_batch(a.batch_shapes, a.batch_scale)}[a.only]
         print(json.dumps({a.only: fn()}), flush=True)
     elif a.impl == "reference":
         run_reference(a)

@@ -206,17 +206,19 @@ typedef struct {
   uint16_t* flags_out;  /* m result words */
 } gfs_shape;
 
-/* P build of many shapes at once: one persistent cull launch covers every
- * shape's candidates (the library keeps the shape table; the caller keeps the
- * buffers alive until the last gfs_batch_query).  Results per shape are those
- * of gfs_build on that shape alone.  The first build also picks the
- * persistent grid sizes by timing a few candidates (autotuning).
+/* P build of many shapes at once: one cull launch covers every shape's
+ * candidates, a block per (shape, direction, 128 spheres) item (the library
+ * keeps the shape table; the caller keeps the buffers alive until the last
+ * gfs_batch_query).  Results per shape are those of gfs_build on that shape
+ * alone.  The first build also picks the persistent query's grid size by
+ * timing a few candidates (autotuning).
  * Synchronises the stream.  Errors: GFS_ERR_ARG (nshapes < 1 or > 65535, a
  * shape with n < 1), GFS_ERR_TOO_LARGE, GFS_ERR_OOM, GFS_ERR_CUDA. */
 int gfs_batch_build(gfs_ctx* ctx, const gfs_shape* shapes_host, int nshapes);
 
-/* Queries of every shape of the last gfs_batch_build in one persistent
- * launch, into each shape's outputs.  Issues no host synchronisation and no
+/* Queries of every shape of the last gfs_batch_build in two persistent
+ * launches (the sphere pass of every point, then the rest), into each
+ * shape's outputs.  Issues no host synchronisation and no
  * allocation, so it can be captured in a CUDA graph and replayed (with new
  * point coordinates written into the same buffers).
  * Errors: GFS_ERR_STATE (no batch build), GFS_ERR_CUDA. */

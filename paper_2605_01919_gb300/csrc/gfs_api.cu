@@ -144,7 +144,7 @@ struct gfs_ctx {
   unsigned b_cap = 0;
   unsigned b_nsurv[2] = {0, 0};
   int64_t b_M = 0, b_qtotal = 0;
-  int b_grid_cull = 0, b_grid_query = 0;
+  int b_grid_query = 0;
   Counters host_cnt{};
   // host-buffer path (gfs_solve_host)
   DevBuf h_p, h_s, h_x, h_sout, h_arg, h_fl;
@@ -802,23 +802,18 @@ int sort64(gfs_ctx* c, unsigned long long* kin, unsigned long long* kout, int* v
   return GFS_OK;
 }
 
-// time one persistent launch configuration on a prefix of the work
-float time_grid(gfs_ctx* c, bool cull, int grid, int64_t limit) {
+// time one persistent query launch configuration (both phases) on a prefix
+// of the work
+float time_grid(gfs_ctx* c, int grid, int64_t limit) {
   cudaStream_t st = c->stream;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  cudaMemsetAsync(c->b_ctr.p, 0, 8, st);
   cudaEventRecord(e0, st);
-  if (cull) {
-    launch_batch_cull(c->b_cviews.as<CullArgs>(), c->b_cw.as<int64_t>(), c->b_ns, limit,
-                      c->b_ctr.as<unsigned long long>(), grid, st);
-  } else {
-    for (int phase = 1; phase <= 2; ++phase) {
-      cudaMemsetAsync(c->b_ctr.p, 0, 8, st);
-      launch_batch_query(c->b_qviews.as<QueryArgs>(), c->b_qw.as<int64_t>(), c->b_ns, limit,
-                         c->b_ctr.as<unsigned long long>(), grid, phase, st);
-    }
+  for (int phase = 1; phase <= 2; ++phase) {
+    cudaMemsetAsync(c->b_ctr.p, 0, 8, st);
+    launch_batch_query(c->b_qviews.as<QueryArgs>(), c->b_qw.as<int64_t>(), c->b_ns, limit,
+                       c->b_ctr.as<unsigned long long>(), grid, phase, st);
   }
   cudaEventRecord(e1, st);
   cudaEventSynchronize(e1);
@@ -829,8 +824,8 @@ float time_grid(gfs_ctx* c, bool cull, int grid, int64_t limit) {
   return ms;
 }
 
-// pick the persistent grid (blocks of 128 threads) for one kernel
-int autotune_grid(gfs_ctx* c, bool cull, int64_t total) {
+// the persistent query's grid: blocks per SM picked by timing a prefix
+int autotune_grid(gfs_ctx* c, int64_t total) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -839,7 +834,7 @@ int autotune_grid(gfs_ctx* c, bool cull, int64_t total) {
   int best = sms * 4;
   float best_ms = 1e30f;
   for (int m : cand) {
-    const float ms = time_grid(c, cull, sms * m, limit);
+    const float ms = time_grid(c, sms * m, limit);
     if (ms < best_ms) {
       best_ms = ms;
       best = sms * m;
@@ -914,7 +909,9 @@ int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
   GFS_TRY(forest_build(c, c->b_st, c->b_stdev, c->b_sph.as<float4>(), item_off, c->b_bcs.as<BuildConsts>(), 1, maxL));
   // culling views and work items (shape, direction, warp of 32 spheres)
   const uint64_t ncand = uint64_t(N) * uint64_t(c->K);
-  uint64_t cap = std::max<uint64_t>(uint64_t(1) << 16, ncand / 16 + 1024);
+  // survivors are typically < 1% of the candidates; the cull is rerun with
+  // room for the counted survivors if this first capacity overflows
+  uint64_t cap = std::max<uint64_t>(uint64_t(1) << 16, ncand / 64 + 1024);
   cap = std::min<uint64_t>(cap, 0xfffffff0u);
   std::vector<CullArgs> cv(ns);
   std::vector<int64_t> cw(ns + 1);
@@ -951,20 +948,14 @@ int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
       a.surv_shape[0] = c->b_sshape[0].as<uint16_t>();
       a.surv_shape[1] = c->b_sshape[1].as<uint16_t>();
       a.shape = s;
-      cw[s + 1] = cw[s] + (shapes[s].n + 31) / 32 * c->K;
+      cw[s + 1] = cw[s] + (shapes[s].n + 127) / 128 * c->K;
     }
     GFS_TRY(ensure(c->b_cviews, size_t(ns) * sizeof(CullArgs)));
     GFS_TRY(ensure(c->b_cw, size_t(ns + 1) * 8));
     GFS_CK(cudaMemcpyAsync(c->b_cviews.p, cv.data(), size_t(ns) * sizeof(CullArgs), cudaMemcpyHostToDevice, st));
     GFS_CK(cudaMemcpyAsync(c->b_cw.p, cw.data(), size_t(ns + 1) * 8, cudaMemcpyHostToDevice, st));
-    if (c->b_grid_cull == 0) {
-      c->b_ns = ns;
-      c->b_grid_cull = autotune_grid(c, true, cw[ns]);
-    }
     GFS_CK(cudaMemsetAsync(c->b_cnt.p, 0, sizeof(Counters), st));
-    GFS_CK(cudaMemsetAsync(c->b_ctr.p, 0, 8, st));
-    GFS_CK(launch_batch_cull(c->b_cviews.as<CullArgs>(), c->b_cw.as<int64_t>(), ns, cw[ns],
-                             c->b_ctr.as<unsigned long long>(), c->b_grid_cull, st));
+    GFS_CK(launch_batch_cull_blocks(c->b_cviews.as<CullArgs>(), c->b_cw.as<int64_t>(), ns, cw[ns], st));
     Counters hc;
     GFS_CK(cudaMemcpyAsync(&hc, c->b_cnt.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     GFS_CK(cudaStreamSynchronize(st));
@@ -1068,7 +1059,7 @@ int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
   c->b_built = true;
   if (c->b_grid_query == 0 && c->b_qtotal > 0) {
     GFS_TRY(gfs_batch_query(c));  // produces the Morton order used while tuning
-    c->b_grid_query = autotune_grid(c, false, c->b_qtotal);
+    c->b_grid_query = autotune_grid(c, c->b_qtotal);
   }
   GFS_CK(cudaStreamSynchronize(st));
   return GFS_OK;

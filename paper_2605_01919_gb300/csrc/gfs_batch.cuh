@@ -140,27 +140,23 @@ __global__ void k_batch_qkeys(const ShapeDesc* __restrict__ d, const int64_t* __
   vals[u] = int(i);
 }
 
-// Persistent cull over all shapes: work item = (shape, direction k, warp of
-// 32 Morton-consecutive spheres); `limit` caps the items (autotuning).
-__global__ void __launch_bounds__(128) k_batch_cull(const CullArgs* __restrict__ views,
-                                                    const int64_t* __restrict__ wprefix, int ns, int64_t limit,
-                                                    unsigned long long* __restrict__ ctr) {
+// Cull over all shapes as one flat launch: block b is item b of (shape,
+// direction k, 128 Morton-consecutive spheres), so the candidates left open
+// by the neighbour pre-test are packed into full warps as in the single-shape
+// cull, and the hardware schedules the uneven blocks.
+__global__ void __launch_bounds__(128) k_batch_cull_blocks(const CullArgs* __restrict__ views,
+                                                           const int64_t* __restrict__ bprefix, int ns) {
   __shared__ uint32_t s_stack[4][kPStack];
-  const int lane = threadIdx.x & 31;
+  __shared__ int s_idx[128], s_wcnt[4];
   WarpStack W{s_stack[threadIdx.x >> 5], 0};
-  for (;;) {
-    unsigned long long w = 0;
-    if (lane == 0) w = atomicAdd(ctr, 1ull);
-    w = __shfl_sync(kAllB, w, 0);
-    if (int64_t(w) >= limit) break;
-    const int s = find_seg(wprefix, ns, int64_t(w));
-    const CullArgs& a = views[s];
-    const int64_t local = int64_t(w) - wprefix[s];
-    const int64_t nw = (a.n + 31) / 32;
-    const int k = int(local / nw);
-    const int64_t wl = local - int64_t(k) * nw;
-    cull_packet<false>(a, wl * 32 + lane, k, W, lane, nullptr, nullptr);
-  }
+  const int64_t w = blockIdx.x;
+  const int s = find_seg(bprefix, ns, w);
+  const CullArgs& a = views[s];
+  const int64_t local = w - bprefix[s];
+  const int64_t nb128 = (a.n + 127) / 128;
+  const int k = int(local / nb128);
+  const int64_t bl = local - int64_t(k) * nb128;
+  cull_packet<true>(a, bl * 128 + threadIdx.x, k, W, threadIdx.x & 31, s_idx, s_wcnt);
 }
 
 // Persistent query over all shapes: work item = (shape, 32 consecutive
@@ -246,9 +242,11 @@ cudaError_t launch_batch_qkeys(const ShapeDesc* d, const int64_t* off, int ns, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_cull(const CullArgs* views, const int64_t* wprefix, int ns, int64_t limit,
-                              unsigned long long* ctr, int grid, cudaStream_t st) {
-  k_batch_cull<<<grid, 128, 0, st>>>(views, wprefix, ns, limit, ctr);
+cudaError_t launch_batch_cull_blocks(const CullArgs* views, const int64_t* bprefix, int ns, int64_t nblocks,
+                                     cudaStream_t st) {
+  if (nblocks <= 0) return cudaSuccess;
+  if (nblocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  k_batch_cull_blocks<<<unsigned(nblocks), 128, 0, st>>>(views, bprefix, ns);
   return cudaGetLastError();
 }
 

@@ -183,10 +183,12 @@ cudaError_t launch_batch_surv_keys(const float4* items, const uint16_t* shape, u
 cudaError_t launch_batch_gather_points(const float4* src, const int* order, unsigned n, float4* dst, cudaStream_t st);
 cudaError_t launch_batch_qkeys(const ShapeDesc* d, const int64_t* off, int ns, int64_t M, unsigned long long* keys,
                                int* vals, cudaStream_t st);
-cudaError_t launch_batch_cull(const CullArgs* views, const int64_t* wprefix, int ns, int64_t limit,
-                              unsigned long long* ctr, int grid, cudaStream_t st);
 // phase 1: the sphere pass of every (shape, 32 points) item, phase 2: the rest
 // (reset ctr between the two launches)
+// cull over all shapes, one block per (shape, k, 128 spheres) item: bprefix
+// holds each shape's first item, nblocks the total
+cudaError_t launch_batch_cull_blocks(const CullArgs* views, const int64_t* bprefix, int ns, int64_t nblocks,
+                                     cudaStream_t st);
 cudaError_t launch_batch_query(const QueryArgs* views, const int64_t* wprefix, int ns, int64_t limit,
                                unsigned long long* ctr, int grid, int phase, cudaStream_t st);
 
