@@ -205,11 +205,12 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 # the CUDA path
 # ----------------------------------------------------------------------------
-KERNEL_TU = ("gfs_kernels.cu", "gfs_batch.cuh", "gfs_internal.cuh", "gfs_kernels.h")
+KERNEL_TU = ("gfs_kernels.cu", "gfs_internal.cuh", "gfs_kernels.h")
 
 
 def kernel_hash() -> str:
-    """Hash of the translation unit that holds the query and cull kernels."""
+    """Hash of the sources of the single-shape query and cull kernels (the
+    batched kernels in gfs_batch.cuh are separate kernels)."""
     h = hashlib.sha256()
     for f in KERNEL_TU:
         h.update(open(os.path.join(ROOT, "paper_2605_01919_gb300", "csrc", f), "rb").read())
