@@ -141,6 +141,27 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def gpu_numa_cpus(gpu_index: int):
+    """CPUs of the NUMA node the GPU is attached to (from nvidia-smi's PCI bus
+    id and sysfs), or None.  Pinned host buffers first touched from those CPUs
+    sit next to the GPU's host link."""
+    try:
+        bus = subprocess.run(["nvidia-smi", f"--id={gpu_index}", "--query-gpu=pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True, timeout=20).stdout.strip()
+        dom, rest = bus.split(":", 1)
+        bdf = f"{int(dom, 16):04x}:{rest}".lower()
+        node = int(open(f"/sys/bus/pci/devices/{bdf}/numa_node").read())
+        if node < 0:
+            return None
+        cpus = set()
+        for part in open(f"/sys/devices/system/node/node{node}/cpulist").read().strip().split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        return node, cpus
+    except Exception:
+        return None
+
+
 # ----------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the same workload
 # ----------------------------------------------------------------------------
@@ -455,6 +476,13 @@ def run_gfs(args):
     # ---- end to end through the host-buffer entry point ----------------------
     e2e = None
     if not args.no_e2e:
+        # run the host side on the CPUs next to this GPU, so that the pinned
+        # buffers are placed in that node's memory (the previous affinity is
+        # restored afterwards)
+        numa = gpu_numa_cpus(local)
+        old_aff = os.sched_getaffinity(0)
+        if numa:
+            os.sched_setaffinity(0, numa[1] & old_aff or numa[1])
         ph = torch.from_numpy(w.p).pin_memory()
         sh = torch.from_numpy(w.s).pin_memory()
         xh_t = torch.from_numpy(xh).pin_memory()
@@ -473,8 +501,10 @@ def run_gfs(args):
             e_times.append(time.perf_counter() - t0)
         ctx_h.close()
         e_s = float(np.mean(e_times))
+        os.sched_setaffinity(0, old_aff)
         e2e = {"value": world * m / e_s, "unit": UNIT, "h2d_bytes_per_step": n * 24 + n * 8 + m * 24,
-               "d2h_bytes_per_step": m * (4 + 8 + 2), "ms_per_step": 1e3 * e_s}
+               "d2h_bytes_per_step": m * (4 + 8 + 2), "ms_per_step": 1e3 * e_s,
+               "host_numa_node": numa[0] if numa else None}
 
     # ---- roofline of the dominant kernel --------------------------------------
     # k_query_spheres, the first of the query's two FP32 kernels (the pass
