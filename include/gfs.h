@@ -101,7 +101,8 @@ int gfs_set_stream(gfs_ctx* ctx, void* cuda_stream);
  * s:     device, n FP64 signed distance samples.
  * Builds the sphere hierarchy, culls all n*K candidates and builds the
  * survivor hierarchies.  Inputs are copied; the caller may free them after
- * the call returns.  Synchronises the stream once to size the survivor set.
+ * the call returns.  Synchronises the stream twice (the coordinate bound
+ * that sets the hierarchy's rounding slack, and the survivor count).
  * Errors: GFS_ERR_ARG (n < 1, null), GFS_ERR_TOO_LARGE (n*(K+1) >= 2^32),
  * GFS_ERR_OOM, GFS_ERR_CUDA. */
 int gfs_build(gfs_ctx* ctx, const double* p_xyz, const double* s, int64_t n);
@@ -113,7 +114,13 @@ int gfs_build(gfs_ctx* ctx, const double* p_xyz, const double* s, int64_t n);
  * s64_out:   device, m FP64 values (nullable).
  * argmin_out:device, m int64 (nullable): candidate id or sphere index, per code.
  * flags_out: device, m uint16 result words (nullable).
- * Errors: GFS_ERR_STATE (no build), GFS_ERR_ARG, GFS_ERR_CUDA. */
+ * Runs as two kernels (the pass over the spheres, then the pass over the
+ * survivors and the exact re-evaluations) plus, for points outside the FP32
+ * error model's coordinate range, the FP64 kernel.  Grows library-owned
+ * scratch when m grows (Morton keys and order, 48 B of state per point).
+ * No host synchronisation.
+ * Errors: GFS_ERR_STATE (no build), GFS_ERR_ARG, GFS_ERR_TOO_LARGE
+ * (m >= 2^32), GFS_ERR_OOM, GFS_ERR_CUDA. */
 int gfs_query(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, float* s_out, double* s64_out,
               int64_t* argmin_out, uint16_t* flags_out);
 
