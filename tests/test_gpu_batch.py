@@ -85,3 +85,55 @@ def test_batch_query_cuda_graph_replay(G):
         assert torch.equal(o["flags"], f["flags"])
         assert torch.equal(o["s64"].view(torch.int64), f["s64"].view(torch.int64))
     ctx.close()
+
+
+def _lazy_worker(args):
+    from oracle import oracle as O
+    p, s, tau, x = args
+    return O.query_lazy(p, s, O.icosphere(tau), x)
+
+
+def test_batch_all_256_shapes_tau3_sampled(G, orc):
+    """All 256 shapes of the batch workload (tau 3, half-size grids and
+    sample counts: 10.2M samples, 80M queries) in one batched build and
+    query: 8 shapes spread over the batch equal the single-shape path
+    bitwise, and a few of their outputs and candidates equal the oracle's."""
+    import multiprocessing as mp
+    tau = 3
+    ws = [W.batch_shape(i, tau=tau, scale=0.5) for i in range(256)]
+    xs = [torch.from_numpy(w.make_queries()).cuda() for w in ws]
+    ctx = G.Context(tau=tau)
+    outs = ctx.batch_build([{"p": torch.from_numpy(w.p).cuda(), "s": torch.from_numpy(w.s).cuda(), "x": x}
+                            for w, x in zip(ws, xs)])
+    ctx.batch_query()
+    torch.cuda.synchronize()
+    picks = [0, 1, 37, 100, 129, 200, 254, 255]
+    rng = np.random.default_rng(5)
+    jobs, checks = [], []
+    for k in picks:
+        w = ws[k]
+        single = G.Context(tau=tau)
+        single.build(torch.from_numpy(w.p).cuda(), torch.from_numpy(w.s).cuda())
+        ref = single.query(xs[k])
+        for key in ("flags", "argmin"):
+            assert torch.equal(outs[k][key], ref[key]), (k, key)
+        assert torch.equal(outs[k]["s64"].view(torch.int64), ref["s64"].view(torch.int64)), k
+        surv = ctx.batch_survivors(k)
+        assert torch.equal(surv, single.survivors()), k
+        single.close()
+        # candidate keep decisions and two queries per shape against the oracle
+        U = orc.icosphere(tau)
+        K = U.shape[0]
+        survset = set(int(g) for g in surv.cpu().numpy())
+        for i, kk in zip(rng.integers(0, w.n, 40), rng.integers(0, K, 40)):
+            assert orc.keep_one(w.p, w.s, U, int(i), int(kk)) == ((int(i) * (K + 1) + int(kk)) in survset)
+        sel = rng.choice(xs[k].shape[0], 2, replace=False)
+        jobs.append((w.p, w.s, tau, xs[k].cpu().numpy()[sel].astype(np.float64)))
+        checks.append((k, sel))
+    with mp.get_context("spawn").Pool(min(16, mp.cpu_count())) as pool:
+        res = pool.map(_lazy_worker, jobs, chunksize=1)
+    for (k, sel), (val, arg, fl, _) in zip(checks, res):
+        assert np.array_equal(outs[k]["argmin"].cpu().numpy()[sel], arg), k
+        assert np.array_equal(outs[k]["flags"].cpu().numpy()[sel].astype(np.int32) & 0xFFFF, fl), k
+        assert np.array_equal(outs[k]["s64"].cpu().numpy()[sel], val, equal_nan=True), k
+    ctx.close()
