@@ -165,43 +165,62 @@ def gpu_numa_cpus(gpu_index: int):
 # ----------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the same workload
 # ----------------------------------------------------------------------------
-def oracle_sample(w, x, n_keep: int, n_query: int, seed: int):
-    """Time keep decisions of n_keep random candidates and the consistent
-    value at n_query random queries (lazy FP64 oracle); return per-unit s."""
+_ORC = {}
+
+
+def _oracle_init(p, s, tau):
+    """Worker start-up: the workload and the icosphere table, loaded once."""
     from oracle import oracle as O
-    U = O.icosphere(w.tau)
-    K = U.shape[0]
-    rng = np.random.default_rng(seed)
-    ii = rng.integers(0, w.n, n_keep)
-    kk = rng.integers(0, K, n_keep)
-    t0 = time.perf_counter()
-    for i, k in zip(ii, kk):
-        O.keep_one(w.p, w.s, U, int(i), int(k))
-    t_keep = (time.perf_counter() - t0) / n_keep
-    sel = rng.integers(0, x.shape[0], n_query)
-    t0 = time.perf_counter()
-    O.query_lazy(w.p, w.s, U, x[sel])
-    t_q = (time.perf_counter() - t0) / n_query
-    return t_keep, t_q, K
+    _ORC.update(O=O, p=p, s=s, U=O.icosphere(tau))
 
 
-def cpu_baseline_line(w, x, steps: int, n_keep: int = 400, n_query: int = 2):
+def _oracle_chunk(args):
+    """One worker's share of an oracle sample: keep decisions for the given
+    (sphere, direction) pairs, then the lazy oracle at the given points."""
+    pairs, xq = args
+    O, p, s, U = _ORC["O"], _ORC["p"], _ORC["s"], _ORC["U"]
+    for i, k in pairs:
+        O.keep_one(p, s, U, int(i), int(k))
+    if len(xq):
+        O.query_lazy(p, s, U, xq)
+    return True
+
+
+def cpu_baseline_line(w, x, steps: int, n_keep: int = 2000, n_query: int = 2, procs: int | None = None):
+    """The FP64 oracle on the host cores: `procs` spawned worker processes
+    (default: all cores, at most 16) each time keep decisions and lazy
+    queries of a seeded random sample; the wall-clock time per unit of each
+    phase, over all workers, is extrapolated to the whole workload."""
+    import multiprocessing as mp
+    procs = procs or max(1, min(16, os.cpu_count() or 1))
+    K = 10 * 4 ** w.tau + 2
     tk, tq = [], []
-    K = 0
-    for st in range(steps):
-        a, b, K = oracle_sample(w, x, n_keep, n_query, seed=st)
-        tk.append(a)
-        tq.append(b)
+    with mp.get_context("spawn").Pool(procs, initializer=_oracle_init, initargs=(w.p, w.s, w.tau)) as pool:
+        pool.map(_oracle_chunk, [([], np.zeros((0, 3)))] * procs)   # start-up, not timed
+        for st in range(steps):
+            rng = np.random.default_rng(st)
+            ii = rng.integers(0, w.n, n_keep * procs)
+            kk = rng.integers(0, K, n_keep * procs)
+            jobs = [(list(zip(ii[c::procs], kk[c::procs])), np.zeros((0, 3))) for c in range(procs)]
+            t0 = time.perf_counter()
+            pool.map(_oracle_chunk, jobs, chunksize=1)
+            tk.append((time.perf_counter() - t0) / (n_keep * procs))
+            sel = rng.integers(0, x.shape[0], n_query * procs)
+            jobs = [([], x[sel[c:c + 1]].astype(np.float64)) for c in range(sel.size)]
+            t0 = time.perf_counter()
+            pool.map(_oracle_chunk, jobs, chunksize=1)
+            tq.append((time.perf_counter() - t0) / sel.size)
     t_keep, t_q = float(np.mean(tk)), float(np.mean(tq))
     total = w.n * K * t_keep + x.shape[0] * t_q
     return {
         "value": x.shape[0] / total,
         "unit": UNIT,
-        "cores": 1,
+        "cores": procs,
         "kind": "oracle",
-        "sample": (f"{steps} x ({n_keep} random candidate keep decisions + {n_query} random queries, lazy FP64 "
-                   f"oracle, single thread); extrapolated to {w.n * K} candidates + {x.shape[0]} queries: "
-                   f"{t_keep * 1e3:.3f} ms/candidate, {t_q:.3f} s/query"),
+        "sample": (f"{steps} x ({n_keep * procs} random candidate keep decisions + {n_query * procs} random "
+                   f"queries, lazy FP64 oracle, {procs} worker processes); extrapolated to {w.n * K} "
+                   f"candidates + {x.shape[0]} queries from the wall-clock time per unit: "
+                   f"{t_keep * 1e3:.4f} ms/candidate, {t_q:.3f} s/query"),
     }
 
 
@@ -212,7 +231,7 @@ def run_reference(args):
     from paper_2605_01919_gb300 import workloads as W
     w = W.union_grid()
     x = w.make_queries()
-    cb = cpu_baseline_line(w, x, max(1, args.warmup + args.steps), n_keep=300, n_query=1)
+    cb = cpu_baseline_line(w, x, max(1, args.warmup + args.steps), n_keep=1000, n_query=1)
     line = {
         "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * x.shape[0] / cb["value"],
@@ -561,7 +580,7 @@ def run_gfs(args):
                 line["extras"][name] = {"error": f"{type(e).__name__}: {e}"}
             torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_line(w, xh, steps=2, n_keep=400, n_query=6)
+        line["cpu_baseline"] = cpu_baseline_line(w, xh, steps=2, n_keep=2000, n_query=2)
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
