@@ -46,6 +46,7 @@
 #define CODE_OUTSIDE 3   /* x lies in no ball: value 0 (Prop. 2 proof) */
 #define CODE_INVALID 4   /* x lies in balls of both signs (input violates Prop. 1) */
 #define CODE_LOWER 5     /* no candidate at all: value = lower bound LB */
+#define CODE_TANGENT 6   /* augmented query: value = distance to an uncovered same-sign tangent point */
 /* violation bits (shifted by 4) */
 #define FLAG_LB_VIOL (1 << 4)
 #define FLAG_FAR_VIOL (1 << 5)
@@ -380,6 +381,85 @@ void orc_query(const double* p, const double* s, int64_t n, const int64_t* sg, c
     argmin[t] = R.argmin;
     flags[t] = R.flags;
     if (gap) gap[t] = R.gap;
+  }
+}
+
+/* Query with same-sign tangent augmentation (the tangent points T of
+ * Def. 1 of the spheres of x's own sign, Sec. 3.2 / Sec. 6): besides the
+ * surviving candidates, the candidate set holds, for every sphere j with
+ * sign(s_j) = sign of x and |s_j| > 0, its near and far tangent points in
+ * the direction of x, t = p_j +- |s_j| (x - p_j)/|x - p_j| (none when
+ * x = p_j), kept when they lie in no ball but j's own (shrunk by tol) and,
+ * with box_cull, in the box.  The nearest candidate (squared distances;
+ * survivors win ties, then the lowest 2j + side, side 0 near, 1 far) gives
+ * the value, clamped by UB_opp exactly as in orc_query; a tangent winner has
+ * code TANGENT and argmin 2j + side.  Brute force: O(n^2) per point. */
+void orc_query_aug(const double* p, const double* s, int64_t n, const int64_t* sg, const int64_t* ssph,
+                   const double* sq, int64_t ns, double tol, int clamp_opp, int box_cull, const double* x,
+                   int64_t m, double* value, int64_t* argmin, int32_t* flags) {
+  for (int64_t t = 0; t < m; ++t) {
+    const double* xq = x + 3 * t;
+    orc_result R = query_one(p, s, n, sg, ssph, sq, ns, tol, clamp_opp, xq, 0);
+    const int code = R.flags & 15;
+    if (code != CODE_SURVIVOR && code != CODE_OPPOSITE && code != CODE_LOWER) {
+      value[t] = R.value;
+      argmin[t] = R.argmin;
+      flags[t] = R.flags;
+      continue;
+    }
+    int sig = 0; /* x's class, from containment (the value may be 0) */
+    classify(p, s, n, tol, xq, &sig);
+    /* the nearest uncovered same-sign tangent point */
+    double tbest = ORC_INF;
+    int64_t tid = -1;
+    for (int64_t j = 0; j < n; ++j) {
+      if (sgn(s[j]) != sig) continue;
+      const double r = fabs(s[j]);
+      const double* pj = p + 3 * j;
+      double v[3] = {xq[0] - pj[0], xq[1] - pj[1], xq[2] - pj[2]};
+      const double dv = norm3(v);
+      if (!(dv > 0.0)) continue;
+      for (int side = 0; side < 2; ++side) {
+        const double sgnr = side == 0 ? r : -r;
+        double tp[3];
+        for (int c = 0; c < 3; ++c) tp[c] = pj[c] + sgnr * (v[c] / dv);
+        if (box_cull && !inbox(tp)) continue;
+        int cov = 0;
+        for (int64_t k = 0; k < n && !cov; ++k)
+          if (k != j && covers(tp, p + 3 * k, s[k], tol)) cov = 1;
+        if (cov) continue;
+        const double d2 = dist2(xq, tp);
+        const int64_t id = 2 * j + side;
+        if (d2 < tbest || (d2 == tbest && id < tid)) {
+          tbest = d2;
+          tid = id;
+        }
+      }
+    }
+    /* survivors first: recompute their nearest (d2, g) for the comparison */
+    double sbest = ORC_INF;
+    int64_t sgbest = -1;
+    for (int64_t u = 0; u < ns; ++u) {
+      int c = sgn(s[ssph[u]]);
+      if (c != sig && c != 0) continue;
+      double d2 = dist2(xq, sq + 3 * u);
+      if (d2 < sbest || (d2 == sbest && sg[u] < sgbest)) {
+        sbest = d2;
+        sgbest = sg[u];
+      }
+    }
+    if (tid >= 0 && tbest < sbest) {
+      /* a tangent point is the nearest candidate: same clamp and checks */
+      orc_result T = finish(p, s, n, tol, clamp_opp, xq, sig, tbest, 0, ORC_INF);
+      if ((T.flags & 15) == CODE_SURVIVOR) {
+        T.flags = (T.flags & ~15) | CODE_TANGENT;
+        T.argmin = tid;
+      }
+      R = T;
+    }
+    value[t] = R.value;
+    argmin[t] = R.argmin;
+    flags[t] = R.flags;
   }
 }
 

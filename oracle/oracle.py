@@ -22,7 +22,7 @@ _LIB = os.path.join(_LIB_DIR, "libgfs_oracle.so")
 
 TOL = 1e-6  # App. B: "all other tolerances are 1e-6"
 
-CODE_SURVIVOR, CODE_OPPOSITE, CODE_SAMPLE, CODE_OUTSIDE, CODE_INVALID, CODE_LOWER = range(6)
+CODE_SURVIVOR, CODE_OPPOSITE, CODE_SAMPLE, CODE_OUTSIDE, CODE_INVALID, CODE_LOWER, CODE_TANGENT = range(7)
 FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 16, 32, 64, 128
 FLAG_NONCONSERVATIVE = 256
 
@@ -56,6 +56,7 @@ def lib():
         L.orc_collect.argtypes = [P, P, i64, P, i32, P, P, P, P]
         L.orc_collect.restype = i64
         L.orc_query.argtypes = [P, P, i64, P, P, P, i64, f64, i32, P, i64, P, P, P, P]
+        L.orc_query_aug.argtypes = [P, P, i64, P, P, P, i64, f64, i32, i32, P, i64, P, P, P]
         L.orc_query.restype = None
         L.orc_query_lazy.argtypes = [P, P, i64, P, i32, f64, i32, i32, P, i64, P, P, P, P]
         L.orc_query_lazy.restype = None
@@ -130,6 +131,22 @@ def query(p, s, surv, x, tol=TOL, clamp_opp=True):
         lib().orc_query(_ptr(p), _ptr(s), s.shape[0], _ptr(g), _ptr(sph), _ptr(q), g.shape[0], tol,
                         int(clamp_opp), _ptr(x), m, _ptr(val), _ptr(arg), _ptr(fl), _ptr(gap))
     return val, arg, fl, gap
+
+
+def query_aug(p, s, surv, x, tol=TOL, clamp_opp=True, box_cull=True):
+    """As ``query``, with the candidate set augmented by the uncovered near
+    and far tangent points of the spheres of x's own sign (code TANGENT,
+    argmin 2j + side).  Returns (value, argmin, flags)."""
+    p, s, x = _c(p, np.float64), _c(s, np.float64), _c(x, np.float64)
+    g, sph, q = (_c(surv[0], np.int64), _c(surv[1], np.int64), _c(surv[2], np.float64))
+    m = x.shape[0]
+    val = np.zeros(m, np.float64)
+    arg = np.zeros(m, np.int64)
+    fl = np.zeros(m, np.int32)
+    if m:
+        lib().orc_query_aug(_ptr(p), _ptr(s), s.shape[0], _ptr(g), _ptr(sph), _ptr(q), g.shape[0], tol,
+                            int(clamp_opp), int(box_cull), _ptr(x), m, _ptr(val), _ptr(arg), _ptr(fl))
+    return val, arg, fl
 
 
 def query_lazy(p, s, U, x, tol=TOL, box_cull=True, clamp_opp=True):

@@ -447,3 +447,55 @@ def test_insert_known_sign_single_sphere_closed_forms(orc):
     K = U.shape[0]
     assert np.array_equal(st["g"], [1 * (K + 1) + k for k in range(K + 1)])   # zero sphere at y: all survive
     assert np.allclose(st["q"], y[0])
+
+
+# ----------------------------------------------------------------------------
+# same-sign tangent augmentation (the first "next" item: oracle side)
+# ----------------------------------------------------------------------------
+
+def test_query_aug_single_sphere_is_the_ball_distance(orc):
+    """One sphere, points inside its ball: the near tangent point is
+    uncovered, so the augmented value is sign * (r - |x - p|), the distance
+    to the sphere, which no icosphere candidate reaches exactly."""
+    U = orc.icosphere(2)
+    rng = np.random.default_rng(41)
+    for sgn in (1.0, -1.0):
+        p = np.array([[0.1, -0.05, 0.02]])
+        s = np.array([0.3 * sgn])
+        surv = orc.collect(p, s, U, orc.keep_all(p, s, U))
+        x = p[0] + rng.uniform(-0.15, 0.15, size=(50, 3))
+        d = np.linalg.norm(x - p[0], axis=1)
+        x, d = x[d < 0.29], d[d < 0.29]
+        val, arg, fl = orc.query_aug(p, s, surv, x)
+        assert np.all(fl & 15 == orc.CODE_TANGENT) and np.all(arg == 0)
+        assert np.all(np.abs(np.abs(val) - (0.3 - d)) < 1e-14) and np.all(np.sign(val) == sgn)
+        plain = orc.query(p, s, surv, x)[0]
+        assert np.all(np.abs(val) <= np.abs(plain))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_query_aug_between_exact_and_plain(orc, seed):
+    """exact r_min <= |s_aug| <= |s_tau| on valid tiny inputs (tol = 0, no
+    box): the added candidates are uncovered tangent points (members of T in
+    Def. 1) and the candidate set only grows; where no tangent point wins the
+    result equals the plain query's."""
+    p, s = W.tiny_random(14, seed)
+    rng = np.random.default_rng(100 + seed)
+    x = rng.uniform(-0.4, 0.4, size=(60, 3))
+    U = orc.icosphere(2)
+    keep = orc.keep_all(p, s, U, tol=0.0, box_cull=False)
+    surv = orc.collect(p, s, U, keep)
+    v0, a0, f0, _ = orc.query(p, s, surv, x, tol=0.0)
+    v1, a1, f1 = orc.query_aug(p, s, surv, x, tol=0.0, box_cull=False)
+    won = (f1 & 15) == orc.CODE_TANGENT
+    assert np.array_equal(v1[~won], v0[~won], equal_nan=True)
+    assert np.array_equal(a1[~won], a0[~won]) and np.array_equal(f1[~won], f0[~won])
+    assert won.any()
+    checked = 0
+    for t in np.nonzero(won)[0]:
+        assert abs(v1[t]) < abs(v0[t]) and np.sign(v1[t]) == np.sign(v0[t])
+        sig = 1 if v1[t] > 0 else -1
+        ex = orc.exact_rmin(p, s, x[t], sig, tol=0.0)
+        assert ex <= abs(v1[t]) + 1e-9
+        checked += 1
+    assert checked >= 3
