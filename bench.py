@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sub-benchmarks of the backward, insertion and batched paths")
-    ap.add_argument("--only", choices=["backward", "repair", "insert", "batch"], default=None,
+    ap.add_argument("--only", choices=["backward", "repair", "insert", "batch", "tangent"], default=None,
                     help="run one sub-benchmark alone and print its JSON (profiling)")
     ap.add_argument("--insert-steps", type=int, default=1024)
     ap.add_argument("--repair-steps", type=int, default=8192)
@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--batch-scale", type=float, default=0.5,
                     help="scale of the batch shapes' grid sides and sample counts (1 = the full workload, "
                          "~4 min of sub-benchmark)")
+    ap.add_argument("--tangent-every", type=int, default=256,
+                    help="tangent sub-benchmark: use every k-th of the 253^3 points (the pass is FP64, one "
+                         "thread per point)")
     ap.add_argument("--query-subsample", type=int, default=1,
                     help="use every k-th query point (small cases for profiler captures)")
     return ap.parse_args()
@@ -434,6 +437,38 @@ def extra_batch(count=256, scale=0.5):
             "input_generation_s": t_gen}
 
 
+def extra_tangent(every=256):
+    """Same-sign tangent augmentation (Def. 1 tangent points as candidates,
+    gfs_query_tangent) on the 64^3 union grid, tau 3, with its 253^3 points
+    (every k-th): the plain query, and the query followed by the tangent pass;
+    how many values a tangent point lowers."""
+    import torch
+    from paper_2605_01919_gb300 import gfs
+    from paper_2605_01919_gb300 import workloads as W
+    w = W.union_grid()
+    x = torch.from_numpy(np.ascontiguousarray(w.make_queries()[::every])).cuda()
+    m = int(x.shape[0])
+    ctx = gfs.Context(tau=w.tau)
+    ctx.build(torch.from_numpy(w.p).cuda(), torch.from_numpy(w.s).cuda())
+    out = {"s": torch.empty(m, dtype=torch.float32, device="cuda"),
+           "argmin": torch.empty(m, dtype=torch.int64, device="cuda"),
+           "flags": torch.empty(m, dtype=torch.int16, device="cuda")}
+
+    def plain():
+        ctx.query_into(x, out["s"], None, out["argmin"], out["flags"])
+
+    def both():
+        plain()
+        ctx.tangent_into(x, out["s"], None, out["argmin"], out["flags"])
+    t_plain = _ev_time(plain, reps=2)
+    t_both = _ev_time(both, reps=2)
+    won = int(((out["flags"].to(torch.int32) & 15) == gfs.CODE_TANGENT).sum().item())
+    ctx.close()
+    return {"workload": f"union64_tau3_253^3_points_every{every}", "queries": m, "query_ms": t_plain,
+            "query_plus_tangent_ms": t_both, "tangent_pass_ms": t_both - t_plain, "tangent_wins": won,
+            "queries_per_s_with_tangent": m / (t_both / 1e3)}
+
+
 def run_gfs(args):
     import torch
     import torch.distributed as dist
@@ -573,7 +608,8 @@ def run_gfs(args):
         line["extras"] = {}
         for name, fn in (("backward", extra_backward), ("repair", lambda: extra_repair(args.repair_steps)),
                          ("insert", lambda: extra_insert(args.insert_steps)),
-                         ("batch", lambda: extra_batch(args.batch_shapes, args.batch_scale))):
+                         ("batch", lambda: extra_batch(args.batch_shapes, args.batch_scale)),
+                         ("tangent", lambda: extra_tangent(args.tangent_every))):
             try:
                 line["extras"][name] = fn()
             except Exception as e:  # a failing sub-benchmark must not hide the headline line
@@ -593,7 +629,8 @@ if __name__ == "__main__":
     if a.only:
         fn = {"backward": extra_backward, "repair": lambda: extra_repair(a.repair_steps),
               "insert": lambda: extra_insert(a.insert_steps),
-              "batch": lambda: extra_batch(a.batch_shapes, a.batch_scale)}[a.only]
+              "batch": lambda: extra_batch(a.batch_shapes, a.batch_scale),
+              "tangent": lambda: extra_tangent(a.tangent_every)}[a.only]
         print(json.dumps({a.only: fn()}), flush=True)
     elif a.impl == "reference":
         run_reference(a)

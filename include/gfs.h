@@ -65,6 +65,8 @@ extern "C" {
 #define GFS_CODE_OUTSIDE 3   /* x lies in no (shrunk) ball: value 0; argmin = -1 */
 #define GFS_CODE_INVALID 4   /* x lies in balls of both signs: value NaN; argmin = -1 */
 #define GFS_CODE_LOWER 5     /* no candidate at all: value = lower bound; argmin = sphere */
+#define GFS_CODE_TANGENT 6   /* gfs_query_tangent: value = distance to an uncovered same-sign tangent point;
+                                argmin = 2 * sphere + side (0 near, 1 far) */
 /* violation bits (Sec. 4.3 bound checks) */
 #define GFS_FLAG_LB_VIOL 0x10     /* |s| < LB - tol  (LB: nearest-tangent bound of the containing spheres) */
 #define GFS_FLAG_FAR_VIOL 0x20    /* |s| > FAR + tol (FAR: nearest far tangent point of any sphere) */
@@ -123,6 +125,29 @@ int gfs_build(gfs_ctx* ctx, const double* p_xyz, const double* s, int64_t n);
  * (m >= 2^32), GFS_ERR_OOM, GFS_ERR_CUDA. */
 int gfs_query(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, float* s_out, double* s64_out,
               int64_t* argmin_out, uint16_t* flags_out);
+
+/* Same-sign tangent augmentation of a gfs_query result (Def. 1: the grow-to
+ * points T include the tangent points of the spheres in the direction of x;
+ * Sec. 6 min_valid_radius takes them as candidates).  For every point whose
+ * code is SURVIVOR, OPPOSITE or LOWER, the candidate set is extended by the
+ * near and far tangent points t = p_j +- |s_j| (x - p_j)/|x - p_j| of every
+ * sphere j of x's sign class (none when x = p_j), kept when no other ball,
+ * shrunk by tol, contains t and (box_cull) t lies in [-1,1]^3.  The nearest
+ * candidate (squared distances; a survivor wins a tie, then the lowest
+ * 2j + side) sets the value, clamped by UB_opp as in gfs_query, with the same
+ * bound checks; a tangent winner gets code GFS_CODE_TANGENT and argmin
+ * 2j + side (side 0 near, 1 far).  Other points are left unchanged.
+ * Decisions are taken in FP64 (one thread per point; slower than gfs_query).
+ * x, m:       the points of the preceding gfs_query on this context.
+ * argmin_out, flags_out: that call's outputs (device, required): read, then
+ *             rewritten in place where a tangent point wins.
+ * s_out, s64_out: its value outputs (device, nullable), rewritten likewise.
+ * gfs_query_backward differentiates TANGENT results as distances to the
+ * moving tangent point (d|x - t|/dx = +-(x - p_j)/|x - p_j|).
+ * No host synchronisation, no allocation.  Errors: GFS_ERR_STATE (no build),
+ * GFS_ERR_ARG, GFS_ERR_TOO_LARGE (m >= 2^32), GFS_ERR_CUDA. */
+int gfs_query_tangent(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, float* s_out, double* s64_out,
+                      int64_t* argmin_out, uint16_t* flags_out);
 
 /* Adjoint of gfs_query through the argmin (the paper has no gradients; the
  * value is piecewise a distance to a point or a sphere, differentiated here).

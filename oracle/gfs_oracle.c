@@ -578,6 +578,9 @@ void orc_query_lazy(const double* p, const double* s, int64_t n, const double* U
  *   ds/dx = sigma w, ds/dp_j = -sigma w, ds/ds_j = -sigma sign(s_j).
  * LOWER j: s = sigma (r_j - |x - p_j|): ds/dx = -sigma w, ds/dp_j = sigma w,
  *   ds/ds_j = sigma sign(s_j).
+ * TANGENT 2j+side (augmented query): s = sigma |d - e r_j|, d = |x - p_j|,
+ *   e = +1 (near) / -1 (far), h = sign(d - e r_j): ds/dx = sigma h w,
+ *   ds/dp_j = -sigma h w, ds/ds_j = -sigma e h sign(s_j).
  * SAMPLE i: ds/ds_i = 1.  OUTSIDE / INVALID / zero distance: 0. */
 void orc_grad(const double* p, const double* s, int64_t n, const double* U, int K, const double* x, int64_t m,
               const double* value, const int64_t* argmin, const int32_t* flags, const double* gup, double* gx,
@@ -624,6 +627,25 @@ void orc_grad(const double* p, const double* s, int64_t n, const double* U, int 
         gp[3 * j + c] += -g * sigma * dir * w[c];
       }
       gs[j] += -g * sigma * dir * sj;
+    } else if (code == CODE_TANGENT) {
+      /* value sigma * |x - t|, t = p_j + e r (x - p_j)/|x - p_j| (e = +1 near,
+       * -1 far): |x - t| = |d - e r| with d = |x - p_j|, so with
+       * w = (x - p_j)/d and h = sign(d - e r) it moves as h w in x, -h w in
+       * p_j and -e h in r = |s_j| */
+      int64_t j = argmin[t] / 2;
+      double e = (argmin[t] % 2) ? -1.0 : 1.0;
+      double w[3] = {xq[0] - p[3 * j], xq[1] - p[3 * j + 1], xq[2] - p[3 * j + 2]};
+      double d = norm3(w);
+      if (!(d > 0)) continue;
+      w[0] /= d; w[1] /= d; w[2] /= d;
+      double r = fabs(s[j]);
+      double h = d - e * r >= 0.0 ? 1.0 : -1.0;
+      double sj = (double)sgn(s[j]);
+      for (int c = 0; c < 3; ++c) {
+        gx[3 * t + c] = g * sigma * h * w[c];
+        gp[3 * j + c] += -g * sigma * h * w[c];
+      }
+      gs[j] += g * sigma * (-e * h) * sj;
     }
   }
 }

@@ -12,6 +12,7 @@
 
 #include "gfs.h"
 #include "gfs_kernels.h"
+#include "gfs_tangent.h"
 
 using namespace gfs;
 
@@ -531,7 +532,27 @@ int gfs_query_backward(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, cons
   a.KS = c->KS;
   a.acc_p = c->acc.as<long long>();
   a.acc_s = c->acc.as<long long>() + 3 * n;
-  GFS_CK(launch_grad(a, n, grad_p, grad_sv, c->stream));
+  GFS_CK(launch_grad(a, n, nullptr, nullptr, c->stream));
+  GFS_CK(launch_tangent_grad(a, n, grad_p, grad_sv, c->stream));
+  return GFS_OK;
+}
+
+int gfs_query_tangent(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, float* s_out, double* s64_out,
+                      int64_t* argmin_out, uint16_t* flags_out) {
+  if (!c || m < 0 || (m > 0 && (!x || !argmin_out || !flags_out))) return GFS_ERR_ARG;
+  if (!c->built) return GFS_ERR_STATE;
+  if (m >= (int64_t(1) << 32)) return GFS_ERR_TOO_LARGE;
+  if (m == 0) return GFS_OK;
+  QueryArgs a;
+  fill_query_args(c, a);
+  if (x_is_fp32) a.x32 = static_cast<const float*>(x);
+  else a.x64 = static_cast<const double*>(x);
+  a.m = m;
+  a.s_out = s_out;
+  a.s64_out = s64_out;
+  a.arg_out = argmin_out;
+  a.fl_out = flags_out;
+  GFS_CK(launch_query_tangent(a, c->opt.box_cull, c->stream));
   return GFS_OK;
 }
 
@@ -1167,7 +1188,7 @@ int gfs_stats(gfs_ctx* c, gfs_stats_t* out) {
   };
   unsigned long long own = 0, sorts = 0;
   launch_counts(&own, &sorts);
-  out->kernel_launches = int64_t(own);
+  out->kernel_launches = int64_t(own + tangent_launch_count());
   out->sort_calls = int64_t(sorts);
   if (c->have_ev && c->built_timed) {
     out->ms_build_total = ms(0, 3);
@@ -1306,6 +1327,7 @@ extern "C" int gfs_query_backward_noalloc(gfs_ctx* c, const void* x, int x_is_fp
   a.KS = c->KS;
   a.acc_p = acc;
   a.acc_s = acc + 3 * n;
-  GFS_CK(launch_grad(a, n, grad_p, grad_sv, c->stream));
+  GFS_CK(launch_grad(a, n, nullptr, nullptr, c->stream));
+  GFS_CK(launch_tangent_grad(a, n, grad_p, grad_sv, c->stream));
   return GFS_OK;
 }

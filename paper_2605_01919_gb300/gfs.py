@@ -14,11 +14,11 @@ import torch
 
 from . import build as _build
 
-CODE_SURVIVOR, CODE_OPPOSITE, CODE_SAMPLE, CODE_OUTSIDE, CODE_INVALID, CODE_LOWER = range(6)
+CODE_SURVIVOR, CODE_OPPOSITE, CODE_SAMPLE, CODE_OUTSIDE, CODE_INVALID, CODE_LOWER, CODE_TANGENT = range(7)
 FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 0x10, 0x20, 0x40, 0x80
 
-EXPORTED = ["gfs_default_options", "gfs_create", "gfs_set_stream", "gfs_build", "gfs_query",
-            "gfs_query_backward", "gfs_insert", "gfs_insert_known", "gfs_survivors", "gfs_batch_build", "gfs_batch_query",
+EXPORTED = ["gfs_default_options", "gfs_create", "gfs_set_stream", "gfs_build", "gfs_query", "gfs_query_tangent",
+            "gfs_query_backward", "gfs_query_backward_noalloc", "gfs_insert", "gfs_insert_known", "gfs_survivors", "gfs_batch_build", "gfs_batch_query",
             "gfs_batch_survivors", "gfs_stats", "gfs_solve_host", "gfs_icosphere", "gfs_strerror",
             "gfs_destroy"]
 
@@ -80,6 +80,8 @@ def load(build_if_missing: bool = True):
     L.gfs_build.restype = i32
     L.gfs_query.argtypes = [P, P, i32, i64, P, P, P, P]
     L.gfs_query.restype = i32
+    L.gfs_query_tangent.argtypes = [P, P, i32, i64, P, P, P, P]
+    L.gfs_query_tangent.restype = i32
     L.gfs_query_backward.argtypes = [P, P, i32, i64, P, P, P, P, P, P, P]
     L.gfs_query_backward.restype = i32
     L.gfs_insert.argtypes = [P, P, i64, P, P, P]
@@ -132,7 +134,10 @@ class Context:
     """A sample set with its candidate/survivor hierarchies on one device."""
 
     def __init__(self, tau: int = 3, tol: float = 1e-6, box_cull: bool = True, clamp_opp: bool = True,
-                 precision: int = 0, stream: torch.cuda.Stream | None = None, timing: bool = False):
+                 precision: int = 0, stream: torch.cuda.Stream | None = None, timing: bool = False,
+                 tangent: bool = False):
+        """tangent: every query is followed by the same-sign tangent
+        augmentation (gfs_query_tangent), also under ConsistentSDF."""
         if not torch.cuda.is_available():
             raise GfsError("no CUDA device: the consistent-SDF library has no CPU path")
         L = load()
@@ -142,6 +147,7 @@ class Context:
         opt.timing = int(timing)
         self.opt = opt
         self.tau = tau
+        self.tangent = tangent
         self.K = 10 * 4 ** tau + 2
         self._stream = stream
         h = ctypes.c_void_p()
@@ -192,15 +198,21 @@ class Context:
             "argmin": torch.empty(m, dtype=torch.int64, device=dev),
             "flags": torch.empty(m, dtype=torch.int16, device=dev),
         }
-        self._sync_stream()
-        _check(load().gfs_query(self._h, _ptr(x), int(x.dtype == torch.float32), m, _ptr(out["s"]),
-                                _ptr(out["s64"]), _ptr(out["argmin"]), _ptr(out["flags"])))
+        self.query_into(x, out["s"], out["s64"], out["argmin"], out["flags"])
         return out
 
     def query_into(self, x, s_out, s64_out, argmin_out, flags_out):
         self._sync_stream()
         _check(load().gfs_query(self._h, _ptr(x), int(x.dtype == torch.float32), x.shape[0], _ptr(s_out),
                                 _ptr(s64_out), _ptr(argmin_out), _ptr(flags_out)))
+        if self.tangent:
+            self.tangent_into(x, s_out, s64_out, argmin_out, flags_out)
+
+    def tangent_into(self, x, s_out, s64_out, argmin_out, flags_out):
+        """Same-sign tangent augmentation of a query's outputs, in place."""
+        self._sync_stream()
+        _check(load().gfs_query_tangent(self._h, _ptr(x), int(x.dtype == torch.float32), x.shape[0], _ptr(s_out),
+                                        _ptr(s64_out), _ptr(argmin_out), _ptr(flags_out)))
 
     def backward(self, x, s, argmin, flags, grad_s, want_x=True, want_p=True, want_s=True):
         m = x.shape[0]

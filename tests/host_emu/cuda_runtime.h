@@ -1,0 +1,31 @@
+// Host stand-in for <cuda_runtime.h>, used only by the tests: it lets the
+// tangent pass's device routines (csrc/gfs_tangent.cuh) compile as plain C++
+// so that their traversal logic can be checked against the oracle on a CPU.
+// The FP64 intrinsics become the plain IEEE operations they name (the
+// harness is compiled with -ffp-contract=off, so nothing is fused).
+#pragma once
+#include <cmath>
+#include <cstddef>
+#include <cstdint>
+#define __device__
+#define __host__
+#define __global__
+#define __forceinline__ inline
+struct float4 {
+  float x, y, z, w;
+};
+struct uint4 {
+  unsigned x, y, z, w;
+};
+typedef int cudaError_t;
+typedef void* cudaStream_t;
+static const int cudaSuccess = 0;
+inline double __dadd_rn(double a, double b) { return a + b; }
+inline double __dsub_rn(double a, double b) { return a - b; }
+inline double __dmul_rn(double a, double b) { return a * b; }
+inline double __ddiv_rn(double a, double b) { return a / b; }
+inline double __dsqrt_rn(double a) { return std::sqrt(a); }
+using std::fabs;
+using std::fmax;
+using std::fmin;
+using std::sqrt;

@@ -1,0 +1,118 @@
+// Test harness: runs the tangent pass's device routines (tangent_one) on the
+// CPU over a sphere hierarchy built here, refining the oracle's plain query
+// results in place.  The hierarchy has the library's layout (implicit 8-ary
+// tree over sorted items) with bounding balls computed directly in FP64 and
+// rounded outwards to FP32, so every bound the routines rely on holds.
+// Item order: Morton order of the FP32 centres (order_seed = 0, as the
+// library sorts) or a seeded shuffle (other seeds: loose, overlapping nodes).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <random>
+#include <vector>
+
+#include "gfs_tangent.cuh"
+
+using namespace gfs;
+
+namespace {
+
+float round_out(double v) {  // an FP32 value >= v
+  if (!(v > -INFINITY)) return -INFINITY;
+  float f = float(v);
+  if (double(f) < v) f = std::nextafter(f, INFINITY);
+  return f * (f > 0 ? 1.000001f : 0.999999f) + 1e-7f;
+}
+
+}  // namespace
+
+extern "C" int tangent_host(const double* p, const double* s, int64_t n, const double* U, int K, double tol,
+                            int clamp_opp, int box_cull, const double* x, int64_t m, double* value,
+                            int64_t* argmin, uint16_t* flags, unsigned order_seed) {
+  std::vector<D4> sph(n);
+  for (int64_t i = 0; i < n; ++i) sph[i] = D4{p[3 * i], p[3 * i + 1], p[3 * i + 2], s[i]};
+  std::vector<int> sid(n);
+  for (int64_t i = 0; i < n; ++i) sid[i] = int(i);
+  if (order_seed == 0) {
+    std::vector<uint32_t> key(n);
+    for (int64_t i = 0; i < n; ++i) key[i] = morton3(float(p[3 * i]), float(p[3 * i + 1]), float(p[3 * i + 2]));
+    std::stable_sort(sid.begin(), sid.end(), [&](int a, int b) { return key[a] < key[b]; });
+  } else {
+    std::mt19937 rng(order_seed);
+    std::shuffle(sid.begin(), sid.end(), rng);
+  }
+  Tree T{};
+  T.nitems = n;
+  int64_t cnt = (n + kLeaf - 1) / kLeaf, total = 0;
+  int L = 0;
+  while (true) {
+    if (L >= kMaxLevels) return -1;
+    T.count[L] = cnt;
+    T.offset[L] = total;
+    total += cnt;
+    ++L;
+    if (cnt <= kFan) break;
+    cnt = (cnt + kFan - 1) / kFan;
+  }
+  T.nlevels = L;
+  std::vector<float4> na(total), nb(total), nf(total), lo(total), hi(total);
+  int64_t span = kLeaf;
+  for (int l = 0; l < L; ++l, span *= kFan) {
+    for (int64_t j = 0; j < T.count[l]; ++j) {
+      const int64_t b = j * span, e = std::min<int64_t>(b + span, n);
+      double cx = 0, cy = 0, cz = 0;
+      for (int64_t t = b; t < e; ++t) {
+        cx += sph[sid[t]].x;
+        cy += sph[sid[t]].y;
+        cz += sph[sid[t]].z;
+      }
+      const float4 C{float(cx / double(e - b)), float(cy / double(e - b)), float(cz / double(e - b)), 0};
+      double wp = -INFINITY, wn = -INFINITY, w0 = 0, wf = -INFINITY;
+      float4 L4{INFINITY, INFINITY, INFINITY, 0}, H4{-INFINITY, -INFINITY, -INFINITY, 0};
+      for (int64_t t = b; t < e; ++t) {
+        const D4& P = sph[sid[t]];
+        const double d = std::sqrt((P.x - C.x) * (P.x - C.x) + (P.y - C.y) * (P.y - C.y) + (P.z - C.z) * (P.z - C.z));
+        const double r = std::fabs(P.w);
+        if (P.w > 0) wp = std::max(wp, d + r);
+        if (P.w < 0) wn = std::max(wn, d + r);
+        w0 = std::max(w0, d);
+        wf = std::max(wf, d - r);
+        L4 = float4{std::min(L4.x, std::nextafter(float(P.x), -INFINITY)),
+                    std::min(L4.y, std::nextafter(float(P.y), -INFINITY)),
+                    std::min(L4.z, std::nextafter(float(P.z), -INFINITY)), 0};
+        H4 = float4{std::max(H4.x, std::nextafter(float(P.x), INFINITY)),
+                    std::max(H4.y, std::nextafter(float(P.y), INFINITY)),
+                    std::max(H4.z, std::nextafter(float(P.z), INFINITY)), 0};
+      }
+      const int64_t k = T.offset[l] + j;
+      na[k] = float4{C.x, C.y, C.z, round_out(std::max(wp, wn))};
+      nb[k] = float4{round_out(wp), round_out(wn), round_out(w0), 0};
+      nf[k] = float4{C.x, C.y, C.z, round_out(wf)};
+      lo[k] = L4;
+      hi[k] = H4;
+    }
+  }
+  T.na = na.data();
+  T.nb = nb.data();
+  T.nf = nf.data();
+  T.lo = lo.data();
+  T.hi = hi.data();
+  QueryArgs a{};
+  a.sid = sid.data();
+  a.sph64 = sph.data();
+  a.st = T;
+  a.n = n;
+  a.U64 = U;
+  a.K = K;
+  a.KS = K + 1;
+  a.tol = tol;
+  a.clamp_opp = clamp_opp;
+  a.x64 = x;
+  a.m = m;
+  a.s64_out = value;
+  a.arg_out = argmin;
+  a.fl_out = flags;
+  for (int64_t q = 0; q < m; ++q) tangent::tangent_one(a, box_cull, q);
+  return 0;
+}

@@ -499,3 +499,79 @@ def test_query_aug_between_exact_and_plain(orc, seed):
         assert ex <= abs(v1[t]) + 1e-9
         checked += 1
     assert checked >= 3
+
+
+def _tangent_fd(orc, p, s, U, x, v, a, f, t, h=1e-7):
+    """Central differences of the augmented value at point t in x, p_j and
+    s_j (j = the winning sphere) next to the analytic gradient; None when a
+    step changes the argmin."""
+    j = a[t] // 2
+    fd = []
+    for kind, c in [("x", 0), ("x", 1), ("x", 2), ("p", 0), ("p", 1), ("p", 2), ("s", 0)]:
+        vals = []
+        for sgn in (1, -1):
+            xx, pp, ss = x[t:t + 1].copy(), p.copy(), s.copy()
+            if kind == "x":
+                xx[0, c] += sgn * h
+            elif kind == "p":
+                pp[j, c] += sgn * h
+            else:
+                ss[j] += sgn * h
+            sv = orc.collect(pp, ss, U, orc.keep_all(pp, ss, U, tol=0.0, box_cull=False))
+            vv, aa, ff = orc.query_aug(pp, ss, sv, xx, tol=0.0, box_cull=False)
+            if aa[0] != a[t] or (ff[0] & 15) != orc.CODE_TANGENT:
+                return None
+            vals.append(vv[0])
+        fd.append((vals[0] - vals[1]) / (2 * h))
+    one = np.zeros(x.shape[0])
+    one[t] = 1.0
+    gx, gp, gs = orc.grad(p, s, U, x, v, a, f, one)
+    return np.array(fd), np.concatenate([gx[t], gp[j], [gs[j]]])
+
+
+# (n, seed, points): seeded tiny inputs, uniform points in [-0.6, 0.6]^3, and
+# points whose winner is a near tangent point seen from outside its ball or a
+# far tangent point (rare: most winners are near points seen from inside)
+TANGENT_FD_CASES = [(30, 1, [67]), (14, 2, [103]), (30, 2, [13, 20])]
+
+
+@pytest.mark.parametrize("n,seed,pts", TANGENT_FD_CASES)
+def test_grad_tangent_rare_sides_match_finite_differences(orc, n, seed, pts):
+    p, s = W.tiny_random(n, seed)
+    x = np.random.default_rng(seed).uniform(-0.6, 0.6, size=(400, 3))
+    U = orc.icosphere(1)
+    surv = orc.collect(p, s, U, orc.keep_all(p, s, U, tol=0.0, box_cull=False))
+    v, a, f = orc.query_aug(p, s, surv, x, tol=0.0, box_cull=False)
+    for t in pts:
+        assert (f[t] & 15) == orc.CODE_TANGENT
+        j = a[t] // 2
+        inside = np.linalg.norm(x[t] - p[j]) < abs(s[j])
+        assert (a[t] % 2 == 1) or not inside    # a far point, or a near one seen from outside
+        r = _tangent_fd(orc, p, s, U, x, v, a, f, t)
+        assert r is not None
+        fd, an = r
+        assert np.allclose(fd, an, atol=1e-6), (fd, an)
+
+
+def test_grad_tangent_matches_finite_differences(orc):
+    """The TANGENT branch of the analytic gradient against central
+    differences of the augmented query itself (in x, in p_j and in s_j),
+    at points where a tangent point wins with the same argmin on both sides
+    of the step: the derivative of the distance to the moving tangent point."""
+    p, s = W.tiny_random(14, 1)
+    rng = np.random.default_rng(7)
+    x = rng.uniform(-0.4, 0.4, size=(80, 3))
+    U = orc.icosphere(1)
+    surv = orc.collect(p, s, U, orc.keep_all(p, s, U, tol=0.0, box_cull=False))
+    v, a, f = orc.query_aug(p, s, surv, x, tol=0.0, box_cull=False)
+    won = np.nonzero((f & 15) == orc.CODE_TANGENT)[0]
+    assert won.size >= 5
+    checked = 0
+    for t in won[:12]:
+        r = _tangent_fd(orc, p, s, U, x, v, a, f, t)
+        if r is None:
+            continue
+        fd, an = r
+        assert np.allclose(fd, an, atol=1e-6), (fd, an)
+        checked += 1
+    assert checked >= 3

@@ -1,0 +1,107 @@
+"""The tangent pass's device routines, compiled as host C++, against the
+oracle's augmented query (CPU, no GPU needed).
+
+`csrc/gfs_tangent.cuh` holds the whole per-point logic of gfs_query_tangent:
+the FP64 pass over the sphere hierarchy, the tangent-point search with its
+pruning and its skip of points covered by the deepest containing ball, and
+the coverage walks.  `tests/host_emu/` supplies a stand-in CUDA header and a
+hierarchy built on the host with the library's layout (Morton-ordered, or
+shuffled so that nodes overlap heavily), and the routines refine the
+oracle's plain query results in place.  Every output must equal the oracle's
+augmented query bit for bit.  This checks the traversal logic on the CPU;
+the GPU tests check the compiled kernel.
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2605_01919_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def host(tmp_path_factory):
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("needs g++")
+    out = str(tmp_path_factory.mktemp("tangent_host") / "tangent_host.so")
+    cmd = [cxx, "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-I", os.path.join(ROOT, "tests", "host_emu"), "-I", os.path.join(ROOT, "include"),
+           "-I", os.path.join(ROOT, "paper_2605_01919_gb300", "csrc"),
+           os.path.join(ROOT, "tests", "host_emu", "tangent_host.cpp"), "-o", out]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    L = ctypes.CDLL(out)
+    P = ctypes.c_void_p
+    L.tangent_host.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                               P, ctypes.c_int64, P, P, P, ctypes.c_uint]
+    L.tangent_host.restype = ctypes.c_int
+    return L
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def check(host, orc, p, s, tau, x, box_cull=True, clamp_opp=True, tol=1e-6, orders=(0, 5)):
+    p, s, x = (np.ascontiguousarray(a, np.float64) for a in (p, s, x))
+    U = orc.icosphere(tau)
+    surv = orc.collect(p, s, U, orc.keep_all(p, s, U, tol=tol, box_cull=box_cull))
+    v0, a0, f0, _ = orc.query(p, s, surv, x, tol=tol, clamp_opp=clamp_opp)
+    v1, a1, f1 = orc.query_aug(p, s, surv, x, tol=tol, clamp_opp=clamp_opp, box_cull=box_cull)
+    for order in orders:
+        val, arg, fl = v0.copy(), a0.copy(), f0.astype(np.uint16)
+        assert host.tangent_host(_ptr(p), _ptr(s), p.shape[0], _ptr(U), U.shape[0], tol, int(clamp_opp),
+                                 int(box_cull), _ptr(x), x.shape[0], _ptr(val), _ptr(arg), _ptr(fl), order) == 0
+        bad = np.nonzero(~((val == v1) | (np.isnan(val) & np.isnan(v1))) | (arg != a1) |
+                         (fl.astype(np.int32) != f1))[0]
+        assert bad.size == 0, f"order {order}: {bad.size} points differ, first {bad[:5]}"
+    return int(np.sum((f1 & 15) == orc.CODE_TANGENT))
+
+
+def test_host_sphere_grid(host, orc):
+    """10^3 sphere grid, tau = 2, every 19^3 point."""
+    w = W.sphere_grid(N=10, up=2, tau=2)
+    assert check(host, orc, w.p, w.s, w.tau, w.make_queries()) > 500
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (7, 2), (37, 3), (100, 4), (257, 5)])
+def test_host_tiny_random(host, orc, n, seed):
+    p, s = W.tiny_random(n, seed, valid=(seed % 3 != 0), spread=0.9)
+    rng = np.random.default_rng(1000 + seed)
+    x = np.concatenate([rng.uniform(-1, 1, size=(300, 3)), p[: min(n, 20)],
+                        rng.uniform(-1.5, 1.5, size=(20, 3))])
+    for tau in (0, 1, 3):
+        for box_cull, clamp in [(True, True), (False, True), (True, False)]:
+            check(host, orc, p, s, tau, x, box_cull, clamp)
+    # tol = 0 (touching balls share boundary points)
+    check(host, orc, p, s, 1, x, tol=0.0)
+
+
+def test_host_degenerate(host, orc):
+    p = np.array([[0.0, 0, 0], [0.0, 0, 0], [0.5, 0, 0], [0.2, 0.1, 0], [0.2, 0.1, 0.0],
+                  [-0.4, 0.3, 0.2], [-0.4, 0.3, 0.2], [0.7, 0.7, 0.7]])
+    s = np.array([0.3, 0.3, 0.2, 0.0, 0.05, -0.25, -0.1, 0.5])
+    rng = np.random.default_rng(9)
+    x = np.concatenate([p, rng.uniform(-1, 1, size=(500, 3)), [[0.3, 0.0, 0.0], [0.25, 0.0, 0.0],
+                                                               [-0.219, 0.164, 0.109]]])
+    for tau in (1, 2):
+        assert check(host, orc, p, s, tau, x) > 0
+
+
+def test_host_union_grid(host, orc):
+    """12^3 union grid, tau = 3: sampled 4x upsampled points and samples."""
+    w = W.union_grid(N=12, up=4)
+    xq = w.make_queries()
+    sel = np.random.default_rng(2).choice(xq.shape[0], 1200, replace=False)
+    assert check(host, orc, w.p, w.s, w.tau, np.concatenate([xq[sel], w.p[::11]]), orders=(0,)) > 50
+
+
+def test_host_torus_fp32_points(host, orc):
+    w = W.torus_grid(N=14, m=600)
+    assert check(host, orc, w.p, w.s, w.tau, w.make_queries().astype(np.float64), orders=(0,)) > 20
