@@ -28,6 +28,9 @@
  *    far bound = nearest far tangent point of any sphere.
  *  - Sec. 6 (min_valid_radius_for_known_sign): the exact T/U/D enumeration,
  *    kept here by brute force for tiny inputs only (orc_exact_rmin).
+ *  - Sec. 4.2 refinement order: the covered area ratio of grid cells from
+ *    regularly spaced sub-points (orc_cell_coverage); the flood-fill order
+ *    itself is plain Python in oracle.py.
  *
  * Readings where the paper is silent are listed in the design notes; the
  * ones that fix arithmetic are repeated at each function.
@@ -931,4 +934,34 @@ double orc_exact_rmin(const double* p, const double* s, int64_t n, double tol, i
   }
 #undef ORC_TRY
   return rmin;
+}
+
+/* ------------------------------------------------------------------------ */
+/* refinement order (Sec. 4.2): covered area ratio of grid cells             */
+/* ------------------------------------------------------------------------ */
+/* Each cell c (integer coordinates i, j, k in cells[3c..3c+2]) is sampled at
+ * sub^3 regularly spaced points, the centres of a sub x sub x sub split of
+ * the cell: coordinate origin + h * (i + (a + 1/2) / sub), a < sub, each
+ * operation rounded on its own in that order.  counts[c] = number of these
+ * points inside some ball, of either sign, shrunk by tol (the cull's
+ * coverage predicate).  The covered area ratio is counts[c] / sub^3. */
+void orc_cell_coverage(const double* p, const double* s, int64_t n, double tol, const int32_t* cells,
+                       int64_t ncells, const double* origin, double h, int sub, uint32_t* counts) {
+  for (int64_t c = 0; c < ncells; ++c) {
+    uint32_t cnt = 0;
+    for (int a = 0; a < sub; ++a)
+      for (int b = 0; b < sub; ++b)
+        for (int e = 0; e < sub; ++e) {
+          const int idx[3] = {a, b, e};
+          double x[3];
+          for (int d = 0; d < 3; ++d)
+            x[d] = origin[d] + h * ((double)cells[3 * c + d] + ((double)idx[d] + 0.5) / (double)sub);
+          for (int64_t j = 0; j < n; ++j)
+            if (covers(x, p + 3 * j, s[j], tol)) {
+              ++cnt;
+              break;
+            }
+        }
+    counts[c] = cnt;
+  }
 }

@@ -68,6 +68,8 @@ def lib():
         L.orc_insert_state.restype = i64
         L.orc_exact_rmin.argtypes = [P, P, i64, f64, i32, P, i32]
         L.orc_exact_rmin.restype = f64
+        L.orc_cell_coverage.argtypes = [P, P, i64, f64, P, i64, P, f64, i32, P]
+        L.orc_cell_coverage.restype = None
         _lib = L
     return _lib
 
@@ -221,3 +223,56 @@ def solve(p, s, tau, x, tol=TOL, box_cull=True, clamp_opp=True):
     keep = keep_all(p, s, U, tol, box_cull)
     surv = collect(p, s, U, keep)
     return keep, surv, query(p, s, surv, x, tol, clamp_opp)
+
+
+# ----------------------------------------------------------------------------
+# refinement order (Sec. 4.2)
+# ----------------------------------------------------------------------------
+
+def cell_coverage(p, s, cells, origin, h, sub=8, tol=TOL):
+    """Covered sub-point count of each cell (cells: (c, 3) integer cell
+    coordinates; points origin + h * (ijk + (abc + 1/2) / sub)): how many of
+    the cell's sub^3 points lie in some ball shrunk by tol."""
+    p, s = _c(p, np.float64), _c(s, np.float64)
+    cells = _c(cells, np.int32)
+    origin = _c(origin, np.float64)
+    out = np.zeros(cells.shape[0], np.uint32)
+    if cells.shape[0]:
+        lib().orc_cell_coverage(_ptr(p), _ptr(s), s.shape[0], tol, _ptr(cells), cells.shape[0], _ptr(origin),
+                                float(h), int(sub), _ptr(out))
+    return out
+
+
+NEIGHBOURS = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1) if (a, b, c) != (0, 0, 0)]
+
+
+def flood_order(cells, counts):
+    """Flood-fill refinement order of Sec. 4.2 (reading: priorities are the
+    covered counts, lowest first, ties to the lower list index; neighbours
+    are the cells of the list that share a face, an edge or a corner).
+    Start from the least covered cell; repeatedly pop the least covered
+    queued cell, emit it and queue its not yet queued neighbours; when the
+    queue runs dry, start again from the least covered cell not yet
+    emitted.  Returns the list indices in emission order."""
+    import heapq
+    cells = [tuple(int(v) for v in c) for c in np.asarray(cells)]
+    counts = [int(v) for v in np.asarray(counts)]
+    where = {c: i for i, c in enumerate(cells)}
+    seeds = sorted(range(len(cells)), key=lambda i: (counts[i], i))
+    queued = [False] * len(cells)
+    heap, order, nxt = [], [], 0
+    while len(order) < len(cells):
+        if not heap:
+            while queued[seeds[nxt]]:
+                nxt += 1
+            queued[seeds[nxt]] = True
+            heap.append((counts[seeds[nxt]], seeds[nxt]))
+        _, i = heapq.heappop(heap)
+        order.append(i)
+        ci = cells[i]
+        for d in NEIGHBOURS:
+            j = where.get((ci[0] + d[0], ci[1] + d[1], ci[2] + d[2]))
+            if j is not None and not queued[j]:
+                queued[j] = True
+                heapq.heappush(heap, (counts[j], j))
+    return order

@@ -575,3 +575,107 @@ def test_grad_tangent_matches_finite_differences(orc):
         assert np.allclose(fd, an, atol=1e-6), (fd, an)
         checked += 1
     assert checked >= 3
+
+
+# ----------------------------------------------------------------------------
+# refinement order (Sec. 4.2): covered counts and the flood-fill order
+# ----------------------------------------------------------------------------
+
+# sub = 8: a sub-point sits at h/16 * (k1, k2, k3) from the cell centre with
+# odd k in {+-1, +-3, +-5, +-7}; the points with k1^2 + k2^2 + k3^2 < R^2 are
+# 8 for 3 < R^2 <= 11 ((1,1,1)), 32 up to 19 (+ (1,1,3) x 24), 56 up to 27
+# (+ (1,3,3) x 24), 88 up to 35 (+ (3,3,3) x 8 and (1,1,5) x 24), all 512
+# above 3 * 49 = 147.
+@pytest.mark.parametrize("R2,count", [(2.0, 0), (7.0, 8), (15.0, 32), (23.0, 56), (31.0, 88), (150.0, 512)])
+def test_cell_coverage_lattice_shells(orc, R2, count):
+    h = 0.05
+    origin = np.array([-1.0, -1.0, -1.0])
+    cell = np.array([[2, -1, 3]])
+    centre = origin + h * (cell[0] + 0.5)
+    for sign in (1.0, -1.0):
+        p = centre[None, :].copy()
+        s = np.array([sign * h / 16 * np.sqrt(R2)])
+        assert orc.cell_coverage(p, s, cell, origin, h, 8, tol=0.0)[0] == count
+
+
+def test_cell_coverage_union_zero_and_far(orc):
+    """Coverage is by any ball of either sign; zero samples and far balls
+    cover nothing; a point counts once however many balls hold it."""
+    h = 0.1
+    origin = np.zeros(3)
+    cells = np.array([[0, 0, 0], [5, 0, 0], [0, 7, 0]])
+    c0 = origin + h * 0.5
+    p = np.array([c0, c0, c0 + [0.5, 0, 0], c0 + [0, 0.7, 0]])
+    s = np.array([0.2, -0.3, 0.0, -1e-3])
+    got = orc.cell_coverage(p, s, cells, origin, h, 8, tol=0.0)
+    assert list(got) == [512, 0, 0]
+    # the tolerance shrinks the balls: with tol = 1e-6 a ball reaching 0.5e-6
+    # past the corner sub-points (7 sqrt(3) h/16 away) misses the 8 corners,
+    # one reaching 2e-6 past them holds all 512 points
+    r_all = h / 16 * np.sqrt(147.0)
+    assert orc.cell_coverage(c0[None], np.array([r_all + 0.5e-6]), cells[:1], origin, h, 8, tol=1e-6)[0] == 504
+    assert orc.cell_coverage(c0[None], np.array([r_all + 2e-6]), cells[:1], origin, h, 8, tol=1e-6)[0] == 512
+
+
+# Hand-worked orders (26-neighbourhood, lowest count first, ties to the
+# lower index):
+FLOOD_CASES = [
+    # chain along x, counts 5 1 3 2: start at 1, queue {0, 2}; pop 2, queue
+    # 3; pop 3 (2 < 5); then 0
+    ([(0, 0, 0), (1, 0, 0), (2, 0, 0), (3, 0, 0)], [5, 1, 3, 2], [1, 2, 3, 0]),
+    # two components: start at the global minimum (2), finish its
+    # component, then the least covered rest
+    ([(0, 0, 0), (1, 0, 0), (5, 5, 5), (6, 5, 5)], [4, 9, 2, 7], [2, 3, 0, 1]),
+    # (0,0,0) and (1,1,1) touch at a corner, so 1 follows 0 before the
+    # less covered but unconnected cell 2
+    ([(0, 0, 0), (1, 1, 1), (5, 0, 0)], [1, 9, 5], [0, 1, 2]),
+    # equal counts in a 2 x 2 square: lowest index first
+    ([(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 0)], [3, 3, 3, 3], [0, 1, 2, 3]),
+    ([(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 0)], [3, 3, 3, 1], [3, 0, 1, 2]),
+    # the flood follows connectivity, not the global order: the other
+    # count-0 cell (4) comes last
+    ([(0, 0, 0), (1, 0, 0), (2, 0, 0), (3, 0, 0), (4, 0, 0)], [0, 9, 1, 9, 0], [0, 1, 2, 3, 4]),
+    # cells two apart are not neighbours
+    ([(0, 0, 0), (2, 0, 0), (1, 5, 0)], [1, 0, 2], [1, 0, 2]),
+]
+
+
+@pytest.mark.parametrize("cells,counts,order", FLOOD_CASES)
+def test_flood_order_hand_worked(orc, cells, counts, order):
+    assert orc.flood_order(np.array(cells), np.array(counts)) == order
+
+
+def test_flood_order_components_contiguous(orc):
+    """On a random sparse set of cells: a permutation; every connected
+    component (26-neighbourhood) is emitted as one contiguous run that starts
+    at its least covered cell, and the runs start in increasing order of
+    that cell's (count, index)."""
+    rng = np.random.default_rng(4)
+    all_cells = np.array([(i, j, k) for i in range(9) for j in range(9) for k in range(3)])
+    cells = all_cells[rng.random(all_cells.shape[0]) < 0.3]
+    counts = rng.integers(0, 20, cells.shape[0])
+    order = orc.flood_order(cells, counts)
+    assert sorted(order) == list(range(cells.shape[0]))
+    # components by union-find over the 26-neighbourhood
+    where = {tuple(c): i for i, c in enumerate(cells)}
+    parent = list(range(len(cells)))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+    for i, c in enumerate(cells):
+        for d in orc.NEIGHBOURS:
+            j = where.get((c[0] + d[0], c[1] + d[1], c[2] + d[2]))
+            if j is not None:
+                parent[find(i)] = find(j)
+    comp = [find(i) for i in order]
+    runs = [comp[0]] + [comp[t] for t in range(1, len(comp)) if comp[t] != comp[t - 1]]
+    assert len(runs) == len(set(runs)) and len(runs) > 3
+    firsts = [order[0]] + [order[t] for t in range(1, len(order)) if comp[t] != comp[t - 1]]
+    for f in firsts:
+        members = [i for i in range(len(cells)) if find(i) == find(f)]
+        assert f == min(members, key=lambda i: (counts[i], i))
+    keys = [(counts[f], f) for f in firsts]
+    assert keys == sorted(keys)
