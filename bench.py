@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sub-benchmarks of the backward, insertion and batched paths")
-    ap.add_argument("--only", choices=["backward", "repair", "insert", "batch", "tangent"], default=None,
+    ap.add_argument("--only", choices=["backward", "repair", "insert", "batch", "tangent", "refine_order"],
+                    default=None,
                     help="run one sub-benchmark alone and print its JSON (profiling)")
     ap.add_argument("--insert-steps", type=int, default=1024)
     ap.add_argument("--repair-steps", type=int, default=8192)
@@ -469,6 +470,72 @@ def extra_tangent(every=256):
             "queries_per_s_with_tangent": m / (t_both / 1e3)}
 
 
+def extra_refine_order(N=32):
+    """Sec. 4.2 refinement order on the N^3 union grid (tau 3): the centres of
+    the cells that may contain the surface are inserted greedily, once in
+    flood-fill order (covered counts of 8^3 points per cell from
+    gfs_cell_coverage, order from gfs_flood_order) and once in raster order;
+    time of the coverage pass, insertions/s, and the mean absolute error of
+    the inserted values against the union's field for both orders."""
+    import torch
+    from paper_2605_01919_gb300 import gfs
+    from paper_2605_01919_gb300 import workloads as W
+    w = W.union_grid(N=N, up=2)
+    field = W.union_field()
+    S = w.s.reshape(N, N, N)
+    near = np.abs(S) < 0.5 * np.sqrt(3) * w.h
+    cell = np.zeros((N - 1,) * 3, dtype=bool)
+    for a in (0, 1):
+        for b in (0, 1):
+            for c in (0, 1):
+                cell |= near[a:N - 1 + a, b:N - 1 + b, c:N - 1 + c]
+    cells = np.argwhere(cell).astype(np.int32)
+    centres = -1.0 + w.h * (cells.astype(np.float64) + 0.5)
+    p, s = torch.from_numpy(w.p).cuda(), torch.from_numpy(w.s).cuda()
+    ctx = gfs.Context(tau=w.tau)
+    ctx.build(p, s)
+    ct = torch.from_numpy(cells).cuda()
+    t_cov = _ev_time(lambda: ctx.cell_coverage(ct, [-1.0, -1.0, -1.0], w.h, 8))
+    counts = ctx.cell_coverage(ct, [-1.0, -1.0, -1.0], w.h, 8).cpu().numpy()
+    t0 = time.perf_counter()
+    flood = gfs.flood_order(cells, counts)
+    t_order = time.perf_counter() - t0
+    res = {"workload": f"union{N}_tau3_surface_cells", "cells": int(cells.shape[0]),
+           "coverage_ms": t_cov, "flood_order_ms": 1e3 * t_order}
+    for name, idx in (("flood", flood), ("raster", np.arange(cells.shape[0]))):
+        y = np.ascontiguousarray(centres[idx])
+        ctx.build(p, s)
+        yt = torch.from_numpy(y).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = ctx.insert(yt)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        v = out["s64"].cpu().numpy()
+        code = out["flags"].cpu().numpy().astype(np.int32) & 15
+        ins = (code == gfs.CODE_SURVIVOR) | (code == gfs.CODE_OPPOSITE) | (code == gfs.CODE_LOWER)
+        err = np.abs(v[ins] - field(y[ins]))
+        res[name] = {"insertions_per_s": y.shape[0] / dt, "inserted": int(ins.sum()),
+                     "mean_abs_err": float(err.mean()), "max_abs_err": float(err.max())}
+    ctx.close()
+    return res
+
+
+def _isolated(only, extra=(), timeout=600):
+    """Run one sub-benchmark in a child process, so that a failure there
+    cannot end this process or its CUDA context; returns its JSON object."""
+    import subprocess
+    cmd = [sys.executable, os.path.abspath(__file__), "--only", only, *extra]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout)
+    except subprocess.TimeoutExpired:
+        return {"error": f"timed out after {timeout} s"}
+    for line in reversed(r.stdout.splitlines()):
+        if line.startswith("{"):
+            return json.loads(line).get(only, {"error": "no result"})
+    return {"error": f"exit {r.returncode}: {r.stderr[-400:]}"}
+
+
 def run_gfs(args):
     import torch
     import torch.distributed as dist
@@ -609,7 +676,8 @@ def run_gfs(args):
         for name, fn in (("backward", extra_backward), ("repair", lambda: extra_repair(args.repair_steps)),
                          ("insert", lambda: extra_insert(args.insert_steps)),
                          ("batch", lambda: extra_batch(args.batch_shapes, args.batch_scale)),
-                         ("tangent", lambda: extra_tangent(args.tangent_every))):
+                         ("tangent", lambda: _isolated("tangent", ["--tangent-every", str(args.tangent_every)])),
+                         ("refine_order", lambda: _isolated("refine_order"))):
             try:
                 line["extras"][name] = fn()
             except Exception as e:  # a failing sub-benchmark must not hide the headline line
@@ -630,7 +698,8 @@ if __name__ == "__main__":
         fn = {"backward": extra_backward, "repair": lambda: extra_repair(a.repair_steps),
               "insert": lambda: extra_insert(a.insert_steps),
               "batch": lambda: extra_batch(a.batch_shapes, a.batch_scale),
-              "tangent": lambda: extra_tangent(a.tangent_every)}[a.only]
+              "tangent": lambda: extra_tangent(a.tangent_every),
+              "refine_order": extra_refine_order}[a.only]
         print(json.dumps({a.only: fn()}), flush=True)
     elif a.impl == "reference":
         run_reference(a)

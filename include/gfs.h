@@ -221,6 +221,37 @@ int gfs_query_backward_noalloc(gfs_ctx* ctx, const void* x, int x_is_fp32, int64
  * Errors: GFS_ERR_STATE, GFS_ERR_ARG (cap too small: *count_host still set). */
 int gfs_survivors(gfs_ctx* ctx, int64_t* g_out, int64_t cap, int64_t* count_host);
 
+/* ---- refinement order (Sec. 4.2) ------------------------------------------ */
+/* The greedy refinement depends on the order of the new points.  The paper
+ * orders the interesting cells by a flood fill that starts at the least
+ * covered cell, with coverage estimated from regularly spaced points.
+ *
+ * gfs_cell_coverage: for each cell c with integer coordinates
+ * (i, j, k) = cells[3c .. 3c+2], its sub^3 points
+ *   origin + h * ((i, j, k) + ((a, b, c) + 1/2) / sub),  a, b, c < sub
+ * (each coordinate rounded per operation in that order) are tested for
+ * containment in the balls of the context's current samples, of either
+ * sign, shrunk by tol (the cull's coverage predicate, decided in FP64);
+ * counts_out[c] = the number contained (the covered area ratio times sub^3).
+ * cells: device, ncells*3 int32.  origin_host: host, 3 FP64.  h > 0.
+ * 1 <= sub <= 64.  counts_out: device, ncells uint32.  One warp per cell; no
+ * host synchronisation, no allocation.  Errors: GFS_ERR_STATE (no build),
+ * GFS_ERR_ARG, GFS_ERR_CUDA. */
+int gfs_cell_coverage(gfs_ctx* ctx, const int32_t* cells, int64_t ncells, const double* origin_host, double h,
+                      int sub, uint32_t* counts_out);
+
+/* gfs_flood_order (host computation, no device needed): the flood-fill
+ * order of ncells cells (cells_host: ncells*3 int32 coordinates, each
+ * within +-(2^20 - 2); counts_host: their covered counts).  Start at the
+ * cell with the lowest count; repeatedly take the queued cell with the
+ * lowest count (ties: lower index), emit it and queue its not yet queued
+ * neighbours among the listed cells (cells sharing a face, an edge or a
+ * corner); when the queue is empty, start again at the lowest-count cell
+ * not yet emitted.  order_out_host: host, ncells int64 indices in emission
+ * order.  Errors: GFS_ERR_ARG (null, negative count, a cell listed twice),
+ * GFS_ERR_TOO_LARGE (coordinates out of range). */
+int gfs_flood_order(const int32_t* cells_host, const uint32_t* counts_host, int64_t ncells, int64_t* order_out_host);
+
 /* ---- batched shapes ------------------------------------------------------ */
 /* One independent shape of a batched call: its samples, its query points and
  * its outputs (all device pointers; outputs nullable).  Layout and meaning

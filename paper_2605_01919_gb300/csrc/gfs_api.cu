@@ -12,6 +12,7 @@
 
 #include "gfs.h"
 #include "gfs_kernels.h"
+#include "gfs_order.h"
 #include "gfs_tangent.h"
 
 using namespace gfs;
@@ -534,6 +535,18 @@ int gfs_query_backward(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, cons
   a.acc_s = c->acc.as<long long>() + 3 * n;
   GFS_CK(launch_grad(a, n, nullptr, nullptr, c->stream));
   GFS_CK(launch_tangent_grad(a, n, grad_p, grad_sv, c->stream));
+  return GFS_OK;
+}
+
+int gfs_cell_coverage(gfs_ctx* c, const int32_t* cells, int64_t ncells, const double* origin_host, double h,
+                      int sub, uint32_t* counts_out) {
+  if (!c || ncells < 0 || !origin_host || !(h > 0.0) || sub < 1 || sub > 64) return GFS_ERR_ARG;
+  if (ncells > 0 && (!cells || !counts_out)) return GFS_ERR_ARG;
+  if (!c->built) return GFS_ERR_STATE;
+  if (ncells == 0) return GFS_OK;
+  QueryArgs a;
+  fill_query_args(c, a);
+  GFS_CK(launch_cell_coverage(a, cells, ncells, origin_host, h, sub, counts_out, c->stream));
   return GFS_OK;
 }
 
@@ -1188,7 +1201,7 @@ int gfs_stats(gfs_ctx* c, gfs_stats_t* out) {
   };
   unsigned long long own = 0, sorts = 0;
   launch_counts(&own, &sorts);
-  out->kernel_launches = int64_t(own + tangent_launch_count());
+  out->kernel_launches = int64_t(own + tangent_launch_count() + order_launch_count());
   out->sort_calls = int64_t(sorts);
   if (c->have_ev && c->built_timed) {
     out->ms_build_total = ms(0, 3);

@@ -20,7 +20,7 @@ FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 0x10, 0x20, 0x40
 EXPORTED = ["gfs_default_options", "gfs_create", "gfs_set_stream", "gfs_build", "gfs_query", "gfs_query_tangent",
             "gfs_query_backward", "gfs_query_backward_noalloc", "gfs_insert", "gfs_insert_known", "gfs_survivors", "gfs_batch_build", "gfs_batch_query",
             "gfs_batch_survivors", "gfs_stats", "gfs_solve_host", "gfs_icosphere", "gfs_strerror",
-            "gfs_destroy"]
+            "gfs_destroy", "gfs_cell_coverage", "gfs_flood_order"]
 
 
 class Options(ctypes.Structure):
@@ -100,6 +100,10 @@ def load(build_if_missing: bool = True):
     L.gfs_stats.restype = i32
     L.gfs_solve_host.argtypes = [P, P, P, i64, P, i32, i64, P, P, P]
     L.gfs_solve_host.restype = i32
+    L.gfs_cell_coverage.argtypes = [P, P, i64, P, f64, i32, P]
+    L.gfs_cell_coverage.restype = i32
+    L.gfs_flood_order.argtypes = [P, P, i64, P]
+    L.gfs_flood_order.restype = i32
     L.gfs_icosphere.argtypes = [i32, P, i64]
     L.gfs_icosphere.restype = i32
     L.gfs_strerror.argtypes = [i32]
@@ -127,6 +131,20 @@ def icosphere(tau: int):
     k = load().gfs_icosphere(tau, out.ctypes.data_as(ctypes.c_void_p), K)
     if k != K:
         raise GfsError("icosphere construction failed")
+    return out
+
+
+def flood_order(cells, counts):
+    """Flood-fill refinement order (Sec. 4.2) of cells ((c, 3) integer
+    coordinates) with covered counts (c,): host computation in the library,
+    returns the cell indices in order (numpy int64)."""
+    import numpy as np
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    counts = np.ascontiguousarray(counts, dtype=np.uint32)
+    assert cells.ndim == 2 and cells.shape[1] == 3 and counts.shape == (cells.shape[0],)
+    out = np.zeros(cells.shape[0], dtype=np.int64)
+    _check(load().gfs_flood_order(cells.ctypes.data_as(ctypes.c_void_p), counts.ctypes.data_as(ctypes.c_void_p),
+                                  cells.shape[0], out.ctypes.data_as(ctypes.c_void_p)))
     return out
 
 
@@ -246,6 +264,21 @@ class Context:
         _check(load().gfs_insert_known(self._h, _ptr(y), _ptr(known), T, _ptr(out["s64"]), _ptr(out["argmin"]),
                                        _ptr(out["flags"])))
         self.n = self.stats()["n_spheres"]
+        return out
+
+    # -- refinement order (Sec. 4.2) ------------------------------------------------
+    def cell_coverage(self, cells: torch.Tensor, origin, h: float, sub: int = 8) -> torch.Tensor:
+        """Covered sub-point counts of grid cells (cells: (c, 3) int32 cuda
+        integer coordinates; points origin + h * (ijk + (abc + 1/2) / sub))
+        against the current samples' balls; returns (c,) int32 counts."""
+        import numpy as np
+        assert cells.is_cuda and cells.dtype == torch.int32 and cells.shape[-1] == 3
+        cells = cells.contiguous()
+        o = np.ascontiguousarray(origin, dtype=np.float64)
+        out = torch.empty(cells.shape[0], dtype=torch.int32, device=cells.device)
+        self._sync_stream()
+        _check(load().gfs_cell_coverage(self._h, _ptr(cells), cells.shape[0], o.ctypes.data_as(ctypes.c_void_p),
+                                        float(h), int(sub), _ptr(out)))
         return out
 
     def survivors(self) -> torch.Tensor:

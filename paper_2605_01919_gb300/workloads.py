@@ -98,21 +98,32 @@ def sphere_grid(N: int = 16, up: int = 2, tau: int = 2) -> Workload:
                     lambda: grid_points(Nq), Nq ** 3, "f64")
 
 
-def union_grid(N: int = 64, up: int = 4, tau: int = 3, seed: int = 2000) -> Workload:
-    """Union (pointwise min) of 6 spheres (r ~ U[0.15,0.4]) and 4 axis-aligned
-    boxes (half-extents ~ U[0.1,0.3]^3), centres ~ U[-0.6,0.6]^3.
+def union_field(seed: int = 2000):
+    """The field of union_grid: pointwise min of 6 spheres (r ~ U[0.15,0.4])
+    and 4 axis-aligned boxes (half-extents ~ U[0.1,0.3]^3), centres
+    ~ U[-0.6,0.6]^3, as a function of (m, 3) points.
 
     The min of exact primitive SDFs is exact outside the union and a lower
     bound of the distance inside overlaps of primitives."""
     rng = np.random.default_rng(seed)
     sph = [(rng.uniform(-0.6, 0.6, 3), rng.uniform(0.15, 0.4)) for _ in range(6)]
     box = [(rng.uniform(-0.6, 0.6, 3), rng.uniform(0.1, 0.3, 3)) for _ in range(4)]
+
+    def field(p: np.ndarray) -> np.ndarray:
+        s = np.full(p.shape[0], np.inf)
+        for c, r in sph:
+            s = np.minimum(s, sdf_sphere(p, c, r))
+        for c, b in box:
+            s = np.minimum(s, sdf_box(p, c, b))
+        return s
+    return field
+
+
+def union_grid(N: int = 64, up: int = 4, tau: int = 3, seed: int = 2000) -> Workload:
+    """N^3 grid samples of union_field(seed); queries on the up-times
+    upsampled node grid."""
     p = grid_points(N)
-    s = np.full(p.shape[0], np.inf)
-    for c, r in sph:
-        s = np.minimum(s, sdf_sphere(p, c, r))
-    for c, b in box:
-        s = np.minimum(s, sdf_box(p, c, b))
+    s = union_field(seed)(p)
     Nq = up * (N - 1) + 1
     return Workload(f"union_grid{N}", p, s, tau, grid_spacing(N),
                     lambda: grid_points(Nq), Nq ** 3, "f64")

@@ -1,6 +1,7 @@
-// Test harness: runs the tangent pass's device routines (tangent_one) on the
-// CPU over a sphere hierarchy built here, refining the oracle's plain query
-// results in place.  The hierarchy has the library's layout (implicit 8-ary
+// Test harness: runs device routines of the library on the CPU over a
+// sphere hierarchy built here: the tangent pass (tangent_one), refining the
+// oracle's plain query results in place, and the cell coverage count of the
+// refinement order (cell_cover_count).  The hierarchy has the library's layout (implicit 8-ary
 // tree over sorted items) with bounding balls computed directly in FP64 and
 // rounded outwards to FP32, so every bound the routines rely on holds.
 // Item order: Morton order of the FP32 centres (order_seed = 0, as the
@@ -12,7 +13,7 @@
 #include <random>
 #include <vector>
 
-#include "gfs_tangent.cuh"
+#include "gfs_order.cuh"
 
 using namespace gfs;
 
@@ -25,29 +26,33 @@ float round_out(double v) {  // an FP32 value >= v
   return f * (f > 0 ? 1.000001f : 0.999999f) + 1e-7f;
 }
 
-}  // namespace
+struct HostTree {
+  std::vector<D4> sph;
+  std::vector<int> sid;
+  std::vector<float4> na, nb, nf, lo, hi;
+  Tree T{};
+};
 
-extern "C" int tangent_host(const double* p, const double* s, int64_t n, const double* U, int K, double tol,
-                            int clamp_opp, int box_cull, const double* x, int64_t m, double* value,
-                            int64_t* argmin, uint16_t* flags, unsigned order_seed) {
-  std::vector<D4> sph(n);
-  for (int64_t i = 0; i < n; ++i) sph[i] = D4{p[3 * i], p[3 * i + 1], p[3 * i + 2], s[i]};
-  std::vector<int> sid(n);
-  for (int64_t i = 0; i < n; ++i) sid[i] = int(i);
+// the hierarchy over (p, s) in the library's layout; false if too deep
+bool build_tree(const double* p, const double* s, int64_t n, unsigned order_seed, HostTree& H) {
+  H.sph.resize(n);
+  for (int64_t i = 0; i < n; ++i) H.sph[i] = D4{p[3 * i], p[3 * i + 1], p[3 * i + 2], s[i]};
+  H.sid.resize(n);
+  for (int64_t i = 0; i < n; ++i) H.sid[i] = int(i);
   if (order_seed == 0) {
     std::vector<uint32_t> key(n);
     for (int64_t i = 0; i < n; ++i) key[i] = morton3(float(p[3 * i]), float(p[3 * i + 1]), float(p[3 * i + 2]));
-    std::stable_sort(sid.begin(), sid.end(), [&](int a, int b) { return key[a] < key[b]; });
+    std::stable_sort(H.sid.begin(), H.sid.end(), [&](int a, int b) { return key[a] < key[b]; });
   } else {
     std::mt19937 rng(order_seed);
-    std::shuffle(sid.begin(), sid.end(), rng);
+    std::shuffle(H.sid.begin(), H.sid.end(), rng);
   }
-  Tree T{};
+  Tree& T = H.T;
   T.nitems = n;
   int64_t cnt = (n + kLeaf - 1) / kLeaf, total = 0;
   int L = 0;
   while (true) {
-    if (L >= kMaxLevels) return -1;
+    if (L >= kMaxLevels) return false;
     T.count[L] = cnt;
     T.offset[L] = total;
     total += cnt;
@@ -56,7 +61,13 @@ extern "C" int tangent_host(const double* p, const double* s, int64_t n, const d
     cnt = (cnt + kFan - 1) / kFan;
   }
   T.nlevels = L;
-  std::vector<float4> na(total), nb(total), nf(total), lo(total), hi(total);
+  H.na.resize(total);
+  H.nb.resize(total);
+  H.nf.resize(total);
+  H.lo.resize(total);
+  H.hi.resize(total);
+  const std::vector<D4>& sph = H.sph;
+  const std::vector<int>& sid = H.sid;
   int64_t span = kLeaf;
   for (int l = 0; l < L; ++l, span *= kFan) {
     for (int64_t j = 0; j < T.count[l]; ++j) {
@@ -86,27 +97,42 @@ extern "C" int tangent_host(const double* p, const double* s, int64_t n, const d
                     std::max(H4.z, std::nextafter(float(P.z), INFINITY)), 0};
       }
       const int64_t k = T.offset[l] + j;
-      na[k] = float4{C.x, C.y, C.z, round_out(std::max(wp, wn))};
-      nb[k] = float4{round_out(wp), round_out(wn), round_out(w0), 0};
-      nf[k] = float4{C.x, C.y, C.z, round_out(wf)};
-      lo[k] = L4;
-      hi[k] = H4;
+      H.na[k] = float4{C.x, C.y, C.z, round_out(std::max(wp, wn))};
+      H.nb[k] = float4{round_out(wp), round_out(wn), round_out(w0), 0};
+      H.nf[k] = float4{C.x, C.y, C.z, round_out(wf)};
+      H.lo[k] = L4;
+      H.hi[k] = H4;
     }
   }
-  T.na = na.data();
-  T.nb = nb.data();
-  T.nf = nf.data();
-  T.lo = lo.data();
-  T.hi = hi.data();
+  T.na = H.na.data();
+  T.nb = H.nb.data();
+  T.nf = H.nf.data();
+  T.lo = H.lo.data();
+  T.hi = H.hi.data();
+  return true;
+}
+
+QueryArgs args_for(const HostTree& H, int64_t n, double tol) {
   QueryArgs a{};
-  a.sid = sid.data();
-  a.sph64 = sph.data();
-  a.st = T;
+  a.sid = H.sid.data();
+  a.sph64 = H.sph.data();
+  a.st = H.T;
   a.n = n;
+  a.tol = tol;
+  return a;
+}
+
+}  // namespace
+
+extern "C" int tangent_host(const double* p, const double* s, int64_t n, const double* U, int K, double tol,
+                            int clamp_opp, int box_cull, const double* x, int64_t m, double* value,
+                            int64_t* argmin, uint16_t* flags, unsigned order_seed) {
+  HostTree H;
+  if (!build_tree(p, s, n, order_seed, H)) return -1;
+  QueryArgs a = args_for(H, n, tol);
   a.U64 = U;
   a.K = K;
   a.KS = K + 1;
-  a.tol = tol;
   a.clamp_opp = clamp_opp;
   a.x64 = x;
   a.m = m;
@@ -114,5 +140,16 @@ extern "C" int tangent_host(const double* p, const double* s, int64_t n, const d
   a.arg_out = argmin;
   a.fl_out = flags;
   for (int64_t q = 0; q < m; ++q) tangent::tangent_one(a, box_cull, q);
+  return 0;
+}
+
+extern "C" int coverage_host(const double* p, const double* s, int64_t n, double tol, const int32_t* cells,
+                             int64_t ncells, const double* origin, double h, int sub, uint32_t* counts,
+                             unsigned order_seed) {
+  HostTree H;
+  if (!build_tree(p, s, n, order_seed, H)) return -1;
+  const QueryArgs a = args_for(H, n, tol);
+  for (int64_t c = 0; c < ncells; ++c)
+    counts[c] = order::cell_cover_count(a, cells + 3 * c, origin[0], origin[1], origin[2], h, sub, 0, 1);
   return 0;
 }

@@ -74,3 +74,37 @@ def test_no_device_fails_loudly(gfs):
     assert L.gfs_create(ctypes.byref(h), None, None) == 3                      # GFS_ERR_CUDA
     with pytest.raises(gfs.GfsError):
         gfs.Context()
+
+
+def test_flood_order_matches_oracle(gfs, orc):
+    """The library's flood-fill order (host code) equals the oracle's on the
+    hand-worked cases and on random sparse cell sets, ties included."""
+    from tests.test_oracle import FLOOD_CASES
+    for cells, counts, order in FLOOD_CASES:
+        assert list(gfs.flood_order(np.array(cells), np.array(counts))) == order
+    rng = np.random.default_rng(11)
+    for trial in range(20):
+        side = int(rng.integers(2, 12))
+        all_cells = np.array([(i, j, k) for i in range(side) for j in range(side) for k in range(side)]) - side // 2
+        cells = all_cells[rng.random(all_cells.shape[0]) < rng.uniform(0.05, 0.6)]
+        if cells.shape[0] == 0:
+            continue
+        cells = cells[rng.permutation(cells.shape[0])]
+        counts = rng.integers(0, 6, cells.shape[0])        # many ties
+        assert list(gfs.flood_order(cells, counts)) == orc.flood_order(cells, counts)
+
+
+def test_flood_order_errors(gfs):
+    L = gfs.load()
+    P = ctypes.c_void_p
+    cells = np.array([[0, 0, 0], [1, 0, 0], [0, 0, 0]], dtype=np.int32)
+    counts = np.zeros(3, dtype=np.uint32)
+    out = np.zeros(3, dtype=np.int64)
+    args = [cells.ctypes.data_as(P), counts.ctypes.data_as(P)]
+    assert L.gfs_flood_order(*args, 3, out.ctypes.data_as(P)) == 1          # a cell listed twice
+    assert L.gfs_flood_order(*args, 2, out.ctypes.data_as(P)) == 0
+    assert list(out[:2]) == [0, 1]
+    assert L.gfs_flood_order(*args, 0, out.ctypes.data_as(P)) == 0          # empty
+    assert L.gfs_flood_order(None, None, 2, None) == 1
+    far = np.array([[1 << 21, 0, 0]], dtype=np.int32)
+    assert L.gfs_flood_order(far.ctypes.data_as(P), counts.ctypes.data_as(P), 1, out.ctypes.data_as(P)) == 6

@@ -1,5 +1,6 @@
-"""The tangent pass's device routines, compiled as host C++, against the
-oracle's augmented query (CPU, no GPU needed).
+"""Device routines compiled as host C++, against the oracle (CPU, no GPU
+needed): the tangent pass and the cell coverage count of the refinement
+order.
 
 `csrc/gfs_tangent.cuh` holds the whole per-point logic of gfs_query_tangent:
 the FP64 pass over the sphere hierarchy, the tangent-point search with its
@@ -41,6 +42,9 @@ def host(tmp_path_factory):
     L.tangent_host.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                P, ctypes.c_int64, P, P, P, ctypes.c_uint]
     L.tangent_host.restype = ctypes.c_int
+    L.coverage_host.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, P, ctypes.c_int64, P, ctypes.c_double,
+                                ctypes.c_int, P, ctypes.c_uint]
+    L.coverage_host.restype = ctypes.c_int
     return L
 
 
@@ -105,3 +109,45 @@ def test_host_union_grid(host, orc):
 def test_host_torus_fp32_points(host, orc):
     w = W.torus_grid(N=14, m=600)
     assert check(host, orc, w.p, w.s, w.tau, w.make_queries().astype(np.float64), orders=(0,)) > 20
+
+
+def _coverage(host, p, s, cells, origin, h, sub, tol, order):
+    p, s = np.ascontiguousarray(p, np.float64), np.ascontiguousarray(s, np.float64)
+    cells = np.ascontiguousarray(cells, np.int32)
+    origin = np.ascontiguousarray(origin, np.float64)
+    out = np.zeros(cells.shape[0], np.uint32)
+    assert host.coverage_host(_ptr(p), _ptr(s), p.shape[0], tol, _ptr(cells), cells.shape[0], _ptr(origin), h, sub,
+                              _ptr(out), order) == 0
+    return out
+
+
+@pytest.mark.parametrize("sub", [1, 3, 8])
+def test_host_cell_coverage(host, orc, sub):
+    """Covered sub-point counts of the surface cells of a 12^3 union grid and
+    of random cells, against the oracle's brute force."""
+    w = W.union_grid(N=12, up=4)
+    N = 12
+    S = w.s.reshape(N, N, N)
+    near = np.abs(S) < 0.5 * np.sqrt(3) * w.h
+    cell = near[:-1, :-1, :-1] | near[1:, 1:, 1:] | near[1:, :-1, :-1] | near[:-1, 1:, 1:]
+    cells = np.argwhere(cell).astype(np.int32)
+    rng = np.random.default_rng(sub)
+    cells = np.concatenate([cells[rng.choice(cells.shape[0], min(150, cells.shape[0]), replace=False)],
+                            rng.integers(-2, N + 1, size=(40, 3)).astype(np.int32)])
+    origin = np.array([-1.0, -1.0, -1.0])
+    want = orc.cell_coverage(w.p, w.s, cells, origin, w.h, sub)
+    assert 0 < want.sum() < cells.shape[0] * sub ** 3
+    for order in (0, 5):
+        got = _coverage(host, w.p, w.s, cells, origin, w.h, sub, 1e-6, order)
+        assert np.array_equal(got, want)
+
+
+def test_host_cell_coverage_lattice_shells(host, orc):
+    """The oracle's shell-count pins hold for the device routine too."""
+    h = 0.05
+    origin = np.array([-1.0, -1.0, -1.0])
+    cell = np.array([[2, -1, 3]])
+    centre = origin + h * (cell[0] + 0.5)
+    for R2, count in [(2.0, 0), (7.0, 8), (15.0, 32), (23.0, 56), (31.0, 88), (150.0, 512)]:
+        s = np.array([-h / 16 * np.sqrt(R2)])
+        assert _coverage(host, centre[None], s, cell, origin, h, 8, 0.0, 0)[0] == count
