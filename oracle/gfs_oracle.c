@@ -965,3 +965,102 @@ void orc_cell_coverage(const double* p, const double* s, int64_t n, double tol, 
     counts[c] = cnt;
   }
 }
+
+/* Lazy variant of orc_query_aug for single points on large inputs: the same
+ * result, with the plain part from orc_query_lazy and the tangent part
+ * restricted to the points that can matter:
+ *  - a tangent point only changes the result when it is nearer than the
+ *    plain result's candidate (squared distance below the survivor's;
+ *    distance at most UB_opp for an OPPOSITE result; anything for LOWER);
+ *  - a point nearer to x than LB - tol (LB = r_j - |x - p_j| for the sphere
+ *    j of x's class that attains it) lies in j's shrunk ball, so it is
+ *    covered (the fact orc_query_lazy uses for candidates); j's own points
+ *    are kept regardless.
+ * The rest are sorted by (squared distance, id) and coverage-tested in that
+ * order; the first uncovered one is the nearest kept tangent point. */
+void orc_query_aug_lazy(const double* p, const double* s, int64_t n, const double* U, int K, double tol,
+                        int box_cull, int clamp_opp, const double* x, int64_t m, double* value, int64_t* argmin,
+                        int32_t* flags) {
+  size_t cap = 1 << 12;
+  orc_cd* buf = (orc_cd*)malloc(sizeof(orc_cd) * cap);
+  for (int64_t t = 0; t < m; ++t) {
+    const double* xq = x + 3 * t;
+    double v0;
+    int64_t a0;
+    int32_t f0;
+    orc_query_lazy(p, s, n, U, K, tol, box_cull, clamp_opp, xq, 1, &v0, &a0, &f0, NULL);
+    value[t] = v0;
+    argmin[t] = a0;
+    flags[t] = f0;
+    const int code = f0 & 15;
+    if (code != CODE_SURVIVOR && code != CODE_OPPOSITE && code != CODE_LOWER) continue;
+    int sig = 0;
+    classify(p, s, n, tol, xq, &sig);
+    double lbv = -ORC_INF, ub = ORC_INF;
+    int64_t lbj = -1;
+    for (int64_t j = 0; j < n; ++j) {
+      double d = sqrt(dist2(xq, p + 3 * j)), r = fabs(s[j]);
+      int c = sgn(s[j]);
+      if (c == sig && r - d > lbv) { lbv = r - d; lbj = j; }
+      if (c == -sig && d - r < ub) ub = d - r;
+    }
+    double sbest = ORC_INF;
+    if (code == CODE_SURVIVOR) {
+      double q[3];
+      cand_pos(p + 3 * (a0 / (K + 1)), s[a0 / (K + 1)], U + 3 * (a0 % (K + 1)), q);
+      sbest = dist2(xq, q);
+    }
+    const double skip = lbv - tol - 1e-9 * (1.0 + fabs(lbv));
+    size_t nc = 0;
+    for (int64_t j = 0; j < n; ++j) {
+      if (sgn(s[j]) != sig) continue;
+      const double r = fabs(s[j]);
+      const double* pj = p + 3 * j;
+      double v[3] = {xq[0] - pj[0], xq[1] - pj[1], xq[2] - pj[2]};
+      const double dv = norm3(v);
+      if (!(dv > 0.0)) continue;
+      for (int side = 0; side < 2; ++side) {
+        const double sgnr = side == 0 ? r : -r;
+        double tp[3];
+        for (int c = 0; c < 3; ++c) tp[c] = pj[c] + sgnr * (v[c] / dv);
+        if (box_cull && !inbox(tp)) continue;
+        const double d2 = dist2(xq, tp);
+        if (code == CODE_SURVIVOR && !(d2 < sbest)) continue;
+        if (code == CODE_OPPOSITE && !(sqrt(d2) <= ub)) continue;
+        if (j != lbj && skip > 0 && sqrt(d2) < skip) continue;
+        if (nc == cap) {
+          cap *= 2;
+          buf = (orc_cd*)realloc(buf, sizeof(orc_cd) * cap);
+        }
+        buf[nc].d2 = d2;
+        buf[nc].g = 2 * j + side;
+        ++nc;
+      }
+    }
+    qsort(buf, nc, sizeof(orc_cd), cmp_cd);
+    for (size_t u = 0; u < nc; ++u) {
+      const int64_t j = buf[u].g / 2;
+      const double r = fabs(s[j]);
+      const double* pj = p + 3 * j;
+      double v[3] = {xq[0] - pj[0], xq[1] - pj[1], xq[2] - pj[2]};
+      const double dv = norm3(v);
+      const double sgnr = buf[u].g % 2 == 0 ? r : -r;
+      double tp[3];
+      for (int c = 0; c < 3; ++c) tp[c] = pj[c] + sgnr * (v[c] / dv);
+      int cov = 0;
+      for (int64_t k = 0; k < n && !cov; ++k)
+        if (k != j && covers(tp, p + 3 * k, s[k], tol)) cov = 1;
+      if (cov) continue;
+      orc_result T = finish(p, s, n, tol, clamp_opp, xq, sig, buf[u].d2, 0, ORC_INF);
+      if ((T.flags & 15) == CODE_SURVIVOR) {
+        T.flags = (T.flags & ~15) | CODE_TANGENT;
+        T.argmin = buf[u].g;
+      }
+      value[t] = T.value;
+      argmin[t] = T.argmin;
+      flags[t] = T.flags;
+      break;
+    }
+  }
+  free(buf);
+}

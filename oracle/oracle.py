@@ -68,6 +68,8 @@ def lib():
         L.orc_insert_state.restype = i64
         L.orc_exact_rmin.argtypes = [P, P, i64, f64, i32, P, i32]
         L.orc_exact_rmin.restype = f64
+        L.orc_query_aug_lazy.argtypes = [P, P, i64, P, i32, f64, i32, i32, P, i64, P, P, P]
+        L.orc_query_aug_lazy.restype = None
         L.orc_cell_coverage.argtypes = [P, P, i64, f64, P, i64, P, f64, i32, P]
         L.orc_cell_coverage.restype = None
         _lib = L
@@ -148,6 +150,21 @@ def query_aug(p, s, surv, x, tol=TOL, clamp_opp=True, box_cull=True):
     if m:
         lib().orc_query_aug(_ptr(p), _ptr(s), s.shape[0], _ptr(g), _ptr(sph), _ptr(q), g.shape[0], tol,
                             int(clamp_opp), int(box_cull), _ptr(x), m, _ptr(val), _ptr(arg), _ptr(fl))
+    return val, arg, fl
+
+
+def query_aug_lazy(p, s, U, x, tol=TOL, box_cull=True, clamp_opp=True):
+    """Same result as ``query_aug`` on the full survivor list, for a few
+    points on large inputs (tangent points coverage-tested only where they
+    can change the result).  Returns (value, argmin, flags)."""
+    p, s, U, x = _c(p, np.float64), _c(s, np.float64), _c(U, np.float64), _c(x, np.float64)
+    m = x.shape[0]
+    val = np.zeros(m, np.float64)
+    arg = np.zeros(m, np.int64)
+    fl = np.zeros(m, np.int32)
+    if m:
+        lib().orc_query_aug_lazy(_ptr(p), _ptr(s), s.shape[0], _ptr(U), U.shape[0], tol, int(box_cull),
+                                 int(clamp_opp), _ptr(x), m, _ptr(val), _ptr(arg), _ptr(fl))
     return val, arg, fl
 
 

@@ -192,3 +192,29 @@ def test_tangent_full_size_properties(G):
     assert np.allclose(np.abs(v1[won]), expect, rtol=1e-12, atol=1e-14)
     assert np.array_equal(w.s[j] < 0, np.signbit(v1[won]))
     print(f"tangent wins: {won.sum()} of {won.size}")
+
+
+def _aug_worker(args):
+    from oracle import oracle as O
+    p, s, tau, x = args
+    return O.query_aug_lazy(p, s, O.icosphere(tau), x)
+
+
+def test_tangent_full_size_sampled(G, orc):
+    """64^3 union grid (262,144 samples, tau = 3): 48 points within 2h of the
+    surface, augmented on the GPU, against the lazy augmented oracle (spawned
+    host processes) bit for bit."""
+    import multiprocessing as mp
+    from tests.test_gpu_parity import _near_surface
+    w = W.union_grid()
+    x = w.make_queries()
+    sel = _near_surface(w, x, 48, 17, 2.0)
+    xs = np.ascontiguousarray(x[sel])
+    res = run_gpu(G, w.p, w.s, w.tau, xs)
+    with mp.get_context("spawn").Pool(min(16, mp.cpu_count())) as pool:
+        outs = pool.map(_aug_worker, [(w.p, w.s, w.tau, xs[i:i + 1]) for i in range(xs.shape[0])], chunksize=1)
+    val = np.concatenate([o[0] for o in outs])
+    arg = np.concatenate([o[1] for o in outs])
+    fl = np.concatenate([o[2] for o in outs])
+    assert np.sum((fl & 15) == G.CODE_TANGENT) > 5
+    assert_parity(res, val, arg, fl, w.h)

@@ -679,3 +679,34 @@ def test_flood_order_components_contiguous(orc):
         assert f == min(members, key=lambda i: (counts[i], i))
     keys = [(counts[f], f) for f in firsts]
     assert keys == sorted(keys)
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (7, 2), (37, 3), (257, 5)])
+def test_query_aug_lazy_equals_brute_force(orc, n, seed):
+    """The lazy augmented query (plain part from query_lazy, tangent points
+    tested only where they can change the result) equals the brute-force
+    augmented query bit for bit, option combinations included."""
+    p, s = W.tiny_random(n, seed, valid=(seed % 3 != 0), spread=0.9)
+    rng = np.random.default_rng(1000 + seed)
+    x = np.concatenate([rng.uniform(-1, 1, size=(200, 3)), p[: min(n, 10)], rng.uniform(-1.5, 1.5, size=(10, 3))])
+    for tau in (0, 2):
+        U = orc.icosphere(tau)
+        for box_cull, clamp in [(True, True), (False, True), (True, False)]:
+            surv = orc.collect(p, s, U, orc.keep_all(p, s, U, box_cull=box_cull))
+            a = orc.query_aug(p, s, surv, x, clamp_opp=clamp, box_cull=box_cull)
+            b = orc.query_aug_lazy(p, s, U, x, box_cull=box_cull, clamp_opp=clamp)
+            assert np.array_equal(a[0], b[0], equal_nan=True)
+            assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_query_aug_lazy_equals_brute_force_grids(orc):
+    for w in (W.sphere_grid(N=10, up=2, tau=2), W.union_grid(N=12, up=4)):
+        x = w.make_queries()
+        x = x[np.random.default_rng(6).choice(x.shape[0], 300, replace=False)]
+        U = orc.icosphere(w.tau)
+        surv = orc.collect(w.p, w.s, U, orc.keep_all(w.p, w.s, U))
+        a = orc.query_aug(w.p, w.s, surv, x)
+        b = orc.query_aug_lazy(w.p, w.s, U, x)
+        assert np.sum((a[2] & 15) == orc.CODE_TANGENT) > 10
+        assert np.array_equal(a[0], b[0], equal_nan=True)
+        assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
