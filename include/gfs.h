@@ -105,8 +105,8 @@ int gfs_set_stream(gfs_ctx* ctx, void* cuda_stream);
  * survivor hierarchies.  Inputs are copied; the caller may free them after
  * the call returns.  Synchronises the stream twice (the coordinate bound
  * that sets the hierarchy's rounding slack, and the survivor count).
- * Errors: GFS_ERR_ARG (n < 1, null), GFS_ERR_TOO_LARGE (n*(K+1) >= 2^32),
- * GFS_ERR_OOM, GFS_ERR_CUDA. */
+ * Errors: GFS_ERR_ARG (n < 1, null), GFS_ERR_TOO_LARGE (n*(K+1) >= 2^32, or
+ * more than 2^30 survivors of one sign class), GFS_ERR_OOM, GFS_ERR_CUDA. */
 int gfs_build(gfs_ctx* ctx, const double* p_xyz, const double* s, int64_t n);
 
 /* Consistent value at m query points (Prop. 2 / Sec. 6 minimum radius,

@@ -90,6 +90,11 @@ void tree_layout(Tree& T, int64_t nitems) {
   T.nlevels = L;
 }
 
+// Survivors of one sign class that a hierarchy can index: node indices are
+// 27-bit fields (pack_node) over leaves of kLeaf items, and sort values are
+// int32.
+constexpr unsigned kMaxSurvivors = 1u << 30;
+
 int64_t tree_nodes(const Tree& T) {
   return T.nlevels ? T.offset[T.nlevels - 1] + T.count[T.nlevels - 1] : 0;
 }
@@ -430,6 +435,7 @@ int build_finish(gfs_ctx* c) {
   }
   c->nsurv[0] = c->host_cnt.nsurv[0];
   c->nsurv[1] = c->host_cnt.nsurv[1];
+  if (std::max(c->nsurv[0], c->nsurv[1]) > kMaxSurvivors) return GFS_ERR_TOO_LARGE;
   GFS_TRY(build_point_tree(c, 0));
   GFS_TRY(build_point_tree(c, 1));
   if (c->have_ev) {
@@ -606,6 +612,7 @@ int ins_rebuild(gfs_ctx* c, int64_t n_total) {
                               c->surv_raw[k].as<float4>(), cnt.as<unsigned>(), st));
     GFS_CK(cudaMemcpyAsync(&hc, cnt.p, 4, cudaMemcpyDeviceToHost, st));
     GFS_CK(cudaStreamSynchronize(st));
+    if (hc > kMaxSurvivors) return GFS_ERR_TOO_LARGE;
     c->nsurv[k] = hc;
     c->cap = std::max(c->cap, hc);
   }
@@ -1001,6 +1008,7 @@ int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
     if (attempt == 2) return GFS_ERR_OOM;
   }
   // survivor forests, one tree per (shape, sign class)
+  if (std::max(c->b_nsurv[0], c->b_nsurv[1]) > kMaxSurvivors) return GFS_ERR_TOO_LARGE;
   for (int k = 0; k < 2; ++k) {
     const unsigned nsv = c->b_nsurv[k];
     GFS_TRY(ensure(c->b_hist, size_t(ns) * 4));
