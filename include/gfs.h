@@ -144,8 +144,10 @@ int gfs_query(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, float* s_ou
  * s_out, s64_out: its value outputs (device, nullable), rewritten likewise.
  * gfs_query_backward differentiates TANGENT results as distances to the
  * moving tangent point (d|x - t|/dx = +-(x - p_j)/|x - p_j|).
- * No host synchronisation, no allocation.  Errors: GFS_ERR_STATE (no build),
- * GFS_ERR_ARG, GFS_ERR_TOO_LARGE (m >= 2^32), GFS_ERR_CUDA. */
+ * Points are processed in Morton order (library-owned key and order
+ * buffers grow when m grows, as in gfs_query).  No host synchronisation.
+ * Errors: GFS_ERR_STATE (no build), GFS_ERR_ARG, GFS_ERR_TOO_LARGE
+ * (m >= 2^32), GFS_ERR_OOM, GFS_ERR_CUDA. */
 int gfs_query_tangent(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, float* s_out, double* s64_out,
                       int64_t* argmin_out, uint16_t* flags_out);
 

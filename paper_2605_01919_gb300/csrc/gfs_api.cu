@@ -571,6 +571,15 @@ int gfs_query_tangent(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, float
   a.s64_out = s64_out;
   a.arg_out = argmin_out;
   a.fl_out = flags_out;
+  // Morton order of the points (as in gfs_query)
+  GFS_TRY(ensure(c->qk_in, size_t(m) * 4));
+  GFS_TRY(ensure(c->qk_out, size_t(m) * 4));
+  GFS_TRY(ensure(c->qv_in, size_t(m) * 4));
+  GFS_TRY(ensure(c->qv_out, size_t(m) * 4));
+  GFS_CK(launch_query_keys(a.x64, a.x32, m, c->qk_in.as<uint32_t>(), c->qv_in.as<int>(), c->stream));
+  GFS_TRY(sort_u32_pairs(c, c->qk_in.as<uint32_t>(), c->qk_out.as<uint32_t>(), c->qv_in.as<int>(),
+                         c->qv_out.as<int>(), m));
+  a.perm = reinterpret_cast<const uint32_t*>(c->qv_out.p);
   GFS_CK(launch_query_tangent(a, c->opt.box_cull, c->stream));
   return GFS_OK;
 }

@@ -10,9 +10,12 @@ namespace gfs {
 
 namespace {
 
+// one thread per point, points taken in the order a.perm gives (Morton
+// order: a warp's points are neighbours and walk similar paths)
 __global__ void __launch_bounds__(128) k_query_tangent(QueryArgs a, int box_cull) {
-  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (q < a.m) tangent::tangent_one(a, box_cull, q);
+  const int64_t slot = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (slot >= a.m) return;
+  tangent::tangent_one(a, box_cull, a.perm ? int64_t(a.perm[slot]) : slot);
 }
 
 constexpr double kFixScale = 1099511627776.0;  // 2^40, the backward's fixed-point scale
