@@ -17,9 +17,10 @@
 //
 // Every value that decides anything is computed in FP64 with each operation
 // rounded on its own, in the order written, so the decisions are those of a
-// plain IEEE-754 evaluation.  Hierarchy pruning uses the FP32 node balls,
-// widened by a relative and an absolute margin, so it only skips nodes that
-// cannot hold a deciding sphere.
+// plain IEEE-754 evaluation.  Node tests and per-sphere screens run in FP32
+// on the FP32 copies of the positions, widened by a bound on their rounding
+// error (err32), so they only skip nodes and spheres that cannot decide
+// anything; what passes them is evaluated in FP64.
 #pragma once
 
 #include <climits>
@@ -35,10 +36,36 @@ constexpr double kAbs = 1e-12;
 
 __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 
-// a bound computed from FP32 node data in FP64, moved outwards by far more
-// than its rounding error
-__device__ __forceinline__ double widen_up(double v) { return v + fabs(v) * 1e-12 + kAbs; }
-__device__ __forceinline__ double widen_dn(double v) { return v - fabs(v) * 1e-12 - kAbs; }
+
+// |x - q| in FP32, x rounded from FP64, q an FP32 point (node centre, or a
+// sphere centre rounded from FP64)
+__device__ __forceinline__ float dist32(float x, float y, float z, const float4& q) {
+  const float dx = x - q.x, dy = y - q.y, dz = z - q.z;
+  return sqrtf(dx * dx + dy * dy + dz * dz);
+}
+
+__device__ __forceinline__ float amax3(float x, float y, float z) { return fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z))); }
+
+// Bound on the error of dist32, and of an FP32 expression dist32 +- r +- this
+// bound for a value r (a radius rounded from FP64, or an exact node radius),
+// against the exact values of the FP64 points: the roundings of the
+// coordinates (u |x| + u |q| per axis, sqrt 3 of that in the norm), of the
+// FP32 norm (about 2.5 u d) and of the sums (a few u (d + r)), u = 2^-24,
+// taken four times over.
+__device__ __forceinline__ float err32(float ax, const float4& q, float d, float r) {
+  return 16.f * 5.9604645e-8f * (ax + amax3(q.x, q.y, q.z) + d + fabsf(r)) + 1e-30f;
+}
+
+// FP32 values on the safe side of an FP64 threshold (one FP32 rounding of
+// relative size <= u, covered twice)
+__device__ __forceinline__ float f_up(double v) {
+  const float f = float(v);
+  return f + fabsf(f) * 2.4e-7f + 1e-37f;
+}
+__device__ __forceinline__ float f_dn(double v) {
+  const float f = float(v);
+  return f - fabsf(f) * 2.4e-7f - 1e-37f;
+}
 
 __device__ __forceinline__ void load_point(const QueryArgs& a, int64_t q, double& x, double& y, double& z) {
   if (a.x32) {
@@ -69,6 +96,11 @@ __device__ inline void sphere_bounds(const QueryArgs& a, double x, double y, dou
   R.bestA[0] = R.bestA[1] = INFINITY;
   R.idxA[0] = R.idxA[1] = INT_MAX;
   R.bestF = INFINITY;
+  const float x32 = float(x), y32 = float(y), z32 = float(z), ax = amax3(x32, y32, z32);
+  // FP32 copies (rounded up) of the thresholds a sphere must reach to matter:
+  // the far bound, and per class the best |x - p| - r (at least -tol while
+  // the class has no containing ball)
+  float thF = INFINITY, thA[2] = {INFINITY, INFINITY};
   const Tree& T = a.st;
   uint32_t stack[kStack];
   int sp = 0;
@@ -81,6 +113,14 @@ __device__ inline void sphere_bounds(const QueryArgs& a, double x, double y, dou
     if (lev == 0) {
       const int64_t b = idx * kLeaf, e = imin64(b + kLeaf, a.n);
       for (int64_t j = b; j < e; ++j) {
+        // screen: the sphere can only matter if it may lower the far bound,
+        // lower (or tie) its class's |x - p| - r, or contain x
+        const float4 S = a.sph[j];
+        const float d32 = dist32(x32, y32, z32, S), r32 = fabsf(S.w);
+        const float er = err32(ax, S, d32, r32);
+        bool need = d32 + r32 - er <= thF;
+        if (S.w != 0.f) need = need || d32 - r32 - er <= thA[S.w < 0.f];
+        if (!need) continue;
         const int o = a.sid[j];
         const D4 P = a.sph64[o];
         const double d2 = ex_d2(x, y, z, P.x, P.y, P.z);
@@ -97,9 +137,13 @@ __device__ inline void sphere_bounds(const QueryArgs& a, double x, double y, dou
             R.bestA[c] = av;
             R.idxA[c] = o;
           }
+          thA[c] = f_up(R.cov[c] ? R.bestA[c] : fmax(R.bestA[c], -tol));
         }
         const double f = __dadd_rn(dl, r);
-        if (f < R.bestF) R.bestF = f;
+        if (f < R.bestF) {
+          R.bestF = f;
+          thF = f_up(f);
+        }
       }
     } else {
       const int64_t cb = idx * kFan, ce = imin64(cb + kFan, T.count[lev - 1]);
@@ -107,20 +151,18 @@ __device__ inline void sphere_bounds(const QueryArgs& a, double x, double y, dou
       for (int64_t c = cb; c < ce; ++c) {
         const float4 B = T.na[off + c], W = T.nb[off + c], Fb = T.nf[off + c];
         // far bound: |x - p_j| + r_j >= |x - F| - wf
-        const double tf = (R.bestF + double(Fb.w)) * kRel + kAbs;
-        bool need = tf > 0.0 && ball_d2_64(x, y, z, Fb) <= tf * tf;
+        const float dF = dist32(x32, y32, z32, Fb);
+        bool need = dF - err32(ax, Fb, dF, Fb.w) - Fb.w <= thF;
         // near bound per class: |x - p_j| - r_j >= |x - C| - w_class; a class
         // without containment yet also needs every ball that could hold x
-        double v = -INFINITY;
-        for (int cl = 0; cl < 2; ++cl) {
-          const float w = cl == 0 ? W.x : W.y;
-          if (!(w > -INFINITY)) continue;
-          double th = R.bestA[cl];
-          if (!R.cov[cl]) th = fmax(th, -tol);
-          v = fmax(v, th + double(w));
+        if (!need) {
+          const float dC = dist32(x32, y32, z32, B);
+          for (int cl = 0; cl < 2 && !need; ++cl) {
+            const float w = cl == 0 ? W.x : W.y;
+            if (!(w > -INFINITY)) continue;
+            need = dC - err32(ax, B, dC, w) - w <= thA[cl];
+          }
         }
-        const double t = v * kRel + kAbs;
-        need = need || (t > 0.0 && ball_d2_64(x, y, z, B) <= t * t);
         if (need) stack[sp++] = pack_node(lev - 1, c);
       }
     }
@@ -131,6 +173,8 @@ __device__ inline void sphere_bounds(const QueryArgs& a, double x, double y, dou
 // t (Sec. 3.1: the open balls; App. B tolerance), or -1.  A ball of the node
 // with centre C and radius bound w can only contain t when |t - C| < w.
 __device__ inline int covered_by_other(const QueryArgs& a, double tx, double ty, double tz, int skip) {
+  const float x32 = float(tx), y32 = float(ty), z32 = float(tz), ax = amax3(x32, y32, z32);
+  const float ntol = -f_dn(a.tol);  // >= -tol
   const Tree& T = a.st;
   uint32_t stack[kStack];
   int sp = 0;
@@ -143,6 +187,11 @@ __device__ inline int covered_by_other(const QueryArgs& a, double tx, double ty,
     if (lev == 0) {
       const int64_t b = idx * kLeaf, e = imin64(b + kLeaf, a.n);
       for (int64_t j = b; j < e; ++j) {
+        // screen: containment needs |t - p| < r - tol
+        const float4 S = a.sph[j];
+        if (S.w == 0.f) continue;
+        const float d32 = dist32(x32, y32, z32, S), r32 = fabsf(S.w);
+        if (d32 - r32 - err32(ax, S, d32, r32) >= ntol) continue;
         const int o = a.sid[j];
         if (o == skip) continue;
         if (ex_cov(tx, ty, tz, a.sph64[o], a.tol)) return o;
@@ -152,9 +201,9 @@ __device__ inline int covered_by_other(const QueryArgs& a, double tx, double ty,
       const int64_t off = T.offset[lev - 1];
       for (int64_t c = cb; c < ce; ++c) {
         const float4 B = T.na[off + c];
-        if (!(B.w > -INFINITY)) continue;
-        const double t = double(B.w) * kRel + kAbs;
-        if (t > 0.0 && ball_d2_64(tx, ty, tz, B) <= t * t) stack[sp++] = pack_node(lev - 1, c);
+        if (!(B.w > 0.f)) continue;
+        const float dC = dist32(x32, y32, z32, B);
+        if (dC - err32(ax, B, dC, B.w) < B.w) stack[sp++] = pack_node(lev - 1, c);
       }
     }
   }
@@ -194,6 +243,7 @@ __device__ inline void tangent_search(const QueryArgs& a, int box_cull, double x
   const int top = T.nlevels - 1;
   for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
   const double lim_d = mode == kBelowSurvivor ? sqrt(lim) : (mode == kWithinOpposite ? lim : INFINITY);
+  const float x32 = float(x), y32 = float(y), z32 = float(z), ax = amax3(x32, y32, z32);
   int hint = -1;  // the ball that covered the last tangent point tested: neighbours often share it
   while (sp > 0) {
     const uint32_t nd = stack[--sp];
@@ -201,21 +251,25 @@ __device__ inline void tangent_search(const QueryArgs& a, int box_cull, double x
     const int64_t idx = node_index(nd);
     // distances beyond hi cannot change the result
     const double hi = (B.id >= 0 ? fmin(lim_d, sqrt(B.d2)) : lim_d) * kRel + kAbs;
+    const float hi_f = f_up(hi), lo_f = f_dn(lo);
     if (lev == 0) {
       const int64_t b = idx * kLeaf, e = imin64(b + kLeaf, a.n);
       for (int64_t j = b; j < e; ++j) {
+        const float4 S = a.sph[j];
+        if (S.w == 0.f || int(S.w < 0.f) != cs) continue;
+        // screen: |x - t| is |d - r| (near) or d + r (far)
+        const float d32 = dist32(x32, y32, z32, S), r32 = fabsf(S.w);
+        const float er = err32(ax, S, d32, r32);
+        const float an32 = fabsf(d32 - r32), af32 = d32 + r32;
+        const bool try_near = an32 + er >= lo_f && an32 - er <= hi_f;
+        const bool try_far = af32 + er >= lo_f && af32 - er <= hi_f;
+        if (!try_near && !try_far) continue;
         const int o = a.sid[j];
         const D4 P = a.sph64[o];
-        if (P.w == 0.0 || int(P.w < 0.0) != cs) continue;
         const double r = fabs(P.w);
         const double vx = __dsub_rn(x, P.x), vy = __dsub_rn(y, P.y), vz = __dsub_rn(z, P.z);
         const double dv = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz)));
         if (!(dv > 0.0)) continue;
-        // |x - t| is |dv - r| (near) or dv + r (far) up to a few roundings
-        const double an = fabs(dv - r), af = dv + r;
-        const bool try_near = an * kRel + kAbs >= lo && an <= hi;
-        const bool try_far = af * kRel + kAbs >= lo && af <= hi;
-        if (!try_near && !try_far) continue;
         const double ux = __ddiv_rn(vx, dv), uy = __ddiv_rn(vy, dv), uz = __ddiv_rn(vz, dv);
         for (int side = 0; side < 2; ++side) {
           if (!(side == 0 ? try_near : try_far)) continue;
@@ -247,16 +301,17 @@ __device__ inline void tangent_search(const QueryArgs& a, int box_cull, double x
         const float4 W = T.nb[off + c];
         const float w = cs == 0 ? W.x : W.y;
         if (!(w > -INFINITY)) continue;
-        const float4 Fb = T.nf[off + c];
-        const double dc = sqrt(ball_d2_64(x, y, z, T.na[off + c]));
-        const double df = sqrt(ball_d2_64(x, y, z, Fb));
+        const float4 Cb = T.na[off + c], Fb = T.nf[off + c];
+        const float dc = dist32(x32, y32, z32, Cb), df = dist32(x32, y32, z32, Fb);
+        const float ec = err32(ax, Cb, dc, w), ef = err32(ax, Fb, df, Fb.w);
         // bounds over the node's spheres j of class cs, with d = |x - p_j|:
         //   near |d - r_j|: >= d - r_j >= dc - w;  r_j - d <= w - dc;
         //                   d - r_j <= df + |p_j - F| - r_j <= df + wf
         //   far d + r_j:    <= dc + w;  >= df - (|p_j - F| - r_j) >= df - wf
-        const double near_lo = widen_dn(dc - double(w)), near_hi = widen_up(fmax(double(w) - dc, df + double(Fb.w)));
-        const double far_lo = widen_dn(df - double(Fb.w)), far_hi = widen_up(dc + double(w));
-        if ((near_lo <= hi && near_hi >= lo) || (far_lo <= hi && far_hi >= lo)) stack[sp++] = pack_node(lev - 1, c);
+        const float near_lo = dc - w - ec, near_hi = fmaxf(w - dc + ec, df + Fb.w + ef);
+        const float far_lo = df - Fb.w - ef, far_hi = dc + w + ec;
+        if ((near_lo <= hi_f && near_hi >= lo_f) || (far_lo <= hi_f && far_hi >= lo_f))
+          stack[sp++] = pack_node(lev - 1, c);
       }
     }
   }

@@ -28,6 +28,7 @@ float round_out(double v) {  // an FP32 value >= v
 
 struct HostTree {
   std::vector<D4> sph;
+  std::vector<float4> sph32;  // sorted FP32 copies, as the library stores them
   std::vector<int> sid;
   std::vector<float4> na, nb, nf, lo, hi;
   Tree T{};
@@ -46,6 +47,13 @@ bool build_tree(const double* p, const double* s, int64_t n, unsigned order_seed
   } else {
     std::mt19937 rng(order_seed);
     std::shuffle(H.sid.begin(), H.sid.end(), rng);
+  }
+  H.sph32.resize(n);
+  for (int64_t j = 0; j < n; ++j) {
+    const D4& P = H.sph[H.sid[j]];
+    float w = float(P.w);
+    if (w == 0.f && P.w != 0.0) w = std::copysign(1.4e-45f, float(P.w));  // keep the sign class
+    H.sph32[j] = float4{float(P.x), float(P.y), float(P.z), w};
   }
   Tree& T = H.T;
   T.nitems = n;
@@ -114,6 +122,7 @@ bool build_tree(const double* p, const double* s, int64_t n, unsigned order_seed
 
 QueryArgs args_for(const HostTree& H, int64_t n, double tol) {
   QueryArgs a{};
+  a.sph = H.sph32.data();
   a.sid = H.sid.data();
   a.sph64 = H.sph.data();
   a.st = H.T;
