@@ -243,7 +243,7 @@ def run_reference(args):
         "data": "synthetic", "config": CONFIG, "cpu_baseline": cb,
         "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    print(json.dumps(_finite(line)), flush=True)
 
 
 # ----------------------------------------------------------------------------
@@ -516,9 +516,22 @@ def extra_refine_order(N=32):
         ins = (code == gfs.CODE_SURVIVOR) | (code == gfs.CODE_OPPOSITE) | (code == gfs.CODE_LOWER)
         err = np.abs(v[ins] - field(y[ins]))
         res[name] = {"insertions_per_s": y.shape[0] / dt, "inserted": int(ins.sum()),
-                     "mean_abs_err": float(err.mean()), "max_abs_err": float(err.max())}
+                     "mean_abs_err": float(err.mean()) if err.size else None,
+                     "max_abs_err": float(err.max()) if err.size else None}
     ctx.close()
     return res
+
+
+def _finite(v):
+    """The JSON line carries no NaN or infinity (strict parsers reject them):
+    such values become null."""
+    if isinstance(v, float):
+        return v if np.isfinite(v) else None
+    if isinstance(v, dict):
+        return {k: _finite(u) for k, u in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [_finite(u) for u in v]
+    return v
 
 
 def _isolated(only, extra=(), timeout=600):
@@ -687,7 +700,7 @@ def run_gfs(args):
         line["cpu_baseline"] = cpu_baseline_line(w, xh, steps=2, n_keep=2000, n_query=2)
     ctx.close()
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(_finite(line)), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
@@ -700,7 +713,7 @@ if __name__ == "__main__":
               "batch": lambda: extra_batch(a.batch_shapes, a.batch_scale),
               "tangent": lambda: extra_tangent(a.tangent_every),
               "refine_order": extra_refine_order}[a.only]
-        print(json.dumps({a.only: fn()}), flush=True)
+        print(json.dumps(_finite({a.only: fn()})), flush=True)
     elif a.impl == "reference":
         run_reference(a)
     else:
