@@ -105,7 +105,38 @@ __device__ inline void sphere_bounds(const QueryArgs& a, double x, double y, dou
   uint32_t stack[kStack];
   int sp = 0;
   const int top = T.nlevels - 1;
-  for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
+  // seed: descend first to the leaf whose balls reach nearest to x (least
+  // |x - C| - w at every level), so that the thresholds are tight before
+  // the full walk; that leaf is visited again by the walk, which changes
+  // nothing (minima with index ties are idempotent)
+  {
+    int64_t best = 0;
+    float bk = INFINITY;
+    for (int64_t j = 0; j < T.count[top]; ++j) {
+      const float4 B = T.na[T.offset[top] + j];
+      const float k = dist32(x32, y32, z32, B) - B.w;
+      if (k < bk) {
+        bk = k;
+        best = j;
+      }
+    }
+    for (int lev = top; lev > 0; --lev) {
+      const int64_t cb = best * kFan, ce = imin64(cb + kFan, T.count[lev - 1]);
+      const int64_t off = T.offset[lev - 1];
+      bk = INFINITY;
+      for (int64_t c = cb; c < ce; ++c) {
+        const float4 B = T.na[off + c];
+        const float k = dist32(x32, y32, z32, B) - B.w;
+        if (k < bk || c == cb) {
+          bk = k;
+          best = c;
+        }
+      }
+    }
+    // the whole hierarchy, then the seed leaf on top of the stack (popped first)
+    for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
+    stack[sp++] = pack_node(0, best);
+  }
   while (sp > 0) {
     const uint32_t nd = stack[--sp];
     const int lev = node_level(nd);
