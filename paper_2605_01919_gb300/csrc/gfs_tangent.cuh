@@ -211,6 +211,35 @@ __device__ inline int covered_by_other(const QueryArgs& a, double tx, double ty,
   int sp = 0;
   const int top = T.nlevels - 1;
   for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
+  // seed: the leaf reached by always entering the child ball that holds t
+  // most deeply (least |t - C| - w) is tested first; a covered point usually
+  // lies in one of its balls
+  {
+    int64_t best = 0;
+    float bk = INFINITY;
+    for (int64_t j = 0; j < T.count[top]; ++j) {
+      const float4 B = T.na[T.offset[top] + j];
+      const float k = dist32(x32, y32, z32, B) - B.w;
+      if (k < bk) {
+        bk = k;
+        best = j;
+      }
+    }
+    for (int lev = top; lev > 0; --lev) {
+      const int64_t cb = best * kFan, ce = imin64(cb + kFan, T.count[lev - 1]);
+      const int64_t off = T.offset[lev - 1];
+      bk = INFINITY;
+      for (int64_t c = cb; c < ce; ++c) {
+        const float4 B = T.na[off + c];
+        const float k = dist32(x32, y32, z32, B) - B.w;
+        if (k < bk || c == cb) {
+          bk = k;
+          best = c;
+        }
+      }
+    }
+    stack[sp++] = pack_node(0, best);
+  }
   while (sp > 0) {
     const uint32_t nd = stack[--sp];
     const int lev = node_level(nd);
@@ -230,11 +259,24 @@ __device__ inline int covered_by_other(const QueryArgs& a, double tx, double ty,
     } else {
       const int64_t cb = idx * kFan, ce = imin64(cb + kFan, T.count[lev - 1]);
       const int64_t off = T.offset[lev - 1];
+      // push the children that may hold a covering ball, the one holding t
+      // most deeply last (popped first)
+      const int base = sp;
+      float key[kFan];
       for (int64_t c = cb; c < ce; ++c) {
         const float4 B = T.na[off + c];
         if (!(B.w > 0.f)) continue;
         const float dC = dist32(x32, y32, z32, B);
-        if (dC - err32(ax, B, dC, B.w) < B.w) stack[sp++] = pack_node(lev - 1, c);
+        if (!(dC - err32(ax, B, dC, B.w) < B.w)) continue;
+        const float k = dC - B.w;
+        int u = sp++;
+        while (u > base && key[u - 1 - base] < k) {
+          stack[u] = stack[u - 1];
+          key[u - base] = key[u - 1 - base];
+          --u;
+        }
+        stack[u] = pack_node(lev - 1, c);
+        key[u - base] = k;
       }
     }
   }
