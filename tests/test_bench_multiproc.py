@@ -43,3 +43,22 @@ def test_aggregate_single_process():
     import bench
     value, ms = bench.aggregate(500.0, units_per_rank=100, steps=5, world=1)
     assert ms == pytest.approx(100.0) and value == pytest.approx(1000.0)
+
+
+def test_json_line_has_no_nonfinite_numbers():
+    import json
+    import bench
+    line = bench._finite({"value": float("nan"), "extras": {"x": [1.0, float("inf")], "y": "ok"}, "n": 3})
+    assert json.loads(json.dumps(line, allow_nan=False)) == {"value": None, "extras": {"x": [1.0, None], "y": "ok"},
+                                                             "n": 3}
+
+
+def test_traffic_record_only_for_current_kernel_sources(monkeypatch):
+    """The roofline's DRAM traffic comes from the committed ncu summary only
+    while the kernel sources still hash to the value recorded beside it."""
+    import bench
+    current = bench.recorded_traffic("k_query_spheres")
+    monkeypatch.setattr(bench, "kernel_hash", lambda: "0000000000000000")
+    assert bench.recorded_traffic("k_query_spheres") is None
+    assert bench.recorded_traffic("no_such_kernel") is None
+    assert current is None or current > 0
