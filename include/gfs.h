@@ -289,6 +289,14 @@ int gfs_batch_build(gfs_ctx* ctx, const gfs_shape* shapes_host, int nshapes);
  * Errors: GFS_ERR_STATE (no batch build), GFS_ERR_CUDA. */
 int gfs_batch_query(gfs_ctx* ctx);
 
+/* Same-sign tangent augmentation (as gfs_query_tangent) of the outputs of
+ * the last gfs_batch_query, shape by shape; every shape with points needs
+ * its argmin and flags outputs.  One launch per shape, in the Morton order
+ * of that gfs_batch_query; no host synchronisation and no allocation.
+ * Errors: GFS_ERR_STATE (no batch build), GFS_ERR_ARG (a shape without
+ * argmin or flags outputs; nothing is launched), GFS_ERR_CUDA. */
+int gfs_batch_query_tangent(gfs_ctx* ctx);
+
 /* Surviving candidate ids of one shape of the batch, ascending (device
  * g_out, capacity cap; *count_host set).  Errors as gfs_survivors. */
 int gfs_batch_survivors(gfs_ctx* ctx, int shape, int64_t* g_out, int64_t cap, int64_t* count_host);

@@ -148,6 +148,7 @@ struct gfs_ctx {
   DevBuf b_lo, b_hi, b_na, b_nb, b_nf, b_stdev, b_prefix, b_ctr, b_cnt, b_cviews, b_cw;
   DevBuf b_sraw[2], b_sshape[2], b_ssorted[2], b_vlo[2], b_vhi[2], b_vtdev[2], b_hist;
   DevBuf b_qkin, b_qkout, b_qvin, b_qvout, b_qviews, b_qw, b_qstate;
+  std::vector<QueryArgs> b_qv;  // host copies of the per-shape query views
   unsigned b_cap = 0;
   unsigned b_nsurv[2] = {0, 0};
   int64_t b_M = 0, b_qtotal = 0;
@@ -1100,6 +1101,7 @@ int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
   GFS_TRY(ensure(c->b_qw, size_t(ns + 1) * 8));
   GFS_CK(cudaMemcpyAsync(c->b_qviews.p, qv.data(), size_t(ns) * sizeof(QueryArgs), cudaMemcpyHostToDevice, st));
   GFS_CK(cudaMemcpyAsync(c->b_qw.p, qw.data(), size_t(ns + 1) * 8, cudaMemcpyHostToDevice, st));
+  c->b_qv = qv;
   c->b_M = M;
   c->b_qtotal = qw[ns];
   // sort scratch for the query order, sized here so gfs_batch_query allocates nothing
@@ -1135,6 +1137,18 @@ int gfs_batch_query(gfs_ctx* c) {
     GFS_CK(launch_batch_query(c->b_qviews.as<QueryArgs>(), c->b_qw.as<int64_t>(), ns, c->b_qtotal,
                               c->b_ctr.as<unsigned long long>(), grid, phase, st));
   }
+  return GFS_OK;
+}
+
+int gfs_batch_query_tangent(gfs_ctx* c) {
+  if (!c) return GFS_ERR_ARG;
+  if (!c->b_built) return GFS_ERR_STATE;
+  for (const QueryArgs& a : c->b_qv)
+    if (a.m > 0 && (!a.arg_out || !a.fl_out)) return GFS_ERR_ARG;
+  // one launch per shape, each over its view (its points in the Morton order
+  // the last gfs_batch_query computed)
+  for (const QueryArgs& a : c->b_qv)
+    if (a.m > 0) GFS_CK(launch_query_tangent(a, c->opt.box_cull, c->stream));
   return GFS_OK;
 }
 

@@ -20,7 +20,7 @@ FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 0x10, 0x20, 0x40
 EXPORTED = ["gfs_default_options", "gfs_create", "gfs_set_stream", "gfs_build", "gfs_query", "gfs_query_tangent",
             "gfs_query_backward", "gfs_query_backward_noalloc", "gfs_insert", "gfs_insert_known", "gfs_survivors", "gfs_batch_build", "gfs_batch_query",
             "gfs_batch_survivors", "gfs_stats", "gfs_solve_host", "gfs_icosphere", "gfs_strerror",
-            "gfs_destroy", "gfs_cell_coverage", "gfs_flood_order"]
+            "gfs_destroy", "gfs_cell_coverage", "gfs_flood_order", "gfs_batch_query_tangent"]
 
 
 class Options(ctypes.Structure):
@@ -92,6 +92,8 @@ def load(build_if_missing: bool = True):
     L.gfs_batch_build.restype = i32
     L.gfs_batch_query.argtypes = [P]
     L.gfs_batch_query.restype = i32
+    L.gfs_batch_query_tangent.argtypes = [P]
+    L.gfs_batch_query_tangent.restype = i32
     L.gfs_batch_survivors.argtypes = [P, i32, P, i64, ctypes.POINTER(i64)]
     L.gfs_batch_survivors.restype = i32
     L.gfs_survivors.argtypes = [P, P, i64, ctypes.POINTER(i64)]
@@ -331,6 +333,8 @@ class Context:
     def batch_query(self):
         self._sync_stream()
         _check(load().gfs_batch_query(self._h))
+        if self.tangent:
+            _check(load().gfs_batch_query_tangent(self._h))
         return self._batch
 
     def batch_survivors(self, shape: int) -> torch.Tensor:

@@ -218,3 +218,39 @@ def test_tangent_full_size_sampled(G, orc):
     fl = np.concatenate([o[2] for o in outs])
     assert np.sum((fl & 15) == G.CODE_TANGENT) > 5
     assert_parity(res, val, arg, fl, w.h)
+
+
+def test_tangent_batched_equals_single_shape_and_oracle(G, orc):
+    """gfs_batch_query_tangent on 8 small batch shapes (grids and scattered
+    samples, tau 1): every shape's refined outputs equal the single-shape
+    pass bit for bit (the batched hierarchies differ, the decisions may not),
+    and the small shapes equal the oracle's augmented query."""
+    tau = 1
+    shapes = []
+    for i in range(8):
+        w = W.batch_shape(i, tau=tau, scale=0.12)
+        x = w.make_queries()
+        if x.shape[0] > 20000:
+            x = x[np.random.default_rng(i).choice(x.shape[0], 20000, replace=False)]
+        shapes.append((w, x))
+    ctx = G.Context(tau=tau, tangent=True)
+    outs = ctx.batch_build([{"p": torch.from_numpy(w.p).cuda(), "s": torch.from_numpy(w.s).cuda(),
+                             "x": torch.from_numpy(x).cuda()} for w, x in shapes])
+    ctx.batch_query()
+    torch.cuda.synchronize()
+    won = 0
+    for k, (w, x) in enumerate(shapes):
+        ref = run_gpu(G, w.p, w.s, tau, x)
+        got = {key: outs[k][key].cpu().numpy() for key in ("s", "s64", "argmin", "flags")}
+        got["flags"] = got["flags"].astype(np.int32) & 0xFFFF
+        for key in ("flags", "argmin"):
+            assert np.array_equal(got[key], ref[key]), (k, key)
+        assert np.array_equal(got["s64"].view(np.int64), ref["s64"].view(np.int64)), k
+        won += int(np.sum((got["flags"] & 15) == G.CODE_TANGENT))
+        if w.n <= 3000:
+            sel = np.arange(0, x.shape[0], max(1, x.shape[0] // 300))
+            val, arg, fl = oracle_aug(orc, w.p, w.s, tau, x[sel])
+            assert np.array_equal(got["argmin"][sel], arg) and np.array_equal(got["flags"][sel], fl)
+            assert np.array_equal(got["s64"][sel], val, equal_nan=True)
+    assert won > 0
+    ctx.close()
