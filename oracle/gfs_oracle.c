@@ -28,6 +28,9 @@
  *    far bound = nearest far tangent point of any sphere.
  *  - Sec. 6 (min_valid_radius_for_known_sign): the exact T/U/D enumeration,
  *    kept here by brute force for tiny inputs only (orc_exact_rmin).
+ *  - Prop. 1 (ii) exactly: whether each sphere keeps a point outside every
+ *    other ball, from the circle and triple points of Def. 1
+ *    (orc_sphere_uncovered).
  *  - Sec. 4.2 refinement order: the covered area ratio of grid cells from
  *    regularly spaced sub-points (orc_cell_coverage); the flood-fill order
  *    itself is plain Python in oracle.py.
@@ -1063,4 +1066,64 @@ void orc_query_aug_lazy(const double* p, const double* s, int64_t n, const doubl
     }
   }
   free(buf);
+}
+
+/* ------------------------------------------------------------------------ */
+/* exact uncovered test per sphere (Prop. 1 (ii); the U and D points of      */
+/* Def. 1 on each sphere)                                                   */
+/* ------------------------------------------------------------------------ */
+/* out[i] = 1 when some point of sphere i lies in no other ball shrunk by tol
+ * (for |s_i| = 0: when p_i does).  Let N_i be the spheres k != i with
+ * rho_k = |s_k| - tol > 0 whose shrunk open ball meets sphere i,
+ * | |p_i - p_k| - |s_i| | < rho_k.  With N_i empty the sphere is uncovered.
+ * Otherwise the uncovered set U of sphere i, if not empty, is a closed proper
+ * subset of the sphere, so it has a boundary point, on some circle
+ * C_k = S_i with the sphere (p_k, rho_k); on C_k, U is either the whole
+ * circle or closed arcs whose ends lie on a third sphere (p_m, rho_m).  So it
+ * suffices to test, against every ball but i and the spheres they were
+ * built from: two points of every circle C_k (its points nearest and
+ * farthest from a fixed reference point) and the two points shared by
+ * sphere i and the spheres (p_k, rho_k), (p_m, rho_m) for every pair k < m
+ * in N_i. */
+static int in_list_meets(const double* p, const double* s, int64_t i, int64_t k, double tol) {
+  const double rho = fabs(s[k]) - tol;
+  if (!(rho > 0.0)) return 0;
+  const double d = sqrt(dist2(p + 3 * i, p + 3 * k));
+  return fabs(d - fabs(s[i])) < rho;
+}
+
+void orc_sphere_uncovered(const double* p, const double* s, int64_t n, double tol, uint8_t* out) {
+  const double e_ref[3] = {0.36, 0.48, 0.8};
+  int64_t* N = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) {
+    const double* pi = p + 3 * i;
+    const double ri = fabs(s[i]);
+    if (ri == 0.0) {
+      out[i] = (uint8_t)uncovered_but(p, s, n, tol, pi, i, -1, -1);
+      continue;
+    }
+    int64_t nn = 0;
+    for (int64_t k = 0; k < n; ++k)
+      if (k != i && in_list_meets(p, s, i, k, tol)) N[nn++] = k;
+    if (nn == 0) {
+      out[i] = 1;
+      continue;
+    }
+    int found = 0;
+    double ref[3];
+    for (int c = 0; c < 3; ++c) ref[c] = pi[c] + (ri + 1.0) * e_ref[c];
+    for (int64_t a = 0; a < nn && !found; ++a) {
+      const int64_t k = N[a];
+      double pts[6];
+      if (circle_points(pi, ri, p + 3 * N[a], fabs(s[k]) - tol, ref, pts) == 2)
+        found = uncovered_but(p, s, n, tol, pts, i, k, -1) || uncovered_but(p, s, n, tol, pts + 3, i, k, -1);
+      for (int64_t b = a + 1; b < nn && !found; ++b) {
+        const int64_t m = N[b];
+        if (tri_intersect(pi, ri, p + 3 * k, fabs(s[k]) - tol, p + 3 * m, fabs(s[m]) - tol, pts) == 2)
+          found = uncovered_but(p, s, n, tol, pts, i, k, m) || uncovered_but(p, s, n, tol, pts + 3, i, k, m);
+      }
+    }
+    out[i] = (uint8_t)found;
+  }
+  free(N);
 }

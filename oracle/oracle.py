@@ -70,6 +70,8 @@ def lib():
         L.orc_exact_rmin.restype = f64
         L.orc_query_aug_lazy.argtypes = [P, P, i64, P, i32, f64, i32, i32, P, i64, P, P, P]
         L.orc_query_aug_lazy.restype = None
+        L.orc_sphere_uncovered.argtypes = [P, P, i64, f64, P]
+        L.orc_sphere_uncovered.restype = None
         L.orc_cell_coverage.argtypes = [P, P, i64, f64, P, i64, P, f64, i32, P]
         L.orc_cell_coverage.restype = None
         _lib = L
@@ -293,3 +295,13 @@ def flood_order(cells, counts):
                 queued[j] = True
                 heapq.heappush(heap, (counts[j], j))
     return order
+
+
+def sphere_uncovered(p, s, tol=TOL):
+    """Exact uncovered test per sphere (Prop. 1 (ii)): 1 where some point of
+    the sphere lies in no other ball shrunk by tol."""
+    p, s = _c(p, np.float64), _c(s, np.float64)
+    out = np.zeros(s.shape[0], np.uint8)
+    if s.shape[0]:
+        lib().orc_sphere_uncovered(_ptr(p), _ptr(s), s.shape[0], tol, _ptr(out))
+    return out

@@ -710,3 +710,61 @@ def test_query_aug_lazy_equals_brute_force_grids(orc):
         assert np.sum((a[2] & 15) == orc.CODE_TANGENT) > 10
         assert np.array_equal(a[0], b[0], equal_nan=True)
         assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+# ----------------------------------------------------------------------------
+# exact uncovered test per sphere (Prop. 1 (ii))
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rho,covered", [(0.93, True), (0.91, False), (0.9194, False), (0.9195, True)])
+def test_sphere_uncovered_octahedral_caps(orc, rho, covered):
+    """The unit sphere with six balls of radius rho centred at +-e_x, +-e_y,
+    +-e_z (tol = 0): a ball covers the cap of half-angle t with
+    2 - 2 cos t = rho^2; the caps cover the sphere exactly when t reaches the
+    corner directions (1,1,1)/sqrt 3, cos t = 1/sqrt 3, i.e.
+    rho > sqrt(2 - 2/sqrt 3) = 0.919401..."""
+    e = np.eye(3)
+    p = np.concatenate([np.zeros((1, 3)), e, -e])
+    s = np.array([1.0] + [rho] * 6)
+    assert orc.sphere_uncovered(p, s, tol=0.0)[0] == (0 if covered else 1)
+
+
+def test_sphere_uncovered_simple_cases(orc):
+    # alone; inside a larger ball (either sign); two overlapping equal balls
+    assert list(orc.sphere_uncovered(np.zeros((1, 3)), np.array([0.3]))) == [1]
+    p = np.array([[0.0, 0, 0], [0.05, 0, 0]])
+    for big in (0.5, -0.5):
+        assert list(orc.sphere_uncovered(p, np.array([big, 0.2]))) == [1, 0]
+    p = np.array([[0.0, 0, 0], [0.3, 0, 0]])
+    assert list(orc.sphere_uncovered(p, np.array([0.25, 0.25]))) == [1, 1]
+    # zero samples: uncovered exactly when the point is outside the others
+    p = np.array([[0.0, 0, 0], [0.1, 0, 0], [0.9, 0, 0]])
+    assert list(orc.sphere_uncovered(p, np.array([0.5, 0.0, 0.0]))) == [1, 0, 1]
+
+
+@pytest.mark.parametrize("case", ["inflated_grid", "invalid0", "invalid2"])
+def test_sphere_uncovered_bounds_the_discrete_survivors(orc, case):
+    """A sphere with a surviving icosphere candidate has an uncovered point,
+    and the candidate sets are nested in tau, so the spheres with survivors
+    grow with tau and stay inside the exact set (no box culling).  Inputs
+    with covered spheres: the 8^3 sphere grid with every value scaled by 1.2
+    (211 of 512 spheres keep an uncovered point; 9, 14, 50, 128, 163 of them
+    have survivors at tau = 0..4), and invalid tiny random inputs."""
+    if case == "inflated_grid":
+        w = W.sphere_grid(N=8, up=2, tau=2)
+        p, s = w.p, 1.2 * w.s
+    else:
+        p, s = W.tiny_random(40, int(case[-1]), valid=False, spread=0.35)
+    exact = orc.sphere_uncovered(p, s).astype(bool)
+    if case == "inflated_grid":
+        assert exact.sum() == 211      # regression value of this oracle, not a pin
+    prev = None
+    for tau in range(0, 5):
+        U = orc.icosphere(tau)
+        keep = orc.keep_all(p, s, U, box_cull=False).reshape(len(s), -1)
+        has = keep.any(axis=1)
+        assert np.all(exact[has])
+        if prev is not None:
+            assert np.all(has[prev])
+        prev = has
+    assert exact.sum() >= prev.sum()
