@@ -223,6 +223,22 @@ int gfs_query_backward_noalloc(gfs_ctx* ctx, const void* x, int x_is_fp32, int64
  * Errors: GFS_ERR_STATE, GFS_ERR_ARG (cap too small: *count_host still set). */
 int gfs_survivors(gfs_ctx* ctx, int64_t* g_out, int64_t cap, int64_t* count_host);
 
+/* ---- exact coverage of each sample sphere (Prop. 1 (ii)) ------------------ */
+/* out[i] for every sphere of the context's current state (input order, n
+ * bytes, device): 1 when some point of sphere i lies in no other ball shrunk
+ * by tol, 0 when every point is covered, 2 when more than 512 balls meet the
+ * sphere (not decided).  Exact in the sense of Def. 1: the test points are
+ * the circles where the other shrunk balls cut the sphere (two points each)
+ * and the points where two of them meet on it (the D points), each tested
+ * against every ball but the ones it was built from, in FP64; a sample with
+ * s_i = 0 is the point p_i.  The icosphere survivors are a subset: a sphere
+ * with a survivor is uncovered.  One thread per sphere; the cost grows with
+ * the cube of the number of balls that meet a sphere, so this is a check for
+ * moderate inputs (it is the exact counterpart of "no survivor at tau").
+ * No host synchronisation, no allocation.  Errors: GFS_ERR_STATE (no build),
+ * GFS_ERR_ARG, GFS_ERR_CUDA. */
+int gfs_sphere_uncovered(gfs_ctx* ctx, uint8_t* out);
+
 /* ---- refinement order (Sec. 4.2) ------------------------------------------ */
 /* The greedy refinement depends on the order of the new points.  The paper
  * orders the interesting cells by a flood fill that starts at the least

@@ -12,6 +12,7 @@
 
 #include "gfs.h"
 #include "gfs_kernels.h"
+#include "gfs_exact.h"
 #include "gfs_order.h"
 #include "gfs_tangent.h"
 
@@ -542,6 +543,15 @@ int gfs_query_backward(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, cons
   a.acc_s = c->acc.as<long long>() + 3 * n;
   GFS_CK(launch_grad(a, n, nullptr, nullptr, c->stream));
   GFS_CK(launch_tangent_grad(a, n, grad_p, grad_sv, c->stream));
+  return GFS_OK;
+}
+
+int gfs_sphere_uncovered(gfs_ctx* c, uint8_t* out) {
+  if (!c || !out) return GFS_ERR_ARG;
+  if (!c->built) return GFS_ERR_STATE;
+  QueryArgs a;
+  fill_query_args(c, a);
+  GFS_CK(launch_sphere_uncovered(a, out, c->stream));
   return GFS_OK;
 }
 
@@ -1232,7 +1242,7 @@ int gfs_stats(gfs_ctx* c, gfs_stats_t* out) {
   };
   unsigned long long own = 0, sorts = 0;
   launch_counts(&own, &sorts);
-  out->kernel_launches = int64_t(own + tangent_launch_count() + order_launch_count());
+  out->kernel_launches = int64_t(own + tangent_launch_count() + order_launch_count() + exact_launch_count());
   out->sort_calls = int64_t(sorts);
   if (c->have_ev && c->built_timed) {
     out->ms_build_total = ms(0, 3);

@@ -200,10 +200,12 @@ __device__ inline void sphere_bounds(const QueryArgs& a, double x, double y, dou
   }
 }
 
-// A ball other than sphere `skip` (input index) that, shrunk by tol, contains
-// t (Sec. 3.1: the open balls; App. B tolerance), or -1.  A ball of the node
-// with centre C and radius bound w can only contain t when |t - C| < w.
-__device__ inline int covered_by_other(const QueryArgs& a, double tx, double ty, double tz, int skip) {
+// A ball other than spheres skip0..skip2 (input indices; -1 for none) that,
+// shrunk by tol, contains t (Sec. 3.1: the open balls; App. B tolerance), or
+// -1.  A ball of the node with centre C and radius bound w can only contain t
+// when |t - C| < w.
+__device__ inline int covered_except(const QueryArgs& a, double tx, double ty, double tz, int skip0, int skip1,
+                                     int skip2) {
   const float x32 = float(tx), y32 = float(ty), z32 = float(tz), ax = amax3(x32, y32, z32);
   const float ntol = -f_dn(a.tol);  // >= -tol
   const Tree& T = a.st;
@@ -253,7 +255,7 @@ __device__ inline int covered_by_other(const QueryArgs& a, double tx, double ty,
         const float d32 = dist32(x32, y32, z32, S), r32 = fabsf(S.w);
         if (d32 - r32 - err32(ax, S, d32, r32) >= ntol) continue;
         const int o = a.sid[j];
-        if (o == skip) continue;
+        if (o == skip0 || o == skip1 || o == skip2) continue;
         if (ex_cov(tx, ty, tz, a.sph64[o], a.tol)) return o;
       }
     } else {
@@ -281,6 +283,10 @@ __device__ inline int covered_by_other(const QueryArgs& a, double tx, double ty,
     }
   }
   return -1;
+}
+
+__device__ __forceinline__ int covered_by_other(const QueryArgs& a, double tx, double ty, double tz, int skip) {
+  return covered_except(a, tx, ty, tz, skip, -1, -1);
 }
 
 // How far a tangent point may lie from x and still change the result.

@@ -20,7 +20,7 @@ FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 0x10, 0x20, 0x40
 EXPORTED = ["gfs_default_options", "gfs_create", "gfs_set_stream", "gfs_build", "gfs_query", "gfs_query_tangent",
             "gfs_query_backward", "gfs_query_backward_noalloc", "gfs_insert", "gfs_insert_known", "gfs_survivors", "gfs_batch_build", "gfs_batch_query",
             "gfs_batch_survivors", "gfs_stats", "gfs_solve_host", "gfs_icosphere", "gfs_strerror",
-            "gfs_destroy", "gfs_cell_coverage", "gfs_flood_order", "gfs_batch_query_tangent"]
+            "gfs_destroy", "gfs_cell_coverage", "gfs_flood_order", "gfs_batch_query_tangent", "gfs_sphere_uncovered"]
 
 
 class Options(ctypes.Structure):
@@ -102,6 +102,8 @@ def load(build_if_missing: bool = True):
     L.gfs_stats.restype = i32
     L.gfs_solve_host.argtypes = [P, P, P, i64, P, i32, i64, P, P, P]
     L.gfs_solve_host.restype = i32
+    L.gfs_sphere_uncovered.argtypes = [P, P]
+    L.gfs_sphere_uncovered.restype = i32
     L.gfs_cell_coverage.argtypes = [P, P, i64, P, f64, i32, P]
     L.gfs_cell_coverage.restype = i32
     L.gfs_flood_order.argtypes = [P, P, i64, P]
@@ -266,6 +268,16 @@ class Context:
         _check(load().gfs_insert_known(self._h, _ptr(y), _ptr(known), T, _ptr(out["s64"]), _ptr(out["argmin"]),
                                        _ptr(out["flags"])))
         self.n = self.stats()["n_spheres"]
+        return out
+
+    # -- exact coverage of the sample spheres (Prop. 1 (ii)) ----------------------
+    def sphere_uncovered(self) -> torch.Tensor:
+        """Per sphere of the current state (input order): 1 keeps a point
+        outside every other shrunk ball, 0 fully covered, 2 undecided (more
+        than 512 balls meet it)."""
+        out = torch.empty(self.stats()["n_spheres"], dtype=torch.uint8, device="cuda")
+        self._sync_stream()
+        _check(load().gfs_sphere_uncovered(self._h, _ptr(out)))
         return out
 
     # -- refinement order (Sec. 4.2) ------------------------------------------------

@@ -1,7 +1,8 @@
 // Test harness: runs device routines of the library on the CPU over a
 // sphere hierarchy built here: the tangent pass (tangent_one), refining the
-// oracle's plain query results in place, and the cell coverage count of the
-// refinement order (cell_cover_count).  The hierarchy has the library's layout (implicit 8-ary
+// oracle's plain query results in place, the cell coverage count of the
+// refinement order (cell_cover_count) and the exact uncovered test per
+// sphere (sphere_uncovered).  The hierarchy has the library's layout (implicit 8-ary
 // tree over sorted items) with bounding balls computed directly in FP64 and
 // rounded outwards to FP32, so every bound the routines rely on holds.
 // Item order: Morton order of the FP32 centres (order_seed = 0, as the
@@ -13,6 +14,7 @@
 #include <random>
 #include <vector>
 
+#include "gfs_exact.cuh"
 #include "gfs_order.cuh"
 
 using namespace gfs;
@@ -160,5 +162,14 @@ extern "C" int coverage_host(const double* p, const double* s, int64_t n, double
   const QueryArgs a = args_for(H, n, tol);
   for (int64_t c = 0; c < ncells; ++c)
     counts[c] = order::cell_cover_count(a, cells + 3 * c, origin[0], origin[1], origin[2], h, sub, 0, 1);
+  return 0;
+}
+
+extern "C" int uncovered_host(const double* p, const double* s, int64_t n, double tol, uint8_t* out,
+                              unsigned order_seed) {
+  HostTree H;
+  if (!build_tree(p, s, n, order_seed, H)) return -1;
+  const QueryArgs a = args_for(H, n, tol);
+  for (int64_t i = 0; i < n; ++i) out[i] = uint8_t(exact::sphere_uncovered(a, int(i)));
   return 0;
 }

@@ -1,0 +1,62 @@
+"""Exact uncovered test per sphere (gfs_sphere_uncovered, Prop. 1 (ii)) on
+the GPU against the oracle's brute force, sphere by sphere, and its relation
+to the icosphere survivors: a sphere with a survivor is uncovered."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2605_01919_gb300 import workloads as W
+
+pytestmark = [pytest.mark.gpu, pytest.mark.widening]
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2605_01919_gb300 import gfs
+    gfs.load()
+    return gfs
+
+
+def gpu_uncovered(G, p, s, tau=1, tol=1e-6):
+    ctx = G.Context(tau=tau, tol=tol)
+    ctx.build(torch.from_numpy(np.ascontiguousarray(p)).cuda(), torch.from_numpy(np.ascontiguousarray(s)).cuda())
+    out = ctx.sphere_uncovered().cpu().numpy()
+    surv = ctx.survivors().cpu().numpy()
+    ctx.close()
+    return out, surv
+
+
+def test_exact_uncovered_parity(G, orc):
+    e = np.eye(3)
+    cases = [(np.concatenate([np.zeros((1, 3)), e, -e]), np.array([1.0] + [rho] * 6))
+             for rho in (0.91, 0.9194, 0.9195, 0.93)]
+    w = W.sphere_grid(N=8, up=2, tau=2)
+    cases += [(w.p, 1.2 * w.s), (w.p, w.s)]
+    cases += [W.tiny_random(40, seed, valid=(seed % 2 == 0), spread=0.35) for seed in range(4)]
+    cases.append((np.array([[0.0, 0, 0], [0.3, 0, 0]]), np.array([0.25, 0.25])))
+    cases.append((np.array([[0.0, 0, 0], [0.1, 0, 0], [0.9, 0, 0], [0.0, 0, 0]]), np.array([0.5, 0.0, 0.0, 0.5])))
+    for p, s in cases:
+        for tol in (0.0, 1e-6):
+            got, _ = gpu_uncovered(G, p, s, tol=tol)
+            assert np.array_equal(got, orc.sphere_uncovered(p, s, tol=tol))
+
+
+def test_exact_uncovered_contains_survivor_spheres(G):
+    """8^3 sphere grid inflated by 1.2 (at most 235 balls meet a sphere;
+    tau 3, no box culling): every sphere with a surviving candidate is
+    uncovered, and there are more uncovered spheres than spheres with
+    survivors."""
+    w = W.sphere_grid(N=8, up=2, tau=2)
+    s = 1.2 * w.s
+    ctx = G.Context(tau=3, box_cull=False)
+    ctx.build(torch.from_numpy(w.p).cuda(), torch.from_numpy(s).cuda())
+    out = ctx.sphere_uncovered().cpu().numpy()
+    surv = ctx.survivors().cpu().numpy()
+    ctx.close()
+    assert np.all(out != 2)
+    has = np.zeros(w.n, dtype=bool)
+    has[surv // (ctx.K + 1)] = True
+    assert np.all(out[has] == 1)
+    assert (out == 1).sum() > has.sum() and (out == 0).any()

@@ -1,6 +1,6 @@
 """Device routines compiled as host C++, against the oracle (CPU, no GPU
-needed): the tangent pass and the cell coverage count of the refinement
-order.
+needed): the tangent pass, the cell coverage count of the refinement order
+and the exact uncovered test per sphere.
 
 `csrc/gfs_tangent.cuh` holds the whole per-point logic of gfs_query_tangent:
 the FP64 pass over the sphere hierarchy, the tangent-point search with its
@@ -45,6 +45,8 @@ def host(tmp_path_factory):
     L.coverage_host.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, P, ctypes.c_int64, P, ctypes.c_double,
                                 ctypes.c_int, P, ctypes.c_uint]
     L.coverage_host.restype = ctypes.c_int
+    L.uncovered_host.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, P, ctypes.c_uint]
+    L.uncovered_host.restype = ctypes.c_int
     return L
 
 
@@ -151,3 +153,33 @@ def test_host_cell_coverage_lattice_shells(host, orc):
     for R2, count in [(2.0, 0), (7.0, 8), (15.0, 32), (23.0, 56), (31.0, 88), (150.0, 512)]:
         s = np.array([-h / 16 * np.sqrt(R2)])
         assert _coverage(host, centre[None], s, cell, origin, h, 8, 0.0, 0)[0] == count
+
+
+def _uncovered(host, p, s, tol, order):
+    p, s = np.ascontiguousarray(p, np.float64), np.ascontiguousarray(s, np.float64)
+    out = np.zeros(s.shape[0], np.uint8)
+    assert host.uncovered_host(_ptr(p), _ptr(s), s.shape[0], tol, _ptr(out), order) == 0
+    return out
+
+
+def test_host_sphere_uncovered(host, orc):
+    """Octahedral caps around the threshold rho = 0.919401, the 8^3 sphere
+    grid inflated by 1.2 (covered spheres), and valid and invalid tiny random
+    inputs, for tol = 0 and 1e-6: equal to the oracle sphere by sphere."""
+    e = np.eye(3)
+    cases = []
+    for rho in (0.91, 0.9194, 0.9195, 0.93):
+        cases.append((np.concatenate([np.zeros((1, 3)), e, -e]), np.array([1.0] + [rho] * 6)))
+    w = W.sphere_grid(N=8, up=2, tau=2)
+    cases.append((w.p, 1.2 * w.s))
+    cases.append((w.p, w.s))
+    for seed in range(4):
+        cases.append(W.tiny_random(40, seed, valid=(seed % 2 == 0), spread=0.35))
+    p = np.array([[0.0, 0, 0], [0.1, 0, 0], [0.9, 0, 0], [0.0, 0, 0]])
+    cases.append((p, np.array([0.5, 0.0, 0.0, 0.5])))      # zero samples, a duplicated ball
+    cases.append((np.array([[0.0, 0, 0], [0.3, 0, 0]]), np.array([0.25, 0.25])))   # one circle each
+    for p, s in cases:
+        for tol in (0.0, 1e-6):
+            want = orc.sphere_uncovered(p, s, tol=tol)
+            for order in (0, 5):
+                assert np.array_equal(_uncovered(host, p, s, tol, order), want)
