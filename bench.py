@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sub-benchmarks of the backward, insertion and batched paths")
-    ap.add_argument("--only", choices=["backward", "repair", "insert", "batch", "tangent", "refine_order"],
+    ap.add_argument("--only", choices=["backward", "repair", "insert", "batch", "tangent", "refine_order",
+                                       "exact_coverage"],
                     default=None,
                     help="run one sub-benchmark alone and print its JSON (profiling)")
     ap.add_argument("--insert-steps", type=int, default=1024)
@@ -522,6 +523,27 @@ def extra_refine_order(N=32):
     return res
 
 
+def extra_exact_coverage(N=12):
+    """Exact coverage of each sample sphere (gfs_sphere_uncovered, Prop. 1
+    (ii)) on the N^3 sphere grid (exact SDF samples: all keep an uncovered
+    point) and on the same grid with every value scaled by 1.2 (covered
+    spheres, whose test runs through all circle and triple points)."""
+    import torch
+    from paper_2605_01919_gb300 import gfs
+    from paper_2605_01919_gb300 import workloads as W
+    w = W.sphere_grid(N=N, up=2, tau=2)
+    res = {"workload": f"sphere{N}_exact_coverage", "spheres": int(w.n)}
+    for name, s in (("exact_sdf", w.s), ("inflated_1.2", 1.2 * w.s)):
+        ctx = gfs.Context(tau=2)
+        ctx.build(torch.from_numpy(w.p).cuda(), torch.from_numpy(np.ascontiguousarray(s)).cuda())
+        t = _ev_time(lambda: ctx.sphere_uncovered(), reps=1)
+        out = ctx.sphere_uncovered().cpu().numpy()
+        ctx.close()
+        res[name] = {"ms": t, "uncovered": int((out == 1).sum()), "covered": int((out == 0).sum()),
+                     "undecided": int((out == 2).sum())}
+    return res
+
+
 def _finite(v):
     """The JSON line carries no NaN or infinity (strict parsers reject them):
     such values become null."""
@@ -690,7 +712,8 @@ def run_gfs(args):
                          ("insert", lambda: extra_insert(args.insert_steps)),
                          ("batch", lambda: extra_batch(args.batch_shapes, args.batch_scale)),
                          ("tangent", lambda: _isolated("tangent", ["--tangent-every", str(args.tangent_every)])),
-                         ("refine_order", lambda: _isolated("refine_order"))):
+                         ("refine_order", lambda: _isolated("refine_order")),
+                         ("exact_coverage", lambda: _isolated("exact_coverage", timeout=300))):
             try:
                 line["extras"][name] = fn()
             except Exception as e:  # a failing sub-benchmark must not hide the headline line
@@ -712,7 +735,8 @@ if __name__ == "__main__":
               "insert": lambda: extra_insert(a.insert_steps),
               "batch": lambda: extra_batch(a.batch_shapes, a.batch_scale),
               "tangent": lambda: extra_tangent(a.tangent_every),
-              "refine_order": extra_refine_order}[a.only]
+              "refine_order": extra_refine_order,
+              "exact_coverage": extra_exact_coverage}[a.only]
         print(json.dumps(_finite({a.only: fn()})), flush=True)
     elif a.impl == "reference":
         run_reference(a)

@@ -60,3 +60,14 @@ def test_exact_uncovered_contains_survivor_spheres(G):
     has[surv // (ctx.K + 1)] = True
     assert np.all(out[has] == 1)
     assert (out == 1).sum() > has.sum() and (out == 0).any()
+
+
+def test_exact_uncovered_exact_sdf_samples(G):
+    """Samples of an exact SDF form a valid input, so by Prop. 1 (ii) every
+    sphere keeps an uncovered point: 12^3 sphere grid (up to 476 balls meet
+    a sphere), all 1,728 spheres are uncovered; at tau 2 only some of them
+    have icosphere survivors."""
+    w = W.sphere_grid(N=12, up=2, tau=2)
+    out, surv = gpu_uncovered(G, w.p, w.s, tau=2)
+    assert np.all(out == 1)
+    assert np.unique(surv // (10 * 4 ** 2 + 3)).size < w.n
