@@ -523,24 +523,26 @@ def extra_refine_order(N=32):
     return res
 
 
-def extra_exact_coverage(N=12):
+def extra_exact_coverage():
     """Exact coverage of each sample sphere (gfs_sphere_uncovered, Prop. 1
-    (ii)) on the N^3 sphere grid (exact SDF samples: all keep an uncovered
-    point) and on the same grid with every value scaled by 1.2 (covered
-    spheres, whose test runs through all circle and triple points)."""
+    (ii)) on the 12^3 sphere grid (exact SDF samples: all keep an uncovered
+    point) and on the 10^3 sphere grid with every value scaled by 1.2
+    (covered spheres, whose test runs through all circle and triple
+    points)."""
     import torch
     from paper_2605_01919_gb300 import gfs
     from paper_2605_01919_gb300 import workloads as W
-    w = W.sphere_grid(N=N, up=2, tau=2)
-    res = {"workload": f"sphere{N}_exact_coverage", "spheres": int(w.n)}
-    for name, s in (("exact_sdf", w.s), ("inflated_1.2", 1.2 * w.s)):
+    res = {}
+    for name, N, f in (("sphere12_exact_sdf", 12, 1.0), ("sphere10_inflated_1.2", 10, 1.2)):
+        w = W.sphere_grid(N=N, up=2, tau=2)
+        s = np.ascontiguousarray(f * w.s)
         ctx = gfs.Context(tau=2)
-        ctx.build(torch.from_numpy(w.p).cuda(), torch.from_numpy(np.ascontiguousarray(s)).cuda())
+        ctx.build(torch.from_numpy(w.p).cuda(), torch.from_numpy(s).cuda())
         t = _ev_time(lambda: ctx.sphere_uncovered(), reps=1)
         out = ctx.sphere_uncovered().cpu().numpy()
         ctx.close()
-        res[name] = {"ms": t, "uncovered": int((out == 1).sum()), "covered": int((out == 0).sum()),
-                     "undecided": int((out == 2).sum())}
+        res[name] = {"spheres": int(w.n), "ms": t, "uncovered": int((out == 1).sum()),
+                     "covered": int((out == 0).sum()), "undecided": int((out == 2).sum())}
     return res
 
 
