@@ -232,7 +232,7 @@ int gfs_survivors(gfs_ctx* ctx, int64_t* g_out, int64_t cap, int64_t* count_host
  * and the points where two of them meet on it (the D points), each tested
  * against every ball but the ones it was built from, in FP64; a sample with
  * s_i = 0 is the point p_i.  The icosphere survivors are a subset: a sphere
- * with a survivor is uncovered.  One thread per sphere; the cost grows with
+ * with a survivor is uncovered.  One warp per sphere; the cost grows with
  * the cube of the number of balls that meet a sphere, so this is a check for
  * moderate inputs (it is the exact counterpart of "no survivor at tau").
  * No host synchronisation, no allocation.  Errors: GFS_ERR_STATE (no build),

@@ -107,69 +107,81 @@ __device__ inline bool triple_points(const double* p1, double r1, const double* 
   return true;
 }
 
-// 1: sphere i (input index) keeps an uncovered point; 0: it does not;
-// 2: undecided (more than kMaxMeet balls meet it)
-__device__ inline int sphere_uncovered(const QueryArgs& a, int i) {
+// N_i of sphere i (input index) into meet[0, kMaxMeet), gathered by a walk
+// over the hierarchy: a ball of a node with centre C and radius bound w can
+// meet sphere i only if |p_i - C| < r_i + w.  Returns the count, or -1 when
+// more than kMaxMeet balls meet the sphere.
+__device__ inline int gather_meet(const QueryArgs& a, int i, int* meet) {
   const D4 P = a.sph64[i];
-  const double pi[3] = {P.x, P.y, P.z};
   const double ri = fabs(P.w);
-  if (ri == 0.0) return tangent::covered_except(a, P.x, P.y, P.z, i, -1, -1) < 0 ? 1 : 0;
-  // N_i, gathered by a walk over the hierarchy: a ball of a node with centre C
-  // and radius bound w can meet sphere i only if |p_i - C| < r_i + w
-  int meet[kMaxMeet];
   int nn = 0;
-  {
-    const float x32 = float(P.x), y32 = float(P.y), z32 = float(P.z), ax = tangent::amax3(x32, y32, z32);
-    const float ri32 = tangent::f_up(ri);
-    const Tree& T = a.st;
-    uint32_t stack[kStack];
-    int sp = 0;
-    const int top = T.nlevels - 1;
-    for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
-    while (sp > 0) {
-      const uint32_t nd = stack[--sp];
-      const int lev = node_level(nd);
-      const int64_t idx = node_index(nd);
-      if (lev == 0) {
-        const int64_t b = idx * kLeaf, e = tangent::imin64(b + kLeaf, a.n);
-        for (int64_t j = b; j < e; ++j) {
-          const int k = a.sid[j];
-          if (k == i) continue;
-          const D4 Q = a.sph64[k];
-          const double rho = __dsub_rn(fabs(Q.w), a.tol);
-          if (!(rho > 0.0)) continue;
-          const double d = __dsqrt_rn(ex_d2(P.x, P.y, P.z, Q.x, Q.y, Q.z));
-          if (!(fabs(__dsub_rn(d, ri)) < rho)) continue;
-          if (nn == kMaxMeet) return 2;
-          meet[nn++] = k;
-        }
-      } else {
-        const int64_t cb = idx * kFan, ce = tangent::imin64(cb + kFan, T.count[lev - 1]);
-        const int64_t off = T.offset[lev - 1];
-        for (int64_t c = cb; c < ce; ++c) {
-          const float4 B = T.na[off + c];
-          if (!(B.w > 0.f)) continue;
-          const float dC = tangent::dist32(x32, y32, z32, B);
-          if (dC - tangent::err32(ax, B, dC, B.w + ri32) < B.w + ri32) stack[sp++] = pack_node(lev - 1, c);
-        }
+  const float x32 = float(P.x), y32 = float(P.y), z32 = float(P.z), ax = tangent::amax3(x32, y32, z32);
+  const float ri32 = tangent::f_up(ri);
+  const Tree& T = a.st;
+  uint32_t stack[kStack];
+  int sp = 0;
+  const int top = T.nlevels - 1;
+  for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
+  while (sp > 0) {
+    const uint32_t nd = stack[--sp];
+    const int lev = node_level(nd);
+    const int64_t idx = node_index(nd);
+    if (lev == 0) {
+      const int64_t b = idx * kLeaf, e = tangent::imin64(b + kLeaf, a.n);
+      for (int64_t j = b; j < e; ++j) {
+        const int k = a.sid[j];
+        if (k == i) continue;
+        const D4 Q = a.sph64[k];
+        const double rho = __dsub_rn(fabs(Q.w), a.tol);
+        if (!(rho > 0.0)) continue;
+        const double d = __dsqrt_rn(ex_d2(P.x, P.y, P.z, Q.x, Q.y, Q.z));
+        if (!(fabs(__dsub_rn(d, ri)) < rho)) continue;
+        if (nn == kMaxMeet) return -1;
+        meet[nn++] = k;
+      }
+    } else {
+      const int64_t cb = idx * kFan, ce = tangent::imin64(cb + kFan, T.count[lev - 1]);
+      const int64_t off = T.offset[lev - 1];
+      for (int64_t c = cb; c < ce; ++c) {
+        const float4 B = T.na[off + c];
+        if (!(B.w > 0.f)) continue;
+        const float dC = tangent::dist32(x32, y32, z32, B);
+        if (dC - tangent::err32(ax, B, dC, B.w + ri32) < B.w + ri32) stack[sp++] = pack_node(lev - 1, c);
       }
     }
   }
-  if (nn == 0) return 1;
+  return nn;
+}
+
+// Does one of the test points handled by `lane` of `nlanes` lie outside every
+// ball but the ones it was built from?  The lane takes the circles of
+// meet[c] with c = lane mod nlanes and the pairs whose running number is
+// lane mod nlanes; it stops early once *found (another lane's success, may
+// be null) is set.  Which lane finds a point does not matter: sphere i is
+// uncovered when any lane does.
+__device__ inline bool lane_candidates(const QueryArgs& a, int i, const int* meet, int nn, int lane, int nlanes,
+                                       const volatile int* found) {
+  const D4 P = a.sph64[i];
+  const double pi[3] = {P.x, P.y, P.z};
+  const double ri = fabs(P.w);
   const double e_ref[3] = {0.36, 0.48, 0.8};
   double ref[3];
   for (int c = 0; c < 3; ++c) ref[c] = __dadd_rn(pi[c], __dmul_rn(__dadd_rn(ri, 1.0), e_ref[c]));
   double pts[6];
+  int64_t pair = 0;
   for (int u = 0; u < nn; ++u) {
+    if (found && *found) return false;
     const int k = meet[u];
     const D4 Q = a.sph64[k];
     const double pk[3] = {Q.x, Q.y, Q.z};
     const double rk = __dsub_rn(fabs(Q.w), a.tol);
-    if (circle_points(pi, ri, pk, rk, ref, pts)) {
-      if (tangent::covered_except(a, pts[0], pts[1], pts[2], i, k, -1) < 0) return 1;
-      if (tangent::covered_except(a, pts[3], pts[4], pts[5], i, k, -1) < 0) return 1;
+    if (u % nlanes == lane && circle_points(pi, ri, pk, rk, ref, pts)) {
+      if (tangent::covered_except(a, pts[0], pts[1], pts[2], i, k, -1) < 0) return true;
+      if (tangent::covered_except(a, pts[3], pts[4], pts[5], i, k, -1) < 0) return true;
     }
-    for (int v = u + 1; v < nn; ++v) {
+    for (int v = u + 1; v < nn; ++v, ++pair) {
+      if (pair % nlanes != lane) continue;
+      if (found && *found) return false;
       const int m = meet[v];
       const D4 R = a.sph64[m];
       const double pm[3] = {R.x, R.y, R.z};
@@ -177,12 +189,33 @@ __device__ inline int sphere_uncovered(const QueryArgs& a, int i) {
       // the oracle takes the pair in increasing index order
       const bool km = k < m;
       if (triple_points(pi, ri, km ? pk : pm, km ? rk : rm, km ? pm : pk, km ? rm : rk, pts)) {
-        if (tangent::covered_except(a, pts[0], pts[1], pts[2], i, k, m) < 0) return 1;
-        if (tangent::covered_except(a, pts[3], pts[4], pts[5], i, k, m) < 0) return 1;
+        if (tangent::covered_except(a, pts[0], pts[1], pts[2], i, k, m) < 0) return true;
+        if (tangent::covered_except(a, pts[3], pts[4], pts[5], i, k, m) < 0) return true;
       }
     }
   }
-  return 0;
+  return false;
+}
+
+// The cases decided before any test point: 1 for a zero sample outside the
+// other balls or a sphere no ball meets, 0 for a covered zero sample, 2 for
+// more than kMaxMeet meeting balls; -1 when the test points decide.
+__device__ inline int trivial_case(const QueryArgs& a, int i, int nn) {
+  const D4 P = a.sph64[i];
+  if (fabs(P.w) == 0.0) return tangent::covered_except(a, P.x, P.y, P.z, i, -1, -1) < 0 ? 1 : 0;
+  if (nn < 0) return 2;
+  if (nn == 0) return 1;
+  return -1;
+}
+
+// 1: sphere i (input index) keeps an uncovered point; 0: it does not;
+// 2: undecided (more than kMaxMeet balls meet it).  One thread.
+__device__ inline int sphere_uncovered(const QueryArgs& a, int i) {
+  int meet[kMaxMeet];
+  const int nn = fabs(a.sph64[i].w) == 0.0 ? 0 : gather_meet(a, i, meet);
+  const int t = trivial_case(a, i, nn);
+  if (t >= 0) return t;
+  return lane_candidates(a, i, meet, nn, 0, 1, nullptr) ? 1 : 0;
 }
 
 }  // namespace exact

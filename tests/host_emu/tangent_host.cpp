@@ -173,3 +173,23 @@ extern "C" int uncovered_host(const double* p, const double* s, int64_t n, doubl
   for (int64_t i = 0; i < n; ++i) out[i] = uint8_t(exact::sphere_uncovered(a, int(i)));
   return 0;
 }
+
+// the warp kernel's split: 32 lanes each testing their share of the points
+extern "C" int uncovered_host_lanes(const double* p, const double* s, int64_t n, double tol, uint8_t* out,
+                                    unsigned order_seed) {
+  HostTree H;
+  if (!build_tree(p, s, n, order_seed, H)) return -1;
+  const QueryArgs a = args_for(H, n, tol);
+  std::vector<int> meet(exact::kMaxMeet);
+  for (int64_t i = 0; i < n; ++i) {
+    const int nn = std::fabs(H.sph[i].w) == 0.0 ? 0 : exact::gather_meet(a, int(i), meet.data());
+    int res = exact::trivial_case(a, int(i), nn);
+    if (res < 0) {
+      res = 0;
+      for (int lane = 0; lane < 32; ++lane)
+        if (exact::lane_candidates(a, int(i), meet.data(), nn, lane, 32, nullptr)) res = 1;
+    }
+    out[i] = uint8_t(res);
+  }
+  return 0;
+}

@@ -47,6 +47,8 @@ def host(tmp_path_factory):
     L.coverage_host.restype = ctypes.c_int
     L.uncovered_host.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, P, ctypes.c_uint]
     L.uncovered_host.restype = ctypes.c_int
+    L.uncovered_host_lanes.argtypes = L.uncovered_host.argtypes
+    L.uncovered_host_lanes.restype = ctypes.c_int
     return L
 
 
@@ -155,10 +157,11 @@ def test_host_cell_coverage_lattice_shells(host, orc):
         assert _coverage(host, centre[None], s, cell, origin, h, 8, 0.0, 0)[0] == count
 
 
-def _uncovered(host, p, s, tol, order):
+def _uncovered(host, p, s, tol, order, lanes=False):
     p, s = np.ascontiguousarray(p, np.float64), np.ascontiguousarray(s, np.float64)
     out = np.zeros(s.shape[0], np.uint8)
-    assert host.uncovered_host(_ptr(p), _ptr(s), s.shape[0], tol, _ptr(out), order) == 0
+    fn = host.uncovered_host_lanes if lanes else host.uncovered_host
+    assert fn(_ptr(p), _ptr(s), s.shape[0], tol, _ptr(out), order) == 0
     return out
 
 
@@ -183,3 +186,5 @@ def test_host_sphere_uncovered(host, orc):
             want = orc.sphere_uncovered(p, s, tol=tol)
             for order in (0, 5):
                 assert np.array_equal(_uncovered(host, p, s, tol, order), want)
+            # the warp kernel's split of the test points over 32 lanes
+            assert np.array_equal(_uncovered(host, p, s, tol, 0, lanes=True), want)
