@@ -151,6 +151,21 @@ int gfs_query(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, float* s_ou
 int gfs_query_tangent(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, float* s_out, double* s64_out,
                       int64_t* argmin_out, uint16_t* flags_out);
 
+/* The point q* that sets each value of a gfs_query / gfs_query_tangent
+ * result (Prop. 2: the nearest valid grow-to point), from its argmin and
+ * result word: SURVIVOR: the candidate p_i + |s_i| u_k (or an inserted
+ * sphere's witness); OPPOSITE and LOWER j: the point of sphere j nearest to
+ * x, p_j + |s_j| (x - p_j)/|x - p_j|; TANGENT 2j + side: that tangent point
+ * (side 1: p_j - ...); OUTSIDE, and OPPOSITE / LOWER with argmin -1: x
+ * itself (value 0); SAMPLE and INVALID: NaN (no point sets the value), and
+ * NaN where x = p_j.  FP64, the expressions of the candidates and tangent
+ * points, so |x - q*| reproduces the value.
+ * x, m: the query points; argmin, flags: that query's outputs (device).
+ * qstar_out: device, m*3 FP64.  No host synchronisation, no allocation.
+ * Errors: GFS_ERR_STATE (no build), GFS_ERR_ARG, GFS_ERR_CUDA. */
+int gfs_query_points(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, const int64_t* argmin,
+                     const uint16_t* flags, double* qstar_out);
+
 /* Adjoint of gfs_query through the argmin (the paper has no gradients; the
  * value is piecewise a distance to a point or a sphere, differentiated here).
  * argmin/flags/s: the forward outputs for the same x (device).

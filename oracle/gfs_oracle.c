@@ -1127,3 +1127,43 @@ void orc_sphere_uncovered(const double* p, const double* s, int64_t n, double to
   }
   free(N);
 }
+
+/* ------------------------------------------------------------------------ */
+/* the point that sets each value (q* of the query)                          */
+/* ------------------------------------------------------------------------ */
+/* From a query's argmin and code: SURVIVOR g = (i, k): the candidate
+ * p_i + |s_i| u_k; OPPOSITE and LOWER j: the near tangent point
+ * p_j + |s_j| (x - p_j)/|x - p_j| (for OPPOSITE the point of the opposite
+ * sphere nearest to x, for LOWER the point where x's deepest containing ball
+ * is nearest to x); TANGENT 2j + side: that tangent point (side 1: far);
+ * OUTSIDE, and LOWER with no sphere (argmin -1): x itself (value 0);
+ * SAMPLE and INVALID: NaN (no point defines the value).  Where x = p_j the
+ * direction is undefined: NaN.  Same expressions, in the same order, as the
+ * candidates and the tangent points of the queries. */
+void orc_argmin_points(const double* p, const double* s, const double* U, int K, const double* x, int64_t m,
+                       const int64_t* argmin, const int32_t* flags, double* out) {
+  const double nan = 0.0 / 0.0;
+  for (int64_t t = 0; t < m; ++t) {
+    const double* xq = x + 3 * t;
+    double* o = out + 3 * t;
+    const int code = flags[t] & 15;
+    const int64_t a = argmin[t];
+    o[0] = o[1] = o[2] = nan;
+    if (code == CODE_SURVIVOR) {
+      cand_pos(p + 3 * (a / (K + 1)), s[a / (K + 1)], U + 3 * (a % (K + 1)), o);
+    } else if (code == CODE_OUTSIDE || ((code == CODE_LOWER || code == CODE_OPPOSITE) && a < 0)) {
+      o[0] = xq[0];
+      o[1] = xq[1];
+      o[2] = xq[2];
+    } else if (code == CODE_OPPOSITE || code == CODE_LOWER || code == CODE_TANGENT) {
+      const int64_t j = code == CODE_TANGENT ? a / 2 : a;
+      const double r = fabs(s[j]);
+      const double sgnr = (code == CODE_TANGENT && a % 2 == 1) ? -r : r;
+      const double* pj = p + 3 * j;
+      double v[3] = {xq[0] - pj[0], xq[1] - pj[1], xq[2] - pj[2]};
+      const double dv = norm3(v);
+      if (dv > 0.0)
+        for (int c = 0; c < 3; ++c) o[c] = pj[c] + sgnr * (v[c] / dv);
+    }
+  }
+}

@@ -70,6 +70,8 @@ def lib():
         L.orc_exact_rmin.restype = f64
         L.orc_query_aug_lazy.argtypes = [P, P, i64, P, i32, f64, i32, i32, P, i64, P, P, P]
         L.orc_query_aug_lazy.restype = None
+        L.orc_argmin_points.argtypes = [P, P, P, i32, P, i64, P, P, P]
+        L.orc_argmin_points.restype = None
         L.orc_sphere_uncovered.argtypes = [P, P, i64, f64, P]
         L.orc_sphere_uncovered.restype = None
         L.orc_cell_coverage.argtypes = [P, P, i64, f64, P, i64, P, f64, i32, P]
@@ -304,4 +306,16 @@ def sphere_uncovered(p, s, tol=TOL):
     out = np.zeros(s.shape[0], np.uint8)
     if s.shape[0]:
         lib().orc_sphere_uncovered(_ptr(p), _ptr(s), s.shape[0], tol, _ptr(out))
+    return out
+
+
+def argmin_points(p, s, U, x, argmin, flags):
+    """The point q* that sets each query value (from the argmin and code);
+    (m, 3), NaN where no point defines the value (SAMPLE, INVALID)."""
+    p, s, U, x = _c(p, np.float64), _c(s, np.float64), _c(U, np.float64), _c(x, np.float64)
+    argmin, flags = _c(argmin, np.int64), _c(flags, np.int32)
+    out = np.zeros((x.shape[0], 3), np.float64)
+    if x.shape[0]:
+        lib().orc_argmin_points(_ptr(p), _ptr(s), _ptr(U), U.shape[0], _ptr(x), x.shape[0], _ptr(argmin),
+                                _ptr(flags), _ptr(out))
     return out

@@ -546,6 +546,20 @@ int gfs_query_backward(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, cons
   return GFS_OK;
 }
 
+int gfs_query_points(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, const int64_t* argmin,
+                     const uint16_t* flags, double* qstar_out) {
+  if (!c || m < 0 || (m > 0 && (!x || !argmin || !flags || !qstar_out))) return GFS_ERR_ARG;
+  if (!c->built) return GFS_ERR_STATE;
+  if (m == 0) return GFS_OK;
+  QueryArgs a;
+  fill_query_args(c, a);
+  if (x_is_fp32) a.x32 = static_cast<const float*>(x);
+  else a.x64 = static_cast<const double*>(x);
+  a.m = m;
+  GFS_CK(launch_argmin_points(a, argmin, flags, qstar_out, c->stream));
+  return GFS_OK;
+}
+
 int gfs_sphere_uncovered(gfs_ctx* c, uint8_t* out) {
   if (!c || !out) return GFS_ERR_ARG;
   if (!c->built) return GFS_ERR_STATE;

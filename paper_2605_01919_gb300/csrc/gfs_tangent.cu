@@ -18,6 +18,15 @@ __global__ void __launch_bounds__(128) k_query_tangent(QueryArgs a, int box_cull
   tangent::tangent_one(a, box_cull, a.perm ? int64_t(a.perm[slot]) : slot);
 }
 
+__global__ void __launch_bounds__(128) k_argmin_points(QueryArgs a, const int64_t* __restrict__ argmin,
+                                                       const uint16_t* __restrict__ flags, double* __restrict__ out) {
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= a.m) return;
+  double x, y, z;
+  tangent::load_point(a, q, x, y, z);
+  tangent::argmin_point(a, x, y, z, flags[q] & 15, argmin[q], out + 3 * q);
+}
+
 constexpr double kFixScale = 1099511627776.0;  // 2^40, the backward's fixed-point scale
 
 __device__ __forceinline__ void acc_add(long long* dst, double v) {
@@ -97,6 +106,14 @@ cudaError_t launch_tangent_grad(const GradArgs& a, int64_t n, float* grad_p, flo
     k_acc_to_float<<<blocks(n, 256), 256, 0, st>>>(a.acc_s, n, grad_sv);
     ++g_tangent_launches;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_argmin_points(const QueryArgs& a, const int64_t* argmin, const uint16_t* flags, double* out,
+                                 cudaStream_t st) {
+  if (a.m <= 0) return cudaSuccess;
+  k_argmin_points<<<blocks(a.m, 128), 128, 0, st>>>(a, argmin, flags, out);
+  ++g_tangent_launches;
   return cudaGetLastError();
 }
 

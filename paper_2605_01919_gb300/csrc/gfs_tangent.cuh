@@ -460,5 +460,39 @@ __device__ inline void tangent_one(const QueryArgs& a, int box_cull, int64_t q) 
   a.fl_out[q] = uint16_t(flags);
 }
 
+// The point q* that sets a query's value, from its argmin g and code:
+// SURVIVOR: the candidate (or witness); OPPOSITE / LOWER j: the near tangent
+// point of sphere j; TANGENT 2j + side: that tangent point; OUTSIDE, and
+// OPPOSITE / LOWER with no sphere: x; SAMPLE, INVALID, an undefined
+// direction (x = p_j) or an id this state does not hold: NaN.
+__device__ inline void argmin_point(const QueryArgs& a, double x, double y, double z, int code, int64_t g,
+                                    double* o) {
+  o[0] = o[1] = o[2] = NAN;
+  if (code == GFS_CODE_SURVIVOR) {
+    double qx, qy, qz;
+    if (survivor_pos(a, g, qx, qy, qz)) {
+      o[0] = qx;
+      o[1] = qy;
+      o[2] = qz;
+    }
+  } else if (code == GFS_CODE_OUTSIDE || ((code == GFS_CODE_LOWER || code == GFS_CODE_OPPOSITE) && g < 0)) {
+    o[0] = x;
+    o[1] = y;
+    o[2] = z;
+  } else if (code == GFS_CODE_OPPOSITE || code == GFS_CODE_LOWER || code == GFS_CODE_TANGENT) {
+    const int64_t j = code == GFS_CODE_TANGENT ? g / 2 : g;
+    if (j < 0 || j >= a.n) return;
+    const D4 P = a.sph64[j];
+    const double r = fabs(P.w);
+    const double sr = (code == GFS_CODE_TANGENT && g % 2 == 1) ? -r : r;
+    const double vx = __dsub_rn(x, P.x), vy = __dsub_rn(y, P.y), vz = __dsub_rn(z, P.z);
+    const double dv = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz)));
+    if (!(dv > 0.0)) return;
+    o[0] = __dadd_rn(P.x, __dmul_rn(sr, __ddiv_rn(vx, dv)));
+    o[1] = __dadd_rn(P.y, __dmul_rn(sr, __ddiv_rn(vy, dv)));
+    o[2] = __dadd_rn(P.z, __dmul_rn(sr, __ddiv_rn(vz, dv)));
+  }
+}
+
 }  // namespace tangent
 }  // namespace gfs

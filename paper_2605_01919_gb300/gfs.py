@@ -20,7 +20,7 @@ FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 0x10, 0x20, 0x40
 EXPORTED = ["gfs_default_options", "gfs_create", "gfs_set_stream", "gfs_build", "gfs_query", "gfs_query_tangent",
             "gfs_query_backward", "gfs_query_backward_noalloc", "gfs_insert", "gfs_insert_known", "gfs_survivors", "gfs_batch_build", "gfs_batch_query",
             "gfs_batch_survivors", "gfs_stats", "gfs_solve_host", "gfs_icosphere", "gfs_strerror",
-            "gfs_destroy", "gfs_cell_coverage", "gfs_flood_order", "gfs_batch_query_tangent", "gfs_sphere_uncovered"]
+            "gfs_destroy", "gfs_cell_coverage", "gfs_flood_order", "gfs_batch_query_tangent", "gfs_sphere_uncovered", "gfs_query_points"]
 
 
 class Options(ctypes.Structure):
@@ -102,6 +102,8 @@ def load(build_if_missing: bool = True):
     L.gfs_stats.restype = i32
     L.gfs_solve_host.argtypes = [P, P, P, i64, P, i32, i64, P, P, P]
     L.gfs_solve_host.restype = i32
+    L.gfs_query_points.argtypes = [P, P, i32, i64, P, P, P]
+    L.gfs_query_points.restype = i32
     L.gfs_sphere_uncovered.argtypes = [P, P]
     L.gfs_sphere_uncovered.restype = i32
     L.gfs_cell_coverage.argtypes = [P, P, i64, P, f64, i32, P]
@@ -229,6 +231,16 @@ class Context:
                                 _ptr(s64_out), _ptr(argmin_out), _ptr(flags_out)))
         if self.tangent:
             self.tangent_into(x, s_out, s64_out, argmin_out, flags_out)
+
+    def query_points(self, x, argmin, flags) -> torch.Tensor:
+        """q*: the point that sets each value of a query's result (m, 3)
+        FP64, NaN where no point does (SAMPLE, INVALID)."""
+        x = x.contiguous()
+        out = torch.empty((x.shape[0], 3), dtype=torch.float64, device=x.device)
+        self._sync_stream()
+        _check(load().gfs_query_points(self._h, _ptr(x), int(x.dtype == torch.float32), x.shape[0],
+                                       _ptr(argmin.contiguous()), _ptr(flags.contiguous()), _ptr(out)))
+        return out
 
     def tangent_into(self, x, s_out, s64_out, argmin_out, flags_out):
         """Same-sign tangent augmentation of a query's outputs, in place."""

@@ -193,3 +193,17 @@ extern "C" int uncovered_host_lanes(const double* p, const double* s, int64_t n,
   }
   return 0;
 }
+
+// q* of each point from the argmin and flags (argmin_point)
+extern "C" int points_host(const double* p, const double* s, int64_t n, const double* U, int K, const double* x,
+                           int64_t m, const int64_t* argmin, const uint16_t* flags, double* out) {
+  HostTree H;
+  if (!build_tree(p, s, n, 0, H)) return -1;
+  QueryArgs a = args_for(H, n, 1e-6);
+  a.U64 = U;
+  a.K = K;
+  a.KS = K + 1;
+  for (int64_t q = 0; q < m; ++q)
+    tangent::argmin_point(a, x[3 * q], x[3 * q + 1], x[3 * q + 2], flags[q] & 15, argmin[q], out + 3 * q);
+  return 0;
+}

@@ -768,3 +768,42 @@ def test_sphere_uncovered_bounds_the_discrete_survivors(orc, case):
             assert np.all(has[prev])
         prev = has
     assert exact.sum() >= prev.sum()
+
+
+# ----------------------------------------------------------------------------
+# the point q* that sets each value
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(4))
+def test_argmin_points_set_the_values(orc, seed):
+    """q* from the argmin and code: its distance to x is the value (bitwise
+    where the value is the distance to a candidate or a tangent point, to
+    rounding where it is d - r or r - d), it lies on its sphere, OUTSIDE
+    gives x itself and SAMPLE / INVALID give NaN."""
+    p, s = W.tiny_random(30, seed, valid=(seed % 2 == 0), spread=0.6)
+    rng = np.random.default_rng(50 + seed)
+    x = np.concatenate([rng.uniform(-1.2, 1.2, size=(300, 3)), p[:5]])
+    U = orc.icosphere(2)
+    K = U.shape[0]
+    surv = orc.collect(p, s, U, orc.keep_all(p, s, U))
+    for val, arg, fl in (orc.query(p, s, surv, x)[:3], orc.query_aug(p, s, surv, x)):
+        q = orc.argmin_points(p, s, U, x, arg, fl)
+        code = fl & 15
+        seen = set()
+        for t in range(x.shape[0]):
+            c = int(code[t])
+            seen.add(c)
+            dx, dy, dz = x[t, 0] - q[t, 0], x[t, 1] - q[t, 1], x[t, 2] - q[t, 2]
+            d = np.sqrt(dx * dx + dy * dy + dz * dz)
+            if c in (orc.CODE_SURVIVOR, orc.CODE_TANGENT):
+                assert d == abs(val[t])
+                j = arg[t] // (K + 1) if c == orc.CODE_SURVIVOR else arg[t] // 2
+                assert abs(np.linalg.norm(q[t] - p[j]) - abs(s[j])) < 1e-12
+            elif c in (orc.CODE_OPPOSITE, orc.CODE_LOWER) and arg[t] >= 0:
+                assert abs(d - abs(val[t])) < 1e-12 or (val[t] == 0 and c == orc.CODE_LOWER)
+                assert abs(np.linalg.norm(q[t] - p[arg[t]]) - abs(s[arg[t]])) < 1e-12
+            elif c == orc.CODE_OUTSIDE:
+                assert np.array_equal(q[t], x[t])
+            else:
+                assert np.all(np.isnan(q[t]))
+        assert {orc.CODE_OUTSIDE, orc.CODE_SAMPLE} <= seen and seen & {orc.CODE_SURVIVOR, orc.CODE_OPPOSITE, orc.CODE_TANGENT}

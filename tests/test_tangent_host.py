@@ -1,6 +1,6 @@
 """Device routines compiled as host C++, against the oracle (CPU, no GPU
-needed): the tangent pass, the cell coverage count of the refinement order
-and the exact uncovered test per sphere.
+needed): the tangent pass, the cell coverage count of the refinement order,
+the exact uncovered test per sphere and the points q* that set the values.
 
 `csrc/gfs_tangent.cuh` holds the whole per-point logic of gfs_query_tangent:
 the FP64 pass over the sphere hierarchy, the tangent-point search with its
@@ -49,6 +49,8 @@ def host(tmp_path_factory):
     L.uncovered_host.restype = ctypes.c_int
     L.uncovered_host_lanes.argtypes = L.uncovered_host.argtypes
     L.uncovered_host_lanes.restype = ctypes.c_int
+    L.points_host.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int, P, ctypes.c_int64, P, P, P]
+    L.points_host.restype = ctypes.c_int
     return L
 
 
@@ -188,3 +190,22 @@ def test_host_sphere_uncovered(host, orc):
                 assert np.array_equal(_uncovered(host, p, s, tol, order), want)
             # the warp kernel's split of the test points over 32 lanes
             assert np.array_equal(_uncovered(host, p, s, tol, 0, lanes=True), want)
+
+
+def test_host_argmin_points(host, orc):
+    """q* from the plain and the augmented query's outputs, bit for bit
+    against the oracle (NaN where no point sets the value)."""
+    for seed in range(4):
+        p, s = W.tiny_random(40, seed, valid=(seed % 2 == 0), spread=0.6)
+        rng = np.random.default_rng(70 + seed)
+        x = np.ascontiguousarray(np.concatenate([rng.uniform(-1.2, 1.2, size=(300, 3)), p[:5]]))
+        U = orc.icosphere(2)
+        surv = orc.collect(p, s, U, orc.keep_all(p, s, U))
+        for _, arg, fl in (orc.query(p, s, surv, x)[:3], orc.query_aug(p, s, surv, x)):
+            want = orc.argmin_points(p, s, U, x, arg, fl)
+            got = np.zeros_like(want)
+            fl16 = np.ascontiguousarray(fl.astype(np.uint16))
+            arg = np.ascontiguousarray(arg)
+            assert host.points_host(_ptr(p), _ptr(s), p.shape[0], _ptr(U), U.shape[0], _ptr(x), x.shape[0],
+                                    _ptr(arg), _ptr(fl16), _ptr(got)) == 0
+            assert np.array_equal(got, want, equal_nan=True)
