@@ -22,6 +22,11 @@
  *  insert   -- the greedy sequential refinement loop (Sec. 4): each new
  *              value is computed against the inputs and all values inserted
  *              before it, then joins the sample set.
+ * and, beyond that path: the same-sign tangent points of Def. 1 as extra
+ * query candidates (gfs_query_tangent), the point q* behind each value
+ * (gfs_query_points), the exact coverage of each sphere (Prop. 1 (ii),
+ * gfs_sphere_uncovered) and the flood-fill refinement order of Sec. 4.2
+ * (gfs_cell_coverage, gfs_flood_order).
  *
  * Conventions shared by every call:
  *  - Positions are FP64 (x, y, z) triples stored row-major (n x 3); values
