@@ -160,8 +160,14 @@ extern "C" int coverage_host(const double* p, const double* s, int64_t n, double
   HostTree H;
   if (!build_tree(p, s, n, order_seed, H)) return -1;
   const QueryArgs a = args_for(H, n, tol);
-  for (int64_t c = 0; c < ncells; ++c)
+  for (int64_t c = 0; c < ncells; ++c) {
     counts[c] = order::cell_cover_count(a, cells + 3 * c, origin[0], origin[1], origin[2], h, sub, 0, 1);
+    // the warp kernel's split: lane l takes the points l, l + 32, ...
+    unsigned warp = 0;
+    for (int lane = 0; lane < 32; ++lane)
+      warp += order::cell_cover_count(a, cells + 3 * c, origin[0], origin[1], origin[2], h, sub, lane, 32);
+    if (warp != counts[c]) return -2;
+  }
   return 0;
 }
 
