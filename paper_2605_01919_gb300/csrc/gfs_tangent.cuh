@@ -21,6 +21,10 @@
 // on the FP32 copies of the positions, widened by a bound on their rounding
 // error (err32), so they only skip nodes and spheres that cannot decide
 // anything; what passes them is evaluated in FP64.
+//
+// Also here, shared with the other exact passes: the screened coverage walk
+// (covered_except: is a point inside a shrunk ball other than up to three
+// given ones) and the point q* behind a query value (argmin_point).
 #pragma once
 
 #include <climits>
