@@ -34,6 +34,9 @@
  *  - Sec. 4.2 refinement order: the covered area ratio of grid cells from
  *    regularly spaced sub-points (orc_cell_coverage); the flood-fill order
  *    itself is plain Python in oracle.py.
+ *  - The same-sign tangent points of Def. 1 as extra query candidates
+ *    (orc_query_aug, orc_query_aug_lazy) and the point behind each value
+ *    (orc_argmin_points).
  *
  * Readings where the paper is silent are listed in the design notes; the
  * ones that fix arithmetic are repeated at each function.
