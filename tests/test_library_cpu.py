@@ -108,3 +108,27 @@ def test_flood_order_errors(gfs):
     assert L.gfs_flood_order(None, None, 2, None) == 1
     far = np.array([[1 << 21, 0, 0]], dtype=np.int32)
     assert L.gfs_flood_order(far.ctypes.data_as(P), counts.ctypes.data_as(P), 1, out.ctypes.data_as(P)) == 6
+
+
+def test_every_context_call_rejects_a_null_context(gfs):
+    """Each entry point that takes a context returns GFS_ERR_ARG for a null
+    one, before touching a device."""
+    L = gfs.load()
+    origin = np.zeros(3)
+    calls = [
+        lambda: L.gfs_set_stream(None, None),
+        lambda: L.gfs_query_tangent(None, None, 0, 1, None, None, None, None),
+        lambda: L.gfs_query_points(None, None, 0, 1, None, None, None),
+        lambda: L.gfs_query_backward(None, None, 0, 1, None, None, None, None, None, None, None),
+        lambda: L.gfs_insert(None, None, 1, None, None, None),
+        lambda: L.gfs_insert_known(None, None, None, 1, None, None, None),
+        lambda: L.gfs_survivors(None, None, 0, ctypes.byref(ctypes.c_int64())),
+        lambda: L.gfs_sphere_uncovered(None, None),
+        lambda: L.gfs_cell_coverage(None, None, 1, origin.ctypes.data_as(ctypes.c_void_p), 0.1, 8, None),
+        lambda: L.gfs_batch_build(None, None, 1),
+        lambda: L.gfs_batch_query(None),
+        lambda: L.gfs_batch_query_tangent(None),
+        lambda: L.gfs_batch_survivors(None, 0, None, 0, ctypes.byref(ctypes.c_int64())),
+    ]
+    for call in calls:
+        assert call() == 1
