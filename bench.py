@@ -713,9 +713,10 @@ def run_gfs(args):
         for name, fn in (("backward", extra_backward), ("repair", lambda: extra_repair(args.repair_steps)),
                          ("insert", lambda: extra_insert(args.insert_steps)),
                          ("batch", lambda: extra_batch(args.batch_shapes, args.batch_scale)),
-                         ("tangent", lambda: _isolated("tangent", ["--tangent-every", str(args.tangent_every)])),
-                         ("refine_order", lambda: _isolated("refine_order")),
-                         ("exact_coverage", lambda: _isolated("exact_coverage", timeout=300))):
+                         ("tangent", lambda: _isolated("tangent", ["--tangent-every", str(args.tangent_every)],
+                                                       timeout=150)),
+                         ("refine_order", lambda: _isolated("refine_order", timeout=150)),
+                         ("exact_coverage", lambda: _isolated("exact_coverage", timeout=150))):
             try:
                 line["extras"][name] = fn()
             except Exception as e:  # a failing sub-benchmark must not hide the headline line
