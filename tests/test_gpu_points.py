@@ -6,7 +6,7 @@ import torch
 
 from paper_2605_01919_gb300 import workloads as W
 
-pytestmark = [pytest.mark.gpu, pytest.mark.widening]
+pytestmark = [pytest.mark.gpu, pytest.mark.widening, pytest.mark.timeout(900)]
 
 
 @pytest.fixture(scope="module")
