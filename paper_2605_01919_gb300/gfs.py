@@ -202,13 +202,24 @@ class Context:
     # -- P build -------------------------------------------------------------
     def build(self, p: torch.Tensor, s: torch.Tensor):
         assert p.is_cuda and s.is_cuda and p.dtype == torch.float64 and s.dtype == torch.float64
+        # what ConsistentSDF checks its sample tensors against: storage,
+        # shape and in-place version of the tensors this state was built from
+        built_from = (p.data_ptr(), s.data_ptr(), tuple(p.shape), tuple(s.shape), p._version, s._version)
         p = p.contiguous()
         s = s.contiguous()
         self._sync_stream()
         _check(load().gfs_build(self._h, _ptr(p), _ptr(s), p.shape[0]))
         self.n = p.shape[0]
         self.p, self.s = p, s
+        self._built_from = built_from
         return self
+
+    def built_from(self, p: torch.Tensor, s: torch.Tensor) -> bool:
+        """True when the current state is the build of exactly these sample
+        tensors, unmodified since (no insertion, no in-place change)."""
+        rec = getattr(self, "_built_from", None)
+        return rec is not None and rec == (p.data_ptr(), s.data_ptr(), tuple(p.shape), tuple(s.shape),
+                                           p._version, s._version)
 
     # -- query ---------------------------------------------------------------
     def query(self, x: torch.Tensor, want_f64: bool = True):
@@ -273,6 +284,7 @@ class Context:
         if known is not None:
             assert known.is_cuda and known.dtype == torch.float64 and known.shape == (T,)
             known = known.contiguous()
+        self._built_from = None   # the state now holds more samples than any caller's tensors
         out = {"s64": torch.empty(T, dtype=torch.float64, device=y.device),
                "argmin": torch.empty(T, dtype=torch.int64, device=y.device),
                "flags": torch.empty(T, dtype=torch.int16, device=y.device)}
@@ -386,6 +398,9 @@ class ConsistentSDF(torch.autograd.Function):
 
     @staticmethod
     def forward(fctx, x, p, s_samples, gctx: Context):
+        if not gctx.built_from(p, s_samples):
+            raise GfsError("ConsistentSDF: the context was not built from these sample tensors, or they "
+                           "changed since its build (in place, or by an insertion); call ctx.build(p, s) first")
         out = gctx.query(x, want_f64=False)
         fctx.gctx = gctx
         fctx.save_for_backward(x, out["s"], out["argmin"], out["flags"])

@@ -360,6 +360,107 @@ def test_grad_matches_finite_differences(orc):
     assert tested >= 4
 
 
+def _query_one(orc, p, s, U, x):
+    """Value, argmin and code at one point after a fresh P build of (p, s)."""
+    surv = orc.collect(p, s, U, orc.keep_all(p, s, U))
+    v, a, f, _ = orc.query(p, s, surv, x[None])
+    return v[0], a[0], f[0] & 15
+
+
+def _fd_sample(orc, p, s, U, x, j, which, h):
+    """Central difference of the value at x in sample j's coordinate `which`
+    (0..2: p_j, 3: s_j), rebuilding the survivor set each side; None when the
+    argmin or the code changes inside the stencil (a tie is crossed)."""
+    pp, pm, sp, sm = p.copy(), p.copy(), s.copy(), s.copy()
+    if which < 3:
+        pp[j, which] += h
+        pm[j, which] -= h
+    else:
+        sp[j] += h
+        sm[j] -= h
+    vp, ap, cp = _query_one(orc, pp, sp, U, x)
+    vm, am, cm = _query_one(orc, pm, sm, U, x)
+    v0, a0, c0 = _query_one(orc, p, s, U, x)
+    if not (ap == a0 == am and cp == c0 == cm):
+        return None
+    return (vp - vm) / (2 * h)
+
+
+@pytest.mark.parametrize("code", [0, 1])
+def test_grad_sample_position_and_value_match_finite_differences(orc, code):
+    """d s*/d p_j and d s*/d s_j of SURVIVOR (code 0: the candidate moves with
+    its sphere) and OPPOSITE (code 1: the tangent point of sphere j) results
+    against central differences of the rebuilt P and the re-run query."""
+    w = W.sphere_grid(N=7, up=2)
+    U = orc.icosphere(2)
+    K = U.shape[0]
+    rng = np.random.default_rng(17 + code)
+    x = rng.uniform(-0.95, 0.95, size=(400, 3))
+    surv = orc.collect(w.p, w.s, U, orc.keep_all(w.p, w.s, U))
+    val, arg, fl, gap = orc.query(w.p, w.s, surv, x)
+    sel = np.nonzero(((fl & 15) == code) & (gap > 1e-4) & (np.abs(val) > 1e-3))[0]
+    h = 1e-7
+    tested = 0
+    for t in sel[:8]:
+        j = arg[t] // (K + 1) if code == 0 else arg[t]
+        gx, gp, gs = orc.grad(w.p, w.s, U, x[t][None], val[t:t + 1], arg[t:t + 1], fl[t:t + 1], np.ones(1))
+        for which in range(4):
+            fd = _fd_sample(orc, w.p, w.s, U, x[t], j, which, h)
+            if fd is None:
+                continue
+            an = gp[j, which] if which < 3 else gs[j]
+            assert abs(fd - an) < 1e-5, (t, which, fd, an)
+            tested += 1
+    assert tested >= 16
+
+
+def _lower_case(sign):
+    # two large spheres of one sign whose candidates all lie outside the box:
+    # no survivor and no opposite sphere, so every query inside is LOWER with
+    # value sign * max_j (r_j - |x - p_j|)
+    p = np.array([[0.1, 0.05, -0.1], [-0.2, 0.1, 0.15]])
+    s = sign * np.array([3.0, 2.5])
+    return p, s
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_grad_lower_branch_matches_closed_form_and_finite_differences(orc, sign):
+    """The LOWER branch (no candidate: value = sign * LB, LB the depth of the
+    deepest containing ball): its value is the closed form, and its
+    derivatives in x, p_j and s_j match central differences."""
+    p, s = _lower_case(sign)
+    U = orc.icosphere(1)
+    K = U.shape[0]
+    rng = np.random.default_rng(23)
+    x = rng.uniform(-0.6, 0.6, size=(12, 3))
+    surv = orc.collect(p, s, U, orc.keep_all(p, s, U))
+    assert surv[0].shape[0] == 0
+    val, arg, fl, _ = orc.query(p, s, surv, x)
+    assert np.all(fl & 15 == orc.CODE_LOWER)
+    depth = np.abs(s)[None, :] - np.linalg.norm(x[:, None, :] - p[None, :, :], axis=2)
+    assert np.array_equal(arg, np.argmax(depth, axis=1))
+    assert np.allclose(val, sign * depth.max(axis=1), rtol=0, atol=1e-15)
+    h = 1e-6
+    for t in range(x.shape[0]):
+        j = arg[t]
+        if abs(depth[t, 0] - depth[t, 1]) < 1e-3:
+            continue
+        gx, gp, gs = orc.grad(p, s, U, x[t][None], val[t:t + 1], arg[t:t + 1], fl[t:t + 1], np.ones(1))
+        for c in range(3):
+            e = np.zeros(3)
+            e[c] = h
+            vp = _query_one(orc, p, s, U, x[t] + e)[0]
+            vm = _query_one(orc, p, s, U, x[t] - e)[0]
+            assert abs((vp - vm) / (2 * h) - gx[0, c]) < 1e-7
+        for which in range(4):
+            fd = _fd_sample(orc, p, s, U, x[t], j, which, h)
+            assert fd is not None
+            an = gp[j, which] if which < 3 else gs[j]
+            assert abs(fd - an) < 1e-7, (t, which, fd, an)
+        # the other sphere does not set the value: no gradient reaches it
+        assert np.all(gp[1 - j] == 0) and gs[1 - j] == 0
+
+
 # ----------------------------------------------------------------------------
 # greedy insertion: the incremental state equals a rebuild from scratch
 # ----------------------------------------------------------------------------
