@@ -38,8 +38,7 @@ CONFIG = {
 }
 METRIC = "consistent SDF queries/sec (incl. P build)"
 UNIT = "queries/s"
-SM_COUNT = 152
-FP32_LANES = 128
+FP32_LANES = 128   # FP32 lanes per SM (nominal figure, reported beside the measured peak)
 
 
 def parse():
@@ -165,6 +164,79 @@ def gpu_numa_cpus(gpu_index: int):
         return node, cpus
     except Exception:
         return None
+
+
+# ----------------------------------------------------------------------------
+# measured arithmetic peaks (the denominators of the ALU rooflines)
+# ----------------------------------------------------------------------------
+def measure_alu_peaks(dev, local, seconds=0.6):
+    """FP32 and FP64 fused multiply-add rates of this GPU, from the library's
+    probe kernel (independent FMA chains on every SM), timed with CUDA events
+    on the launching stream: the best launch (burst) and the median over a
+    loop of about `seconds` (sustained), with the SM clock sampled meanwhile."""
+    import torch
+    from paper_2605_01919_gb300 import gfs
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sink = torch.empty(sms * 8 * 256, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {"sm_count": sms, "probe": "gfs_fma_probe: 4 blocks x 256 threads per SM, 16 independent FMA chains "
+                                     "per thread"}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for name, fp64 in (("fp32", False), ("fp64", True)):
+        iters = 64
+        for _ in range(12):            # size one launch to about 20 ms
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            gfs.fma_probe(fp64, iters, sink, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            if ms > 10.0:
+                break
+            iters = int(iters * max(2.0, min(64.0, 20.0 / max(ms, 1e-3))))
+        ts, flops = [], 0.0
+        t_end = time.perf_counter() + seconds
+        while time.perf_counter() < t_end or len(ts) < 5:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            flops = gfs.fma_probe(fp64, iters, sink, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        out[f"{name}_tflops"] = flops / (min(ts) / 1e3) / 1e12
+        out[f"{name}_tflops_sustained"] = flops / (float(np.median(ts)) / 1e3) / 1e12
+        out[f"{name}_launch_ms"] = float(np.median(ts))
+    out["clocks"] = clocks.stop()
+    out["fp32_tflops_nominal_max_clock"] = sms * FP32_LANES * 2 * 2070.0e6 / 1e12
+    return out
+
+
+def alu_roofline(kernel, units, flops_per_unit, unit_def, ms, peaks, fp64=False, **extra):
+    """Roofline block of an ALU-bound kernel: algorithmic flops (units x
+    flops per unit) over its measured duration, against the measured FMA
+    peak of the pipe that bounds it."""
+    key = "fp64_tflops" if fp64 else "fp32_tflops"
+    peak = peaks.get(key) if peaks else None
+    achieved = flops_per_unit * units / (ms / 1e3) / 1e12 if ms and ms > 0 else None
+    r = {"kernel": kernel, "bound": "alu", "pipe": "fp64" if fp64 else "fp32", "achieved": achieved, "peak": peak,
+         "unit": "TFLOP/s", "frac": (achieved / peak) if (achieved is not None and peak) else None,
+         "traffic": None, "units_per_launch": units, "flops_per_unit": flops_per_unit, "unit_def": unit_def,
+         "ms_per_launch": ms, "peak_source": f"measured {key} (FMA probe, burst) in this run"}
+    r.update(extra)
+    return r
+
+
+def hbm_roofline(kernel, bytes_, unit_def, ms, **extra):
+    peak = measured_peaks().get("hbm_gbs")
+    achieved = bytes_ / (ms / 1e3) / 1e9 if ms and ms > 0 else None
+    r = {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+         "frac": (achieved / peak) if (achieved is not None and peak) else None, "traffic": None,
+         "bytes_per_launch": bytes_, "unit_def": unit_def, "ms_per_launch": ms,
+         "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
+    r.update(extra)
+    return r
 
 
 # ----------------------------------------------------------------------------
@@ -312,8 +384,13 @@ def extra_backward():
     t_fwd = _ev_time(lambda: ctx.query(x, want_f64=False))
     t_bwd = _ev_time(lambda: ctx.backward(x, out["s"], out["argmin"], out["flags"], g))
     m = x.shape[0]
+    n = w.n
     ctx.close()
-    return {"workload": "torus128_tau3_2^22_fp32_points", "build_ms": t_build, "forward_ms": t_fwd,
+    # the adjoint reads each point's coordinates, value, argmin, result word and
+    # upstream gradient and writes its d/dx (42 B per point), and writes d/dp
+    # and d/ds of every sample (16 B per sample)
+    roof = hbm_roofline("k_query_grad", 42 * m + 16 * n, "42 B per query point + 16 B per sample", t_bwd)
+    return {"workload": "torus128_tau3_2^22_fp32_points", "roofline": roof, "build_ms": t_build, "forward_ms": t_fwd,
             "backward_ms": t_bwd, "forward_queries_per_s": m / (t_fwd / 1e3),
             "forward_backward_queries_per_s": m / ((t_fwd + t_bwd) / 1e3),
             "queries_per_s_incl_build": m / ((t_build + t_fwd) / 1e3)}
@@ -674,18 +751,23 @@ def run_gfs(args):
     q_exact = float(np.mean([ph_["ms_query_exact"] for ph_ in phases]))
     cull = float(np.mean([ph_["ms_build_cull"] for ph_ in phases]))
     build = float(np.mean([ph_["ms_build_total"] for ph_ in phases]))
-    # distance evaluations of the sphere pass: (point, sphere) pairs plus
-    # (point, child node) bound tests, 8 flops each (3 differences, 3
-    # multiply-adds)
-    pair_tests = last["query_sphere_items"] + last["query_sphere_node_tests"]
-    flops = 8.0 * pair_tests
-    clock_mhz = 2070.0
-    peak = SM_COUNT * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
-    achieved = flops / (q_sph / 1e3) / 1e12 if q_sph > 0 else 0.0
-    roofline = {"kernel": "k_query_spheres", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": recorded_traffic("k_query_spheres"),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
-                "units_per_launch": pair_tests, "flops_per_unit": 8}
+    # the method's work in the sphere pass: one distance test per (query
+    # point, sphere) pair it evaluates, 8 flops (3 differences, 3
+    # multiply-adds); the hierarchy's child-node bound tests are the
+    # implementation's pruning and are reported separately
+    peaks = measure_alu_peaks(dev, local)
+    items = last["query_sphere_items"]
+    nodes = last["query_sphere_node_tests"]
+    roofline = alu_roofline("k_query_spheres", items, 8, "(query point, sphere) distance tests of the sphere pass",
+                            q_sph, peaks, traffic=recorded_traffic("k_query_spheres"),
+                            node_tests_per_launch=nodes)
+    roofline["frac_incl_node_tests"] = (8.0 * (items + nodes) / (q_sph / 1e3) / 1e12 / roofline["peak"]
+                                        if roofline["peak"] else None)
+    roofline["frac_of_nominal_peak"] = (roofline["achieved"] / peaks["fp32_tflops_nominal_max_clock"]
+                                        if roofline["achieved"] else None)
+    cull_roofline = alu_roofline("k_cull", last["cull_items"], 8,
+                                 "(open candidate, sphere) coverage tests after the neighbour pre-test", cull,
+                                 peaks, node_tests_per_launch=last["cull_node_tests"])
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -694,6 +776,8 @@ def run_gfs(args):
         "config": dict(CONFIG, queries=m, parallelism=f"replicas{world}", l2="256 MiB buffer written between steps "
                        "(outside the timed interval); queries (389 MB) exceed L2"),
         "roofline": roofline,
+        "rooflines_other": {"cull": cull_roofline},
+        "peaks": peaks,
         "phases_ms": {"build_total": build, "cull": cull, "query_spheres": q_sph, "query_finish": q_fin,
                       "query_exact": q_exact},
         "counters": {k: last[k] for k in ("n_survivors_pos", "n_survivors_neg", "cull_fp64_rechecks",

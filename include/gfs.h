@@ -382,6 +382,21 @@ int gfs_solve_host(gfs_ctx* ctx, const double* p_host, const double* s_host, int
                    int x_is_fp32, int64_t m, float* s_out_host, int64_t* argmin_out_host,
                    uint16_t* flags_out_host);
 
+/* ---- measurement ----------------------------------------------------------- */
+/* Arithmetic peak probe (not part of the method): one launch of
+ * blocks_per_sm x (SM count) blocks of 256 threads, each thread running 16
+ * independent fused multiply-add chains for iters x 8 steps in FP32
+ * (fp64 = 0) or FP64 (fp64 = 1), on the given stream.  The path's kernels
+ * are bound by these pipes; their roofline fractions divide by the rate this
+ * launch reaches (time it with events on the same stream).
+ * sink: device buffer of at least blocks x 256 elements of the chosen type
+ * (sink_bytes), overwritten.  *flops_host (host) receives the launch's flop
+ * count (2 per multiply-add).  No synchronisation, no allocation.
+ * Errors: GFS_ERR_ARG (iters < 1, blocks_per_sm outside 1..8, sink too small,
+ * null pointers), GFS_ERR_CUDA. */
+int gfs_fma_probe(int fp64, int64_t iters, int blocks_per_sm, void* sink, int64_t sink_bytes, void* cuda_stream,
+                  double* flops_host);
+
 /* The icosphere direction table the library uses (host computation, no
  * device needed): writes K = 10*4^tau+2 rows of FP64 (x,y,z) into out_host
  * (capacity cap_rows).  Returns K, or -1 on bad arguments. */

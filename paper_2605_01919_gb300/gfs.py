@@ -110,6 +110,8 @@ def load(build_if_missing: bool = True):
     L.gfs_cell_coverage.restype = i32
     L.gfs_flood_order.argtypes = [P, P, i64, P]
     L.gfs_flood_order.restype = i32
+    L.gfs_fma_probe.argtypes = [i32, i64, i32, P, i64, P, ctypes.POINTER(f64)]
+    L.gfs_fma_probe.restype = i32
     L.gfs_icosphere.argtypes = [i32, P, i64]
     L.gfs_icosphere.restype = i32
     L.gfs_strerror.argtypes = [i32]
@@ -127,6 +129,18 @@ def _check(st: int):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def fma_probe(fp64: bool, iters: int, sink: torch.Tensor, blocks_per_sm: int = 4,
+              stream: torch.cuda.Stream | None = None) -> float:
+    """Launch the FMA peak probe (FP32 or FP64) on `stream` (default: the
+    current stream); returns the launch's flop count."""
+    st = stream if stream is not None else torch.cuda.current_stream()
+    flops = ctypes.c_double(0.0)
+    _check(load().gfs_fma_probe(int(fp64), int(iters), int(blocks_per_sm), _ptr(sink),
+                                sink.numel() * sink.element_size(), ctypes.c_void_p(st.cuda_stream),
+                                ctypes.byref(flops)))
+    return flops.value
 
 
 def icosphere(tau: int):
