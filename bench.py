@@ -52,15 +52,14 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sub-benchmarks of the backward, insertion and batched paths")
     ap.add_argument("--only", choices=["backward", "repair", "insert", "batch", "tangent", "refine_order",
-                                       "exact_coverage"],
+                                       "exact_coverage", "sphere16"],
                     default=None,
                     help="run one sub-benchmark alone and print its JSON (profiling)")
-    ap.add_argument("--insert-steps", type=int, default=1024)
-    ap.add_argument("--repair-steps", type=int, default=8192)
+    ap.add_argument("--insert-steps", type=int, default=8192)
+    ap.add_argument("--repair-steps", type=int, default=1 << 20)
     ap.add_argument("--batch-shapes", type=int, default=256)
-    ap.add_argument("--batch-scale", type=float, default=0.5,
-                    help="scale of the batch shapes' grid sides and sample counts (1 = the full workload, "
-                         "~4 min of sub-benchmark)")
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="scale of the batch shapes' grid sides and sample counts (1 = the full workload)")
     ap.add_argument("--tangent-every", type=int, default=256,
                     help="tangent sub-benchmark: use every k-th of the 253^3 points (the pass is FP64, one "
                          "thread per point)")
@@ -308,7 +307,7 @@ def run_reference(args):
     from paper_2605_01919_gb300 import workloads as W
     w = W.union_grid()
     x = w.make_queries()
-    cb = cpu_baseline_line(w, x, max(1, args.warmup + args.steps), n_keep=1000, n_query=1)
+    cb = cpu_baseline_line(w, x, max(1, args.warmup + args.steps), n_keep=1000, n_query=2)
     line = {
         "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * x.shape[0] / cb["value"],
@@ -396,7 +395,7 @@ def extra_backward():
             "queries_per_s_incl_build": m / ((t_build + t_fwd) / 1e3)}
 
 
-def extra_insert(T=1024):
+def extra_insert(T=8192, peaks=None):
     """Greedy sequential refinement on the 128^3 CSG pseudo-SDF (tau 3): new
     points at the centres of the cells whose eight corner samples do not all
     exceed half the cell diagonal (the cells that may contain the surface),
@@ -416,7 +415,7 @@ def extra_insert(T=1024):
     ix, iy, iz = np.nonzero(cell)
     y = np.stack([c[ix], c[iy], c[iz]], axis=1)[:T]
     p, s = torch.from_numpy(w.p).cuda(), torch.from_numpy(w.s).cuda()
-    ctx = gfs.Context(tau=w.tau)
+    ctx = gfs.Context(tau=w.tau, timing=True)
     t_build = _ev_time(lambda: ctx.build(p, s), reps=1)
     yt = torch.from_numpy(np.ascontiguousarray(y)).cuda()
     torch.cuda.synchronize()
@@ -424,53 +423,131 @@ def extra_insert(T=1024):
     out = ctx.insert(yt)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    st = ctx.stats()
     fl = out["flags"].cpu().numpy().astype(np.int32) & 0xFFFF
     ctx.close()
     return {"workload": "csg128_tau3_refine_surface_cells", "candidate_cells": int(cell.sum()),
             "inserted": int(y.shape[0]), "build_ms": t_build, "insert_s": dt,
-            "insertions_per_s": y.shape[0] / dt, "codes": np.bincount(fl & 15, minlength=6).tolist(),
+            "insertions_per_s": y.shape[0] / dt, "rounds": st["insert_rounds"],
+            "roofline": _insert_roofline(st, peaks), "codes": np.bincount(fl & 15, minlength=6).tolist(),
             "lost_witness_steps": int(np.sum((fl & 0x80) != 0)),
             "far_violations": int(np.sum((fl & 0x20) != 0))}
 
 
-def extra_repair(T=8192):
-    """Repair of the 128^3 CSG pseudo-SDF (tau 3, Sec. 6): build on all
-    samples; the samples left with no surviving candidate are removed; rebuild
-    on the rest; re-insert the removed samples in index order with their own
-    values known (their signs fix the classes, NONCONSERVATIVE counts values
-    below them).  Times the first T insertions."""
+def _insert_roofline(st, peaks):
+    """Roofline of the insertion's step queries (k_ins_query): FP32 screens of
+    spheres and survivors (8 flops each) over the query kernels' device time
+    against the FP32 peak, with the FP64 evaluations (about 20 flops each:
+    differences, products, a square root) against the FP64 peak beside it."""
+    ms = st["insert_ms_query"]
+    screens = st["insert_sph_tested"] + st["insert_surv_tested"]
+    exact = st["insert_sph_exact"] + st["insert_surv_exact"]
+    r = alu_roofline("k_ins_query", screens, 8, "(step point, sphere or survivor) FP32 screens of the step queries",
+                     ms, peaks)
+    if peaks and ms > 0:
+        a64 = 20.0 * exact / (ms / 1e3) / 1e12
+        r["fp64"] = {"units": exact, "flops_per_unit": 20, "achieved": a64, "peak": peaks.get("fp64_tflops"),
+                     "frac": a64 / peaks["fp64_tflops"] if peaks.get("fp64_tflops") else None}
+    r["launches"] = st["insert_rounds"]
+    return r
+
+
+def _repair_setup():
     import torch
     from paper_2605_01919_gb300 import gfs
     from paper_2605_01919_gb300 import workloads as W
     w = W.csg_pseudo_grid()
     p, s = torch.from_numpy(w.p).cuda(), torch.from_numpy(w.s).cuda()
-    ctx = gfs.Context(tau=w.tau)
+    ctx = gfs.Context(tau=w.tau, timing=True)
     ctx.build(p, s)
     surv = ctx.survivors().cpu().numpy()
     cnt = np.bincount(surv // (ctx.K + 1), minlength=w.n)
     removed = np.nonzero(cnt == 0)[0]
     kept = torch.from_numpy(cnt > 0).cuda()
-    p2, s2 = p[kept].contiguous(), s[kept].contiguous()
+    return w, ctx, removed, p[kept].contiguous(), s[kept].contiguous()
+
+
+def extra_repair(T=1 << 20, T_index=8192, peaks=None):
+    """Repair of the 128^3 CSG pseudo-SDF (tau 3, Sec. 6): build on all
+    samples; the samples left with no surviving candidate are removed; rebuild
+    on the rest; re-insert T removed samples with their own values known
+    (their signs fix the classes, NONCONSERVATIVE counts values below them)
+    by the greedy loop.  The paper assigns the repaired values in parallel and
+    fixes no order; the sequential loop needs one: a seeded permutation of the
+    removed samples (consecutive points far apart, so the rounds commit many
+    steps), and for comparison the first T_index in index order (neighbours,
+    mostly within each other's reach)."""
+    import torch
+    w, ctx, removed, p2, s2 = _repair_setup()
     t_build = _ev_time(lambda: ctx.build(p2, s2), reps=1)
-    sel = removed[:T]
-    yt = torch.from_numpy(np.ascontiguousarray(w.p[sel])).cuda()
-    kn = torch.from_numpy(np.ascontiguousarray(w.s[sel])).cuda()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    out = ctx.insert(yt, known=kn)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    fl = out["flags"].cpu().numpy().astype(np.int32) & 0xFFFF
+    res = {"workload": "csg128_tau3_repair_known_values", "samples": int(w.n), "removed": int(removed.size),
+           "rebuild_ms": t_build}
+    for name, sel in (("scattered", np.random.default_rng(3001).permutation(removed)[:T]),
+                      ("index_order", removed[:T_index])):
+        ctx.build(p2, s2)
+        yt = torch.from_numpy(np.ascontiguousarray(w.p[sel])).cuda()
+        kn = torch.from_numpy(np.ascontiguousarray(w.s[sel])).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = ctx.insert(yt, known=kn)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = ctx.stats()
+        fl = out["flags"].cpu().numpy().astype(np.int32) & 0xFFFF
+        res[name] = {"inserted": int(sel.size), "insert_s": dt, "insertions_per_s": sel.size / dt,
+                     "rounds": st["insert_rounds"], "rebuilds": st["insert_rebuilds"],
+                     "step_queries": st["insert_slots"], "ms_query": st["insert_ms_query"],
+                     "ms_commit": st["insert_ms_commit"], "ms_update": st["insert_ms_update"],
+                     "ms_rebuild": st["insert_ms_rebuild"], "roofline": _insert_roofline(st, peaks),
+                     "codes": np.bincount(fl & 15, minlength=6).tolist(),
+                     "nonconservative": int(np.sum((fl & 0x100) != 0)),
+                     "lost_witness_steps": int(np.sum((fl & 0x80) != 0)),
+                     "far_violations": int(np.sum((fl & 0x20) != 0)),
+                     "survivors_after": st["n_survivors_pos"] + st["n_survivors_neg"]}
+        del yt, kn, out
     ctx.close()
-    return {"workload": "csg128_tau3_repair_known_values", "samples": int(w.n), "removed": int(removed.size),
-            "inserted": int(sel.size), "rebuild_ms": t_build, "insert_s": dt,
-            "insertions_per_s": sel.size / dt, "codes": np.bincount(fl & 15, minlength=6).tolist(),
-            "nonconservative": int(np.sum((fl & 0x100) != 0)),
-            "lost_witness_steps": int(np.sum((fl & 0x80) != 0)),
-            "far_violations": int(np.sum((fl & 0x20) != 0))}
+    return res
 
 
-def extra_batch(count=256, scale=0.5):
+def extra_sphere16(peaks=None, reps=20):
+    """The small workload: 16^3 grid of the exact SDF of a sphere (r 0.6), tau
+    2 (663,552 candidates), FP64 queries at the 31^3 points of the 2x
+    upsampled grid; build + query per step, inputs resident, median of reps."""
+    import torch
+    from paper_2605_01919_gb300 import gfs
+    from paper_2605_01919_gb300 import workloads as W
+    w = W.sphere_grid()
+    x = torch.from_numpy(w.make_queries()).cuda()
+    p, s = torch.from_numpy(w.p).cuda(), torch.from_numpy(w.s).cuda()
+    m = int(x.shape[0])
+    out = {"s": torch.empty(m, dtype=torch.float32, device="cuda"),
+           "argmin": torch.empty(m, dtype=torch.int64, device="cuda"),
+           "flags": torch.empty(m, dtype=torch.int16, device="cuda")}
+    ctx = gfs.Context(tau=w.tau, timing=True)
+
+    def step():
+        ctx.build(p, s)
+        ctx.query_into(x, out["s"], None, out["argmin"], out["flags"])
+    for _ in range(3):
+        step()
+    ts, st = [], None
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step()
+        b.record()
+        st = ctx.stats()
+        ts.append(a.elapsed_time(b))
+    ms = float(np.median(ts))
+    ctx.close()
+    return {"workload": "sphere16_tau2_q31^3_f64", "candidates": int(w.n) * 162, "queries": m, "ms_per_step": ms,
+            "queries_per_s_incl_build": m / (ms / 1e3), "survivors": st["n_survivors_pos"] + st["n_survivors_neg"],
+            "roofline": alu_roofline("k_query_spheres", st["query_sphere_items"], 8,
+                                     "(query point, sphere) distance tests of the sphere pass", st["ms_query_spheres"],
+                                     peaks, node_tests_per_launch=st["query_sphere_node_tests"])}
+
+
+def extra_batch(count=256, scale=1.0, peaks=None):
     """The first `count` shapes of the 256-shape batch (unions of 1-8
     primitives; even index = grid with 2x upsampled queries, odd = scattered
     samples with 8n uniform queries), sizes scaled by `scale`: one batched
@@ -500,6 +577,7 @@ def extra_batch(count=256, scale=0.5):
             ctx.batch_query()
     torch.cuda.synchronize()
     t_graph = _ev_time(lambda: g.replay())
+    bst = ctx.stats()
     single = gfs.Context(tau=3)
 
     def one_by_one():
@@ -510,6 +588,9 @@ def extra_batch(count=256, scale=0.5):
     ctx.close()
     single.close()
     return {"workload": f"batch{count}_scale{scale}_tau3", "shapes": count, "samples": Nn, "queries": M,
+            "roofline": alu_roofline("k_batch_query (both phases)", bst["batch_sphere_items"] + bst["batch_surv_items"],
+                                     8, "(query point, sphere or survivor) distance tests of the batched query",
+                                     t_graph, peaks, node_tests_per_launch=bst["batch_sphere_node_tests"]),
             "batched_build_ms": t_build, "batched_query_ms": t_query, "graph_replay_query_ms": t_graph,
             "batched_queries_per_s_incl_build": M / ((t_build + t_query) / 1e3),
             "one_by_one_ms": t_single, "one_by_one_queries_per_s_incl_build": M / (t_single / 1e3),
@@ -794,20 +875,23 @@ def run_gfs(args):
         del p, s, x, s_out, arg_out, fl_out, flush
         torch.cuda.empty_cache()
         line["extras"] = {}
-        for name, fn in (("backward", extra_backward), ("repair", lambda: extra_repair(args.repair_steps)),
-                         ("insert", lambda: extra_insert(args.insert_steps)),
-                         ("batch", lambda: extra_batch(args.batch_shapes, args.batch_scale)),
+        for name, fn in (("sphere16", lambda: extra_sphere16(peaks)), ("backward", extra_backward),
+                         ("repair", lambda: extra_repair(args.repair_steps, peaks=peaks)),
+                         ("insert", lambda: extra_insert(args.insert_steps, peaks=peaks)),
+                         ("batch", lambda: extra_batch(args.batch_shapes, args.batch_scale, peaks=peaks)),
                          ("tangent", lambda: _isolated("tangent", ["--tangent-every", str(args.tangent_every)],
                                                        timeout=150)),
                          ("refine_order", lambda: _isolated("refine_order", timeout=150)),
                          ("exact_coverage", lambda: _isolated("exact_coverage", timeout=150))):
+            t_x = time.perf_counter()
             try:
                 line["extras"][name] = fn()
             except Exception as e:  # a failing sub-benchmark must not hide the headline line
                 line["extras"][name] = {"error": f"{type(e).__name__}: {e}"}
+            line["extras"][name]["wall_s"] = time.perf_counter() - t_x
             torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_line(w, xh, steps=2, n_keep=2000, n_query=2)
+        line["cpu_baseline"] = cpu_baseline_line(w, xh, steps=2, n_keep=2000, n_query=8)
     ctx.close()
     if rank == 0:
         print(json.dumps(_finite(line)), flush=True)
@@ -818,9 +902,13 @@ def run_gfs(args):
 if __name__ == "__main__":
     a = parse()
     if a.only:
-        fn = {"backward": extra_backward, "repair": lambda: extra_repair(a.repair_steps),
-              "insert": lambda: extra_insert(a.insert_steps),
-              "batch": lambda: extra_batch(a.batch_shapes, a.batch_scale),
+        import torch
+        pk = measure_alu_peaks(torch.device("cuda", 0), 0) if a.only in ("repair", "insert", "batch",
+                                                                          "sphere16") else None
+        fn = {"backward": extra_backward, "repair": lambda: extra_repair(a.repair_steps, peaks=pk),
+              "insert": lambda: extra_insert(a.insert_steps, peaks=pk),
+              "batch": lambda: extra_batch(a.batch_shapes, a.batch_scale, peaks=pk),
+              "sphere16": lambda: extra_sphere16(pk),
               "tangent": lambda: extra_tangent(a.tangent_every),
               "refine_order": extra_refine_order,
               "exact_coverage": extra_exact_coverage}[a.only]

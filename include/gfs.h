@@ -198,9 +198,22 @@ int gfs_query_backward(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, co
  * s_out:      device, T FP64 values (nullable).
  * argmin_out: device, T int64 (nullable); flags_out: device, T uint16 (nullable).
  * The context's state is updated: later gfs_query / gfs_survivors calls see
- * the inserted samples.  Synchronises the stream periodically (hierarchy
- * rebuilds).  Errors: GFS_ERR_STATE (no build), GFS_ERR_ARG,
- * GFS_ERR_TOO_LARGE ((n+T+1)*(K+1) >= 2^32), GFS_ERR_OOM, GFS_ERR_CUDA. */
+ * the inserted samples (numbered n, n+1, ... in step order).
+ * Execution: deterministic parallel rounds with the sequential results.  A
+ * round evaluates a window of the first pending steps against the state at
+ * its start (one block per step) and commits every step that no earlier
+ * pending step can influence or be influenced by: the ball of an earlier
+ * step t, whose radius in any later state is at most its nearest opposite
+ * tangent distance R_t (or exactly its value when t commits in the same
+ * round), must stay more than a margin away from the region that decides the
+ * later step's result (its value around its point).  The first pending step
+ * always commits.  The window grows while most of it commits and shrinks when
+ * little does; far-apart points commit many steps per round, points within
+ * each other's reach one.  Synchronises the stream once per round.
+ * Errors: GFS_ERR_STATE (no build), GFS_ERR_ARG,
+ * GFS_ERR_TOO_LARGE ((n+T+1)*(K+1) >= 2^32), GFS_ERR_OOM, GFS_ERR_CUDA,
+ * GFS_ERR_TIMEOUT (more rounds than steps: cannot happen unless the device
+ * state is corrupted). */
 /* As gfs_insert, with a known value per point (Sec. 6 repair: the removed
  * samples are re-inserted knowing their own sample values).
  * known: device, T FP64 values (nullable: then this is gfs_insert).  The sign
@@ -364,6 +377,23 @@ typedef struct {
   int64_t cull_items;          /* sphere coverage tests of the last build (sum over open candidates) */
   double ms_query_spheres;     /* first of the query's two FP32 kernels (the pass over the spheres); part of
                                   ms_query_fast (timing = 1 only) */
+  int64_t insert_rounds;       /* rounds of the last gfs_insert / gfs_insert_known call */
+  int64_t insert_steps;        /* steps it committed (its T) */
+  int64_t insert_rebuilds;     /* hierarchy rebuilds between its rounds */
+  double insert_ms_total;      /* host wall time of that call */
+  double insert_ms_rebuild;    /* of which in the rebuilds between rounds */
+  double insert_ms_final;      /* of which in the final renumbering and rebuild */
+  double insert_ms_query;      /* device time of its step queries (timing = 1 only) */
+  double insert_ms_commit;     /* device time of its commit tests and commits (timing = 1 only) */
+  double insert_ms_update;     /* device time of its state updates (timing = 1 only) */
+  int64_t insert_slots;        /* step queries it evaluated (window slots over all rounds) */
+  int64_t insert_sph_exact;    /* spheres its step queries evaluated exactly in FP64 */
+  int64_t insert_sph_tested;   /* spheres they screened in FP32 */
+  int64_t insert_surv_exact;   /* survivors they evaluated exactly in FP64 */
+  int64_t insert_surv_tested;  /* survivors they screened in FP32 */
+  int64_t batch_sphere_items;  /* (point, sphere) tests of the last gfs_batch_query */
+  int64_t batch_sphere_node_tests; /* its child-node bound tests of the sphere pass */
+  int64_t batch_surv_items;    /* its (point, survivor) tests */
 } gfs_stats_t;
 
 /* Synchronises the stream and fills *out (host). */

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cmath>
 #include <cstddef>
@@ -139,6 +140,12 @@ struct gfs_ctx {
   DevBuf qk_in, qk_out, qv_in, qv_out;  // query Morton keys / processing order
   // insertion state
   DevBuf ins_counts, ins_tomb[2], ins_dsurv[2], ins_dtomb[2], ins_misc;
+  DevBuf ins_maxrem, ins_slot_t, ins_slots, ins_cbuf, ins_new, ins_lost, ins_inserted, ins_codes, ins_dyn;
+  DevBuf ins_present, ins_scan, ins_cmp, ins_dynf4, ins_near, ins_nearcnt;
+  int64_t ins_rounds = 0, ins_steps = 0, ins_rebuilds = 0, ins_queried = 0;  // of the last insertion call
+  double ins_ms_total = 0.0, ins_ms_rebuild = 0.0, ins_ms_final = 0.0;  // host wall time of its phases
+  double ins_ms_query = 0.0, ins_ms_commit = 0.0, ins_ms_update = 0.0;  // device time (timing = 1)
+  unsigned long long ins_work[4] = {0, 0, 0, 0};  // step-query work counters (InsMisc::work)
   // batched shapes
   int b_ns = 0;
   bool b_built = false;
@@ -231,9 +238,17 @@ void fill_query_args(gfs_ctx* c, QueryArgs& a) {
 
 // a2: Morton-sort the samples in sph64[0, n) and build the sphere hierarchy
 // (also used to rebuild it after insertions).
-int build_sphere_hierarchy(gfs_ctx* c, int64_t n) {
+int build_sphere_hierarchy(gfs_ctx* c, int64_t n, const int* ids = nullptr) {
   cudaStream_t st = c->stream;
   c->n = n;
+  // with ids: the hierarchy holds the spheres sph64[ids[0..n)] and its sorted
+  // slots map to those indices (the insertion rounds' provisional numbering)
+  const D4* src = c->sph64.as<D4>();
+  if (ids) {
+    GFS_TRY(ensure(c->ins_cmp, size_t(n) * sizeof(D4)));
+    GFS_CK(launch_gather_d4(c->sph64.as<D4>(), ids, n, c->ins_cmp.as<D4>(), st));
+    src = c->ins_cmp.as<D4>();
+  }
   GFS_TRY(ensure(c->keys_in, size_t(n) * 4));
   GFS_TRY(ensure(c->keys_out, size_t(n) * 4));
   GFS_TRY(ensure(c->vals_in, size_t(n) * 4));
@@ -242,13 +257,14 @@ int build_sphere_hierarchy(gfs_ctx* c, int64_t n) {
   GFS_TRY(ensure(c->thr, size_t(n) * sizeof(float4)));
   GFS_TRY(ensure(c->sid, size_t(n) * 4));
   GFS_CK(cudaMemsetAsync(c->bound_bits.p, 0, 16, st));
-  GFS_CK(launch_keys_d4(c->sph64.as<D4>(), n, c->keys_in.as<uint32_t>(), c->vals_in.as<int>(),
+  GFS_CK(launch_keys_d4(src, n, c->keys_in.as<uint32_t>(), c->vals_in.as<int>(),
                         c->bound_bits.as<unsigned int>(), c->consts.as<BuildConsts>(), st));
   GFS_TRY(sort_u32_pairs(c, c->keys_in.as<uint32_t>(), c->keys_out.as<uint32_t>(), c->vals_in.as<int>(),
                          c->vals_out.as<int>(), n));
-  GFS_CK(launch_gather_spheres(c->sph64.as<D4>(), c->vals_out.as<int>(), n, c->consts.as<BuildConsts>(),
+  GFS_CK(launch_gather_spheres(src, c->vals_out.as<int>(), n, c->consts.as<BuildConsts>(),
                                float(c->opt.tol), c->opt.tol, c->sph.as<float4>(), c->thr.as<float4>(),
                                c->sid.as<int>(), st));
+  if (ids) GFS_CK(launch_remap_sid(c->sid.as<int>(), ids, n, st));
   tree_layout(c->st, n);
   const int64_t nodes = tree_nodes(c->st);
   GFS_TRY(ensure(c->st_lo, size_t(nodes) * sizeof(float4)));
@@ -611,28 +627,22 @@ int gfs_query_tangent(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, float
 
 namespace {
 
-// layout of the small insertion control block (device)
-struct InsMisc {
-  int n_total;
-  unsigned dcount[2];
-  unsigned dcount_start[2];
-  StepRec rec;
-  unsigned lost;
-  unsigned err;
-  unsigned done;
-};
+// Insertion rounds: window capacity, and the spheres inserted between
+// hierarchy rebuilds (the step queries scan them and their candidate slots).
+constexpr int kInsWindow = 4096;
+constexpr int kInsDynSpheres = 8192;  // at most the step query's walk stack (8192 entries), which lists them
+constexpr int kInsPasses = 4;
+constexpr int kInsNear = 1024;  // the kernels' per-new-sphere list capacity (kNear)
 
-// Rebuild the hierarchies from the current state: live survivors compacted
-// into fresh lists, all spheres re-sorted.
-int ins_rebuild(gfs_ctx* c, int64_t n_total) {
+// Compact the live survivors of both classes (hierarchy slots without a
+// tombstone, then the dynamic lists) into surv_raw.
+int ins_compact_survivors(gfs_ctx* c, const InsMisc& hm) {
   cudaStream_t st = c->stream;
-  InsMisc hm;
-  GFS_CK(cudaMemcpyAsync(&hm, c->ins_misc.p, sizeof(InsMisc), cudaMemcpyDeviceToHost, st));
-  GFS_CK(cudaStreamSynchronize(st));
   DevBuf cnt;
   GFS_TRY(ensure(cnt, 16));
   for (int k = 0; k < 2; ++k) {
-    const unsigned need = c->nsurv[k] + hm.dcount[k];
+    const unsigned nd = unsigned(hm.ndyn) * unsigned(c->KS);
+    const unsigned need = c->nsurv[k] + nd;
     if (size_t(need) * sizeof(float4) > c->surv_raw[k].bytes) {
       DevBuf fresh;
       GFS_TRY(ensure(fresh, size_t(need) * sizeof(float4) + 16));
@@ -642,16 +652,38 @@ int ins_rebuild(gfs_ctx* c, int64_t n_total) {
     unsigned hc = 0;
     GFS_CK(cudaMemsetAsync(cnt.p, 0, 4, st));
     GFS_CK(launch_ins_compact(c->surv_sorted[k].as<float4>(), c->ins_tomb[k].as<uint32_t>(), c->nsurv[k],
-                              c->ins_dsurv[k].as<float4>(), c->ins_dtomb[k].as<uint32_t>(), hm.dcount[k],
+                              c->ins_dsurv[k].as<float4>(), c->ins_dtomb[k].as<uint32_t>(), nd,
                               c->surv_raw[k].as<float4>(), cnt.as<unsigned>(), st));
     GFS_CK(cudaMemcpyAsync(&hc, cnt.p, 4, cudaMemcpyDeviceToHost, st));
     GFS_CK(cudaStreamSynchronize(st));
-    if (hc > kMaxSurvivors) return GFS_ERR_TOO_LARGE;
+    if (hc > kMaxSurvivors) {
+      release(cnt);
+      return GFS_ERR_TOO_LARGE;
+    }
     c->nsurv[k] = hc;
     c->cap = std::max(c->cap, hc);
   }
   release(cnt);
-  GFS_TRY(build_sphere_hierarchy(c, n_total));
+  return GFS_OK;
+}
+
+// Mid-call rebuild: survivors compacted, the sphere hierarchy rebuilt over
+// the present spheres (inputs and the spheres inserted so far, provisional
+// indices), dynamic lists emptied.
+int ins_rebuild_rounds(gfs_ctx* c, int64_t n0, int64_t n_present) {
+  cudaStream_t st = c->stream;
+  InsMisc hm;
+  GFS_CK(cudaMemcpyAsync(&hm, c->ins_misc.p, sizeof(InsMisc), cudaMemcpyDeviceToHost, st));
+  GFS_CK(cudaStreamSynchronize(st));
+  GFS_TRY(ins_compact_survivors(c, hm));
+  // the present list: inputs (written at the start of the call), then the
+  // inserted spheres in the order they joined (dynamic list appended)
+  const int64_t before = n_present - hm.ndyn;
+  if (hm.ndyn > 0)
+    GFS_CK(cudaMemcpyAsync(c->ins_present.as<int>() + before, c->ins_dyn.p, size_t(hm.ndyn) * 4,
+                           cudaMemcpyDeviceToDevice, st));
+  (void)n0;
+  GFS_TRY(build_sphere_hierarchy(c, n_present, c->ins_present.as<int>()));
   GFS_TRY(build_point_tree(c, 0));
   GFS_TRY(build_point_tree(c, 1));
   for (int k = 0; k < 2; ++k) {
@@ -659,8 +691,9 @@ int ins_rebuild(gfs_ctx* c, int64_t n_total) {
     GFS_TRY(ensure(c->ins_tomb[k], words * 4));
     GFS_CK(cudaMemsetAsync(c->ins_tomb[k].p, 0, words * 4, st));
   }
-  GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->ins_misc.p) + offsetof(InsMisc, dcount), 0, 4 * sizeof(unsigned),
-                         st));
+  InsMisc* dm = c->ins_misc.as<InsMisc>();
+  GFS_CK(cudaMemsetAsync(&dm->ndyn, 0, sizeof(int), st));
+  GFS_CK(cudaMemsetAsync(&dm->ndyn_start, 0, sizeof(int), st));
   return GFS_OK;
 }
 
@@ -679,15 +712,25 @@ int gfs_insert_known(gfs_ctx* c, const double* y, const double* known, int64_t T
   const int64_t n0 = c->n;
   const int64_t cap = n0 + T + 1;
   if (uint64_t(cap) * uint64_t(c->KS) >= (uint64_t(1) << 32) || cap >= (int64_t(1) << 30)) return GFS_ERR_TOO_LARGE;
-  const int kRebuild = 256;  // steps between hierarchy rebuilds
   GFS_TRY(grow_keep(c->sph64, size_t(cap) * sizeof(D4), size_t(n0) * sizeof(D4), st));
   const size_t wkeep = c->witness64.p ? std::min(c->witness64.bytes, size_t(n0) * 24) : 0;
   GFS_TRY(grow_keep(c->witness64, size_t(cap) * 24, wkeep, st));
   GFS_TRY(ensure(c->ins_counts, size_t(cap) * 4));
-  GFS_CK(cudaMemsetAsync(c->ins_counts.p, 0, size_t(cap) * 4, st));
-  GFS_CK(launch_ins_counts(c->surv_raw[0].as<float4>(), c->nsurv[0], c->surv_raw[1].as<float4>(), c->nsurv[1],
-                           c->sph64.as<D4>(), c->KS, c->ins_counts.as<int>(), st));
-  const unsigned dcap = unsigned(c->KS) * kRebuild;
+  GFS_TRY(ensure(c->ins_maxrem, size_t(cap) * 4));
+  GFS_TRY(ensure(c->ins_lost, size_t(cap) * 4));
+  GFS_TRY(ensure(c->ins_present, size_t(cap) * 4));
+  GFS_TRY(ensure(c->ins_inserted, size_t(T) * 4));
+  GFS_TRY(ensure(c->ins_codes, size_t(T)));
+  GFS_TRY(ensure(c->ins_scan, size_t(T) * 4));
+  GFS_TRY(ensure(c->ins_slot_t, size_t(kInsWindow) * 4));
+  GFS_TRY(ensure(c->ins_slots, size_t(kInsWindow) * sizeof(InsSlot)));
+  GFS_TRY(ensure(c->ins_cbuf, size_t(2 * kInsWindow)));
+  GFS_TRY(ensure(c->ins_new, size_t(kInsWindow) * 4));
+  GFS_TRY(ensure(c->ins_dyn, size_t(kInsDynSpheres) * 4));
+  GFS_TRY(ensure(c->ins_dynf4, size_t(kInsDynSpheres) * sizeof(float4)));
+  GFS_TRY(ensure(c->ins_near, size_t(kInsWindow) * kInsNear * 4));
+  GFS_TRY(ensure(c->ins_nearcnt, size_t(kInsWindow) * 4));
+  const unsigned dcap = unsigned(c->KS) * unsigned(kInsDynSpheres);
   for (int k = 0; k < 2; ++k) {
     const size_t words = (size_t(c->nsurv[k]) + 31) / 32 + 1;
     GFS_TRY(ensure(c->ins_tomb[k], words * 4));
@@ -696,68 +739,192 @@ int gfs_insert_known(gfs_ctx* c, const double* y, const double* known, int64_t T
     GFS_TRY(ensure(c->ins_dtomb[k], size_t(dcap) * 4));
   }
   GFS_TRY(ensure(c->ins_misc, sizeof(InsMisc)));
-  InsMisc hm;
-  std::memset(&hm, 0, sizeof(hm));
-  hm.n_total = int(n0);
-  GFS_CK(cudaMemcpyAsync(c->ins_misc.p, &hm, sizeof(hm), cudaMemcpyHostToDevice, st));
+  GFS_CK(cudaMemsetAsync(c->ins_counts.p, 0, size_t(cap) * 4, st));
+  GFS_CK(cudaMemsetAsync(c->ins_maxrem.p, 0xff, size_t(cap) * 4, st));
+  GFS_CK(cudaMemsetAsync(c->ins_inserted.p, 0, size_t(T) * 4, st));
+  GFS_CK(cudaMemsetAsync(c->ins_codes.p, 0, size_t(T), st));
+  GFS_CK(cudaMemsetAsync(c->ins_misc.p, 0, sizeof(InsMisc), st));
+  GFS_CK(launch_ins_counts(c->surv_raw[0].as<float4>(), c->nsurv[0], c->surv_raw[1].as<float4>(), c->nsurv[1],
+                           c->sph64.as<D4>(), c->KS, c->ins_counts.as<int>(), st));
+  {
+    std::vector<int> ids(static_cast<size_t>(n0));
+    for (int64_t i = 0; i < n0; ++i) ids[size_t(i)] = int(i);
+    GFS_CK(cudaMemcpyAsync(c->ins_present.p, ids.data(), size_t(n0) * 4, cudaMemcpyHostToDevice, st));
+    GFS_CK(cudaStreamSynchronize(st));
+  }
   InsMisc* dm = c->ins_misc.as<InsMisc>();
-  int64_t n_static = n0;
-  int since = 0;
-  for (int64_t t = 0; t < T; ++t) {
-    if (since == kRebuild) {
-      int nt = 0;
-      GFS_CK(cudaMemcpyAsync(&nt, &dm->n_total, 4, cudaMemcpyDeviceToHost, st));
-      GFS_CK(cudaStreamSynchronize(st));
-      GFS_TRY(ins_rebuild(c, nt));
-      n_static = nt;
-      since = 0;
+  c->ins_rounds = c->ins_steps = c->ins_rebuilds = c->ins_queried = 0;
+  c->ins_ms_rebuild = c->ins_ms_query = c->ins_ms_commit = c->ins_ms_update = 0.0;
+  // device time of the round phases (timing = 1): query, commit, update
+  cudaEvent_t iev[5] = {};
+  bool timed = c->have_ev;
+  for (int k = 0; k < 5 && timed; ++k)
+    if (cudaEventCreate(&iev[k]) != cudaSuccess) {
+      cudaGetLastError();
+      timed = false;
     }
-    InsertArgs a;
-    std::memset(&a, 0, sizeof(a));
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() {
+      for (int k = 0; k < 5; ++k)
+        if (e[k]) cudaEventDestroy(e[k]);
+    }
+  } ev_guard{iev};
+  auto ev_ms = [&](int x, int y) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, iev[x], iev[y]) != cudaSuccess) {
+      cudaGetLastError();
+      t = 0.f;
+    }
+    return double(t);
+  };
+  bool update_pending = false;
+  const auto t_start = std::chrono::steady_clock::now();
+  auto ms_since = [](std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  };
+  InsertArgs a;
+  std::memset(&a, 0, sizeof(a));
+  auto refresh_static = [&]() {
     a.sph = c->sph.as<float4>();
     a.sid = c->sid.as<int>();
     a.st = c->st;
-    a.n_static = int(n_static);
-    a.sph64 = c->sph64.as<D4>();
-    a.witness64 = c->witness64.as<double>();
-    a.counts = c->ins_counts.as<int>();
-    a.n_total = &dm->n_total;
     for (int k = 0; k < 2; ++k) {
       a.surv[k] = c->surv_sorted[k].as<float4>();
       a.vt[k] = c->vt[k];
       a.tomb[k] = c->ins_tomb[k].as<uint32_t>();
-      a.dsurv[k] = c->ins_dsurv[k].as<float4>();
-      a.dtomb[k] = c->ins_dtomb[k].as<uint32_t>();
     }
-    a.dcount = dm->dcount;
-    a.dcount_start = dm->dcount_start;
-    a.dcap = dcap;
-    a.U64 = c->U64.as<double>();
-    a.K = c->K;
-    a.KS = c->KS;
-    a.tol = c->opt.tol;
-    a.box_cull = c->opt.box_cull;
-    a.clamp_opp = c->opt.clamp_opp;
     a.bc = c->consts.as<BuildConsts>();
-    a.y = y;
-    a.known = known;
-    a.s_out = s_out;
-    a.arg_out = argmin_out;
-    a.fl_out = flags_out;
-    a.rec = &dm->rec;
-    a.lost = &dm->lost;
-    a.err = &dm->err;
-    a.done = &dm->done;
-    GFS_CK(launch_ins_step(a, t, st));
-    ++since;
+  };
+  refresh_static();
+  a.n0 = int(n0);
+  a.dyn_ids = c->ins_dyn.as<int>();
+  a.dyn_ids_w = c->ins_dyn.as<int>();
+  a.dyn_f4 = c->ins_dynf4.as<float4>();
+  a.near_list = c->ins_near.as<int>();
+  a.near_cnt = c->ins_nearcnt.as<int>();
+  a.sph64 = c->sph64.as<D4>();
+  a.witness64 = c->witness64.as<double>();
+  a.counts = c->ins_counts.as<int>();
+  a.maxrem = c->ins_maxrem.as<int>();
+  for (int k = 0; k < 2; ++k) {
+    a.dsurv[k] = c->ins_dsurv[k].as<float4>();
+    a.dtomb[k] = c->ins_dtomb[k].as<uint32_t>();
   }
-  int nt = 0;
-  GFS_CK(cudaMemcpyAsync(&nt, &dm->n_total, 4, cudaMemcpyDeviceToHost, st));
+  a.U64 = c->U64.as<double>();
+  a.K = c->K;
+  a.KS = c->KS;
+  a.tol = c->opt.tol;
+  a.box_cull = c->opt.box_cull;
+  a.clamp_opp = c->opt.clamp_opp;
+  a.y = y;
+  a.known = known;
+  a.T = T;
+  a.s_out = s_out;
+  a.arg_out = argmin_out;
+  a.fl_out = flags_out;
+  a.slot_t = c->ins_slot_t.as<int>();
+  a.slots = c->ins_slots.as<InsSlot>();
+  a.cbuf = c->ins_cbuf.as<unsigned char>();
+  a.wcap = kInsWindow;
+  a.new_ids = c->ins_new.as<int>();
+  a.lost_list = c->ins_lost.as<int>();
+  a.inserted = c->ins_inserted.as<int>();
+  a.codes = c->ins_codes.as<unsigned char>();
+  a.misc = dm;
+  // rounds: the window grows while most of it commits and shrinks when little
+  // does; every round commits at least its first step
+  int W = int(std::min<int64_t>(T, 64));
+  double commit_rate = 0.0;  // moving average of the steps a round commits
+  int nslots = 0;
+  int64_t done = 0, rounds = 0;
+  InsMisc hm;
+  std::memset(&hm, 0, sizeof(hm));
+  for (;;) {
+    if (timed) GFS_CK(cudaEventRecord(iev[0], st));
+    GFS_CK(launch_ins_query(a, nslots, st));
+    c->ins_queried += nslots;
+    if (timed) GFS_CK(cudaEventRecord(iev[1], st));
+    GFS_CK(launch_ins_commit(a, nslots, kInsPasses, W, st));
+    if (timed) GFS_CK(cudaEventRecord(iev[2], st));
+    GFS_CK(cudaMemcpyAsync(&hm, dm, sizeof(InsMisc), cudaMemcpyDeviceToHost, st));
+    GFS_CK(cudaStreamSynchronize(st));
+    if (timed) {
+      c->ins_ms_query += ev_ms(0, 1);
+      c->ins_ms_commit += ev_ms(1, 2);
+      if (update_pending) c->ins_ms_update += ev_ms(3, 4);
+      update_pending = false;
+    }
+    if (hm.err) return GFS_ERR_CUDA;
+    ++rounds;
+    done += hm.ncommit;
+    if (hm.nnew > 0) {
+      if (timed) GFS_CK(cudaEventRecord(iev[3], st));
+      GFS_CK(launch_ins_update(a, hm.nnew, hm.ndyn_start, st));
+      if (timed) {
+        GFS_CK(cudaEventRecord(iev[4], st));
+        update_pending = true;
+      }
+    }
+    if (nslots > 0) {
+      if (2 * hm.ncommit >= nslots) W = std::min(kInsWindow, 2 * W);
+      else if (8 * hm.ncommit < nslots) W = std::max(1, W / 2);
+    }
+    nslots = hm.npend;
+    if (hm.npend == 0 && hm.next >= T) break;
+    if (rounds > 4 * T + 8) return GFS_ERR_TIMEOUT;  // every round commits at least one step
+    // rebuild when the dynamic sphere list has no room for the next round's
+    // spheres, or when it has grown long for the rate at which rounds commit
+    // (every step query scans it and the slots of the spheres near its point;
+    // a rebuild costs about as much as a few dozen rounds)
+    commit_rate = 0.9 * commit_rate + 0.1 * double(hm.ncommit);
+    const int dyn_soft = int(std::min(double(kInsDynSpheres - kInsWindow), std::max(256.0, 64.0 * commit_rate)));
+    if (hm.ndyn + kInsWindow > kInsDynSpheres || hm.ndyn >= dyn_soft) {
+      const auto t_rb = std::chrono::steady_clock::now();
+      GFS_TRY(ins_rebuild_rounds(c, n0, n0 + hm.ninserted));
+      refresh_static();
+      ++c->ins_rebuilds;
+      c->ins_ms_rebuild += ms_since(t_rb);
+    }
+  }
+  c->ins_rounds = rounds;
+  c->ins_steps = done;
+  const auto t_final = std::chrono::steady_clock::now();
+  // renumber the inserted spheres consecutively (step order) and rebuild
+  GFS_CK(cudaMemcpyAsync(&hm, dm, sizeof(InsMisc), cudaMemcpyDeviceToHost, st));
   GFS_CK(cudaStreamSynchronize(st));
-  GFS_TRY(ins_rebuild(c, nt));
-  GFS_CK(cudaMemcpyAsync(&hm, c->ins_misc.p, sizeof(hm), cudaMemcpyDeviceToHost, st));
-  GFS_CK(cudaStreamSynchronize(st));
+  if (timed && update_pending) c->ins_ms_update += ev_ms(3, 4);
   if (hm.err) return GFS_ERR_CUDA;
+  GFS_TRY(ins_compact_survivors(c, hm));
+  {
+    size_t bytes = 0;
+    GFS_CK(exclusive_scan_i32(nullptr, bytes, c->ins_inserted.as<int>(), c->ins_scan.as<int>(), T, st));
+    GFS_TRY(cub_ensure(c, bytes));
+    bytes = c->cub_temp.bytes;
+    GFS_CK(exclusive_scan_i32(c->cub_temp.p, bytes, c->ins_inserted.as<int>(), c->ins_scan.as<int>(), T, st));
+  }
+  const int64_t n_final = n0 + hm.ninserted;
+  {
+    DevBuf sph_new, wit_new;
+    GFS_TRY(ensure(sph_new, std::max(c->sph64.bytes, size_t(cap) * sizeof(D4))));
+    GFS_TRY(ensure(wit_new, std::max(c->witness64.bytes, size_t(cap) * 24)));
+    GFS_CK(launch_ins_renumber(a, c->ins_scan.as<int>(), sph_new.as<D4>(), wit_new.as<double>(), st));
+    GFS_CK(cudaStreamSynchronize(st));
+    std::swap(sph_new, c->sph64);
+    std::swap(wit_new, c->witness64);
+    release(sph_new);
+    release(wit_new);
+  }
+  for (int k = 0; k < 2; ++k)
+    GFS_CK(launch_ins_remap_survivors(c->surv_raw[k].as<float4>(), c->nsurv[k], c->ins_scan.as<int>(), int(n0),
+                                      c->KS, st));
+  GFS_TRY(build_sphere_hierarchy(c, n_final));
+  GFS_TRY(build_point_tree(c, 0));
+  GFS_TRY(build_point_tree(c, 1));
+  GFS_CK(cudaStreamSynchronize(st));
+  c->ins_ms_final = ms_since(t_final);
+  for (int k = 0; k < 4; ++k) c->ins_work[k] = hm.work[k];
+  c->ins_ms_total = ms_since(t_start);
   return GFS_OK;
 }
 
@@ -1156,6 +1323,9 @@ int gfs_batch_query(gfs_ctx* c) {
   GFS_CK(sort_pairs64(c->cub_temp.p, bytes, c->b_qkin.as<unsigned long long>(), c->b_qkout.as<unsigned long long>(),
                       c->b_qvin.as<int>(), c->b_qvout.as<int>(), c->b_M, end_bit, st));
   const int grid = c->b_grid_query ? c->b_grid_query : 152 * 4;
+  // the work counters of this query (a memset node under capture)
+  GFS_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->b_cnt.p) + offsetof(Counters, q_sphere_ntests), 0,
+                         5 * sizeof(unsigned long long), st));
   for (int phase = 1; phase <= 2; ++phase) {
     GFS_CK(cudaMemsetAsync(c->b_ctr.p, 0, 8, st));
     GFS_CK(launch_batch_query(c->b_qviews.as<QueryArgs>(), c->b_qw.as<int64_t>(), ns, c->b_qtotal,
@@ -1256,7 +1426,30 @@ int gfs_stats(gfs_ctx* c, gfs_stats_t* out) {
   };
   unsigned long long own = 0, sorts = 0;
   launch_counts(&own, &sorts);
-  out->kernel_launches = int64_t(own + tangent_launch_count() + order_launch_count() + exact_launch_count());
+  out->kernel_launches = int64_t(own + tangent_launch_count() + order_launch_count() + exact_launch_count() +
+                                 insert_launch_count());
+  out->insert_rounds = c->ins_rounds;
+  out->insert_steps = c->ins_steps;
+  out->insert_rebuilds = c->ins_rebuilds;
+  out->insert_ms_total = c->ins_ms_total;
+  out->insert_ms_rebuild = c->ins_ms_rebuild;
+  out->insert_ms_final = c->ins_ms_final;
+  out->insert_ms_query = c->ins_ms_query;
+  out->insert_slots = c->ins_queried;
+  if (c->b_built) {
+    Counters bc;
+    GFS_CK(cudaMemcpyAsync(&bc, c->b_cnt.p, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+    GFS_CK(cudaStreamSynchronize(c->stream));
+    out->batch_sphere_items = int64_t(bc.q_sphere_items);
+    out->batch_sphere_node_tests = int64_t(bc.q_sphere_ntests);
+    out->batch_surv_items = int64_t(bc.q_surv_items);
+  }
+  out->insert_sph_exact = int64_t(c->ins_work[0]);
+  out->insert_sph_tested = int64_t(c->ins_work[1]);
+  out->insert_surv_exact = int64_t(c->ins_work[2]);
+  out->insert_surv_tested = int64_t(c->ins_work[3]);
+  out->insert_ms_commit = c->ins_ms_commit;
+  out->insert_ms_update = c->ins_ms_update;
   out->sort_calls = int64_t(sorts);
   if (c->have_ev && c->built_timed) {
     out->ms_build_total = ms(0, 3);
@@ -1321,7 +1514,9 @@ void gfs_destroy(gfs_ctx* c) {
                     &c->h_p, &c->h_s, &c->h_x, &c->h_sout, &c->h_arg, &c->h_fl,
                     &c->qk_in, &c->qk_out, &c->qv_in, &c->qv_out, &c->ins_counts,
                     &c->ins_tomb[0], &c->ins_tomb[1], &c->ins_dsurv[0], &c->ins_dsurv[1], &c->ins_dtomb[0],
-                    &c->ins_dtomb[1], &c->ins_misc,
+                    &c->ins_dtomb[1], &c->ins_misc, &c->ins_maxrem, &c->ins_slot_t, &c->ins_slots, &c->ins_cbuf,
+                    &c->ins_new, &c->ins_lost, &c->ins_inserted, &c->ins_codes, &c->ins_dyn, &c->ins_present,
+                    &c->ins_scan, &c->ins_cmp, &c->ins_dynf4, &c->ins_near, &c->ins_nearcnt,
                     &c->b_desc, &c->b_offd, &c->b_qoffd, &c->b_sph64, &c->b_k64in, &c->b_k64out, &c->b_sph,
                     &c->b_thr, &c->b_sid, &c->b_bits, &c->b_bcs, &c->b_lo, &c->b_hi, &c->b_na, &c->b_nb, &c->b_nf,
                     &c->b_stdev, &c->b_prefix, &c->b_ctr, &c->b_cnt, &c->b_cviews, &c->b_cw, &c->b_sraw[0],

@@ -74,25 +74,61 @@ struct QueryArgs {
   uint4* state;             // 3 x uint4 per processing slot, between the query's two kernels
 };
 
+// One pending step of the insertion window: its value against the state at
+// the start of the round, and what the commit test needs.
+struct InsSlot {
+  double value;          // FP64 value
+  double wx, wy, wz;     // witness: the point that set the value
+  double R;              // upper bound of the step's value in any later state (< 0: never inserts)
+  double rho;            // radius within which the state decides this result (inf: any change may)
+  long long arg;         // argmin (provisional sphere numbering)
+  int t;                 // step index
+  unsigned short flags;  // result word without LOST_WITNESS
+  unsigned char insert;  // 1: the result joins the samples
+  unsigned char pad;
+};
+
+// Device-side counters of the insertion rounds (read back once per round).
+struct InsMisc {
+  int npend;                 // valid window slots
+  int next;                  // next step not yet in the window
+  int ncommit;               // steps committed by the last round
+  int nnew;                  // spheres inserted by the last round
+  int ndyn;                  // spheres inserted since the last rebuild (the dynamic list)
+  int ndyn_start;            // ndyn before the last round's commits (its new spheres follow)
+  unsigned nlost;            // spheres that lost their last survivor in the last round
+  unsigned err;              // bit 0: walk stack overflow, bit 1: dynamic list overflow
+  int ninserted;             // spheres inserted by this call so far
+  // step-query work over the call: spheres evaluated exactly in FP64, spheres
+  // screened in FP32, survivors evaluated exactly, survivors screened
+  unsigned long long work[4];
+};
+
 struct InsertArgs {
-  // spheres: [0, n_static) in the hierarchy, [n_static, *n_total) since the last rebuild
+  // spheres in the hierarchy (sid: provisional index), plus the ones inserted
+  // since the last rebuild (dyn_ids); step t's sphere has provisional index
+  // n0 + t until the call renumbers the inserted spheres consecutively
   const float4* sph;
   const int* sid;
   Tree st;
-  int n_static;
-  D4* sph64;            // every sphere, global index order
+  int n0;
+  const int* dyn_ids;
+  float4* dyn_f4;       // FP32 (x, y, z, value) of the dynamic list's spheres (sign class kept)
+  int* near_list;       // per new sphere of a round: dynamic-list spheres that reach it
+  int* near_cnt;
+  D4* sph64;            // by provisional index
   double* witness64;    // witness point per sphere (inserted spheres)
   int* counts;          // live survivors per sphere
-  int* n_total;         // device counter
-  // survivors: hierarchies with tombstone bits, plus lists added since the rebuild
+  int* maxrem;          // largest step that removed one of the sphere's survivors
+  // survivors: hierarchies with tombstone bits, plus the candidates and
+  // witnesses of the spheres inserted since the rebuild: KS slots per
+  // dynamic-list sphere (slot d * KS + k), a tombstone word each (1: culled
+  // at insertion or covered since)
   const float4* surv[2];
   Tree vt[2];
   uint32_t* tomb[2];
   float4* dsurv[2];
   uint32_t* dtomb[2];
-  unsigned* dcount;        // entries per dynamic list
-  unsigned* dcount_start;  // entries at the start of the current step
-  unsigned dcap;
   const double* U64;
   int K, KS;
   double tol;
@@ -100,25 +136,45 @@ struct InsertArgs {
   const BuildConsts* bc;
   const double* y;
   const double* known;  // nullable: per-point known value (its sign fixes the class)
+  int64_t T;
   double* s_out;
   int64_t* arg_out;
   uint16_t* fl_out;
-  struct StepRec* rec;
-  unsigned* lost;
-  unsigned* err;   // bit 0: walk stack overflow, bit 1: dynamic list overflow
-  unsigned* done;  // blocks of the update kernel that have finished (reset by the last)
+  // the window of pending steps
+  int* slot_t;           // step of each slot, in step order
+  InsSlot* slots;
+  unsigned char* cbuf;   // commit decisions, 2 x window capacity (passes alternate halves)
+  int wcap;              // window capacity
+  int* new_ids;          // provisional indices of the spheres inserted by the round
+  int* lost_list;        // spheres that lost their last survivor in the round
+  int* inserted;            // per step: 1 when it joined the samples
+  unsigned char* codes;     // per step: result code (for the final renumbering of the argmins)
+  int* dyn_ids_w;        // writable view of dyn_ids
+  InsMisc* misc;
 };
 
-struct StepRec {
-  int insert;
-  int pad;
-};
-
-cudaError_t launch_ins_step(const InsertArgs& a, int64_t t, cudaStream_t st);
+// one round of the insertion: speculative queries of the window's nslots
+// steps, then the commit passes and the commit itself (window compaction and
+// refill up to wnext slots); the host reads InsMisc afterwards
+cudaError_t launch_ins_query(const InsertArgs& a, int nslots, cudaStream_t st);
+cudaError_t launch_ins_commit(const InsertArgs& a, int nslots, int passes, int wnext, cudaStream_t st);
+// state update of the spheres the last round inserted (nnew of them)
+// (ndyn_start: spheres of the dynamic list before the round's commits)
+cudaError_t launch_ins_update(const InsertArgs& a, int nnew, int ndyn_start, cudaStream_t st);
 cudaError_t launch_ins_counts(const float4* s0, unsigned n0, const float4* s1, unsigned n1, const D4* sph64, int KS,
                               int* counts, cudaStream_t st);
 cudaError_t launch_ins_compact(const float4* ssurv, const uint32_t* tomb, unsigned ns, const float4* dsurv,
                                const uint32_t* dtomb, unsigned nd, float4* out, unsigned* count, cudaStream_t st);
+// renumbering after the call: newid[n0 + t] = n0 + (inserted steps before t)
+cudaError_t launch_ins_renumber(const InsertArgs& a, const int* newid, D4* sph_out, double* wit_out,
+                                cudaStream_t st);
+cudaError_t launch_ins_remap_survivors(float4* items, unsigned n, const int* newid, int n0, int KS, cudaStream_t st);
+cudaError_t exclusive_scan_i32(void* temp, size_t& bytes, const int* in, int* out, int64_t n,
+                              cudaStream_t st);
+cudaError_t launch_gather_d4(const D4* src, const int* ids, int64_t n, D4* dst, cudaStream_t st);
+cudaError_t launch_remap_sid(int* sid, const int* ids, int64_t n, cudaStream_t st);
+// kernels the insertion file has launched in this process
+unsigned long long insert_launch_count();
 
 struct GradArgs {
   const double* x64;

@@ -37,7 +37,12 @@ class Stats(ctypes.Structure):
         "query_surv_items")] + [(n, ctypes.c_double) for n in (
         "ms_build_total", "ms_build_cull", "ms_query_fast", "ms_query_exact")] + [
         (n, ctypes.c_int64) for n in ("kernel_launches", "sort_calls", "cull_node_tests", "cull_items")] + [
-        ("ms_query_spheres", ctypes.c_double)]
+        ("ms_query_spheres", ctypes.c_double)] + [
+        (n, ctypes.c_int64) for n in ("insert_rounds", "insert_steps", "insert_rebuilds")] + [
+        (n, ctypes.c_double) for n in ("insert_ms_total", "insert_ms_rebuild", "insert_ms_final", "insert_ms_query",
+                                       "insert_ms_commit", "insert_ms_update")] + [
+        (n, ctypes.c_int64) for n in ("insert_slots", "insert_sph_exact", "insert_sph_tested", "insert_surv_exact",
+                                      "insert_surv_tested", "batch_sphere_items", "batch_sphere_node_tests", "batch_surv_items")]
 
 
 class Shape(ctypes.Structure):

@@ -2,6 +2,8 @@
 loop: every step's value (FP64, bitwise), argmin and result word
 (including LOST_WITNESS), the final survivor set, and queries against the
 final state."""
+import functools
+
 import numpy as np
 import pytest
 import torch
@@ -20,12 +22,14 @@ def G():
     return gfs
 
 
-def _compare(G, orc, p, s, tau, y, xq):
+def _compare(G, orc, p, s, tau, y, xq, known=None, clamp_opp=True, stats=None):
     U = orc.icosphere(tau)
-    val, arg, fl, st = orc.insert(p, s, U, y)
-    ctx = G.Context(tau=tau)
+    val, arg, fl, st = orc.insert(p, s, U, y, known=known, clamp_opp=clamp_opp)
+    ctx = G.Context(tau=tau, clamp_opp=clamp_opp)
     ctx.build(torch.from_numpy(p).cuda(), torch.from_numpy(s).cuda())
-    out = ctx.insert(torch.from_numpy(y).cuda())
+    out = ctx.insert(torch.from_numpy(y).cuda(), known=None if known is None else torch.from_numpy(known).cuda())
+    if stats is not None:
+        stats.update(ctx.stats())
     torch.cuda.synchronize()
     gv = out["s64"].cpu().numpy()
     ga = out["argmin"].cpu().numpy()
@@ -37,7 +41,7 @@ def _compare(G, orc, p, s, tau, y, xq):
     assert np.array_equal(surv, st["g"])
     # queries against the final state use the inserted samples and witnesses
     res = ctx.query(torch.from_numpy(xq).cuda())
-    ov, oa, of, _ = orc.query(st["p"], st["s"], (st["g"], st["sph"], st["q"]), xq)
+    ov, oa, of, _ = orc.query(st["p"], st["s"], (st["g"], st["sph"], st["q"]), xq, clamp_opp=clamp_opp)
     assert np.array_equal(res["flags"].cpu().numpy().astype(np.int32) & 0xFFFF, of)
     assert np.array_equal(res["argmin"].cpu().numpy(), oa)
     assert np.array_equal(res["s64"].cpu().numpy(), ov, equal_nan=True)
@@ -104,3 +108,63 @@ def test_insert_known_values_repair(G, orc):
     assert np.array_equal(ctx.survivors().cpu().numpy(), st["g"])
     assert np.any(fl & orc.FLAG_NONCONSERVATIVE) and not np.any(np.isin(fl & 15, [3, 4]))
     ctx.close()
+
+
+@functools.lru_cache(maxsize=1)
+def _csg24_repair(orc):
+    """The 24^3 CSG pseudo-SDF at tau 2: the samples with no surviving
+    candidate are removed, the rest kept."""
+    w = W.csg_pseudo_grid(N=24, tau=2)
+    U = orc.icosphere(w.tau)
+    covered = orc.keep_all(w.p, w.s, U).sum(axis=1) == 0
+    return w, covered
+
+
+def test_insert_csg24_repair_2000_steps(G, orc):
+    """Config-3 style repair on a 24^3 CSG pseudo-SDF grid: 2,000 removed
+    samples re-inserted with known values in index order (neighbours, mostly
+    within each other's reach), step by step against the sequential oracle."""
+    w, covered = _csg24_repair(orc)
+    idx = np.nonzero(covered)[0][:2000]
+    assert idx.size == 2000
+    xq = np.random.default_rng(4).uniform(-1, 1, size=(400, 3))
+    _compare(G, orc, w.p[~covered], w.s[~covered], w.tau, w.p[idx], xq, known=w.s[idx])
+
+
+def test_insert_csg24_repair_scattered_order(G, orc):
+    """The same repair in a seeded random order: points far apart commit
+    together (fewer rounds than steps, out-of-order commits with provisional
+    sphere numbering), with the sequential loop's results step by step."""
+    w, covered = _csg24_repair(orc)
+    idx = np.random.default_rng(8).permutation(np.nonzero(covered)[0])[:2400]
+    xq = np.random.default_rng(6).uniform(-1, 1, size=(400, 3))
+    st = {}
+    _compare(G, orc, w.p[~covered], w.s[~covered], w.tau, w.p[idx], xq, known=w.s[idx], stats=st)
+    assert st["insert_steps"] == idx.size
+    assert st["insert_rounds"] < idx.size // 4, st["insert_rounds"]
+
+
+def test_insert_refinement_parallel_rounds(G, orc):
+    """Refinement with inferred signs at scattered points of a 16^3 union
+    grid, enough steps for rebuilds between rounds; values, argmins (renumbered
+    spheres) and result words against the sequential oracle."""
+    w = W.union_grid(N=16, up=2, tau=1)
+    rng = np.random.default_rng(41)
+    y = rng.uniform(-1, 1, size=(3000, 3))
+    y[2000:2020] = y[1500:1520]                    # repeats: SAMPLE of a renumbered sphere
+    xq = rng.uniform(-1, 1, size=(400, 3))
+    st = {}
+    fl = _compare(G, orc, w.p, w.s, w.tau, y, xq, stats=st)
+    assert st["insert_rounds"] < 1000, st["insert_rounds"]
+    assert np.any((fl[2000:2020] & 15) == 2)
+
+
+def test_insert_lost_witness_without_clamp(G, orc):
+    """Without the opposite clamp a new ball can swallow the last survivors of
+    an opposite sphere: LOST_WITNESS on the step that removes the last one
+    (no value bound, so one step per round)."""
+    w = W.union_grid(N=10, up=2, tau=0)
+    y = np.random.default_rng(5).uniform(-1, 1, size=(800, 3))
+    xq = np.random.default_rng(7).uniform(-1, 1, size=(300, 3))
+    fl = _compare(G, orc, w.p, w.s, w.tau, y, xq, clamp_opp=False)
+    assert np.sum((fl & 0x80) != 0) >= 5
