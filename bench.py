@@ -578,6 +578,15 @@ def extra_batch(count=256, scale=1.0, peaks=None):
     torch.cuda.synchronize()
     t_graph = _ev_time(lambda: g.replay())
     bst = ctx.stats()
+    # the whole batched path (rebuild from the samples + query) as one graph
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g2, stream=st):
+            ctx.batch_rebuild()
+            ctx.batch_query()
+    torch.cuda.synchronize()
+    t_graph_full = _ev_time(lambda: g2.replay(), reps=2)
+    status = ctx.batch_status()
     single = gfs.Context(tau=3)
 
     def one_by_one():
@@ -592,6 +601,9 @@ def extra_batch(count=256, scale=1.0, peaks=None):
                                      8, "(query point, sphere or survivor) distance tests of the batched query",
                                      t_graph, peaks, node_tests_per_launch=bst["batch_sphere_node_tests"]),
             "batched_build_ms": t_build, "batched_query_ms": t_query, "graph_replay_query_ms": t_graph,
+            "graph_replay_build_query_ms": t_graph_full,
+            "graph_queries_per_s_incl_build": M / (t_graph_full / 1e3), "graph_status": status,
+            "cull_tiles_by_size_class": bst["batch_cull_tile"], "query_grid": bst["batch_query_grid"],
             "batched_queries_per_s_incl_build": M / ((t_build + t_query) / 1e3),
             "one_by_one_ms": t_single, "one_by_one_queries_per_s_incl_build": M / (t_single / 1e3),
             "input_generation_s": t_gen}

@@ -324,11 +324,34 @@ typedef struct {
  * candidates, a block per (shape, direction, 128 spheres) item (the library
  * keeps the shape table; the caller keeps the buffers alive until the last
  * gfs_batch_query).  Results per shape are those of gfs_build on that shape
- * alone.  The first build also picks the persistent query's grid size by
- * timing a few candidates (autotuning).
- * Synchronises the stream.  Errors: GFS_ERR_ARG (nshapes < 1 or > 65535, a
+ * alone.  Sizes every buffer (the survivor capacity is grown and the cull
+ * rerun until the counts fit) and uploads the shape table, so that
+ * gfs_batch_rebuild can later repeat the build without the host.  The first
+ * build also picks the persistent query's grid size by timing a few
+ * candidates (autotuning).  Synchronises the stream.  Errors: GFS_ERR_ARG (nshapes < 1 or > 65535, a
  * shape with n < 1), GFS_ERR_TOO_LARGE, GFS_ERR_OOM, GFS_ERR_CUDA. */
 int gfs_batch_build(gfs_ctx* ctx, const gfs_shape* shapes_host, int nshapes);
+
+/* Rebuild of the last gfs_batch_build's shapes from the current contents of
+ * their sample buffers (the same shape table: same pointers and sample and
+ * query counts; new positions and values): the whole build -- inputs copied
+ * and Morton-sorted, sample forest, cull, survivor forests laid out from the
+ * device-side survivor counts, query views -- issues no host
+ * synchronisation, no allocation and no host-to-device copy, so it can be
+ * captured in a CUDA graph together with gfs_batch_query and replayed.
+ * Capacities are the first build's: survivors beyond the survivor capacity
+ * are dropped and set a status bit (read with gfs_batch_status; the
+ * results of that rebuild are then not valid -- call gfs_batch_build again,
+ * which sizes the capacity for the new counts).
+ * Errors: GFS_ERR_STATE (no batch build), GFS_ERR_CUDA. */
+int gfs_batch_rebuild(gfs_ctx* ctx);
+
+/* Status bits of the batched builds since the last call (then cleared):
+ * 1 and 2 -- survivors of the positive / negative class exceeded the
+ * capacity; 4 -- a survivor forest exceeded its node capacity.  0: every
+ * build was complete.  Synchronises the stream.
+ * Errors: GFS_ERR_ARG (null), GFS_ERR_STATE (no batch build), GFS_ERR_CUDA. */
+int gfs_batch_status(gfs_ctx* ctx, unsigned* status_host);
 
 /* Queries of every shape of the last gfs_batch_build in two persistent
  * launches (the sphere pass of every point, then the rest), into each
@@ -394,6 +417,9 @@ typedef struct {
   int64_t batch_sphere_items;  /* (point, sphere) tests of the last gfs_batch_query */
   int64_t batch_sphere_node_tests; /* its child-node bound tests of the sphere pass */
   int64_t batch_surv_items;    /* its (point, survivor) tests */
+  int64_t batch_cull_tile[3];  /* autotuned cull tile (spheres per block) of the batch's shapes with < 32k,
+                                  < 256k and more samples (0: no such shape) */
+  int64_t batch_query_grid;    /* autotuned grid of the persistent batched query (blocks) */
 } gfs_stats_t;
 
 /* Synchronises the stream and fills *out (host). */

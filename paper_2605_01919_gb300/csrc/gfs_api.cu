@@ -151,12 +151,24 @@ struct gfs_ctx {
   bool b_built = false;
   std::vector<gfs_shape> b_shapes;
   std::vector<int64_t> b_off, b_qoff, b_soff[2];
-  std::vector<Tree> b_st, b_vt[2];
+  std::vector<Tree> b_st;
   DevBuf b_desc, b_offd, b_qoffd, b_sph64, b_k64in, b_k64out, b_sph, b_thr, b_sid, b_bits, b_bcs;
   DevBuf b_lo, b_hi, b_na, b_nb, b_nf, b_stdev, b_prefix, b_ctr, b_cnt, b_cviews, b_cw;
   DevBuf b_sraw[2], b_sshape[2], b_ssorted[2], b_vlo[2], b_vhi[2], b_vtdev[2], b_hist;
   DevBuf b_qkin, b_qkout, b_qvin, b_qvout, b_qviews, b_qw, b_qstate;
   std::vector<QueryArgs> b_qv;  // host copies of the per-shape query views
+  DevBuf b_status, b_vprefix[2], b_sodev[2];
+  std::vector<int64_t> b_sph_level_total;  // nodes per level of the sample forest, over all shapes
+  int b_sph_levels = 0, b_surv_levels = 0, b_end_bit = 32;
+  int64_t b_node_cap = 0;
+  // cull tiles per size class (autotuned on the first build): shapes of
+  // class k are views [b_cls_off[k], b_cls_off[k+1]) of b_cviews, with block
+  // prefixes at b_cw + b_cls_off[k] + k
+  int b_tile[3] = {128, 128, 128};
+  bool b_tiles_tuned = false;
+  int b_cls_off[4] = {0, 0, 0, 0};
+  int64_t b_cls_blocks[3] = {0, 0, 0};
+  std::vector<int> b_cls_order;     // shape index of each view, grouped by class
   unsigned b_cap = 0;
   unsigned b_nsurv[2] = {0, 0};
   int64_t b_M = 0, b_qtotal = 0;
@@ -1002,48 +1014,6 @@ int64_t forest_layout(std::vector<Tree>& trees, const std::vector<int64_t>& nite
   return base;
 }
 
-// Build every level of a forest: one launch per level over all shapes.
-int forest_build(gfs_ctx* c, std::vector<Tree>& trees, DevBuf& trees_dev, const float4* items,
-                 const std::vector<int64_t>& item_off, const BuildConsts* bc, int is_sphere, int max_levels) {
-  cudaStream_t st = c->stream;
-  const int ns = int(trees.size());
-  GFS_TRY(ensure(trees_dev, trees.size() * sizeof(Tree)));
-  GFS_CK(cudaMemcpyAsync(trees_dev.p, trees.data(), trees.size() * sizeof(Tree), cudaMemcpyHostToDevice, st));
-  std::vector<int64_t> pre(size_t(ns + 1) * std::max(1, max_levels) + item_off.size());
-  for (int l = 0; l < max_levels; ++l) {
-    int64_t acc = 0;
-    for (int s = 0; s < ns; ++s) {
-      pre[size_t(l) * (ns + 1) + s] = acc;
-      acc += trees[s].nlevels > l ? trees[s].count[l] : 0;
-    }
-    pre[size_t(l) * (ns + 1) + ns] = acc;
-  }
-  const size_t io = size_t(ns + 1) * std::max(1, max_levels);
-  for (size_t s = 0; s < item_off.size(); ++s) pre[io + s] = item_off[s];
-  DevBuf& pd = c->b_prefix;
-  GFS_TRY(ensure(pd, pre.size() * 8));
-  GFS_CK(cudaMemcpyAsync(pd.p, pre.data(), pre.size() * 8, cudaMemcpyHostToDevice, st));
-  for (int l = 0; l < max_levels; ++l) {
-    const int64_t total = pre[size_t(l) * (ns + 1) + ns];
-    GFS_CK(launch_batch_tree_level(trees_dev.as<Tree>(), pd.as<int64_t>() + size_t(l) * (ns + 1), total, ns, l,
-                                   items, pd.as<int64_t>() + io, bc, is_sphere, st));
-  }
-  // the prefix buffer is reused by the next forest: finish before returning
-  GFS_CK(cudaStreamSynchronize(st));
-  return GFS_OK;
-}
-
-int sort64(gfs_ctx* c, unsigned long long* kin, unsigned long long* kout, int* vin, int* vout, int64_t n, int ns) {
-  int end_bit = 32;
-  while ((int64_t(1) << (end_bit - 32)) < ns) ++end_bit;
-  size_t bytes = 0;
-  GFS_CK(sort_pairs64(nullptr, bytes, kin, kout, vin, vout, n, end_bit, c->stream));
-  GFS_TRY(ensure(c->cub_temp, bytes));
-  bytes = c->cub_temp.bytes;
-  GFS_CK(sort_pairs64(c->cub_temp.p, bytes, kin, kout, vin, vout, n, end_bit, c->stream));
-  return GFS_OK;
-}
-
 // time one persistent query launch configuration (both phases) on a prefix
 // of the work
 float time_grid(gfs_ctx* c, int grid, int64_t limit) {
@@ -1088,6 +1058,85 @@ int autotune_grid(gfs_ctx* c, int64_t total) {
 
 }  // namespace
 
+namespace {
+
+// Size class of a shape for the cull tile choice: up to 32k, up to 256k, more.
+int batch_size_class(int64_t n) { return n < 32768 ? 0 : (n < 262144 ? 1 : 2); }
+
+// Levels of the sample forest (static layout uploaded by the first build).
+int batch_sphere_levels(gfs_ctx* c) {
+  const int ns = c->b_ns;
+  const size_t io = size_t(ns + 1) * std::max(1, c->b_sph_levels);
+  for (int l = 0; l < c->b_sph_levels; ++l)
+    GFS_CK(launch_batch_tree_level(c->b_stdev.as<Tree>(), c->b_prefix.as<int64_t>() + size_t(l) * (ns + 1),
+                                   c->b_sph_level_total[size_t(l)], ns, l, c->b_sph.as<float4>(),
+                                   c->b_prefix.as<int64_t>() + io, c->b_bcs.as<BuildConsts>(), 1, c->stream));
+  return GFS_OK;
+}
+
+// The sample part of the device-side build (copy, sort, sample forest).
+int batch_build_device_samples(gfs_ctx* c) {
+  cudaStream_t st = c->stream;
+  const int ns = c->b_ns;
+  const int64_t N = c->b_off[size_t(ns)];
+  GFS_CK(cudaMemsetAsync(c->b_bits.p, 0, size_t(ns) * 8, st));
+  GFS_CK(launch_batch_copy(c->b_desc.as<ShapeDesc>(), c->b_offd.as<int64_t>(), ns, N, c->b_sph64.as<D4>(),
+                           c->b_k64in.as<unsigned long long>(), c->vals_in.as<int>(), c->b_bits.as<unsigned int>(),
+                           c->b_bcs.as<BuildConsts>(), st));
+  size_t bytes = c->cub_temp.bytes;
+  GFS_CK(sort_pairs64(c->cub_temp.p, bytes, c->b_k64in.as<unsigned long long>(), c->b_k64out.as<unsigned long long>(),
+                      c->vals_in.as<int>(), c->vals_out.as<int>(), N, c->b_end_bit, st));
+  GFS_CK(launch_batch_gather(c->b_sph64.as<D4>(), c->vals_out.as<int>(), c->b_offd.as<int64_t>(), ns, N,
+                             c->b_bcs.as<BuildConsts>(), float(c->opt.tol), c->opt.tol, c->b_sph.as<float4>(),
+                             c->b_thr.as<float4>(), c->b_sid.as<int>(), st));
+  return batch_sphere_levels(c);
+}
+
+// The part of the batched build that depends on the sample values only:
+// inputs copied and Morton-sorted, sample forest, cull, survivor forests and
+// query views, all on the device with the sizes and capacities the first
+// build fixed.  No host synchronisation, allocation or host-to-device copy.
+int batch_build_device(gfs_ctx* c, bool cull_only) {
+  cudaStream_t st = c->stream;
+  const int ns = c->b_ns;
+  const int64_t N = c->b_off[size_t(ns)];
+  (void)N;
+  if (!cull_only) GFS_TRY(batch_build_device_samples(c));
+  GFS_CK(cudaMemsetAsync(c->b_cnt.p, 0, sizeof(Counters), st));
+  for (int k = 0; k < 3; ++k)
+    GFS_CK(launch_batch_cull_blocks(c->b_cviews.as<CullArgs>() + c->b_cls_off[k],
+                                    c->b_cw.as<int64_t>() + c->b_cls_off[k] + k, c->b_cls_off[k + 1] - c->b_cls_off[k],
+                                    c->b_cls_blocks[k], c->b_tile[k], st));
+  if (cull_only) return GFS_OK;
+  for (int k = 0; k < 2; ++k)
+    GFS_CK(launch_batch_surv_forest(
+        c->b_sshape[k].as<uint16_t>(), c->b_sraw[k].as<float4>(), c->b_cnt.as<Counters>(), k, c->b_cap, ns,
+        c->b_hist.as<unsigned>(), c->b_k64in.as<unsigned long long>(), c->b_k64out.as<unsigned long long>(),
+        c->vals_in.as<int>(), c->vals_out.as<int>(), c->cub_temp.p, c->cub_temp.bytes, c->b_end_bit,
+        c->b_ssorted[k].as<float4>(), c->b_node_cap, c->b_vlo[k].as<float4>(), c->b_vhi[k].as<float4>(),
+        c->b_vtdev[k].as<Tree>(), c->b_vprefix[k].as<int64_t>(), c->b_surv_levels, c->b_sodev[k].as<int64_t>(),
+        c->b_qviews.as<QueryArgs>(), c->b_status.as<unsigned>(), st));
+  return GFS_OK;
+}
+
+// Host copies of what the device-side build laid out (survivor offsets and
+// the query views): read back whenever a host-driven call needs them (a
+// rebuild replayed from a captured graph changes them without the host).
+int batch_sync_host(gfs_ctx* c) {
+  const int ns = c->b_ns;
+  cudaStream_t st = c->stream;
+  for (int k = 0; k < 2; ++k) {
+    c->b_soff[k].assign(size_t(ns) + 1, 0);
+    GFS_CK(cudaMemcpyAsync(c->b_soff[k].data(), c->b_sodev[k].p, size_t(ns + 1) * 8, cudaMemcpyDeviceToHost, st));
+  }
+  c->b_qv.resize(size_t(ns));
+  GFS_CK(cudaMemcpyAsync(c->b_qv.data(), c->b_qviews.p, size_t(ns) * sizeof(QueryArgs), cudaMemcpyDeviceToHost, st));
+  GFS_CK(cudaStreamSynchronize(st));
+  return GFS_OK;
+}
+
+}  // namespace
+
 int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
   if (!c || !shapes || ns < 1 || ns > 65535) return GFS_ERR_ARG;
   cudaStream_t st = c->stream;
@@ -1108,6 +1157,8 @@ int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
   if (N >= (int64_t(1) << 31)) return GFS_ERR_TOO_LARGE;
   c->b_off = off;
   c->b_qoff = qoff;
+  c->b_end_bit = 32;
+  while ((int64_t(1) << (c->b_end_bit - 32)) < ns) ++c->b_end_bit;
   GFS_TRY(ensure(c->b_desc, size_t(ns) * sizeof(ShapeDesc)));
   GFS_TRY(ensure(c->b_offd, size_t(ns + 1) * 8));
   GFS_TRY(ensure(c->b_qoffd, size_t(ns + 1) * 8));
@@ -1125,16 +1176,16 @@ int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
   GFS_TRY(ensure(c->b_sid, size_t(N) * 4));
   GFS_TRY(ensure(c->b_bits, size_t(ns) * 8));
   GFS_TRY(ensure(c->b_bcs, size_t(ns) * sizeof(BuildConsts)));
-  GFS_CK(cudaMemsetAsync(c->b_bits.p, 0, size_t(ns) * 8, st));
-  GFS_CK(launch_batch_copy(c->b_desc.as<ShapeDesc>(), c->b_offd.as<int64_t>(), ns, N, c->b_sph64.as<D4>(),
-                           c->b_k64in.as<unsigned long long>(), c->vals_in.as<int>(), c->b_bits.as<unsigned int>(),
-                           c->b_bcs.as<BuildConsts>(), st));
-  GFS_TRY(sort64(c, c->b_k64in.as<unsigned long long>(), c->b_k64out.as<unsigned long long>(), c->vals_in.as<int>(),
-                 c->vals_out.as<int>(), N, ns));
-  GFS_CK(launch_batch_gather(c->b_sph64.as<D4>(), c->vals_out.as<int>(), c->b_offd.as<int64_t>(), ns, N,
-                             c->b_bcs.as<BuildConsts>(), float(c->opt.tol), c->opt.tol, c->b_sph.as<float4>(),
-                             c->b_thr.as<float4>(), c->b_sid.as<int>(), st));
-  // sphere forest
+  GFS_TRY(ensure(c->b_hist, size_t(ns) * 4));
+  GFS_TRY(ensure(c->b_status, 16));
+  GFS_CK(cudaMemsetAsync(c->b_status.p, 0, 16, st));
+  {
+    size_t bytes = 0;
+    GFS_CK(sort_pairs64(nullptr, bytes, c->b_k64in.as<unsigned long long>(), c->b_k64out.as<unsigned long long>(),
+                        c->vals_in.as<int>(), c->vals_out.as<int>(), N, c->b_end_bit, st));
+    GFS_TRY(ensure(c->cub_temp, bytes));
+  }
+  // sample forest: static layout (depends on the sample counts only)
   c->b_st.assign(ns, Tree{});
   std::vector<int64_t> nits(ns);
   for (int s = 0; s < ns; ++s) nits[s] = shapes[s].n;
@@ -1147,57 +1198,98 @@ int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
   GFS_TRY(ensure(c->b_nf, size_t(nodes) * sizeof(float4)));
   forest_layout(c->b_st, nits, c->b_lo.as<float4>(), c->b_hi.as<float4>(), c->b_na.as<float4>(), c->b_nb.as<float4>(),
                 c->b_nf.as<float4>(), maxL);
-  std::vector<int64_t> item_off(off.begin(), off.end() - 1);
-  GFS_TRY(forest_build(c, c->b_st, c->b_stdev, c->b_sph.as<float4>(), item_off, c->b_bcs.as<BuildConsts>(), 1, maxL));
-  // culling views and work items (shape, direction, warp of 32 spheres)
+  {
+    GFS_TRY(ensure(c->b_stdev, size_t(ns) * sizeof(Tree)));
+    GFS_CK(cudaMemcpyAsync(c->b_stdev.p, c->b_st.data(), size_t(ns) * sizeof(Tree), cudaMemcpyHostToDevice, st));
+    std::vector<int64_t> pre(size_t(ns + 1) * std::max(1, maxL) + size_t(ns));
+    c->b_sph_level_total.assign(size_t(std::max(1, maxL)), 0);
+    for (int l = 0; l < maxL; ++l) {
+      int64_t acc = 0;
+      for (int s = 0; s < ns; ++s) {
+        pre[size_t(l) * (ns + 1) + s] = acc;
+        acc += c->b_st[s].nlevels > l ? c->b_st[s].count[l] : 0;
+      }
+      pre[size_t(l) * (ns + 1) + ns] = acc;
+      c->b_sph_level_total[size_t(l)] = acc;
+    }
+    const size_t io = size_t(ns + 1) * std::max(1, maxL);
+    for (int s = 0; s < ns; ++s) pre[io + s] = off[s];
+    GFS_TRY(ensure(c->b_prefix, pre.size() * 8));
+    GFS_CK(cudaMemcpyAsync(c->b_prefix.p, pre.data(), pre.size() * 8, cudaMemcpyHostToDevice, st));
+    GFS_CK(cudaStreamSynchronize(st));  // the pageable host arrays above are copied before they go out of scope
+    c->b_sph_levels = maxL;
+  }
+  // culling views and work items (shape, direction, 128 spheres)
   const uint64_t ncand = uint64_t(N) * uint64_t(c->K);
   // survivors are typically < 1% of the candidates; the cull is rerun with
   // room for the counted survivors if this first capacity overflows
   uint64_t cap = std::max<uint64_t>(uint64_t(1) << 16, ncand / 64 + 1024);
   cap = std::min<uint64_t>(cap, 0xfffffff0u);
-  std::vector<CullArgs> cv(ns);
-  std::vector<int64_t> cw(ns + 1);
   GFS_TRY(ensure(c->b_ctr, 16));
   GFS_TRY(ensure(c->b_cnt, sizeof(Counters)));
+  GFS_TRY(ensure(c->b_cviews, size_t(ns) * sizeof(CullArgs)));
+  // the samples (the cull reads them) -- built once here, then the cull is
+  // repeated until its survivor capacity suffices
+  GFS_TRY(batch_build_device_samples(c));
+  // size classes of the shapes (the cull tile is chosen per class)
+  c->b_cls_order.clear();
+  for (int k = 0; k < 3; ++k) {
+    c->b_cls_off[k] = int(c->b_cls_order.size());
+    for (int s = 0; s < ns; ++s)
+      if (batch_size_class(shapes[s].n) == k) c->b_cls_order.push_back(s);
+  }
+  c->b_cls_off[3] = ns;
+  // upload the views and the per-class block prefixes for the current tiles
+  auto upload_cull = [&](unsigned capv) -> int {
+    std::vector<CullArgs> cv(ns);
+    std::vector<int64_t> cw(size_t(ns) + 3);
+    for (int k = 0; k < 3; ++k) {
+      int64_t acc = 0;
+      for (int v = c->b_cls_off[k]; v < c->b_cls_off[k + 1]; ++v) {
+        const int s = c->b_cls_order[size_t(v)];
+        CullArgs& a = cv[size_t(v)];
+        std::memset(&a, 0, sizeof(a));
+        a.sph = c->b_sph.as<float4>() + off[s];
+        a.thr = c->b_thr.as<float4>() + off[s];
+        a.sid = c->b_sid.as<int>() + off[s];
+        a.sph64 = c->b_sph64.as<D4>() + off[s];
+        a.U32 = c->U32.as<float>();
+        a.U64 = c->U64.as<double>();
+        a.K = c->K;
+        a.KS = c->KS;
+        a.tree = c->b_st[s];
+        a.tol32 = float(c->opt.tol);
+        a.tol = c->opt.tol;
+        a.box_cull = c->opt.box_cull;
+        a.bc = c->b_bcs.as<BuildConsts>() + s;
+        a.n = shapes[s].n;
+        a.surv[0] = c->b_sraw[0].as<float4>();
+        a.surv[1] = c->b_sraw[1].as<float4>();
+        a.cap = capv;
+        a.cnt = c->b_cnt.as<Counters>();
+        a.surv_shape[0] = c->b_sshape[0].as<uint16_t>();
+        a.surv_shape[1] = c->b_sshape[1].as<uint16_t>();
+        a.shape = s;
+        cw[size_t(v + k)] = acc;
+        acc += (shapes[s].n + c->b_tile[k] - 1) / c->b_tile[k] * c->K;
+      }
+      cw[size_t(c->b_cls_off[k + 1] + k)] = acc;
+      c->b_cls_blocks[k] = acc;
+    }
+    GFS_CK(cudaMemcpyAsync(c->b_cviews.p, cv.data(), size_t(ns) * sizeof(CullArgs), cudaMemcpyHostToDevice, st));
+    GFS_CK(cudaMemcpyAsync(c->b_cw.p, cw.data(), cw.size() * 8, cudaMemcpyHostToDevice, st));
+    GFS_CK(cudaStreamSynchronize(st));  // pageable sources
+    return GFS_OK;
+  };
+  GFS_TRY(ensure(c->b_cw, size_t(ns + 3) * 8));
   for (int attempt = 0; attempt < 3; ++attempt) {
     c->b_cap = unsigned(cap);
     for (int k = 0; k < 2; ++k) {
       GFS_TRY(ensure(c->b_sraw[k], size_t(cap) * sizeof(float4)));
       GFS_TRY(ensure(c->b_sshape[k], size_t(cap) * 2));
     }
-    cw[0] = 0;
-    for (int s = 0; s < ns; ++s) {
-      CullArgs& a = cv[s];
-      std::memset(&a, 0, sizeof(a));
-      a.sph = c->b_sph.as<float4>() + off[s];
-      a.thr = c->b_thr.as<float4>() + off[s];
-      a.sid = c->b_sid.as<int>() + off[s];
-      a.sph64 = c->b_sph64.as<D4>() + off[s];
-      a.U32 = c->U32.as<float>();
-      a.U64 = c->U64.as<double>();
-      a.K = c->K;
-      a.KS = c->KS;
-      a.tree = c->b_st[s];
-      a.tol32 = float(c->opt.tol);
-      a.tol = c->opt.tol;
-      a.box_cull = c->opt.box_cull;
-      a.bc = c->b_bcs.as<BuildConsts>() + s;
-      a.n = shapes[s].n;
-      a.surv[0] = c->b_sraw[0].as<float4>();
-      a.surv[1] = c->b_sraw[1].as<float4>();
-      a.cap = c->b_cap;
-      a.cnt = c->b_cnt.as<Counters>();
-      a.surv_shape[0] = c->b_sshape[0].as<uint16_t>();
-      a.surv_shape[1] = c->b_sshape[1].as<uint16_t>();
-      a.shape = s;
-      cw[s + 1] = cw[s] + (shapes[s].n + 127) / 128 * c->K;
-    }
-    GFS_TRY(ensure(c->b_cviews, size_t(ns) * sizeof(CullArgs)));
-    GFS_TRY(ensure(c->b_cw, size_t(ns + 1) * 8));
-    GFS_CK(cudaMemcpyAsync(c->b_cviews.p, cv.data(), size_t(ns) * sizeof(CullArgs), cudaMemcpyHostToDevice, st));
-    GFS_CK(cudaMemcpyAsync(c->b_cw.p, cw.data(), size_t(ns + 1) * 8, cudaMemcpyHostToDevice, st));
-    GFS_CK(cudaMemsetAsync(c->b_cnt.p, 0, sizeof(Counters), st));
-    GFS_CK(launch_batch_cull_blocks(c->b_cviews.as<CullArgs>(), c->b_cw.as<int64_t>(), ns, cw[ns], st));
+    GFS_TRY(upload_cull(c->b_cap));
+    GFS_TRY(batch_build_device(c, true));
     Counters hc;
     GFS_CK(cudaMemcpyAsync(&hc, c->b_cnt.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     GFS_CK(cudaStreamSynchronize(st));
@@ -1208,46 +1300,75 @@ int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
     cap = uint64_t(need) + need / 8 + 1024;
     if (attempt == 2) return GFS_ERR_OOM;
   }
-  // survivor forests, one tree per (shape, sign class)
-  if (std::max(c->b_nsurv[0], c->b_nsurv[1]) > kMaxSurvivors) return GFS_ERR_TOO_LARGE;
-  for (int k = 0; k < 2; ++k) {
-    const unsigned nsv = c->b_nsurv[k];
-    GFS_TRY(ensure(c->b_hist, size_t(ns) * 4));
-    GFS_CK(cudaMemsetAsync(c->b_hist.p, 0, size_t(ns) * 4, st));
-    GFS_CK(launch_batch_hist(c->b_sshape[k].as<uint16_t>(), nsv, c->b_hist.as<unsigned>(), st));
-    std::vector<unsigned> cnts(ns);
-    GFS_CK(cudaMemcpyAsync(cnts.data(), c->b_hist.p, size_t(ns) * 4, cudaMemcpyDeviceToHost, st));
-    GFS_CK(cudaStreamSynchronize(st));
-    std::vector<int64_t> so(ns + 1), sn(ns);
-    so[0] = 0;
-    for (int s = 0; s < ns; ++s) {
-      so[s + 1] = so[s] + cnts[s];
-      sn[s] = cnts[s];
+  // cull tile per size class: each class's cull timed with tiles of 64, 128
+  // and 256 spheres (the first build only; the fastest is kept), then the
+  // whole cull rerun with the chosen tiles
+  if (!c->b_tiles_tuned) {
+    cudaEvent_t e0, e1;
+    GFS_CK(cudaEventCreate(&e0));
+    GFS_CK(cudaEventCreate(&e1));
+    for (int k = 0; k < 3; ++k) {
+      if (c->b_cls_off[k + 1] == c->b_cls_off[k]) continue;
+      float best = 0.f;
+      int best_tile = 128;
+      for (int tile : {64, 128, 256}) {
+        c->b_tile[k] = tile;
+        if (upload_cull(c->b_cap) != GFS_OK) break;
+        float ms = 0.f;
+        if (cudaMemsetAsync(c->b_cnt.p, 0, sizeof(Counters), st) != cudaSuccess ||
+            cudaEventRecord(e0, st) != cudaSuccess ||
+            launch_batch_cull_blocks(c->b_cviews.as<CullArgs>() + c->b_cls_off[k],
+                                     c->b_cw.as<int64_t>() + c->b_cls_off[k] + k,
+                                     c->b_cls_off[k + 1] - c->b_cls_off[k], c->b_cls_blocks[k], tile, st) !=
+                cudaSuccess ||
+            cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          cudaGetLastError();
+          break;
+        }
+        if (best == 0.f || ms < best) {
+          best = ms;
+          best_tile = tile;
+        }
+      }
+      c->b_tile[k] = best_tile;
     }
-    c->b_soff[k] = so;
-    GFS_TRY(ensure(c->b_ssorted[k], size_t(nsv) * sizeof(float4) + 16));
-    if (nsv) {
-      GFS_TRY(ensure(c->b_k64in, size_t(nsv) * 8));
-      GFS_TRY(ensure(c->b_k64out, size_t(nsv) * 8));
-      GFS_TRY(ensure(c->vals_in, size_t(nsv) * 4));
-      GFS_TRY(ensure(c->vals_out, size_t(nsv) * 4));
-      GFS_CK(launch_batch_surv_keys(c->b_sraw[k].as<float4>(), c->b_sshape[k].as<uint16_t>(), nsv,
-                                    c->b_k64in.as<unsigned long long>(), c->vals_in.as<int>(), st));
-      GFS_TRY(sort64(c, c->b_k64in.as<unsigned long long>(), c->b_k64out.as<unsigned long long>(),
-                     c->vals_in.as<int>(), c->vals_out.as<int>(), nsv, ns));
-      GFS_CK(launch_batch_gather_points(c->b_sraw[k].as<float4>(), c->vals_out.as<int>(), nsv,
-                                        c->b_ssorted[k].as<float4>(), st));
-    }
-    c->b_vt[k].assign(ns, Tree{});
-    int mL = 0;
-    const int64_t vn = forest_layout(c->b_vt[k], sn, nullptr, nullptr, nullptr, nullptr, nullptr, mL);
-    GFS_TRY(ensure(c->b_vlo[k], size_t(vn) * sizeof(float4) + 16));
-    GFS_TRY(ensure(c->b_vhi[k], size_t(vn) * sizeof(float4) + 16));
-    forest_layout(c->b_vt[k], sn, c->b_vlo[k].as<float4>(), c->b_vhi[k].as<float4>(), nullptr, nullptr, nullptr, mL);
-    std::vector<int64_t> io(so.begin(), so.end() - 1);
-    GFS_TRY(forest_build(c, c->b_vt[k], c->b_vtdev[k], c->b_ssorted[k].as<float4>(), io, nullptr, 0, mL));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->b_tiles_tuned = true;
+    GFS_TRY(upload_cull(c->b_cap));
+    GFS_TRY(batch_build_device(c, true));
   }
-  // query views and work items (shape, 32 points)
+  if (std::max(c->b_nsurv[0], c->b_nsurv[1]) > kMaxSurvivors) return GFS_ERR_TOO_LARGE;
+  // survivor forests: sized for the capacity (the layout is computed on the
+  // device from the counts, so later rebuilds need no host round trip)
+  const unsigned capu = c->b_cap;
+  c->b_node_cap = int64_t(capu) / (kLeaf - 1) + int64_t(ns) * (kMaxLevels + 1) + 16;
+  {
+    Tree T;
+    tree_layout(T, int64_t(capu));
+    c->b_surv_levels = std::max(1, T.nlevels);
+  }
+  GFS_TRY(ensure(c->b_k64in, size_t(std::max<int64_t>(std::max(N, M), capu)) * 8));
+  GFS_TRY(ensure(c->b_k64out, size_t(std::max<int64_t>(std::max(N, M), capu)) * 8));
+  GFS_TRY(ensure(c->vals_in, size_t(std::max<int64_t>(N, capu)) * 4));
+  GFS_TRY(ensure(c->vals_out, size_t(std::max<int64_t>(N, capu)) * 4));
+  for (int k = 0; k < 2; ++k) {
+    GFS_TRY(ensure(c->b_ssorted[k], size_t(capu) * sizeof(float4) + 16));
+    GFS_TRY(ensure(c->b_vlo[k], size_t(c->b_node_cap) * sizeof(float4)));
+    GFS_TRY(ensure(c->b_vhi[k], size_t(c->b_node_cap) * sizeof(float4)));
+    GFS_TRY(ensure(c->b_vtdev[k], size_t(ns) * sizeof(Tree)));
+    GFS_TRY(ensure(c->b_vprefix[k], size_t(c->b_surv_levels) * (ns + 1) * 8));
+    GFS_TRY(ensure(c->b_sodev[k], size_t(ns + 1) * 8));
+  }
+  {
+    size_t bytes = 0;
+    GFS_CK(sort_pairs64(nullptr, bytes, c->b_k64in.as<unsigned long long>(), c->b_k64out.as<unsigned long long>(),
+                        c->vals_in.as<int>(), c->vals_out.as<int>(), int64_t(capu), c->b_end_bit, st));
+    GFS_TRY(ensure(c->cub_temp, bytes));
+  }
+  // query views and work items (shape, 32 points); the survivor pointers and
+  // trees are filled in by the device-side survivor forests
   std::vector<QueryArgs> qv(ns);
   std::vector<int64_t> qw(ns + 1);
   qw[0] = 0;
@@ -1265,10 +1386,6 @@ int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
     a.sph64 = c->b_sph64.as<D4>() + off[s];
     a.st = c->b_st[s];
     a.n = shapes[s].n;
-    for (int k = 0; k < 2; ++k) {
-      a.surv[k] = c->b_ssorted[k].as<float4>() + c->b_soff[k][s];
-      a.vt[k] = c->b_vt[k][s];
-    }
     a.U64 = c->U64.as<double>();
     a.K = c->K;
     a.KS = c->KS;
@@ -1292,7 +1409,6 @@ int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
   GFS_TRY(ensure(c->b_qw, size_t(ns + 1) * 8));
   GFS_CK(cudaMemcpyAsync(c->b_qviews.p, qv.data(), size_t(ns) * sizeof(QueryArgs), cudaMemcpyHostToDevice, st));
   GFS_CK(cudaMemcpyAsync(c->b_qw.p, qw.data(), size_t(ns + 1) * 8, cudaMemcpyHostToDevice, st));
-  c->b_qv = qv;
   c->b_M = M;
   c->b_qtotal = qw[ns];
   // sort scratch for the query order, sized here so gfs_batch_query allocates nothing
@@ -1300,12 +1416,38 @@ int gfs_batch_build(gfs_ctx* c, const gfs_shape* shapes, int ns) {
   GFS_CK(sort_pairs64(nullptr, bytes, c->b_qkin.as<unsigned long long>(), c->b_qkout.as<unsigned long long>(),
                       c->b_qvin.as<int>(), c->b_qvout.as<int>(), M, 64, st));
   GFS_TRY(ensure(c->cub_temp, bytes));
+  GFS_CK(cudaStreamSynchronize(st));  // qv, qw (pageable) copied before they go out of scope
+  // the survivor forests and the views' survivor parts, on the device
+  for (int k = 0; k < 2; ++k)
+    GFS_CK(launch_batch_surv_forest(
+        c->b_sshape[k].as<uint16_t>(), c->b_sraw[k].as<float4>(), c->b_cnt.as<Counters>(), k, c->b_cap, ns,
+        c->b_hist.as<unsigned>(), c->b_k64in.as<unsigned long long>(), c->b_k64out.as<unsigned long long>(),
+        c->vals_in.as<int>(), c->vals_out.as<int>(), c->cub_temp.p, c->cub_temp.bytes, c->b_end_bit,
+        c->b_ssorted[k].as<float4>(), c->b_node_cap, c->b_vlo[k].as<float4>(), c->b_vhi[k].as<float4>(),
+        c->b_vtdev[k].as<Tree>(), c->b_vprefix[k].as<int64_t>(), c->b_surv_levels, c->b_sodev[k].as<int64_t>(),
+        c->b_qviews.as<QueryArgs>(), c->b_status.as<unsigned>(), st));
   c->b_built = true;
+  GFS_TRY(batch_sync_host(c));
   if (c->b_grid_query == 0 && c->b_qtotal > 0) {
     GFS_TRY(gfs_batch_query(c));  // produces the Morton order used while tuning
     c->b_grid_query = autotune_grid(c, c->b_qtotal);
   }
   GFS_CK(cudaStreamSynchronize(st));
+  return GFS_OK;
+}
+
+int gfs_batch_rebuild(gfs_ctx* c) {
+  if (!c) return GFS_ERR_ARG;
+  if (!c->b_built) return GFS_ERR_STATE;
+  return batch_build_device(c, false);
+}
+
+int gfs_batch_status(gfs_ctx* c, unsigned* status_host) {
+  if (!c || !status_host) return GFS_ERR_ARG;
+  if (!c->b_built) return GFS_ERR_STATE;
+  GFS_CK(cudaMemcpyAsync(status_host, c->b_status.p, 4, cudaMemcpyDeviceToHost, c->stream));
+  GFS_CK(cudaMemsetAsync(c->b_status.p, 0, 4, c->stream));
+  GFS_CK(cudaStreamSynchronize(c->stream));
   return GFS_OK;
 }
 
@@ -1337,6 +1479,7 @@ int gfs_batch_query(gfs_ctx* c) {
 int gfs_batch_query_tangent(gfs_ctx* c) {
   if (!c) return GFS_ERR_ARG;
   if (!c->b_built) return GFS_ERR_STATE;
+  GFS_TRY(batch_sync_host(c));
   for (const QueryArgs& a : c->b_qv)
     if (a.m > 0 && (!a.arg_out || !a.fl_out)) return GFS_ERR_ARG;
   // one launch per shape, each over its view (its points in the Morton order
@@ -1350,6 +1493,7 @@ int gfs_batch_survivors(gfs_ctx* c, int shape, int64_t* g_out, int64_t cap, int6
   if (!c || !count_host || cap < 0) return GFS_ERR_ARG;
   if (!c->b_built) return GFS_ERR_STATE;
   if (shape < 0 || shape >= c->b_ns) return GFS_ERR_ARG;
+  GFS_TRY(batch_sync_host(c));
   cudaStream_t st = c->stream;
   const int64_t n0 = c->b_soff[0][shape + 1] - c->b_soff[0][shape];
   const int64_t n1 = c->b_soff[1][shape + 1] - c->b_soff[1][shape];
@@ -1443,6 +1587,8 @@ int gfs_stats(gfs_ctx* c, gfs_stats_t* out) {
     out->batch_sphere_items = int64_t(bc.q_sphere_items);
     out->batch_sphere_node_tests = int64_t(bc.q_sphere_ntests);
     out->batch_surv_items = int64_t(bc.q_surv_items);
+    for (int k = 0; k < 3; ++k) out->batch_cull_tile[k] = c->b_cls_off[k + 1] > c->b_cls_off[k] ? c->b_tile[k] : 0;
+    out->batch_query_grid = c->b_grid_query;
   }
   out->insert_sph_exact = int64_t(c->ins_work[0]);
   out->insert_sph_tested = int64_t(c->ins_work[1]);
@@ -1522,7 +1668,8 @@ void gfs_destroy(gfs_ctx* c) {
                     &c->b_stdev, &c->b_prefix, &c->b_ctr, &c->b_cnt, &c->b_cviews, &c->b_cw, &c->b_sraw[0],
                     &c->b_sraw[1], &c->b_sshape[0], &c->b_sshape[1], &c->b_ssorted[0], &c->b_ssorted[1],
                     &c->b_vlo[0], &c->b_vlo[1], &c->b_vhi[0], &c->b_vhi[1], &c->b_vtdev[0], &c->b_vtdev[1],
-                    &c->b_hist, &c->b_qkin, &c->b_qkout, &c->b_qvin, &c->b_qvout, &c->b_qviews, &c->b_qw, &c->b_qstate};
+                    &c->b_hist, &c->b_qkin, &c->b_qkout, &c->b_qvin, &c->b_qvout, &c->b_qviews, &c->b_qw, &c->b_qstate,
+                    &c->b_status, &c->b_vprefix[0], &c->b_vprefix[1], &c->b_sodev[0], &c->b_sodev[1]};
   for (DevBuf* b : bufs) release(*b);
   delete c;
 }

@@ -140,23 +140,25 @@ __global__ void k_batch_qkeys(const ShapeDesc* __restrict__ d, const int64_t* __
   vals[u] = int(i);
 }
 
-// Cull over all shapes as one flat launch: block b is item b of (shape,
-// direction k, 128 Morton-consecutive spheres), so the candidates left open
-// by the neighbour pre-test are packed into full warps as in the single-shape
-// cull, and the hardware schedules the uneven blocks.
-__global__ void __launch_bounds__(128) k_batch_cull_blocks(const CullArgs* __restrict__ views,
-                                                           const int64_t* __restrict__ bprefix, int ns) {
-  __shared__ uint32_t s_stack[4][kPStack];
-  __shared__ int s_idx[128], s_wcnt[4];
+// Cull over a group of shapes as one flat launch: block b is item b of
+// (shape, direction k, BS Morton-consecutive spheres) -- BS the group's tile,
+// picked by the autotuner --, so the candidates left open by the neighbour
+// pre-test are packed into full warps as in the single-shape cull, and the
+// hardware schedules the uneven blocks.
+template <int BS>
+__global__ void __launch_bounds__(BS) k_batch_cull_blocks(const CullArgs* __restrict__ views,
+                                                          const int64_t* __restrict__ bprefix, int ns) {
+  __shared__ uint32_t s_stack[BS / 32][kPStack];
+  __shared__ int s_idx[BS], s_wcnt[BS / 32];
   WarpStack W{s_stack[threadIdx.x >> 5], 0};
   const int64_t w = blockIdx.x;
   const int s = find_seg(bprefix, ns, w);
   const CullArgs& a = views[s];
   const int64_t local = w - bprefix[s];
-  const int64_t nb128 = (a.n + 127) / 128;
-  const int k = int(local / nb128);
-  const int64_t bl = local - int64_t(k) * nb128;
-  cull_packet<true>(a, bl * 128 + threadIdx.x, k, W, threadIdx.x & 31, s_idx, s_wcnt);
+  const int64_t nbs = (a.n + BS - 1) / BS;
+  const int k = int(local / nbs);
+  const int64_t bl = local - int64_t(k) * nbs;
+  cull_packet<true>(a, bl * BS + threadIdx.x, k, W, threadIdx.x & 31, s_idx, s_wcnt);
 }
 
 // Persistent query over all shapes: work item = (shape, 32 consecutive
@@ -182,7 +184,134 @@ __global__ void __launch_bounds__(128) k_batch_query(const QueryArgs* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// Survivor forests laid out on the device (no host round trip, so a rebuild
+// can be captured in a CUDA graph): the survivor counts of a class are read
+// where the cull left them, capped at the list capacity.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned surv_count(const Counters* cnt, int cls, unsigned cap) {
+  return min(cnt->nsurv[cls], cap);
+}
+
+__global__ void k_batch_hist_dev(const uint16_t* __restrict__ shape, const Counters* __restrict__ cnt, int cls,
+                                 unsigned cap, unsigned* __restrict__ counts) {
+  const unsigned n = surv_count(cnt, cls, cap);
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+    atomicAdd(counts + shape[t], 1u);
+}
+
+// keys of the capacity's slots: live survivors by (shape, Morton code),
+// slots past the count last (so the sorted prefix is the live survivors)
+__global__ void k_batch_surv_keys_dev(const float4* __restrict__ items, const uint16_t* __restrict__ shape,
+                                      const Counters* __restrict__ cnt, int cls, unsigned cap,
+                                      unsigned long long* __restrict__ keys, int* __restrict__ vals) {
+  const unsigned n = surv_count(cnt, cls, cap);
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < cap; t += gridDim.x * blockDim.x) {
+    if (t < n) {
+      const float4 v = items[t];
+      keys[t] = (static_cast<unsigned long long>(shape[t]) << 32) | morton_of(v.x, v.y, v.z);
+    } else {
+      keys[t] = ~0ull;
+    }
+    vals[t] = int(t);
+  }
+}
+
+__global__ void k_batch_gather_points_dev(const float4* __restrict__ src, const int* __restrict__ order,
+                                          const Counters* __restrict__ cnt, int cls, unsigned cap,
+                                          float4* __restrict__ dst) {
+  const unsigned n = surv_count(cnt, cls, cap);
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) dst[t] = src[order[t]];
+}
+
+// The forest of one class from the per-shape counts (one block; thread 0
+// walks the shapes in order): each shape's tree layout (the host's
+// tree_layout, levels of ceil(n / 8^l) nodes until a level has at most 8),
+// its node range in the shared node arrays, the per-level node prefixes the
+// level kernel reads, the shape's survivor offset, and the query views'
+// survivor pointer and tree.  status bit (1 << cls): the capacity
+// overflowed (counts were capped; results are not valid).
+__global__ void k_batch_surv_layout(const unsigned* __restrict__ counts, int ns, const Counters* __restrict__ cnt,
+                                    int cls, unsigned cap, int64_t node_cap, float4* lo, float4* hi,
+                                    const float4* sorted, Tree* __restrict__ trees, int64_t* __restrict__ prefix,
+                                    int nlev, int64_t* __restrict__ soff, QueryArgs* __restrict__ views,
+                                    unsigned* __restrict__ status) {
+  if (threadIdx.x != 0) return;
+  if (cnt->nsurv[cls] > cap) atomicOr(status, 1u << cls);
+  int64_t base = 0, so = 0;
+  for (int l = 0; l < nlev; ++l) prefix[int64_t(l) * (ns + 1)] = 0;
+  for (int s = 0; s < ns; ++s) {
+    Tree T;
+    T.nitems = counts[s];
+    T.nlevels = 0;
+    for (int l = 0; l < kMaxLevels; ++l) T.count[l] = T.offset[l] = 0;
+    if (T.nitems > 0) {
+      int64_t c = (T.nitems + kLeaf - 1) / kLeaf, off = 0;
+      int L = 0;
+      for (;;) {
+        T.count[L] = c;
+        T.offset[L] = off;
+        off += c;
+        ++L;
+        if (c <= kFan || L == kMaxLevels) break;
+        c = (c + kFan - 1) / kFan;
+      }
+      T.nlevels = L;
+    }
+    const int64_t nodes = T.nlevels ? T.offset[T.nlevels - 1] + T.count[T.nlevels - 1] : 0;
+    if (base + nodes > node_cap) {  // cannot happen with the node capacity the build sized
+      atomicOr(status, 4u);
+      T.nlevels = 0;
+      T.nitems = 0;
+    }
+    T.lo = lo + base;
+    T.hi = hi + base;
+    T.na = T.nb = T.nf = nullptr;
+    trees[s] = T;
+    for (int l = 0; l < nlev; ++l) {
+      int64_t* P = prefix + int64_t(l) * (ns + 1);
+      P[s + 1] = P[s] + (l < T.nlevels ? T.count[l] : 0);
+    }
+    soff[s] = so;
+    views[s].surv[cls] = sorted + so;
+    views[s].vt[cls] = T;
+    base += T.nlevels ? nodes : 0;
+    so += T.nitems;
+  }
+  soff[ns] = so;
+}
+
+// ---------------------------------------------------------------------------
 static inline unsigned int nb(int64_t n, int b) { return (unsigned int)((n + b - 1) / b); }
+
+cudaError_t launch_batch_surv_forest(const uint16_t* shape, const float4* raw, const Counters* cnt, int cls,
+                                     unsigned cap, int ns, unsigned* hist, unsigned long long* kin,
+                                     unsigned long long* kout, int* vin, int* vout, void* sort_temp,
+                                     size_t sort_bytes, int end_bit, float4* sorted, int64_t node_cap, float4* lo,
+                                     float4* hi, Tree* trees, int64_t* prefix, int nlev, int64_t* soff,
+                                     QueryArgs* views, unsigned* status, cudaStream_t st) {
+  const unsigned g = cap ? (nb(cap, 256) > 8192 ? 8192 : nb(cap, 256)) : 1;
+  cudaMemsetAsync(hist, 0, size_t(ns) * 4, st);
+  k_batch_hist_dev<<<g, 256, 0, st>>>(shape, cnt, cls, cap, hist);
+  k_batch_surv_layout<<<1, 32, 0, st>>>(hist, ns, cnt, cls, cap, node_cap, lo, hi, sorted, trees, prefix, nlev, soff,
+                                        views, status);
+  if (cap > 0) {
+    k_batch_surv_keys_dev<<<g, 256, 0, st>>>(raw, shape, cnt, cls, cap, kin, vin);
+    size_t bytes = sort_bytes;
+    cudaError_t e = cub::DeviceRadixSort::SortPairs(sort_temp, bytes, kin, kout, vin, vout, int64_t(cap), 0,
+                                                    end_bit, st);
+    if (e != cudaSuccess) return e;
+    k_batch_gather_points_dev<<<g, 256, 0, st>>>(raw, vout, cnt, cls, cap, sorted);
+  }
+  // levels: an upper bound of each level's node count over all shapes sizes
+  // the grid (the kernel reads the exact total from the prefix)
+  int64_t bound = int64_t(cap) / kLeaf + ns + 1;
+  for (int l = 0; l < nlev; ++l) {
+    k_batch_tree_level<<<nb(bound, 128), 128, 0, st>>>(trees, prefix + int64_t(l) * (ns + 1), ns, l, sorted,
+                                                       soff, nullptr, 0);
+    bound = bound / kFan + ns + 1;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_batch_copy(const ShapeDesc* d, const int64_t* off, int ns, int64_t N, D4* sph64,
                               unsigned long long* keys, int* vals, unsigned int* bits, BuildConsts* bc,
@@ -242,11 +371,14 @@ cudaError_t launch_batch_qkeys(const ShapeDesc* d, const int64_t* off, int ns, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_cull_blocks(const CullArgs* views, const int64_t* bprefix, int ns, int64_t nblocks,
+cudaError_t launch_batch_cull_blocks(const CullArgs* views, const int64_t* bprefix, int ns, int64_t nblocks, int tile,
                                      cudaStream_t st) {
   if (nblocks <= 0) return cudaSuccess;
   if (nblocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  k_batch_cull_blocks<<<unsigned(nblocks), 128, 0, st>>>(views, bprefix, ns);
+  if (tile == 64) k_batch_cull_blocks<64><<<unsigned(nblocks), 64, 0, st>>>(views, bprefix, ns);
+  else if (tile == 256) k_batch_cull_blocks<256><<<unsigned(nblocks), 256, 0, st>>>(views, bprefix, ns);
+  else if (tile == 128) k_batch_cull_blocks<128><<<unsigned(nblocks), 128, 0, st>>>(views, bprefix, ns);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

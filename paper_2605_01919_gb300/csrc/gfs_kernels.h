@@ -241,11 +241,22 @@ cudaError_t launch_batch_qkeys(const ShapeDesc* d, const int64_t* off, int ns, i
                                int* vals, cudaStream_t st);
 // phase 1: the sphere pass of every (shape, 32 points) item, phase 2: the rest
 // (reset ctr between the two launches)
-// cull over all shapes, one block per (shape, k, 128 spheres) item: bprefix
-// holds each shape's first item, nblocks the total
-cudaError_t launch_batch_cull_blocks(const CullArgs* views, const int64_t* bprefix, int ns, int64_t nblocks,
+// cull over a group of shapes, one block per (shape, k, tile spheres) item
+// (tile 64, 128 or 256): bprefix holds each shape's first item, nblocks the
+// total
+cudaError_t launch_batch_cull_blocks(const CullArgs* views, const int64_t* bprefix, int ns, int64_t nblocks, int tile,
                                      cudaStream_t st);
 cudaError_t launch_batch_query(const QueryArgs* views, const int64_t* wprefix, int ns, int64_t limit,
                                unsigned long long* ctr, int grid, int phase, cudaStream_t st);
+// the survivor forest of one class laid out and built on the device from the
+// cull's counts (capacity cap survivor slots, node_cap nodes, nlev levels;
+// the query views' survivor pointers and trees are patched; overflow sets a
+// status bit); no host synchronisation
+cudaError_t launch_batch_surv_forest(const uint16_t* shape, const float4* raw, const Counters* cnt, int cls,
+                                     unsigned cap, int ns, unsigned* hist, unsigned long long* kin,
+                                     unsigned long long* kout, int* vin, int* vout, void* sort_temp,
+                                     size_t sort_bytes, int end_bit, float4* sorted, int64_t node_cap, float4* lo,
+                                     float4* hi, Tree* trees, int64_t* prefix, int nlev, int64_t* soff,
+                                     QueryArgs* views, unsigned* status, cudaStream_t st);
 
 }  // namespace gfs

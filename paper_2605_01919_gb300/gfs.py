@@ -42,7 +42,8 @@ class Stats(ctypes.Structure):
         (n, ctypes.c_double) for n in ("insert_ms_total", "insert_ms_rebuild", "insert_ms_final", "insert_ms_query",
                                        "insert_ms_commit", "insert_ms_update")] + [
         (n, ctypes.c_int64) for n in ("insert_slots", "insert_sph_exact", "insert_sph_tested", "insert_surv_exact",
-                                      "insert_surv_tested", "batch_sphere_items", "batch_sphere_node_tests", "batch_surv_items")]
+                                      "insert_surv_tested", "batch_sphere_items", "batch_sphere_node_tests", "batch_surv_items")] + [
+        ("batch_cull_tile", ctypes.c_int64 * 3), ("batch_query_grid", ctypes.c_int64)]
 
 
 class Shape(ctypes.Structure):
@@ -97,6 +98,10 @@ def load(build_if_missing: bool = True):
     L.gfs_batch_build.restype = i32
     L.gfs_batch_query.argtypes = [P]
     L.gfs_batch_query.restype = i32
+    L.gfs_batch_rebuild.argtypes = [P]
+    L.gfs_batch_rebuild.restype = i32
+    L.gfs_batch_status.argtypes = [P, ctypes.POINTER(ctypes.c_uint)]
+    L.gfs_batch_status.restype = i32
     L.gfs_batch_query_tangent.argtypes = [P]
     L.gfs_batch_query_tangent.restype = i32
     L.gfs_batch_survivors.argtypes = [P, i32, P, i64, ctypes.POINTER(i64)]
@@ -385,6 +390,22 @@ class Context:
         self._batch = outs
         return outs
 
+    def batch_rebuild(self):
+        """Repeat the last batch_build from the shapes' current sample values
+        (same tensors, same sizes): no host synchronisation or allocation, so
+        it can be captured in a CUDA graph with batch_query."""
+        self._sync_stream()
+        _check(load().gfs_batch_rebuild(self._h))
+        return self._batch
+
+    def batch_status(self) -> int:
+        """Status bits of the batched builds since the last call (0: complete;
+        1/2: survivor capacity exceeded; 4: node capacity exceeded)."""
+        st = ctypes.c_uint(0)
+        self._sync_stream()
+        _check(load().gfs_batch_status(self._h, ctypes.byref(st)))
+        return st.value
+
     def batch_query(self):
         self._sync_stream()
         _check(load().gfs_batch_query(self._h))
@@ -405,7 +426,7 @@ class Context:
     def stats(self) -> dict:
         st = Stats()
         _check(load().gfs_stats(self._h, ctypes.byref(st)))
-        return {n: getattr(st, n) for n, _ in Stats._fields_}
+        return {n: (list(getattr(st, n)) if n == "batch_cull_tile" else getattr(st, n)) for n, _ in Stats._fields_}
 
 
 class ConsistentSDF(torch.autograd.Function):

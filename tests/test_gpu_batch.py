@@ -87,6 +87,83 @@ def test_batch_query_cuda_graph_replay(G):
     ctx.close()
 
 
+def test_batch_build_and_query_cuda_graph_replay(G):
+    """The whole batched path -- rebuild from the samples and query -- captured
+    in one CUDA graph and replayed with new sample values and query points
+    written into the same buffers: every replay equals a fresh single-shape
+    build and query of that data, bitwise."""
+    tau = 2
+    shapes = _shapes(6, 0.1, tau)
+    tensors = [{"p": torch.from_numpy(w.p).cuda(), "s": torch.from_numpy(w.s).cuda(),
+                "x": torch.from_numpy(x).cuda()} for w, x in shapes]
+    ctx = G.Context(tau=tau)
+    outs = ctx.batch_build(tensors)
+    ctx.batch_query()
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            ctx.batch_rebuild()
+            ctx.batch_query()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(17)
+    single = G.Context(tau=tau)
+    for variant in range(3):
+        # new data in place: values scaled (survivor counts change), points moved
+        for t, (w, x) in zip(tensors, shapes):
+            f = 1.0 + 0.02 * variant
+            t["s"].copy_(torch.from_numpy(w.s * f))
+            t["x"].copy_(torch.from_numpy(np.clip(x + rng.normal(0, 0.01, x.shape), -1, 1)))
+        for o in outs:
+            o["s64"].fill_(7.0)
+            o["argmin"].fill_(-7)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert ctx.batch_status() == 0
+        for o, t in zip(outs, tensors):
+            single.build(t["p"], t["s"])
+            ref = single.query(t["x"])
+            assert torch.equal(o["argmin"], ref["argmin"])
+            assert torch.equal(o["flags"], ref["flags"])
+            assert torch.equal(o["s64"].view(torch.int64), ref["s64"].view(torch.int64))
+        for k, t in enumerate(tensors):
+            single.build(t["p"], t["s"])
+            assert torch.equal(ctx.batch_survivors(k), single.survivors())
+    single.close()
+    ctx.close()
+
+
+def test_batch_rebuild_reports_capacity_overflow(G):
+    """A rebuild whose survivors exceed the first build's capacity sets the
+    status bits instead of writing past the lists; a new gfs_batch_build then
+    sizes for the counts and matches the single-shape path."""
+    rng = np.random.default_rng(9)
+    p = rng.uniform(-0.9, 0.9, size=(6000, 3))
+    s_big = np.full(6000, -0.5)                  # overlapping balls: few survivors
+    s_small = np.full(6000, -1e-3)               # tiny disjoint balls: nearly all survive
+    x = rng.uniform(-1, 1, size=(2000, 3))
+    t = {"p": torch.from_numpy(p).cuda(), "s": torch.from_numpy(s_big).cuda(), "x": torch.from_numpy(x).cuda()}
+    ctx = G.Context(tau=0)
+    ctx.batch_build([t])
+    assert ctx.batch_status() == 0
+    t["s"].copy_(torch.from_numpy(s_small))
+    ctx.batch_rebuild()
+    assert ctx.batch_status() & 2                 # negative class overflowed
+    outs = ctx.batch_build([t])
+    ctx.batch_query()
+    assert ctx.batch_status() == 0
+    single = G.Context(tau=0)
+    single.build(t["p"], t["s"])
+    ref = single.query(t["x"])
+    assert torch.equal(outs[0]["argmin"], ref["argmin"])
+    assert torch.equal(outs[0]["flags"], ref["flags"])
+    single.close()
+    ctx.close()
+
+
 def _lazy_worker(args):
     from oracle import oracle as O
     p, s, tau, x = args
