@@ -37,6 +37,8 @@
  *  - The same-sign tangent points of Def. 1 as extra query candidates
  *    (orc_query_aug, orc_query_aug_lazy) and the point behind each value
  *    (orc_argmin_points).
+ *  - Sec. 3.3 scored value (score_for_radius, interpolate_sdf_to): the
+ *    best-scoring valid grow-to radius (orc_query_scored).
  *
  * Readings where the paper is silent are listed in the design notes; the
  * ones that fix arithmetic are repeated at each function.
@@ -470,6 +472,186 @@ void orc_query_aug(const double* p, const double* s, int64_t n, const int64_t* s
     argmin[t] = R.argmin;
     flags[t] = R.flags;
   }
+}
+
+/* ------------------------------------------------------------------------ */
+/* scored value (Sec. 3.3: score_for_radius, interpolate_sdf_to)            */
+/* ------------------------------------------------------------------------ */
+#define FLAG_SCORE_FALLBACK (1 << 9) /* scored value: no valid candidate, minimum value kept */
+
+/* The paper scores every grow-to point q (with the input sphere i it lies
+ * on) for both signs of the radius |x - q| and returns the best-scoring
+ * value that keeps the samples valid.  Discrete form, with readings:
+ *  - grow-to points: the survivors S_tau (standing in for the intersection
+ *    points U, D) and the near and far tangent points of every sphere
+ *    (x != p_j, |s_j| > 0) that no other shrunk ball covers and, with the
+ *    box cull, that lie in the box (T of Def. 1);
+ *  - validity of the new sample (x, sign * r), Prop. 1 discretely:
+ *      (V1) no ball of the opposite sign is intersected: not
+ *           UB < r - tol, UB the nearest opposite tangent distance (the
+ *           query's OPP_VIOL test);
+ *      (V2) no other sphere with survivors loses all of them: for each
+ *           sphere j != i with survivors, some survivor lies outside the
+ *           new ball shrunk by tol (the cull's coverage predicate); sphere
+ *           i keeps the grow-to point q, on the new sphere;
+ *      (V3) no sphere lies strictly inside the new ball: not
+ *           r > FAR + tol (the query's FAR_VIOL test);
+ *    a sign is possible only where x is not inside a ball of the other
+ *    sign (V1 then fails for every r >= 0);
+ *  - normals_agree (undefined in the paper): the normals the two spheres
+ *    give the surface at q, sign * (x - q) and sign(s_i) * (p_i - q), have
+ *    a positive dot product;
+ *  - max_possible_radius (undefined): any bound above twice every valid
+ *    radius makes the type score dominate; the order is then (type class:
+ *    tangency agreeing 3 > intersection agreeing 2 > intersection
+ *    disagreeing 1 > tangency disagreeing 0; then sign score * r with sign
+ *    score 1 for positive and 2 for negative radii);
+ *  - ties (the paper's sort is unspecified): the lower candidate key
+ *    (survivor id g; tangent points 2^40 + 2j + side), then the negative
+ *    sign;
+ *  - a sample position keeps its sample (SAMPLE), both-sign containment is
+ *    INVALID; with no valid candidate the minimum value of the plain query
+ *    is kept (the paper's fallback to the minimum valid radius) with
+ *    FLAG_SCORE_FALLBACK.
+ * Result codes: SURVIVOR (argmin g) or TANGENT (argmin 2j + side); the value
+ * is sign * r; LB_VIOL is set as in the query. */
+#define SCORE_TKEY ((int64_t)1 << 40)
+
+typedef struct {
+  int cls;     /* type class 0..3 */
+  double sr;   /* sign score * r */
+  int64_t key; /* candidate key */
+  int sign;    /* +1 / -1 */
+  double r;
+} orc_score;
+
+static int score_better(const orc_score* a, const orc_score* b) {
+  if (a->cls != b->cls) return a->cls > b->cls;
+  if (a->sr != b->sr) return a->sr > b->sr;
+  if (a->key != b->key) return a->key < b->key;
+  return a->sign < b->sign;
+}
+
+void orc_query_scored(const double* p, const double* s, int64_t n, const int64_t* sg, const int64_t* ssph,
+                      const double* sq, int64_t ns, double tol, int box_cull, const double* x, int64_t m,
+                      double* value, int64_t* argmin, int32_t* flags) {
+  double* maxd2 = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  for (int64_t t = 0; t < m; ++t) {
+    const double* xq = x + 3 * t;
+    const orc_result R = query_one(p, s, n, sg, ssph, sq, ns, tol, 1, xq, 0);
+    const int code = R.flags & 15;
+    if (code == CODE_SAMPLE || code == CODE_INVALID) {
+      value[t] = R.value;
+      argmin[t] = R.argmin;
+      flags[t] = R.flags;
+      continue;
+    }
+    int sig = 0;
+    classify(p, s, n, tol, xq, &sig);
+    /* bounds: nearest opposite tangent distance per sign, far bound, and the
+     * deepest containment per sign (for LB_VIOL) */
+    double ub[2] = {ORC_INF, ORC_INF}; /* [0]: for a positive value (negative spheres), [1]: negative */
+    double far = ORC_INF, lb[2] = {-ORC_INF, -ORC_INF};
+    for (int64_t j = 0; j < n; ++j) {
+      const double d = sqrt(dist2(xq, p + 3 * j));
+      const double r = fabs(s[j]);
+      if (d + r < far) far = d + r;
+      if (s[j] < 0.0 && d - r < ub[0]) ub[0] = d - r;
+      if (s[j] > 0.0 && d - r < ub[1]) ub[1] = d - r;
+      if (covers(xq, p + 3 * j, s[j], tol)) {
+        if (s[j] > 0.0 && r - d > lb[0]) lb[0] = r - d;
+        if (s[j] < 0.0 && r - d > lb[1]) lb[1] = r - d;
+      }
+    }
+    /* (V2) per sphere, the farthest survivor's squared distance; the two
+     * smallest over spheres with survivors */
+    for (int64_t j = 0; j < n; ++j) maxd2[j] = -1.0;
+    for (int64_t g = 0; g < ns; ++g) {
+      const double d2 = dist2(xq, sq + 3 * g);
+      if (d2 > maxd2[ssph[g]]) maxd2[ssph[g]] = d2;
+    }
+    double m1 = ORC_INF, m2 = ORC_INF;
+    int64_t j1 = -1;
+    for (int64_t j = 0; j < n; ++j) {
+      if (maxd2[j] < 0.0) continue;
+      if (maxd2[j] < m1) {
+        m2 = m1;
+        m1 = maxd2[j];
+        j1 = j;
+      } else if (maxd2[j] < m2) {
+        m2 = maxd2[j];
+      }
+    }
+    orc_score best;
+    best.cls = -1;
+    int have = 0;
+    /* one candidate q on sphere i, of type tan (1) or intersection (0) */
+#define TRY_CANDIDATE(QPTR, I, TAN, KEY)                                                  \
+    do {                                                                                  \
+      const double* q_ = (QPTR);                                                          \
+      const int64_t i_ = (I);                                                             \
+      const double r_ = sqrt(dist2(xq, q_));                                              \
+      const double dn_ = (xq[0] - q_[0]) * (p[3 * i_] - q_[0]) + (xq[1] - q_[1]) * (p[3 * i_ + 1] - q_[1]) + \
+                         (xq[2] - q_[2]) * (p[3 * i_ + 2] - q_[2]);                       \
+      for (int sgi = 0; sgi < 2; ++sgi) {                                                 \
+        const int sign_ = sgi == 0 ? 1 : -1;                                              \
+        if (sig != 0 && sign_ != sig) continue;                                           \
+        if (ub[sgi] < r_ - tol) continue;                           /* V1 */              \
+        if (r_ > far + tol) continue;                               /* V3 */              \
+        if (r_ > tol) {                                             /* V2 */              \
+          const double rt_ = r_ - tol;                                                    \
+          const double eff_ = (i_ == j1) ? m2 : m1;                                       \
+          if (eff_ < rt_ * rt_) continue;                                                 \
+        }                                                                                 \
+        const int agree_ = (double)(sign_ * sgn(s[i_])) * dn_ > 0.0;                     \
+        orc_score c_;                                                                     \
+        c_.cls = (TAN) ? (agree_ ? 3 : 0) : (agree_ ? 2 : 1);                             \
+        c_.sr = sign_ > 0 ? r_ : 2.0 * r_;                                                \
+        c_.key = (KEY);                                                                   \
+        c_.sign = sign_;                                                                  \
+        c_.r = r_;                                                                        \
+        if (!have || score_better(&c_, &best)) {                                          \
+          best = c_;                                                                      \
+          have = 1;                                                                       \
+        }                                                                                 \
+      }                                                                                   \
+    } while (0)
+    for (int64_t g = 0; g < ns; ++g) TRY_CANDIDATE(sq + 3 * g, ssph[g], 0, sg[g]);
+    for (int64_t j = 0; j < n; ++j) {
+      const double r = fabs(s[j]);
+      if (!(r > 0.0)) continue;
+      const double* pj = p + 3 * j;
+      double v[3] = {xq[0] - pj[0], xq[1] - pj[1], xq[2] - pj[2]};
+      const double dv = norm3(v);
+      if (!(dv > 0.0)) continue;
+      for (int side = 0; side < 2; ++side) {
+        const double sgnr = side == 0 ? r : -r;
+        double tp[3];
+        for (int c = 0; c < 3; ++c) tp[c] = pj[c] + sgnr * (v[c] / dv);
+        if (box_cull && !inbox(tp)) continue;
+        int cov = 0;
+        for (int64_t k = 0; k < n && !cov; ++k)
+          if (k != j && covers(tp, p + 3 * k, s[k], tol)) cov = 1;
+        if (cov) continue;
+        TRY_CANDIDATE(tp, j, 1, SCORE_TKEY + 2 * j + side);
+      }
+    }
+#undef TRY_CANDIDATE
+    if (!have) {
+      value[t] = R.value;
+      argmin[t] = R.argmin;
+      flags[t] = R.flags | FLAG_SCORE_FALLBACK;
+      continue;
+    }
+    const int tan = best.key >= SCORE_TKEY;
+    value[t] = best.sign * best.r;
+    argmin[t] = tan ? best.key - SCORE_TKEY : best.key;
+    int fl = tan ? CODE_TANGENT : CODE_SURVIVOR;
+    const double lbv = lb[best.sign > 0 ? 0 : 1];
+    if (best.r < lbv - tol) fl |= FLAG_LB_VIOL;
+    flags[t] = fl;
+  }
+  free(maxd2);
 }
 
 /* Lazy variant for single queries on large inputs: the same result as

@@ -25,6 +25,7 @@ TOL = 1e-6  # App. B: "all other tolerances are 1e-6"
 CODE_SURVIVOR, CODE_OPPOSITE, CODE_SAMPLE, CODE_OUTSIDE, CODE_INVALID, CODE_LOWER, CODE_TANGENT = range(7)
 FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 16, 32, 64, 128
 FLAG_NONCONSERVATIVE = 256
+FLAG_SCORE_FALLBACK = 512
 
 
 def build(force: bool = False) -> str:
@@ -57,6 +58,8 @@ def lib():
         L.orc_collect.restype = i64
         L.orc_query.argtypes = [P, P, i64, P, P, P, i64, f64, i32, P, i64, P, P, P, P]
         L.orc_query_aug.argtypes = [P, P, i64, P, P, P, i64, f64, i32, i32, P, i64, P, P, P]
+        L.orc_query_scored.argtypes = [P, P, i64, P, P, P, i64, f64, i32, P, i64, P, P, P]
+        L.orc_query_scored.restype = None
         L.orc_query.restype = None
         L.orc_query_lazy.argtypes = [P, P, i64, P, i32, f64, i32, i32, P, i64, P, P, P, P]
         L.orc_query_lazy.restype = None
@@ -154,6 +157,25 @@ def query_aug(p, s, surv, x, tol=TOL, clamp_opp=True, box_cull=True):
     if m:
         lib().orc_query_aug(_ptr(p), _ptr(s), s.shape[0], _ptr(g), _ptr(sph), _ptr(q), g.shape[0], tol,
                             int(clamp_opp), int(box_cull), _ptr(x), m, _ptr(val), _ptr(arg), _ptr(fl))
+    return val, arg, fl
+
+
+def query_scored(p, s, surv, x, tol=TOL, box_cull=True):
+    """Sec. 3.3 scored value at every row of x against the survivor list
+    ``surv = (g, sphere, q)``: the best-scoring valid grow-to radius over the
+    survivors and the uncovered tangent points (codes SURVIVOR / TANGENT),
+    SAMPLE / INVALID as in ``query``, and the plain query's result with
+    FLAG_SCORE_FALLBACK where no candidate is valid.  Returns (value,
+    argmin, flags)."""
+    p, s, x = _c(p, np.float64), _c(s, np.float64), _c(x, np.float64)
+    g, sph, q = (_c(surv[0], np.int64), _c(surv[1], np.int64), _c(surv[2], np.float64))
+    m = x.shape[0]
+    val = np.zeros(m, np.float64)
+    arg = np.zeros(m, np.int64)
+    fl = np.zeros(m, np.int32)
+    if m:
+        lib().orc_query_scored(_ptr(p), _ptr(s), s.shape[0], _ptr(g), _ptr(sph), _ptr(q), g.shape[0], tol,
+                               int(box_cull), _ptr(x), m, _ptr(val), _ptr(arg), _ptr(fl))
     return val, arg, fl
 
 

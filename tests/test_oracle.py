@@ -908,3 +908,111 @@ def test_argmin_points_set_the_values(orc, seed):
             else:
                 assert np.all(np.isnan(q[t]))
         assert {orc.CODE_OUTSIDE, orc.CODE_SAMPLE} <= seen and seen & {orc.CODE_SURVIVOR, orc.CODE_OPPOSITE, orc.CODE_TANGENT}
+
+
+# ----------------------------------------------------------------------------
+# scored value (Sec. 3.3): closed forms, hand-worked cases, validity after
+# insertion
+# ----------------------------------------------------------------------------
+
+def _scored(orc, p, s, x, tau=2):
+    U = orc.icosphere(tau)
+    surv = orc.collect(p, s, U, orc.keep_all(p, s, U))
+    return orc.query_scored(p, s, surv, np.atleast_2d(x)), surv, U
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+@pytest.mark.parametrize("xpt", [(0.1, 0.0, 0.0), (0.8, 0.0, 0.0), (0.05, -0.3, 0.2), (-0.6, 0.4, 0.1)])
+def test_scored_single_sphere_is_the_lipschitz_maximum(orc, sign, xpt):
+    """One sample: every value within the Lipschitz bound of it is consistent,
+    and the score prefers tangency points whose normals agree, then the
+    largest radius: the far tangent point, value sign(s) (|x - p| + |s|)."""
+    p = np.array([[0.02, -0.01, 0.03]])
+    s = np.array([sign * 0.5])
+    (v, a, f), _, _ = _scored(orc, p, s, xpt)
+    d = np.linalg.norm(np.asarray(xpt) - p[0])
+    assert f[0] & 15 == orc.CODE_TANGENT and a[0] == 1            # sphere 0, far side
+    assert abs(v[0] - sign * (d + 0.5)) < 1e-15
+
+
+def test_scored_two_spheres_hand_worked(orc):
+    """Two positive spheres A (r 0.2 at 0) and B (r 0.05 at (0.5,0,0)), x at
+    (0.3,0,0) outside both: A's far tangent point (radius 0.5) would strictly
+    enclose B (far bound 0.25); B's far tangent point (radius 0.25) agrees
+    and is valid; the negative radii are capped at 0.1 by the positive
+    spheres (A's near tangent, score 2 * 0.1 < 0.25)."""
+    p = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0]])
+    s = np.array([0.2, 0.05])
+    (v, a, f), _, _ = _scored(orc, p, s, (0.3, 0.0, 0.0))
+    assert f[0] & 15 == orc.CODE_TANGENT and a[0] == 2 * 1 + 1
+    assert abs(v[0] - 0.25) < 1e-15
+
+
+def test_scored_prefers_negative_radii(orc):
+    """x halfway between a positive and a negative sphere (both r 0.1 at
+    distance 0.3): the near tangent points of both agree for one sign each
+    at radius 0.2; the negative one scores 2 * 0.2 and wins."""
+    p = np.array([[-0.3, 0.0, 0.0], [0.3, 0.0, 0.0]])
+    s = np.array([0.1, -0.1])
+    (v, a, f), _, _ = _scored(orc, p, s, (0.0, 0.0, 0.0))
+    assert f[0] & 15 == orc.CODE_TANGENT and a[0] == 0
+    assert abs(v[0] + 0.2) < 1e-15
+
+
+def test_scored_fallback_without_candidates(orc):
+    """A ball larger than the box: its candidates and tangent points all lie
+    outside the box, so no grow-to point exists; the plain query's value (the
+    lower bound) is kept and flagged."""
+    p = np.array([[0.1, 0.05, -0.1]])
+    s = np.array([-3.0])
+    x = np.array([[0.2, 0.1, 0.0]])
+    (v, a, f), surv, _ = _scored(orc, p, s, x, tau=1)
+    v0, a0, f0, _ = orc.query(p, s, surv, x)
+    assert f[0] == f0[0] | orc.FLAG_SCORE_FALLBACK and v[0] == v0[0] and a[0] == a0[0]
+
+
+def test_scored_values_keep_the_samples_valid(orc):
+    """On random valid inputs, each scored sample added to the inputs (and
+    the P build redone from scratch) keeps every other sphere's surviving
+    candidates (some survive), intersects no opposite ball, and its grow-to
+    point lies on its sphere outside every input ball."""
+    rng = np.random.default_rng(41)
+    w = W.sphere_grid(N=6, up=2)
+    U = orc.icosphere(1)
+    K = U.shape[0]
+    keep = orc.keep_all(w.p, w.s, U)
+    surv = orc.collect(w.p, w.s, U, keep)
+    had = keep.sum(axis=1) > 0
+    x = rng.uniform(-0.9, 0.9, size=(25, 3))
+    v, a, f = orc.query_scored(w.p, w.s, surv, x)
+    tested = 0
+    for t in range(x.shape[0]):
+        code = f[t] & 15
+        if code not in (orc.CODE_SURVIVOR, orc.CODE_TANGENT):
+            continue
+        i = a[t] // (K + 1) if code == orc.CODE_SURVIVOR else a[t] // 2
+        p2 = np.vstack([w.p, x[t]])
+        s2 = np.append(w.s, v[t])
+        keep2 = orc.keep_all(p2, s2, U)
+        others = had.copy()
+        others[i] = False
+        assert np.all(keep2[:-1][others].sum(axis=1) > 0), t
+        opp = np.sign(w.s) == -np.sign(v[t])
+        dist = np.linalg.norm(w.p - x[t], axis=1)
+        assert np.all(dist[opp] >= abs(v[t]) + np.abs(w.s[opp]) - 1e-6 - 1e-12)
+        tested += 1
+    assert tested >= 15
+
+
+def test_scored_far_bound_excludes_enclosing_a_covered_sphere(orc):
+    """A small positive sphere C inside the ball of a larger one A has no
+    survivor; x outside both.  A's far tangent point (radius 0.8) would
+    strictly enclose C (far bound 0.55) and is invalid although no survivor
+    is lost; the best valid candidate is A's near tangent point with the
+    negative radius 0.2 (its normals agree; score 2 * 0.2)."""
+    p = np.array([[0.0, 0.0, 0.0], [0.05, 0.0, 0.0]])
+    s = np.array([0.3, 0.1])
+    (v, a, f), surv, _ = _scored(orc, p, s, (0.5, 0.0, 0.0))
+    assert not np.any(surv[1] == 1)                     # C keeps no survivor
+    assert f[0] & 15 == orc.CODE_TANGENT and a[0] == 0
+    assert abs(v[0] + 0.2) < 1e-15
