@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sub-benchmarks of the backward, insertion and batched paths")
     ap.add_argument("--only", choices=["backward", "repair", "insert", "batch", "tangent", "refine_order",
-                                       "exact_coverage", "sphere16"],
+                                       "exact_coverage", "sphere16", "scored"],
                     default=None,
                     help="run one sub-benchmark alone and print its JSON (profiling)")
     ap.add_argument("--insert-steps", type=int, default=8192)
@@ -641,6 +641,41 @@ def extra_tangent(every=256):
             "queries_per_s_with_tangent": m / (t_both / 1e3)}
 
 
+def extra_scored(every=256):
+    """Scored value (Sec. 3.3, gfs_query_scored) on the 64^3 union grid, tau
+    3, at every k-th of its 253^3 points: the plain query, and the query
+    followed by the scored pass; how the results split by code, and how many
+    fall back to the minimum value."""
+    import torch
+    from paper_2605_01919_gb300 import gfs
+    from paper_2605_01919_gb300 import workloads as W
+    w = W.union_grid()
+    x = torch.from_numpy(np.ascontiguousarray(w.make_queries()[::every])).cuda()
+    m = int(x.shape[0])
+    ctx = gfs.Context(tau=w.tau)
+    ctx.build(torch.from_numpy(w.p).cuda(), torch.from_numpy(w.s).cuda())
+    out = {"s": torch.empty(m, dtype=torch.float32, device="cuda"),
+           "s64": torch.empty(m, dtype=torch.float64, device="cuda"),
+           "argmin": torch.empty(m, dtype=torch.int64, device="cuda"),
+           "flags": torch.empty(m, dtype=torch.int16, device="cuda")}
+
+    def plain():
+        ctx.query_into(x, out["s"], out["s64"], out["argmin"], out["flags"])
+
+    def both():
+        plain()
+        ctx.scored_into(x, out["s"], out["s64"], out["argmin"], out["flags"])
+    both()  # the per-sphere survivor lists are sorted on the first call
+    t_plain = _ev_time(plain, reps=2)
+    t_both = _ev_time(both, reps=2)
+    fl = out["flags"].cpu().numpy().astype(np.int32) & 0xFFFF
+    ctx.close()
+    return {"workload": f"union64_tau3_253^3_points_every{every}", "queries": m, "query_ms": t_plain,
+            "query_plus_scored_ms": t_both, "scored_pass_ms": t_both - t_plain,
+            "queries_per_s_scored": m / (t_both / 1e3), "codes": np.bincount(fl & 15, minlength=7).tolist(),
+            "fallbacks": int(np.sum((fl & 0x200) != 0))}
+
+
 def extra_refine_order(N=32):
     """Sec. 4.2 refinement order on the N^3 union grid (tau 3): the centres of
     the cells that may contain the surface are inserted greedily, once in
@@ -894,6 +929,7 @@ def run_gfs(args):
                          ("tangent", lambda: _isolated("tangent", ["--tangent-every", str(args.tangent_every)],
                                                        timeout=150)),
                          ("refine_order", lambda: _isolated("refine_order", timeout=150)),
+                         ("scored", lambda: _isolated("scored", timeout=150)),
                          ("exact_coverage", lambda: _isolated("exact_coverage", timeout=150))):
             t_x = time.perf_counter()
             try:
@@ -921,6 +957,7 @@ if __name__ == "__main__":
               "insert": lambda: extra_insert(a.insert_steps, peaks=pk),
               "batch": lambda: extra_batch(a.batch_shapes, a.batch_scale, peaks=pk),
               "sphere16": lambda: extra_sphere16(pk),
+              "scored": extra_scored,
               "tangent": lambda: extra_tangent(a.tangent_every),
               "refine_order": extra_refine_order,
               "exact_coverage": extra_exact_coverage}[a.only]

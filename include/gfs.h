@@ -78,6 +78,7 @@ extern "C" {
 #define GFS_FLAG_OPP_VIOL 0x40    /* |s| > UB_opp + tol (only possible with clamp_opp = 0) */
 #define GFS_FLAG_LOST_WITNESS 0x80 /* insertion: some sphere lost its last surviving candidate */
 #define GFS_FLAG_NONCONSERVATIVE 0x100 /* insertion with known values: |value| < |known| - tol */
+#define GFS_FLAG_SCORE_FALLBACK 0x200 /* gfs_query_scored: no valid candidate, the minimum value kept */
 
 /* ---- options ------------------------------------------------------------ */
 typedef struct {
@@ -155,6 +156,36 @@ int gfs_query(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, float* s_ou
  * (m >= 2^32), GFS_ERR_OOM, GFS_ERR_CUDA. */
 int gfs_query_tangent(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, float* s_out, double* s64_out,
                       int64_t* argmin_out, uint16_t* flags_out);
+
+/* Scored value of a gfs_query result (Sec. 3.3: score_for_radius,
+ * interpolate_sdf_to): instead of the minimum valid radius, the best-scoring
+ * valid one over the grow-to points -- the survivors (standing in for the
+ * intersection points U, D of Def. 1) and the near and far tangent points of
+ * every sphere that no other shrunk ball covers (with box_cull, inside the
+ * box), each with the sphere i it lies on, for both signs of r = |x - q|.
+ * Order: type class (tangency point whose normals agree > intersection point
+ * that agrees > intersection point that disagrees > tangency point that
+ * disagrees; the normals sign * (x - q) and sign(s_i) * (p_i - q) agree when
+ * their dot product is positive), then sign score * r (1 for positive, 2 for
+ * negative values), then the lower candidate key (survivor id; tangent
+ * points after every survivor), then the negative sign.  Valid: no ball of
+ * the opposite sign intersected (not UB < r - tol), no sphere other than i
+ * loses all its survivors to the new ball shrunk by tol, no sphere strictly
+ * inside it (not r > FAR + tol).  Result codes: SURVIVOR (argmin g) or
+ * TANGENT (argmin 2j + side), value sign * r, LB_VIOL as in gfs_query.  SAMPLE
+ * and INVALID results are kept; where no candidate is valid the query's
+ * result is kept with GFS_FLAG_SCORE_FALLBACK.
+ * x, m: the points of the preceding gfs_query on this context (with
+ * clamp_opp = 1 that result is the minimum valid value the paper falls back
+ * to).  argmin_out, flags_out: that call's outputs (device, required), read
+ * and rewritten; s_out, s64_out: its values (device, nullable), rewritten.
+ * The first call after a build or an insertion sorts the survivor ids into
+ * per-sphere lists (library-owned, synchronises the stream); one thread per
+ * point in Morton order, decisions in FP64.
+ * Errors: GFS_ERR_STATE (no build), GFS_ERR_ARG, GFS_ERR_TOO_LARGE
+ * (m >= 2^32), GFS_ERR_OOM, GFS_ERR_CUDA. */
+int gfs_query_scored(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, float* s_out, double* s64_out,
+                     int64_t* argmin_out, uint16_t* flags_out);
 
 /* The point q* that sets each value of a gfs_query / gfs_query_tangent
  * result (Prop. 2: the nearest valid grow-to point), from its argmin and

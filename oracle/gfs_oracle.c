@@ -517,6 +517,13 @@ void orc_query_aug(const double* p, const double* s, int64_t n, const int64_t* s
  * is sign * r; LB_VIOL is set as in the query. */
 #define SCORE_TKEY ((int64_t)1 << 40)
 
+/* some ball other than j's, shrunk by tol, contains t */
+static int covered_by_other(const double* p, const double* s, int64_t n, double tol, const double* t, int64_t j) {
+  for (int64_t k = 0; k < n; ++k)
+    if (k != j && covers(t, p + 3 * k, s[k], tol)) return 1;
+  return 0;
+}
+
 typedef struct {
   int cls;     /* type class 0..3 */
   double sr;   /* sign score * r */
@@ -585,8 +592,10 @@ void orc_query_scored(const double* p, const double* s, int64_t n, const int64_t
     orc_score best;
     best.cls = -1;
     int have = 0;
-    /* one candidate q on sphere i, of type tan (1) or intersection (0) */
-#define TRY_CANDIDATE(QPTR, I, TAN, KEY)                                                  \
+    /* one candidate q on sphere i, of type tan (1) or intersection (0);
+     * UNCOVERED: whether q keeps out of every other ball, evaluated only for
+     * a candidate that would become the best (the result is the same) */
+#define TRY_CANDIDATE(QPTR, I, TAN, KEY, UNCOVERED)                                       \
     do {                                                                                  \
       const double* q_ = (QPTR);                                                          \
       const int64_t i_ = (I);                                                             \
@@ -610,13 +619,13 @@ void orc_query_scored(const double* p, const double* s, int64_t n, const int64_t
         c_.key = (KEY);                                                                   \
         c_.sign = sign_;                                                                  \
         c_.r = r_;                                                                        \
-        if (!have || score_better(&c_, &best)) {                                          \
+        if ((!have || score_better(&c_, &best)) && (UNCOVERED)) {                         \
           best = c_;                                                                      \
           have = 1;                                                                       \
         }                                                                                 \
       }                                                                                   \
     } while (0)
-    for (int64_t g = 0; g < ns; ++g) TRY_CANDIDATE(sq + 3 * g, ssph[g], 0, sg[g]);
+    for (int64_t g = 0; g < ns; ++g) TRY_CANDIDATE(sq + 3 * g, ssph[g], 0, sg[g], 1);
     for (int64_t j = 0; j < n; ++j) {
       const double r = fabs(s[j]);
       if (!(r > 0.0)) continue;
@@ -629,11 +638,7 @@ void orc_query_scored(const double* p, const double* s, int64_t n, const int64_t
         double tp[3];
         for (int c = 0; c < 3; ++c) tp[c] = pj[c] + sgnr * (v[c] / dv);
         if (box_cull && !inbox(tp)) continue;
-        int cov = 0;
-        for (int64_t k = 0; k < n && !cov; ++k)
-          if (k != j && covers(tp, p + 3 * k, s[k], tol)) cov = 1;
-        if (cov) continue;
-        TRY_CANDIDATE(tp, j, 1, SCORE_TKEY + 2 * j + side);
+        TRY_CANDIDATE(tp, j, 1, SCORE_TKEY + 2 * j + side, !covered_by_other(p, s, n, tol, tp, j));
       }
     }
 #undef TRY_CANDIDATE

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgfs.so")
-SOURCES = ["gfs_kernels.cu", "gfs_insert.cu", "gfs_tangent.cu", "gfs_order.cu", "gfs_exact.cu", "gfs_probe.cu", "gfs_api.cu",
+SOURCES = ["gfs_kernels.cu", "gfs_insert.cu", "gfs_tangent.cu", "gfs_scored.cu", "gfs_order.cu", "gfs_exact.cu", "gfs_probe.cu", "gfs_api.cu",
            "gfs_icosphere.cpp", "gfs_flood.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -15,6 +15,7 @@
 #include "gfs_kernels.h"
 #include "gfs_exact.h"
 #include "gfs_order.h"
+#include "gfs_scored.h"
 #include "gfs_tangent.h"
 
 using namespace gfs;
@@ -142,6 +143,10 @@ struct gfs_ctx {
   DevBuf ins_counts, ins_tomb[2], ins_dsurv[2], ins_dtomb[2], ins_misc;
   DevBuf ins_maxrem, ins_slot_t, ins_slots, ins_cbuf, ins_new, ins_lost, ins_inserted, ins_codes, ins_dyn;
   DevBuf ins_present, ins_scan, ins_cmp, ins_dynf4, ins_near, ins_nearcnt;
+  // per-sphere survivor lists for the scored value (sorted ids + offsets),
+  // valid while csr_state equals state_id (every build or insertion changes it)
+  DevBuf csr_ids, csr_off, scored_status;
+  int64_t state_id = 0, csr_state = -1;
   int64_t ins_rounds = 0, ins_steps = 0, ins_rebuilds = 0, ins_queried = 0;  // of the last insertion call
   double ins_ms_total = 0.0, ins_ms_rebuild = 0.0, ins_ms_final = 0.0;  // host wall time of its phases
   double ins_ms_query = 0.0, ins_ms_commit = 0.0, ins_ms_update = 0.0;  // device time (timing = 1)
@@ -487,6 +492,7 @@ int ensure_side(gfs_ctx* c) {
 }  // namespace
 
 int gfs_build(gfs_ctx* c, const double* p, const double* s, int64_t n) {
+  if (c) ++c->state_id;
   GFS_TRY(build_begin(c, p, s, n));
   return build_finish(c);
 }
@@ -635,6 +641,65 @@ int gfs_query_tangent(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, float
   a.perm = reinterpret_cast<const uint32_t*>(c->qv_out.p);
   GFS_CK(launch_query_tangent(a, c->opt.box_cull, c->stream));
   return GFS_OK;
+}
+
+int gfs_query_scored(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, float* s_out, double* s64_out,
+                     int64_t* argmin_out, uint16_t* flags_out) {
+  if (!c || m < 0 || (m > 0 && (!x || !argmin_out || !flags_out))) return GFS_ERR_ARG;
+  if (!c->built) return GFS_ERR_STATE;
+  if (m >= (int64_t(1) << 32)) return GFS_ERR_TOO_LARGE;
+  if (m == 0) return GFS_OK;
+  cudaStream_t st = c->stream;
+  // per-sphere survivor lists of the current state (built once per state)
+  if (c->csr_state != c->state_id) {
+    const int64_t tot = int64_t(c->nsurv[0]) + c->nsurv[1];
+    DevBuf ids, cnt;
+    GFS_TRY(ensure(ids, size_t(tot) * 4 + 16));
+    GFS_TRY(ensure(cnt, 16));
+    GFS_TRY(ensure(c->csr_ids, size_t(tot) * 4 + 16));
+    GFS_TRY(ensure(c->csr_off, size_t(c->n + 1) * 8));
+    unsigned hc = 0;
+    GFS_CK(cudaMemsetAsync(cnt.p, 0, 4, st));
+    GFS_CK(launch_collect_ids(c->surv_raw[0].as<float4>(), c->nsurv[0], c->surv_raw[1].as<float4>(), c->nsurv[1],
+                              c->sph64.as<D4>(), c->KS, ids.as<uint32_t>(), cnt.as<unsigned int>(), st));
+    GFS_CK(cudaMemcpyAsync(&hc, cnt.p, 4, cudaMemcpyDeviceToHost, st));
+    GFS_CK(cudaStreamSynchronize(st));
+    if (hc > 0) {
+      size_t bytes = 0;
+      GFS_CK(sort_keys_u32(nullptr, bytes, ids.as<uint32_t>(), c->csr_ids.as<uint32_t>(), hc, st));
+      GFS_TRY(cub_ensure(c, bytes));
+      bytes = c->cub_temp.bytes;
+      GFS_CK(sort_keys_u32(c->cub_temp.p, bytes, ids.as<uint32_t>(), c->csr_ids.as<uint32_t>(), hc, st));
+    }
+    GFS_CK(launch_csr_offsets(c->csr_ids.as<uint32_t>(), int64_t(hc), c->n, c->KS, c->csr_off.as<int64_t>(), st));
+    GFS_CK(cudaStreamSynchronize(st));
+    c->csr_state = c->state_id;
+  }
+  QueryArgs a;
+  fill_query_args(c, a);
+  if (x_is_fp32) a.x32 = static_cast<const float*>(x);
+  else a.x64 = static_cast<const double*>(x);
+  a.m = m;
+  a.s_out = s_out;
+  a.s64_out = s64_out;
+  a.arg_out = argmin_out;
+  a.fl_out = flags_out;
+  GFS_TRY(ensure(c->qk_in, size_t(m) * 4));
+  GFS_TRY(ensure(c->qk_out, size_t(m) * 4));
+  GFS_TRY(ensure(c->qv_in, size_t(m) * 4));
+  GFS_TRY(ensure(c->qv_out, size_t(m) * 4));
+  GFS_CK(launch_query_keys(a.x64, a.x32, m, c->qk_in.as<uint32_t>(), c->qv_in.as<int>(), st));
+  GFS_TRY(sort_u32_pairs(c, c->qk_in.as<uint32_t>(), c->qk_out.as<uint32_t>(), c->qv_in.as<int>(),
+                         c->qv_out.as<int>(), m));
+  a.perm = reinterpret_cast<const uint32_t*>(c->qv_out.p);
+  GFS_TRY(ensure(c->scored_status, 16));
+  GFS_CK(cudaMemsetAsync(c->scored_status.p, 0, 4, st));
+  GFS_CK(launch_query_scored(a, c->opt.box_cull, c->csr_ids.as<uint32_t>(), c->csr_off.as<int64_t>(),
+                             c->scored_status.as<unsigned>(), st));
+  unsigned status = 0;
+  GFS_CK(cudaMemcpyAsync(&status, c->scored_status.p, 4, cudaMemcpyDeviceToHost, st));
+  GFS_CK(cudaStreamSynchronize(st));
+  return status ? GFS_ERR_TIMEOUT : GFS_OK;
 }
 
 namespace {
@@ -935,6 +1000,7 @@ int gfs_insert_known(gfs_ctx* c, const double* y, const double* known, int64_t T
   GFS_TRY(build_point_tree(c, 1));
   GFS_CK(cudaStreamSynchronize(st));
   c->ins_ms_final = ms_since(t_final);
+  ++c->state_id;
   for (int k = 0; k < 4; ++k) c->ins_work[k] = hm.work[k];
   c->ins_ms_total = ms_since(t_start);
   return GFS_OK;
@@ -1571,7 +1637,7 @@ int gfs_stats(gfs_ctx* c, gfs_stats_t* out) {
   unsigned long long own = 0, sorts = 0;
   launch_counts(&own, &sorts);
   out->kernel_launches = int64_t(own + tangent_launch_count() + order_launch_count() + exact_launch_count() +
-                                 insert_launch_count());
+                                 insert_launch_count() + scored_launch_count());
   out->insert_rounds = c->ins_rounds;
   out->insert_steps = c->ins_steps;
   out->insert_rebuilds = c->ins_rebuilds;
@@ -1662,7 +1728,8 @@ void gfs_destroy(gfs_ctx* c) {
                     &c->ins_tomb[0], &c->ins_tomb[1], &c->ins_dsurv[0], &c->ins_dsurv[1], &c->ins_dtomb[0],
                     &c->ins_dtomb[1], &c->ins_misc, &c->ins_maxrem, &c->ins_slot_t, &c->ins_slots, &c->ins_cbuf,
                     &c->ins_new, &c->ins_lost, &c->ins_inserted, &c->ins_codes, &c->ins_dyn, &c->ins_present,
-                    &c->ins_scan, &c->ins_cmp, &c->ins_dynf4, &c->ins_near, &c->ins_nearcnt,
+                    &c->ins_scan, &c->ins_cmp, &c->ins_dynf4, &c->ins_near, &c->ins_nearcnt, &c->csr_ids,
+                    &c->csr_off, &c->scored_status,
                     &c->b_desc, &c->b_offd, &c->b_qoffd, &c->b_sph64, &c->b_k64in, &c->b_k64out, &c->b_sph,
                     &c->b_thr, &c->b_sid, &c->b_bits, &c->b_bcs, &c->b_lo, &c->b_hi, &c->b_na, &c->b_nb, &c->b_nf,
                     &c->b_stdev, &c->b_prefix, &c->b_ctr, &c->b_cnt, &c->b_cviews, &c->b_cw, &c->b_sraw[0],

@@ -208,12 +208,12 @@ __device__ inline void sphere_bounds(const QueryArgs& a, double x, double y, dou
 // shrunk by tol, contains t (Sec. 3.1: the open balls; App. B tolerance), or
 // -1.  A ball of the node with centre C and radius bound w can only contain t
 // when |t - C| < w.
-__device__ inline int covered_except(const QueryArgs& a, double tx, double ty, double tz, int skip0, int skip1,
-                                     int skip2) {
+// The walk on a stack of kStack entries that the caller provides.
+__device__ inline int covered_except_on(uint32_t* stack, const QueryArgs& a, double tx, double ty, double tz,
+                                        int skip0, int skip1, int skip2) {
   const float x32 = float(tx), y32 = float(ty), z32 = float(tz), ax = amax3(x32, y32, z32);
   const float ntol = -f_dn(a.tol);  // >= -tol
   const Tree& T = a.st;
-  uint32_t stack[kStack];
   int sp = 0;
   const int top = T.nlevels - 1;
   for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
@@ -287,6 +287,12 @@ __device__ inline int covered_except(const QueryArgs& a, double tx, double ty, d
     }
   }
   return -1;
+}
+
+__device__ inline int covered_except(const QueryArgs& a, double tx, double ty, double tz, int skip0, int skip1,
+                                     int skip2) {
+  uint32_t stack[kStack];
+  return covered_except_on(stack, a, tx, ty, tz, skip0, skip1, skip2);
 }
 
 __device__ __forceinline__ int covered_by_other(const QueryArgs& a, double tx, double ty, double tz, int skip) {

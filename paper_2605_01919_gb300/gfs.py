@@ -16,6 +16,7 @@ from . import build as _build
 
 CODE_SURVIVOR, CODE_OPPOSITE, CODE_SAMPLE, CODE_OUTSIDE, CODE_INVALID, CODE_LOWER, CODE_TANGENT = range(7)
 FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 0x10, 0x20, 0x40, 0x80
+FLAG_SCORE_FALLBACK = 0x200
 
 EXPORTED = ["gfs_default_options", "gfs_create", "gfs_set_stream", "gfs_build", "gfs_query", "gfs_query_tangent",
             "gfs_query_backward", "gfs_query_backward_noalloc", "gfs_insert", "gfs_insert_known", "gfs_survivors", "gfs_batch_build", "gfs_batch_query",
@@ -88,6 +89,8 @@ def load(build_if_missing: bool = True):
     L.gfs_query.restype = i32
     L.gfs_query_tangent.argtypes = [P, P, i32, i64, P, P, P, P]
     L.gfs_query_tangent.restype = i32
+    L.gfs_query_scored.argtypes = [P, P, i32, i64, P, P, P, P]
+    L.gfs_query_scored.restype = i32
     L.gfs_query_backward.argtypes = [P, P, i32, i64, P, P, P, P, P, P, P]
     L.gfs_query_backward.restype = i32
     L.gfs_insert.argtypes = [P, P, i64, P, P, P]
@@ -282,6 +285,19 @@ class Context:
         self._sync_stream()
         _check(load().gfs_query_tangent(self._h, _ptr(x), int(x.dtype == torch.float32), x.shape[0], _ptr(s_out),
                                         _ptr(s64_out), _ptr(argmin_out), _ptr(flags_out)))
+
+    def scored_into(self, x, s_out, s64_out, argmin_out, flags_out):
+        """Sec. 3.3 scored value over a query's outputs, in place."""
+        self._sync_stream()
+        _check(load().gfs_query_scored(self._h, _ptr(x), int(x.dtype == torch.float32), x.shape[0], _ptr(s_out),
+                                       _ptr(s64_out), _ptr(argmin_out), _ptr(flags_out)))
+
+    def query_scored(self, x: torch.Tensor):
+        """The scored value at x (a plain query, then the scored pass)."""
+        x = x.contiguous()
+        out = self.query(x)
+        self.scored_into(x, out["s"], out["s64"], out["argmin"], out["flags"])
+        return out
 
     def backward(self, x, s, argmin, flags, grad_s, want_x=True, want_p=True, want_s=True):
         m = x.shape[0]

@@ -1,6 +1,7 @@
 // Test harness: runs device routines of the library on the CPU over a
 // sphere hierarchy built here: the tangent pass (tangent_one), refining the
-// oracle's plain query results in place, the cell coverage count of the
+// oracle's plain query results in place, the scored value (scored_one, over
+// survivor hierarchies built here too), the cell coverage count of the
 // refinement order (cell_cover_count) and the exact uncovered test per
 // sphere (sphere_uncovered).  The hierarchy has the library's layout (implicit 8-ary
 // tree over sorted items) with bounding balls computed directly in FP64 and
@@ -16,6 +17,7 @@
 
 #include "gfs_exact.cuh"
 #include "gfs_order.cuh"
+#include "gfs_scored.cuh"
 
 using namespace gfs;
 
@@ -212,4 +214,117 @@ extern "C" int points_host(const double* p, const double* s, int64_t n, const do
   for (int64_t q = 0; q < m; ++q)
     tangent::argmin_point(a, x[3 * q], x[3 * q + 1], x[3 * q + 2], flags[q] & 15, argmin[q], out + 3 * q);
   return 0;
+}
+
+namespace {
+
+// A survivor hierarchy in the library's layout: FP32 items (x, y, z, id
+// bits) in Morton order, leaves of kLeaf, boxes over the FP32 positions
+// widened by one ulp.
+struct HostPoints {
+  std::vector<float4> items, lo, hi;
+  Tree T{};
+};
+
+void build_points(const std::vector<float4>& in, HostPoints& H) {
+  const int64_t n = int64_t(in.size());
+  std::vector<int64_t> ord(n);
+  for (int64_t i = 0; i < n; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) {
+    return morton3(in[a].x, in[a].y, in[a].z) < morton3(in[b].x, in[b].y, in[b].z);
+  });
+  H.items.resize(n);
+  for (int64_t i = 0; i < n; ++i) H.items[i] = in[ord[i]];
+  Tree& T = H.T;
+  T = Tree{};
+  T.nitems = n;
+  if (n == 0) return;
+  int64_t cnt = (n + kLeaf - 1) / kLeaf, total = 0;
+  int L = 0;
+  while (true) {
+    T.count[L] = cnt;
+    T.offset[L] = total;
+    total += cnt;
+    ++L;
+    if (cnt <= kFan || L == kMaxLevels) break;
+    cnt = (cnt + kFan - 1) / kFan;
+  }
+  T.nlevels = L;
+  H.lo.resize(total);
+  H.hi.resize(total);
+  int64_t span = kLeaf;
+  for (int l = 0; l < L; ++l, span *= kFan)
+    for (int64_t j = 0; j < T.count[l]; ++j) {
+      const int64_t b = j * span, e = std::min<int64_t>(b + span, n);
+      float4 L4{INFINITY, INFINITY, INFINITY, 0}, H4{-INFINITY, -INFINITY, -INFINITY, 0};
+      for (int64_t t = b; t < e; ++t) {
+        const float4& P = H.items[t];
+        L4 = float4{std::min(L4.x, std::nextafter(P.x, -INFINITY)), std::min(L4.y, std::nextafter(P.y, -INFINITY)),
+                    std::min(L4.z, std::nextafter(P.z, -INFINITY)), 0};
+        H4 = float4{std::max(H4.x, std::nextafter(P.x, INFINITY)), std::max(H4.y, std::nextafter(P.y, INFINITY)),
+                    std::max(H4.z, std::nextafter(P.z, INFINITY)), 0};
+      }
+      H.lo[T.offset[l] + j] = L4;
+      H.hi[T.offset[l] + j] = H4;
+    }
+  T.lo = H.lo.data();
+  T.hi = H.hi.data();
+  T.na = T.nb = T.nf = nullptr;
+}
+
+}  // namespace
+
+// Scored value (scored_one) refining the oracle's plain query results in
+// place; survivors given as the oracle's list (ids g, their spheres, FP64
+// positions).
+extern "C" int scored_host(const double* p, const double* s, int64_t n, const double* U, int K, double tol,
+                           int box_cull, const int64_t* sg, const int64_t* ssph, const double* sq, int64_t ns,
+                           const double* x, int64_t m, double* value, int64_t* argmin, uint16_t* flags,
+                           unsigned order_seed) {
+  HostTree H;
+  if (!build_tree(p, s, n, order_seed, H)) return -1;
+  QueryArgs a = args_for(H, n, tol);
+  a.U64 = U;
+  a.K = K;
+  a.KS = K + 1;
+  a.clamp_opp = 1;
+  a.x64 = x;
+  a.m = m;
+  a.s64_out = value;
+  a.arg_out = argmin;
+  a.fl_out = flags;
+  // survivor lists per class (a zero sample's survivors in both)
+  std::vector<float4> cls[2];
+  for (int64_t g = 0; g < ns; ++g) {
+    const float4 it{float(sq[3 * g]), float(sq[3 * g + 1]), float(sq[3 * g + 2]), __uint_as_float(uint32_t(sg[g]))};
+    const double sv = s[ssph[g]];
+    if (!(sv < 0.0)) cls[0].push_back(it);
+    if (!(sv > 0.0)) cls[1].push_back(it);
+  }
+  HostPoints V[2];
+  for (int k = 0; k < 2; ++k) {
+    build_points(cls[k], V[k]);
+    a.surv[k] = V[k].items.data();
+    a.vt[k] = V[k].T;
+  }
+  // the candidate error bound of the build constants (FP32 vs FP64 survivor
+  // positions), as the library derives it from the data bounds
+  double A = 1.0, R = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    A = std::max(A, std::max(std::fabs(p[3 * i]), std::max(std::fabs(p[3 * i + 1]), std::fabs(p[3 * i + 2]))));
+    R = std::max(R, std::fabs(s[i]));
+  }
+  BuildConsts bc{};
+  bc.eq = float(5.9604645e-8 * (2.0 * A + 2.0 * R + 0.01) * 1.01 + 1e-12);
+  a.bc = &bc;
+  // per-sphere sorted survivor ids
+  std::vector<uint32_t> ids(ns);
+  for (int64_t g = 0; g < ns; ++g) ids[g] = uint32_t(sg[g]);
+  std::sort(ids.begin(), ids.end());
+  std::vector<int64_t> off(n + 1);
+  for (int64_t i = 0; i <= n; ++i)
+    off[i] = std::lower_bound(ids.begin(), ids.end(), uint32_t(uint64_t(i) * uint64_t(K + 1))) - ids.begin();
+  unsigned status = 0;
+  for (int64_t q = 0; q < m; ++q) scored::scored_one(a, box_cull, ids.data(), off.data(), q, &status);
+  return status ? -3 : 0;
 }

@@ -51,6 +51,9 @@ def host(tmp_path_factory):
     L.uncovered_host_lanes.restype = ctypes.c_int
     L.points_host.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int, P, ctypes.c_int64, P, P, P]
     L.points_host.restype = ctypes.c_int
+    L.scored_host.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int, ctypes.c_double, ctypes.c_int, P, P, P,
+                              ctypes.c_int64, P, ctypes.c_int64, P, P, P, ctypes.c_uint]
+    L.scored_host.restype = ctypes.c_int
     return L
 
 
@@ -209,3 +212,43 @@ def test_host_argmin_points(host, orc):
             assert host.points_host(_ptr(p), _ptr(s), p.shape[0], _ptr(U), U.shape[0], _ptr(x), x.shape[0],
                                     _ptr(arg), _ptr(fl16), _ptr(got)) == 0
             assert np.array_equal(got, want, equal_nan=True)
+
+
+def _scored_check(host, orc, p, s, tau, x, box_cull=True, orders=(0, 5)):
+    p, s, x = (np.ascontiguousarray(a, np.float64) for a in (p, s, x))
+    U = orc.icosphere(tau)
+    surv = orc.collect(p, s, U, orc.keep_all(p, s, U, box_cull=box_cull))
+    g, sph, q = (np.ascontiguousarray(surv[0], np.int64), np.ascontiguousarray(surv[1], np.int64),
+                 np.ascontiguousarray(surv[2], np.float64))
+    v0, a0, f0, _ = orc.query(p, s, surv, x)
+    v1, a1, f1 = orc.query_scored(p, s, surv, x, box_cull=box_cull)
+    for order in orders:
+        val, arg, fl = v0.copy(), a0.copy(), f0.astype(np.uint16)
+        assert host.scored_host(_ptr(p), _ptr(s), p.shape[0], _ptr(U), U.shape[0], 1e-6, int(box_cull), _ptr(g),
+                                _ptr(sph), _ptr(q), g.shape[0], _ptr(x), x.shape[0], _ptr(val), _ptr(arg),
+                                _ptr(fl), order) == 0
+        bad = np.nonzero(~((val == v1) | (np.isnan(val) & np.isnan(v1))) | (arg != a1) |
+                         (fl.astype(np.int32) != f1))[0]
+        assert bad.size == 0, (f"order {order}: {bad.size} points differ, first {bad[:5]}: host {val[bad[:3]]} "
+                               f"{arg[bad[:3]]} {fl[bad[:3]]} oracle {v1[bad[:3]]} {a1[bad[:3]]} {f1[bad[:3]]}")
+    return f1
+
+
+def test_host_scored_sphere_grid(host, orc):
+    w = W.sphere_grid(N=8, up=2, tau=2)
+    f = _scored_check(host, orc, w.p, w.s, w.tau, w.make_queries())
+    assert np.sum((f & 15) == orc.CODE_TANGENT) > 50
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (9, 2), (60, 3), (200, 4)])
+def test_host_scored_tiny_random(host, orc, n, seed):
+    p, s = W.tiny_random(n, seed)
+    x = np.random.default_rng(200 + seed).uniform(-1.1, 1.1, size=(200, 3))
+    for tau in (0, 2):
+        for box in (True, False):
+            _scored_check(host, orc, p, s, tau, x, box_cull=box)
+
+
+def test_host_scored_union_grid(host, orc):
+    w = W.union_grid(N=10, up=2, tau=1)
+    _scored_check(host, orc, w.p, w.s, w.tau, w.make_queries())
