@@ -31,6 +31,9 @@
  *  - Prop. 1 (ii) exactly: whether each sphere keeps a point outside every
  *    other ball, from the circle and triple points of Def. 1
  *    (orc_sphere_uncovered).
+ *  - The U and D precomputation of Sec. 4.1: the intersection circles with
+ *    an uncovered point and the uncovered points shared by three spheres
+ *    (orc_uncovered_intersections).
  *  - Sec. 4.2 refinement order: the covered area ratio of grid cells from
  *    regularly spaced sub-points (orc_cell_coverage); the flood-fill order
  *    itself is plain Python in oracle.py.
@@ -1316,6 +1319,81 @@ void orc_sphere_uncovered(const double* p, const double* s, int64_t n, double to
     out[i] = (uint8_t)found;
   }
   free(N);
+}
+
+/* ------------------------------------------------------------------------ */
+/* uncovered intersection circles and points (Def. 1 U and the circles of D; */
+/* the U and D precomputation of Sec. 4.1)                                  */
+/* ------------------------------------------------------------------------ */
+/* Over the spheres S_i = (p_i, |s_i|) with |s_i| > 0:
+ *  circles: the pairs i < j whose spheres cut in a circle C_ij (the
+ *    construction of circle_points) that has a point in no ball but i and j
+ *    shrunk by tol.  The uncovered part of C_ij is closed; if it is not
+ *    empty and not the whole circle, its ends lie where C_ij crosses some
+ *    sphere (p_m, |s_m| - tol), m != i, j.  So the test points are the two
+ *    points of C_ij nearest to and farthest from p_i + (|s_i| + 1) e,
+ *    e = (0.36, 0.48, 0.8), and, for every m with |s_m| - tol > 0, the two
+ *    points shared by S_i, S_j and the sphere (p_m, |s_m| - tol), each tested
+ *    against every ball but i, j and the m it was built from.
+ *  points (U): for every triple i < j < m, the two points shared by S_i, S_j
+ *    and S_m (the trilateration's order: side 0, side 1) that lie in no ball
+ *    but i, j, m shrunk by tol.
+ * Outputs in lexicographic order: circles as (i, j) pairs, points as
+ * (i, j, m, side) quadruples with their coordinates.  Returns the number of
+ * circles; *n_points receives the number of points; entries past the
+ * capacities are counted, not written. */
+int64_t orc_uncovered_intersections(const double* p, const double* s, int64_t n, double tol, int64_t* circles,
+                                    int64_t cap_circles, int64_t* quads, double* pts, int64_t cap_points,
+                                    int64_t* n_points) {
+  const double e_ref[3] = {0.36, 0.48, 0.8};
+  int64_t nc = 0, np = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const double ri = fabs(s[i]);
+    if (!(ri > 0.0)) continue;
+    const double* pi = p + 3 * i;
+    double ref[3];
+    for (int c = 0; c < 3; ++c) ref[c] = pi[c] + (ri + 1.0) * e_ref[c];
+    for (int64_t j = i + 1; j < n; ++j) {
+      const double rj = fabs(s[j]);
+      if (!(rj > 0.0)) continue;
+      const double* pj = p + 3 * j;
+      double q[6];
+      if (circle_points(pi, ri, pj, rj, ref, q) != 2) continue;
+      int found = uncovered_but(p, s, n, tol, q, i, j, -1) || uncovered_but(p, s, n, tol, q + 3, i, j, -1);
+      for (int64_t m = 0; m < n && !found; ++m) {
+        if (m == i || m == j) continue;
+        const double rho = fabs(s[m]) - tol;
+        if (!(rho > 0.0)) continue;
+        if (tri_intersect(pi, ri, pj, rj, p + 3 * m, rho, q) == 2)
+          found = uncovered_but(p, s, n, tol, q, i, j, m) || uncovered_but(p, s, n, tol, q + 3, i, j, m);
+      }
+      if (found) {
+        if (nc < cap_circles) {
+          circles[2 * nc] = i;
+          circles[2 * nc + 1] = j;
+        }
+        ++nc;
+      }
+      for (int64_t m = j + 1; m < n; ++m) {
+        const double rm = fabs(s[m]);
+        if (!(rm > 0.0)) continue;
+        if (tri_intersect(pi, ri, pj, rj, p + 3 * m, rm, q) != 2) continue;
+        for (int side = 0; side < 2; ++side) {
+          if (!uncovered_but(p, s, n, tol, q + 3 * side, i, j, m)) continue;
+          if (np < cap_points) {
+            quads[4 * np] = i;
+            quads[4 * np + 1] = j;
+            quads[4 * np + 2] = m;
+            quads[4 * np + 3] = side;
+            for (int c = 0; c < 3; ++c) pts[3 * np + c] = q[3 * side + c];
+          }
+          ++np;
+        }
+      }
+    }
+  }
+  *n_points = np;
+  return nc;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -77,6 +77,8 @@ def lib():
         L.orc_argmin_points.restype = None
         L.orc_sphere_uncovered.argtypes = [P, P, i64, f64, P]
         L.orc_sphere_uncovered.restype = None
+        L.orc_uncovered_intersections.argtypes = [P, P, i64, f64, P, i64, P, P, i64, P]
+        L.orc_uncovered_intersections.restype = i64
         L.orc_cell_coverage.argtypes = [P, P, i64, f64, P, i64, P, f64, i32, P]
         L.orc_cell_coverage.restype = None
         _lib = L
@@ -329,6 +331,25 @@ def sphere_uncovered(p, s, tol=TOL):
     if s.shape[0]:
         lib().orc_sphere_uncovered(_ptr(p), _ptr(s), s.shape[0], tol, _ptr(out))
     return out
+
+
+def uncovered_intersections(p, s, tol=TOL):
+    """Sec. 4.1 U and D precomputation (Def. 1): the pairs i < j whose
+    intersection circle has a point in no other ball shrunk by tol, (c, 2)
+    int64; the uncovered points shared by three spheres, (u, 4) int64
+    (i, j, m, side) and (u, 3) float64 positions; lexicographic order."""
+    p, s = _c(p, np.float64), _c(s, np.float64)
+    cap_c, cap_p = 1024, 1024
+    while True:
+        circ = np.zeros((cap_c, 2), np.int64)
+        quads = np.zeros((cap_p, 4), np.int64)
+        pts = np.zeros((cap_p, 3), np.float64)
+        npt = ctypes.c_int64(0)
+        nc = lib().orc_uncovered_intersections(_ptr(p), _ptr(s), s.shape[0], tol, _ptr(circ), cap_c, _ptr(quads),
+                                               _ptr(pts), cap_p, ctypes.byref(npt))
+        if nc <= cap_c and npt.value <= cap_p:
+            return circ[:nc], quads[:npt.value], pts[:npt.value]
+        cap_c, cap_p = max(cap_c, int(nc)), max(cap_p, int(npt.value))
 
 
 def argmin_points(p, s, U, x, argmin, flags):

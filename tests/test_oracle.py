@@ -830,6 +830,109 @@ def test_sphere_uncovered_octahedral_caps(orc, rho, covered):
     assert orc.sphere_uncovered(p, s, tol=0.0)[0] == (0 if covered else 1)
 
 
+# ----------------------------------------------------------------------------
+# uncovered intersection circles and points (Def. 1 U, D; Sec. 4.1)
+# ----------------------------------------------------------------------------
+
+def test_uncovered_intersections_three_spheres(orc):
+    """Three unit spheres centred on an equilateral triangle of side a = 1:
+    three circles, and two points shared by all three at the centroid
+    +- sqrt(1 - a^2/3) along the normal; a fourth ball around the upper point
+    covers it and leaves the lower one."""
+    h = np.sqrt(3) / 2
+    p = np.array([[0.0, 0, 0], [1.0, 0, 0], [0.5, h, 0]])
+    s = np.ones(3)
+    circ, quads, pts = orc.uncovered_intersections(p, s, tol=0.0)
+    assert circ.tolist() == [[0, 1], [0, 2], [1, 2]]
+    assert quads.tolist() == [[0, 1, 2, 0], [0, 1, 2, 1]]
+    z = np.sqrt(1 - 1 / 3)
+    centroid = np.array([0.5, h / 3, 0.0])
+    got = sorted(pts.tolist(), key=lambda q: q[2])
+    assert np.allclose(got, [centroid - [0, 0, z], centroid + [0, 0, z]], atol=1e-15)
+    p4 = np.concatenate([p, [[0.5, h / 3, 1.3]]])
+    s4 = np.array([1.0, 1.0, 1.0, 0.6])
+    circ, quads, pts = orc.uncovered_intersections(p4, s4, tol=1e-6)
+    assert [0, 1] in circ.tolist() and [0, 2] in circ.tolist() and [1, 2] in circ.tolist()
+    own = [k for k, q in enumerate(quads.tolist()) if q[:3] == [0, 1, 2]]
+    assert len(own) == 1 and pts[own[0], 2] < 0 and abs(pts[own[0], 2] + z) < 1e-15
+
+
+@pytest.mark.parametrize("rho,covered", [(0.93, True), (0.91, False), (0.9194, False), (0.9195, True)])
+def test_uncovered_intersections_octahedral(orc, rho, covered):
+    """The unit sphere (index 0) with six balls of radius rho at +-e_x,
+    +-e_y, +-e_z (tol 0).  The circle with ball e_a is at cos t = c =
+    1 - rho^2/2 from the axis; the points it shares with an adjacent ball e_b
+    are c e_a + c e_b +- w e_c, w = sqrt(1 - 2c^2), and the third ball e_c
+    covers the one on its side exactly when w > c, i.e. rho >
+    sqrt(2 - 2/sqrt 3), the threshold at which the caps cover the sphere.
+    Below it: all six circles of sphere 0 and the 24 points (12 adjacent
+    pairs, two each) are uncovered; above it: none."""
+    e = np.eye(3)
+    p = np.concatenate([np.zeros((1, 3)), e, -e])
+    s = np.array([1.0] + [rho] * 6)
+    circ, quads, pts = orc.uncovered_intersections(p, s, tol=0.0)
+    mine_c = [c for c in circ.tolist() if c[0] == 0]
+    mine_q = [k for k, q in enumerate(quads.tolist()) if q[0] == 0]
+    if covered:
+        assert mine_c == [] and mine_q == []
+        return
+    assert mine_c == [[0, k] for k in range(1, 7)]
+    assert len(mine_q) == 24
+    c = 1 - rho ** 2 / 2
+    w = np.sqrt(1 - 2 * c * c)
+    for k in mine_q:
+        a = np.sort(np.abs(pts[k]))
+        assert np.allclose(a, [w, c, c], atol=1e-14)
+        assert abs(np.linalg.norm(pts[k]) - 1) < 1e-14
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_uncovered_intersections_properties(orc, seed):
+    """Random inputs (tol 0): every reported point lies on its three spheres
+    and in no other ball; no circle or point involves a sphere that the
+    other balls cover entirely (Prop. 1 (ii) test); a circle on which one of
+    720 sampled points lies clear of every other ball is reported."""
+    rng = np.random.default_rng(40 + seed)
+    n = 24
+    p = rng.uniform(-0.5, 0.5, size=(n, 3))
+    s = rng.uniform(0.15, 0.45, size=n) * rng.choice([-1, 1], size=n)
+    circ, quads, pts = orc.uncovered_intersections(p, s, tol=0.0)
+    r = np.abs(s)
+    for (i, j, m, _), q in zip(quads, pts):
+        for k in (i, j, m):
+            assert abs(np.linalg.norm(q - p[k]) - r[k]) < 1e-12
+        d = np.linalg.norm(p - q, axis=1)
+        inside = d < r
+        inside[[i, j, m]] = False
+        assert not inside.any()
+    unc = orc.sphere_uncovered(p, s, tol=0.0)
+    involved = set(circ.ravel().tolist()) | set(quads[:, :3].ravel().tolist())
+    assert all(unc[k] == 1 for k in involved)
+    reported = set(map(tuple, circ.tolist()))
+    phi = np.linspace(0, 2 * np.pi, 720, endpoint=False)
+    for i in range(n):
+        for j in range(i + 1, n):
+            dv = p[j] - p[i]
+            d = np.linalg.norm(dv)
+            if not (abs(r[i] - r[j]) < d < r[i] + r[j]):
+                continue
+            mu = dv / d
+            a = (d * d + r[i] ** 2 - r[j] ** 2) / (2 * d)
+            rad = np.sqrt(r[i] ** 2 - a * a)
+            u = np.cross(mu, [1.0, 0, 0] if abs(mu[0]) < 0.9 else [0, 1.0, 0])
+            u /= np.linalg.norm(u)
+            v = np.cross(mu, u)
+            q = p[i] + a * mu + rad * (np.outer(np.cos(phi), u) + np.outer(np.sin(phi), v))
+            dd = np.linalg.norm(q[:, None, :] - p[None, :, :], axis=2)
+            cov = dd < r[None, :]
+            cov[:, [i, j]] = False
+            free = ~cov.any(axis=1)
+            # a sampled point clear of every ball by a margin decides
+            margin = (dd - r[None, :]).min(axis=1, initial=np.inf, where=~np.isin(np.arange(n), [i, j])[None, :])
+            if np.any(free & (margin > 1e-9)):
+                assert (i, j) in reported, (i, j)
+
+
 def test_sphere_uncovered_simple_cases(orc):
     # alone; inside a larger ball (either sign); two overlapping equal balls
     assert list(orc.sphere_uncovered(np.zeros((1, 3)), np.array([0.3]))) == [1]
