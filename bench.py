@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--tangent-every", type=int, default=256,
                     help="tangent sub-benchmark: use every k-th of the 253^3 points (the pass is FP64, one "
                          "thread per point)")
+    ap.add_argument("--scored-every", type=int, default=256,
+                    help="scored sub-benchmark: use every k-th of the 253^3 points")
     ap.add_argument("--query-subsample", type=int, default=1,
                     help="use every k-th query point (small cases for profiler captures)")
     return ap.parse_args()
@@ -453,6 +455,9 @@ def _insert_roofline(st, peaks):
 
 
 def _repair_setup():
+    """Sec. 6 repair set-up on the 128^3 CSG pseudo-SDF: build on all samples,
+    decide each sphere's exact coverage (Prop. 1 (ii)), remove the covered
+    ones (undecided spheres stay), rebuild on the rest."""
     import torch
     from paper_2605_01919_gb300 import gfs
     from paper_2605_01919_gb300 import workloads as W
@@ -462,26 +467,33 @@ def _repair_setup():
     ctx.build(p, s)
     surv = ctx.survivors().cpu().numpy()
     cnt = np.bincount(surv // (ctx.K + 1), minlength=w.n)
-    removed = np.nonzero(cnt == 0)[0]
-    kept = torch.from_numpy(cnt > 0).cuda()
-    return w, ctx, removed, p[kept].contiguous(), s[kept].contiguous()
+    cov = {}
+    cov["ms"] = _ev_time(lambda: cov.__setitem__("out", ctx.sphere_uncovered()), reps=1)
+    out = cov["out"].cpu().numpy()
+    removed = np.nonzero(out == 0)[0]
+    info = {"exact_covered": int(removed.size), "exact_uncovered": int(np.sum(out == 1)),
+            "undecided": int(np.sum(out == 2)), "no_survivor_at_tau": int(np.sum(cnt == 0)),
+            "covered_with_survivor": int(np.sum((out == 0) & (cnt > 0))), "exact_coverage_ms": cov["ms"]}
+    kept = torch.from_numpy(out != 0).cuda()
+    return w, ctx, removed, p[kept].contiguous(), s[kept].contiguous(), info
 
 
 def extra_repair(T=1 << 20, T_index=8192, peaks=None):
     """Repair of the 128^3 CSG pseudo-SDF (tau 3, Sec. 6): build on all
-    samples; the samples left with no surviving candidate are removed; rebuild
-    on the rest; re-insert T removed samples with their own values known
-    (their signs fix the classes, NONCONSERVATIVE counts values below them)
-    by the greedy loop.  The paper assigns the repaired values in parallel and
-    fixes no order; the sequential loop needs one: a seeded permutation of the
-    removed samples (consecutive points far apart, so the rounds commit many
-    steps), and for comparison the first T_index in index order (neighbours,
-    mostly within each other's reach)."""
+    samples; the samples whose spheres are exactly covered by the other balls
+    (gfs_sphere_uncovered) are removed; rebuild on the rest; re-insert T
+    removed samples with their own values known (their signs fix the classes,
+    NONCONSERVATIVE counts values below them) by the greedy loop.  The paper
+    assigns the repaired values in parallel and fixes no order; the
+    sequential loop needs one: a seeded permutation of the removed samples
+    (consecutive points far apart, so the rounds commit many steps), and for
+    comparison the first T_index in index order (neighbours, mostly within
+    each other's reach)."""
     import torch
-    w, ctx, removed, p2, s2 = _repair_setup()
+    w, ctx, removed, p2, s2, info = _repair_setup()
     t_build = _ev_time(lambda: ctx.build(p2, s2), reps=1)
     res = {"workload": "csg128_tau3_repair_known_values", "samples": int(w.n), "removed": int(removed.size),
-           "rebuild_ms": t_build}
+           "removal": info, "rebuild_ms": t_build}
     for name, sel in (("scattered", np.random.default_rng(3001).permutation(removed)[:T]),
                       ("index_order", removed[:T_index])):
         ctx.build(p2, s2)
@@ -676,8 +688,9 @@ def extra_scored(every=256):
             "fallbacks": int(np.sum((fl & 0x200) != 0))}
 
 
-def extra_refine_order(N=32):
-    """Sec. 4.2 refinement order on the N^3 union grid (tau 3): the centres of
+def extra_refine_order(N=64):
+    """Sec. 4.2 refinement order on the N^3 union grid (tau 3; N = 64 is the
+    headline workload's sample grid): the centres of
     the cells that may contain the surface are inserted greedily, once in
     flood-fill order (covered counts of 8^3 points per cell from
     gfs_cell_coverage, order from gfs_flood_order) and once in raster order;
@@ -730,24 +743,40 @@ def extra_refine_order(N=32):
 
 def extra_exact_coverage():
     """Exact coverage of each sample sphere (gfs_sphere_uncovered, Prop. 1
-    (ii)) on the 12^3 sphere grid (exact SDF samples: all keep an uncovered
-    point) and on the 10^3 sphere grid with every value scaled by 1.2
-    (covered spheres, whose test runs through all circle and triple
-    points)."""
+    (ii)): the 12^3 sphere grid (exact SDF samples: all keep an uncovered
+    point), the 10^3 sphere grid with every value scaled by 1.2 (covered
+    spheres), and the 64^3 CSG pseudo-SDF (most spheres covered, thousands of
+    balls meeting a deep sphere); spheres per second and the split."""
     import torch
     from paper_2605_01919_gb300 import gfs
     from paper_2605_01919_gb300 import workloads as W
     res = {}
-    for name, N, f in (("sphere12_exact_sdf", 12, 1.0), ("sphere10_inflated_1.2", 10, 1.2)):
-        w = W.sphere_grid(N=N, up=2, tau=2)
+    cases = [("sphere12_exact_sdf", W.sphere_grid(N=12, up=2, tau=2), 1.0),
+             ("sphere10_inflated_1.2", W.sphere_grid(N=10, up=2, tau=2), 1.2),
+             ("csg64_pseudo_sdf", W.csg_pseudo_grid(N=64, tau=2), 1.0)]
+    for name, w, f in cases:
         s = np.ascontiguousarray(f * w.s)
         ctx = gfs.Context(tau=2)
         ctx.build(torch.from_numpy(w.p).cuda(), torch.from_numpy(s).cuda())
         t = _ev_time(lambda: ctx.sphere_uncovered(), reps=1)
         out = ctx.sphere_uncovered().cpu().numpy()
+        surv = ctx.survivors().cpu().numpy()
         ctx.close()
-        res[name] = {"spheres": int(w.n), "ms": t, "uncovered": int((out == 1).sum()),
-                     "covered": int((out == 0).sum()), "undecided": int((out == 2).sum())}
+        res[name] = {"spheres": int(w.n), "ms": t, "spheres_per_s": w.n / (t / 1e3),
+                     "uncovered": int((out == 1).sum()), "covered": int((out == 0).sum()),
+                     "undecided": int((out == 2).sum()),
+                     "no_survivor_at_tau2": int(w.n - np.unique(surv // (10 * 4 ** 2 + 3)).size)}
+        if name.startswith("csg"):
+            # the U and D precomputation of Sec. 4.1 (includes its own
+            # per-sphere test, the sort and the copies to the caller)
+            ctx = gfs.Context(tau=2)
+            ctx.build(torch.from_numpy(w.p).cuda(), torch.from_numpy(s).cuda())
+            t0 = time.perf_counter()
+            circ, quads, _, status = ctx.uncovered_intersections()
+            torch.cuda.synchronize()
+            res[name]["intersections"] = {"s": time.perf_counter() - t0, "circles": int(circ.shape[0]),
+                                          "points": int(quads.shape[0]), "status": status}
+            ctx.close()
     return res
 
 
@@ -929,8 +958,9 @@ def run_gfs(args):
                          ("tangent", lambda: _isolated("tangent", ["--tangent-every", str(args.tangent_every)],
                                                        timeout=150)),
                          ("refine_order", lambda: _isolated("refine_order", timeout=150)),
-                         ("scored", lambda: _isolated("scored", timeout=150)),
-                         ("exact_coverage", lambda: _isolated("exact_coverage", timeout=150))):
+                         ("scored", lambda: _isolated("scored", ["--scored-every", str(args.scored_every)],
+                                                      timeout=150)),
+                         ("exact_coverage", lambda: _isolated("exact_coverage", timeout=300))):
             t_x = time.perf_counter()
             try:
                 line["extras"][name] = fn()
@@ -957,7 +987,7 @@ if __name__ == "__main__":
               "insert": lambda: extra_insert(a.insert_steps, peaks=pk),
               "batch": lambda: extra_batch(a.batch_shapes, a.batch_scale, peaks=pk),
               "sphere16": lambda: extra_sphere16(pk),
-              "scored": extra_scored,
+              "scored": lambda: extra_scored(a.scored_every),
               "tangent": lambda: extra_tangent(a.tangent_every),
               "refine_order": extra_refine_order,
               "exact_coverage": extra_exact_coverage}[a.only]

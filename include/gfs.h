@@ -290,18 +290,54 @@ int gfs_survivors(gfs_ctx* ctx, int64_t* g_out, int64_t cap, int64_t* count_host
 /* ---- exact coverage of each sample sphere (Prop. 1 (ii)) ------------------ */
 /* out[i] for every sphere of the context's current state (input order, n
  * bytes, device): 1 when some point of sphere i lies in no other ball shrunk
- * by tol, 0 when every point is covered, 2 when more than 512 balls meet the
- * sphere (not decided).  Exact in the sense of Def. 1: the test points are
- * the circles where the other shrunk balls cut the sphere (two points each)
- * and the points where two of them meet on it (the D points), each tested
- * against every ball but the ones it was built from, in FP64; a sample with
- * s_i = 0 is the point p_i.  The icosphere survivors are a subset: a sphere
- * with a survivor is uncovered.  One warp per sphere; the cost grows with
- * the cube of the number of balls that meet a sphere, so this is a check for
- * moderate inputs (it is the exact counterpart of "no survivor at tau").
- * No host synchronisation, no allocation.  Errors: GFS_ERR_STATE (no build),
+ * by tol, 0 when every point is covered, 2 when not decided (the certificate
+ * below outgrew its 512 members).  Exact in the sense of Def. 1: the test
+ * points are the circles where the other shrunk balls cut the sphere (two
+ * points each) and the points where two of them meet on it (the D points),
+ * each tested against every ball but the ones it was built from, in FP64; a
+ * sample with s_i = 0 is the point p_i.  Rather than every pair of the balls
+ * that meet the sphere, each sphere grows a certificate: a set of those
+ * balls, started from the ones holding six probe points, whose test points
+ * are checked first against the set and then against all balls; a ball that
+ * holds a point joins the set, a point no ball holds decides "uncovered",
+ * and a set whose every test point is held by another member covers the
+ * sphere (the boundary argument of Prop. 1 applied to its caps).
+ * witness (device, 3n doubles, or null): for out[i] = 1 the uncovered test
+ * point (p_i for a zero sample, p_i + (|s_i|, 0, 0) when no ball meets the
+ * sphere), NaN otherwise.  The icosphere survivors are a subset: a sphere
+ * with a survivor is uncovered.  One thread per sphere.  No host
+ * synchronisation, no allocation.  Errors: GFS_ERR_STATE (no build),
  * GFS_ERR_ARG, GFS_ERR_CUDA. */
-int gfs_sphere_uncovered(gfs_ctx* ctx, uint8_t* out);
+int gfs_sphere_uncovered(gfs_ctx* ctx, uint8_t* out, double* witness);
+
+/* ---- uncovered intersection circles and points (Sec. 4.1, Def. 1) --------- */
+/* The U and D precomputation of Sec. 4.1 for the context's current state,
+ * over the spheres S_i = (p_i, |s_i|) with |s_i| > 0 (input indices):
+ *  circles: the pairs i < j whose spheres cut in a circle with a point in no
+ *    other ball shrunk by tol -- the circles whose points D of Def. 1 a
+ *    query at any x may grow to;
+ *  points (U of Def. 1): the points shared by three spheres i < j < m (two
+ *    per triple: side 0 and 1 of the trilateration in the frame of p_i, p_j,
+ *    p_m) that lie in no ball but those three shrunk by tol.
+ * Where the paper finds candidate pairs and triples by rasterising the
+ * contour of the union of spheres, the library starts from the spheres
+ * that gfs_sphere_uncovered finds uncovered (a circle or point of a covered
+ * sphere is covered), walks the sphere hierarchy for the spheres that cut
+ * each, decides each circle with a growing certificate of covering balls
+ * (its extreme points and its crossings with the members' shrunk spheres,
+ * the same test points and tests as a full enumeration) and, on an
+ * uncovered circle, tests the points shared with every sphere that crosses
+ * it.  Outputs (device, sorted lexicographically): circles_out 2 int64 per
+ * circle (i, j); quads_out 4 int64 per point (i, j, m, side); points_out 3
+ * doubles per point.  counts_host (host, 3 int64): the numbers of circles
+ * and points, and a status word (bit 0: a circle's certificate outgrew 512
+ * members and the circle was taken as uncovered).  Synchronises the
+ * context's stream and allocates scratch on the device.
+ * Errors: GFS_ERR_STATE (no build), GFS_ERR_ARG (null pointers, negative
+ * capacities, or counts above the capacities: counts_host still set, nothing
+ * written), GFS_ERR_TOO_LARGE (2^31 entries or more), GFS_ERR_CUDA. */
+int gfs_uncovered_intersections(gfs_ctx* ctx, int64_t cap_circles, int64_t* circles_out, int64_t cap_points,
+                                int64_t* quads_out, double* points_out, int64_t* counts_host);
 
 /* ---- refinement order (Sec. 4.2) ------------------------------------------ */
 /* The greedy refinement depends on the order of the new points.  The paper

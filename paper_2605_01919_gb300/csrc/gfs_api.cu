@@ -146,6 +146,8 @@ struct gfs_ctx {
   // per-sphere survivor lists for the scored value (sorted ids + offsets),
   // valid while csr_state equals state_id (every build or insertion changes it)
   DevBuf csr_ids, csr_off, scored_status;
+  // uncovered intersection circles and points (raw outputs, sort buffers)
+  DevBuf ud_uncov, ud_cnt, ud_circ, ud_quad, ud_pts, ud_k0, ud_k1, ud_v0, ud_v1;
   int64_t state_id = 0, csr_state = -1;
   int64_t ins_rounds = 0, ins_steps = 0, ins_rebuilds = 0, ins_queried = 0;  // of the last insertion call
   double ins_ms_total = 0.0, ins_ms_rebuild = 0.0, ins_ms_final = 0.0;  // host wall time of its phases
@@ -594,12 +596,89 @@ int gfs_query_points(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, const 
   return GFS_OK;
 }
 
-int gfs_sphere_uncovered(gfs_ctx* c, uint8_t* out) {
+int gfs_sphere_uncovered(gfs_ctx* c, uint8_t* out, double* witness) {
   if (!c || !out) return GFS_ERR_ARG;
   if (!c->built) return GFS_ERR_STATE;
   QueryArgs a;
   fill_query_args(c, a);
-  GFS_CK(launch_sphere_uncovered(a, out, c->stream));
+  GFS_CK(launch_sphere_uncovered(a, out, witness, c->stream));
+  return GFS_OK;
+}
+
+int gfs_uncovered_intersections(gfs_ctx* c, int64_t cap_circles, int64_t* circles_out, int64_t cap_points,
+                                int64_t* quads_out, double* points_out, int64_t* counts_host) {
+  if (!c || !counts_host || cap_circles < 0 || cap_points < 0) return GFS_ERR_ARG;
+  if ((cap_circles > 0 && !circles_out) || (cap_points > 0 && (!quads_out || !points_out))) return GFS_ERR_ARG;
+  if (!c->built) return GFS_ERR_STATE;
+  counts_host[0] = counts_host[1] = counts_host[2] = 0;
+  if (c->n == 0) return GFS_OK;
+  cudaStream_t st = c->stream;
+  QueryArgs a;
+  fill_query_args(c, a);
+  GFS_TRY(ensure(c->ud_uncov, size_t(c->n) + 16));
+  GFS_TRY(ensure(c->ud_cnt, 32));
+  GFS_CK(launch_sphere_uncovered(a, c->ud_uncov.as<uint8_t>(), nullptr, st));
+  // raw outputs: a first guess, then exactly the counts (the decisions do not
+  // depend on the capacities, so a second run finds the same entries)
+  int64_t cap_c = std::max<int64_t>(4096, c->n), cap_p = std::max<int64_t>(4096, c->n);
+  unsigned long long hc[2] = {0, 0};
+  unsigned hstatus = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    GFS_TRY(ensure(c->ud_circ, size_t(cap_c) * 16));
+    GFS_TRY(ensure(c->ud_quad, size_t(cap_p) * 32));
+    GFS_TRY(ensure(c->ud_pts, size_t(cap_p) * 24));
+    GFS_CK(cudaMemsetAsync(c->ud_cnt.p, 0, 32, st));
+    exact::UDOut o{c->ud_cnt.as<unsigned long long>(), cap_c, cap_p, c->ud_circ.as<int64_t>(), c->ud_quad.as<int64_t>(),
+                   c->ud_pts.as<double>(), reinterpret_cast<unsigned*>(c->ud_cnt.as<unsigned long long>() + 2)};
+    GFS_CK(launch_intersections(a, c->ud_uncov.as<uint8_t>(), o, st));
+    GFS_CK(cudaMemcpyAsync(hc, c->ud_cnt.p, 16, cudaMemcpyDeviceToHost, st));
+    GFS_CK(cudaMemcpyAsync(&hstatus, c->ud_cnt.as<unsigned long long>() + 2, 4, cudaMemcpyDeviceToHost, st));
+    GFS_CK(cudaStreamSynchronize(st));
+    if (int64_t(hc[0]) <= cap_c && int64_t(hc[1]) <= cap_p) break;
+    if (pass == 1) return GFS_ERR_CUDA;  // cannot happen: the second run finds the same entries
+    cap_c = std::max<int64_t>(cap_c, int64_t(hc[0]));
+    cap_p = std::max<int64_t>(cap_p, int64_t(hc[1]));
+  }
+  const int64_t nc = int64_t(hc[0]), np = int64_t(hc[1]);
+  counts_host[0] = nc;
+  counts_host[1] = np;
+  counts_host[2] = int64_t(hstatus);
+  if (nc > cap_circles || np > cap_points) return GFS_ERR_ARG;
+  if (nc >= (int64_t(1) << 31) || np >= (int64_t(1) << 31)) return GFS_ERR_TOO_LARGE;
+  const int64_t nk = std::max<int64_t>(std::max<int64_t>(nc, np), 1);
+  GFS_TRY(ensure(c->ud_k0, size_t(nk) * 8));
+  GFS_TRY(ensure(c->ud_k1, size_t(nk) * 8));
+  GFS_TRY(ensure(c->ud_v0, size_t(nk) * 4));
+  GFS_TRY(ensure(c->ud_v1, size_t(nk) * 4));
+  auto sort64 = [&](int64_t cnt) -> int {
+    size_t bytes = 0;
+    GFS_CK(sort_pairs64(nullptr, bytes, c->ud_k0.as<unsigned long long>(), c->ud_k1.as<unsigned long long>(),
+                        c->ud_v0.as<int>(), c->ud_v1.as<int>(), cnt, 64, st));
+    GFS_TRY(cub_ensure(c, bytes));
+    bytes = c->cub_temp.bytes;
+    GFS_CK(sort_pairs64(c->cub_temp.p, bytes, c->ud_k0.as<unsigned long long>(), c->ud_k1.as<unsigned long long>(),
+                        c->ud_v0.as<int>(), c->ud_v1.as<int>(), cnt, 64, st));
+    return GFS_OK;
+  };
+  // points: by (m, side), then stably by (i, j)
+  if (np > 0) {
+    GFS_CK(launch_ud_point_keys(c->ud_quad.as<int64_t>(), nullptr, np, 0, c->ud_k0.as<unsigned long long>(),
+                                c->ud_v0.as<int>(), st));
+    GFS_TRY(sort64(np));
+    GFS_CK(launch_ud_point_keys(c->ud_quad.as<int64_t>(), c->ud_v1.as<int>(), np, 1,
+                                c->ud_k0.as<unsigned long long>(), c->ud_v0.as<int>(), st));
+    GFS_TRY(sort64(np));
+    GFS_CK(launch_ud_gather(nullptr, 0, nullptr, c->ud_v1.as<int>(), c->ud_quad.as<int64_t>(), c->ud_pts.as<double>(),
+                            np, quads_out, points_out, st));
+  }
+  if (nc > 0) {
+    // the keys carry the pairs; the sort's payload is unused
+    GFS_CK(launch_ud_circle_keys(c->ud_circ.as<int64_t>(), nc, c->ud_k0.as<unsigned long long>(), st));
+    GFS_TRY(sort64(nc));
+    GFS_CK(launch_ud_gather(c->ud_k1.as<unsigned long long>(), nc, circles_out, nullptr, nullptr, nullptr, 0, nullptr,
+                            nullptr, st));
+  }
+  GFS_CK(cudaStreamSynchronize(st));
   return GFS_OK;
 }
 

@@ -1,8 +1,8 @@
 // Exact uncovered test per sphere (Prop. 1 (ii)), device routines.
 //
 // Sphere i keeps a point outside every other ball shrunk by tol exactly when
-// one of these points is outside every ball but i and the spheres it was
-// built from (N_i: the spheres k != i with rho_k = |s_k| - tol > 0 whose
+// one of these test points is outside every ball but i and the spheres it
+// was built from (N_i: the spheres k != i with rho_k = |s_k| - tol > 0 whose
 // shrunk open ball meets sphere i, | |p_i - p_k| - |s_i| | < rho_k):
 //  - any point, when N_i is empty;
 //  - the two points of each circle C_k = S_i with the sphere (p_k, rho_k)
@@ -12,19 +12,32 @@
 //    (p_m, rho_m), k < m in N_i -- the ends of the uncovered arcs of a
 //    partly covered circle (the D points of Def. 1).
 // The uncovered set, if not empty, is a closed proper subset of the sphere,
-// so its boundary holds one of these points.  A sample with s_i = 0 is the
-// point p_i.  Every value is computed in FP64 with each operation rounded on
-// its own, in the order written (the circle and triple constructions of the
-// exact grow-to points), so the decisions are those of a plain IEEE-754
-// evaluation.
+// so its boundary holds one of these points.  The argument holds for the
+// caps of any subset S of N_i: if every test point built from S lies in the
+// cap of another member of S, the caps of S cover the sphere.
+//
+// So instead of all |N_i|^2 test points (|N_i| reaches millions for a deep
+// sphere of a 128^3 grid) the routine grows a certificate S: it starts from
+// the balls that hold six probe points of the sphere, and tests the points
+// of S's circles and pairs in the order the members joined.  A point that a
+// member of S holds is covered; otherwise a walk over the sphere hierarchy
+// tests it against every ball but the ones it was built from: if none holds
+// it, it is an uncovered test point of N_i (the same point and the same test
+// as the full enumeration) and the sphere is uncovered; if a ball of N_i
+// holds it, that ball joins S.  When every point of S is covered, the sphere
+// is covered.  A sample with s_i = 0 is the point p_i.  Every value is
+// computed in FP64 with each operation rounded on its own, in the order
+// written (the circle and triple constructions of the exact grow-to points),
+// so the decisions are those of a plain IEEE-754 evaluation.
 #pragma once
 
+#include "gfs_exact.h"
 #include "gfs_tangent.cuh"
 
 namespace gfs {
 namespace exact {
 
-constexpr int kMaxMeet = 512;  // balls meeting one sphere that a thread can hold
+constexpr int kMaxSet = 512;  // members of one sphere's certificate
 
 __device__ __forceinline__ double dot(const double* a, const double* b) {
   return __dadd_rn(__dadd_rn(__dmul_rn(a[0], b[0]), __dmul_rn(a[1], b[1])), __dmul_rn(a[2], b[2]));
@@ -107,18 +120,24 @@ __device__ inline bool triple_points(const double* p1, double r1, const double* 
   return true;
 }
 
-// N_i of sphere i (input index) into meet[0, kMaxMeet), gathered by a walk
-// over the hierarchy: a ball of a node with centre C and radius bound w can
-// meet sphere i only if |p_i - C| < r_i + w.  Returns the count, or -1 when
-// more than kMaxMeet balls meet the sphere.
-__device__ inline int gather_meet(const QueryArgs& a, int i, int* meet) {
+// Is sphere k in N_i (same arithmetic as the full enumeration)?
+__device__ __forceinline__ bool meets(const QueryArgs& a, const D4& P, double ri, int k) {
+  const D4 Q = a.sph64[k];
+  const double rho = __dsub_rn(fabs(Q.w), a.tol);
+  if (!(rho > 0.0)) return false;
+  const double d = __dsqrt_rn(ex_d2(P.x, P.y, P.z, Q.x, Q.y, Q.z));
+  return fabs(__dsub_rn(d, ri)) < rho;
+}
+
+// The first ball of N_i in hierarchy order, or -1 when N_i is empty: a ball
+// of a node with centre C and radius bound w can meet sphere i only if
+// |p_i - C| < r_i + w.
+__device__ inline int first_member(const QueryArgs& a, int i, uint32_t* stack) {
   const D4 P = a.sph64[i];
   const double ri = fabs(P.w);
-  int nn = 0;
   const float x32 = float(P.x), y32 = float(P.y), z32 = float(P.z), ax = tangent::amax3(x32, y32, z32);
   const float ri32 = tangent::f_up(ri);
   const Tree& T = a.st;
-  uint32_t stack[kStack];
   int sp = 0;
   const int top = T.nlevels - 1;
   for (int64_t j = 0; j < T.count[top]; ++j) stack[sp++] = pack_node(top, j);
@@ -130,14 +149,7 @@ __device__ inline int gather_meet(const QueryArgs& a, int i, int* meet) {
       const int64_t b = idx * kLeaf, e = tangent::imin64(b + kLeaf, a.n);
       for (int64_t j = b; j < e; ++j) {
         const int k = a.sid[j];
-        if (k == i) continue;
-        const D4 Q = a.sph64[k];
-        const double rho = __dsub_rn(fabs(Q.w), a.tol);
-        if (!(rho > 0.0)) continue;
-        const double d = __dsqrt_rn(ex_d2(P.x, P.y, P.z, Q.x, Q.y, Q.z));
-        if (!(fabs(__dsub_rn(d, ri)) < rho)) continue;
-        if (nn == kMaxMeet) return -1;
-        meet[nn++] = k;
+        if (k != i && meets(a, P, ri, k)) return k;
       }
     } else {
       const int64_t cb = idx * kFan, ce = tangent::imin64(cb + kFan, T.count[lev - 1]);
@@ -150,72 +162,314 @@ __device__ inline int gather_meet(const QueryArgs& a, int i, int* meet) {
       }
     }
   }
-  return nn;
+  return -1;
 }
 
-// Does one of the test points handled by `lane` of `nlanes` lie outside every
-// ball but the ones it was built from?  The lane takes the circles of
-// meet[c] with c = lane mod nlanes and the pairs whose running number is
-// lane mod nlanes; it stops early once *found (another lane's success, may
-// be null) is set.  Which lane finds a point does not matter: sphere i is
-// uncovered when any lane does.
-__device__ inline bool lane_candidates(const QueryArgs& a, int i, const int* meet, int nn, int lane, int nlanes,
-                                       const volatile int* found) {
+// The certificate: members in the order they joined.
+struct Cert {
+  int* S;
+  int ns;
+  uint32_t* stack;  // kStack entries for the hierarchy walks
+};
+
+// Add ball j (found to hold a point of sphere i) to the certificate when it
+// is in N_i and not yet a member.  False when the certificate is full.
+__device__ inline bool join(const QueryArgs& a, const D4& P, double ri, int j, Cert& C) {
+  for (int u = 0; u < C.ns; ++u)
+    if (C.S[u] == j) return true;
+  if (!meets(a, P, ri, j)) return true;  // holds the point, but no circle of N_i
+  if (C.ns == kMaxSet) return false;
+  C.S[C.ns++] = j;
+  return true;
+}
+
+// Test point t built from i, k and m (m = -1 for a circle point): 1 when no
+// ball but those holds it; 0 when one does (joining the certificate if it is
+// not a member); -1 when the certificate is full.
+__device__ inline int test_point(const QueryArgs& a, const D4& P, double ri, int i, const double* t, int k, int m,
+                                 Cert& C) {
+  for (int u = 0; u < C.ns; ++u) {
+    const int o = C.S[u];
+    if (o == k || o == m) continue;
+    if (ex_cov(t[0], t[1], t[2], a.sph64[o], a.tol)) return 0;
+  }
+  const int j = tangent::covered_except_on(C.stack, a, t[0], t[1], t[2], i, k, m);
+  if (j < 0) return 1;
+  return join(a, P, ri, j, C) ? 0 : -1;
+}
+
+// 1: sphere i (input index) keeps an uncovered point (witness, when not
+// null, receives it: a test point, or p_i for a zero sample); 0: every point
+// is covered; 2: undecided (the certificate outgrew kMaxSet members).
+// S: kMaxSet entries; stack: kStack entries.
+__device__ inline int sphere_uncovered(const QueryArgs& a, int i, int* S, uint32_t* stack, double* witness) {
   const D4 P = a.sph64[i];
   const double pi[3] = {P.x, P.y, P.z};
   const double ri = fabs(P.w);
+  if (ri == 0.0) {
+    if (tangent::covered_except_on(stack, a, P.x, P.y, P.z, i, -1, -1) >= 0) return 0;
+    if (witness)
+      for (int c = 0; c < 3; ++c) witness[c] = pi[c];
+    return 1;
+  }
+  Cert C{S, 0, stack};
+  // probe points p_i +- r_i e_c: the balls that hold them start the
+  // certificate (they are not test points: an uncovered probe decides nothing)
+  for (int c = 0; c < 6; ++c) {
+    double t[3] = {pi[0], pi[1], pi[2]};
+    t[c >> 1] = __dadd_rn(pi[c >> 1], (c & 1) ? -ri : ri);
+    const int j = tangent::covered_except_on(stack, a, t[0], t[1], t[2], i, -1, -1);
+    if (j >= 0) join(a, P, ri, j, C);
+  }
+  if (C.ns == 0) {
+    const int k = first_member(a, i, stack);
+    if (k < 0) {  // N_i is empty: every point is uncovered
+      if (witness)
+        for (int c = 0; c < 3; ++c) witness[c] = c == 0 ? __dadd_rn(pi[0], ri) : pi[c];
+      return 1;
+    }
+    S[C.ns++] = k;
+  }
   const double e_ref[3] = {0.36, 0.48, 0.8};
   double ref[3];
   for (int c = 0; c < 3; ++c) ref[c] = __dadd_rn(pi[c], __dmul_rn(__dadd_rn(ri, 1.0), e_ref[c]));
   double pts[6];
-  int64_t pair = 0;
-  for (int u = 0; u < nn; ++u) {
-    if (found && *found) return false;
-    const int k = meet[u];
+  for (int n = 0; n < C.ns; ++n) {
+    const int k = S[n];
     const D4 Q = a.sph64[k];
     const double pk[3] = {Q.x, Q.y, Q.z};
     const double rk = __dsub_rn(fabs(Q.w), a.tol);
-    if (u % nlanes == lane && circle_points(pi, ri, pk, rk, ref, pts)) {
-      if (tangent::covered_except(a, pts[0], pts[1], pts[2], i, k, -1) < 0) return true;
-      if (tangent::covered_except(a, pts[3], pts[4], pts[5], i, k, -1) < 0) return true;
-    }
-    for (int v = u + 1; v < nn; ++v, ++pair) {
-      if (pair % nlanes != lane) continue;
-      if (found && *found) return false;
-      const int m = meet[v];
-      const D4 R = a.sph64[m];
-      const double pm[3] = {R.x, R.y, R.z};
-      const double rm = __dsub_rn(fabs(R.w), a.tol);
-      // the oracle takes the pair in increasing index order
-      const bool km = k < m;
-      if (triple_points(pi, ri, km ? pk : pm, km ? rk : rm, km ? pm : pk, km ? rm : rk, pts)) {
-        if (tangent::covered_except(a, pts[0], pts[1], pts[2], i, k, m) < 0) return true;
-        if (tangent::covered_except(a, pts[3], pts[4], pts[5], i, k, m) < 0) return true;
+    // the pairs of k with the members before it, then k's circle
+    for (int u = 0; u <= n; ++u) {
+      const int m = u < n ? S[u] : -1;
+      bool have;
+      if (m < 0) {
+        have = circle_points(pi, ri, pk, rk, ref, pts);
+      } else {
+        const D4 R = a.sph64[m];
+        const double pm[3] = {R.x, R.y, R.z};
+        const double rm = __dsub_rn(fabs(R.w), a.tol);
+        // the full enumeration takes each pair in increasing index order
+        const bool km = k < m;
+        have = triple_points(pi, ri, km ? pk : pm, km ? rk : rm, km ? pm : pk, km ? rm : rk, pts);
+      }
+      if (!have) continue;
+      for (int h = 0; h < 2; ++h) {
+        const int r = test_point(a, P, ri, i, pts + 3 * h, k, m, C);
+        if (r < 0) return 2;
+        if (r == 1) {
+          if (witness)
+            for (int c = 0; c < 3; ++c) witness[c] = pts[3 * h + c];
+          return 1;
+        }
       }
     }
   }
-  return false;
+  return 0;
 }
 
-// The cases decided before any test point: 1 for a zero sample outside the
-// other balls or a sphere no ball meets, 0 for a covered zero sample, 2 for
-// more than kMaxMeet meeting balls; -1 when the test points decide.
-__device__ inline int trivial_case(const QueryArgs& a, int i, int nn) {
+// ---------------------------------------------------------------------------
+// Uncovered intersection circles and points (Def. 1 U and the circles of D;
+// the U and D precomputation of Sec. 4.1).
+//
+// For spheres S_i = (p_i, |s_i|), |s_i| > 0, i < j: the circle C_ij where
+// S_i and S_j cut is uncovered when some point of it lies in no ball but i
+// and j shrunk by tol.  Its uncovered part is closed; if it is not empty
+// and not the whole circle its ends lie where C_ij crosses a shrunk sphere
+// (p_m, |s_m| - tol).  The test points are C_ij's points nearest to and
+// farthest from p_i + (|s_i| + 1) e and its crossings with every such
+// sphere, each tested against every ball but i, j and the m it was built
+// from.  As for a whole sphere, a circle grows a certificate M instead of
+// taking every m: the balls that hold the two extreme points start it, the
+// crossings of its members are tested against M and then against all
+// balls, a ball that holds a crossing joins M, and a point that no ball
+// holds decides "uncovered" (the full enumeration's own decision on one of
+// its points).  A ball that holds a point but whose shrunk sphere does not
+// cross the circle holds the whole circle: covered.  The uncovered points U
+// on an uncovered circle C_ij are the points shared by S_i, S_j and S_m,
+// m > j, in no ball but i, j, m shrunk by tol; a covered circle has none,
+// and neither has a circle on a sphere that the other balls cover, so the
+// kernel starts from the uncovered spheres only.
+// ---------------------------------------------------------------------------
+
+// Circle C_ij (extreme points q): 1 uncovered, 0 covered, -1 certificate full.
+// M: kMaxSet entries; stack: kStack entries.
+__device__ inline int circle_uncovered(const QueryArgs& a, int i, int j, const double* pi, double ri,
+                                       const double* pj, double rj, const double* q, int* M, uint32_t* stack) {
+  int nm = 0;
+  // ball b holds a point of C_ij: joins M; 2 when it holds the whole circle
+  auto join = [&](int b) -> int {
+    for (int u = 0; u < nm; ++u)
+      if (M[u] == b) return 1;
+    const D4 B = a.sph64[b];
+    const double pb[3] = {B.x, B.y, B.z};
+    double t[6];
+    if (!triple_points(pi, ri, pj, rj, pb, __dsub_rn(fabs(B.w), a.tol), t)) return 2;
+    if (nm == kMaxSet) return -1;
+    M[nm++] = b;
+    return 1;
+  };
+  // 1: no ball holds t; 0: held; 2: held by a ball that holds the circle; -1: full
+  auto test = [&](const double* t, int m) -> int {
+    for (int u = 0; u < nm; ++u) {
+      const int o = M[u];
+      if (o != m && ex_cov(t[0], t[1], t[2], a.sph64[o], a.tol)) return 0;
+    }
+    const int b = tangent::covered_except_on(stack, a, t[0], t[1], t[2], i, j, m);
+    if (b < 0) return 1;
+    const int r = join(b);
+    return r == 1 ? 0 : r;
+  };
+  for (int h = 0; h < 2; ++h) {
+    const int r = test(q + 3 * h, -1);
+    if (r == 1 || r == -1) return r;
+    if (r == 2) return 0;
+  }
+  for (int n = 0; n < nm; ++n) {
+    const int m = M[n];
+    const D4 B = a.sph64[m];
+    const double pm[3] = {B.x, B.y, B.z};
+    double t[6];
+    if (!triple_points(pi, ri, pj, rj, pm, __dsub_rn(fabs(B.w), a.tol), t)) continue;
+    for (int h = 0; h < 2; ++h) {
+      const int r = test(t + 3 * h, m);
+      if (r == 1 || r == -1) return r;
+      if (r == 2) return 0;
+    }
+  }
+  return 0;
+}
+
+__device__ inline void ud_record_circle(const UDOut& o, int i, int j) {
+  const unsigned long long k = atomicAdd(o.cnt, 1ull);
+  if (k < (unsigned long long)o.cap_c) {
+    o.circ[2 * k] = i;
+    o.circ[2 * k + 1] = j;
+  }
+}
+
+__device__ inline void ud_record_point(const UDOut& o, int i, int j, int m, int side, const double* t) {
+  const unsigned long long k = atomicAdd(o.cnt + 1, 1ull);
+  if (k < (unsigned long long)o.cap_p) {
+    o.quad[4 * k] = i;
+    o.quad[4 * k + 1] = j;
+    o.quad[4 * k + 2] = m;
+    o.quad[4 * k + 3] = side;
+    for (int c = 0; c < 3; ++c) o.pts[3 * k + c] = t[c];
+  }
+}
+
+// The uncovered points of circle C_ij: spheres m > j whose sphere may cross
+// the circle (centre zeta, radius rc): ||p_m - zeta| - r_m| <= rc, node
+// bound |C - zeta| - w <= rc.
+__device__ inline void circle_points_u(const QueryArgs& a, int i, int j, const double* pi, double ri,
+                                       const double* pj, double rj, uint32_t* stack, uint32_t* cstack,
+                                       const UDOut& o) {
+  double mu[3] = {__dsub_rn(pj[0], pi[0]), __dsub_rn(pj[1], pi[1]), __dsub_rn(pj[2], pi[2])};
+  const double d = norm(mu);
+  const double al = (d * d + ri * ri - rj * rj) / (2.0 * d);
+  const double rc = sqrt(fmax(ri * ri - al * al, 0.0));
+  double zeta[3];
+  for (int c = 0; c < 3; ++c) zeta[c] = pi[c] + al * mu[c] / d;
+  const float zx = float(zeta[0]), zy = float(zeta[1]), zz = float(zeta[2]);
+  const float az = tangent::amax3(zx, zy, zz);
+  // rounding of zeta and rc in FP64 is far below the FP32 screens' margins
+  const float rc32 = tangent::f_up(rc) + 1e-6f * (1.f + az);
+  const Tree& T = a.st;
+  int sp = 0;
+  const int top = T.nlevels - 1;
+  for (int64_t u = 0; u < T.count[top]; ++u) stack[sp++] = pack_node(top, u);
+  while (sp > 0) {
+    const uint32_t nd = stack[--sp];
+    const int lev = node_level(nd);
+    const int64_t idx = node_index(nd);
+    if (lev == 0) {
+      const int64_t b = idx * kLeaf, e = tangent::imin64(b + kLeaf, a.n);
+      for (int64_t u = b; u < e; ++u) {
+        const int m = a.sid[u];
+        if (m <= j) continue;
+        const float4 S = a.sph[u];
+        if (S.w == 0.f) continue;
+        const float dm = tangent::dist32(zx, zy, zz, S), rm32 = fabsf(S.w);
+        if (fabsf(dm - rm32) - tangent::err32(az, S, dm, rm32) > rc32) continue;
+        const D4 Q = a.sph64[m];
+        const double rm = fabs(Q.w);
+        if (!(rm > 0.0)) continue;
+        const double pm[3] = {Q.x, Q.y, Q.z};
+        double t[6];
+        if (!triple_points(pi, ri, pj, rj, pm, rm, t)) continue;
+        for (int h = 0; h < 2; ++h)
+          if (tangent::covered_except_on(cstack, a, t[3 * h], t[3 * h + 1], t[3 * h + 2], i, j, m) < 0)
+            ud_record_point(o, i, j, m, h, t + 3 * h);
+      }
+    } else {
+      const int64_t cb = idx * kFan, ce = tangent::imin64(cb + kFan, T.count[lev - 1]);
+      const int64_t off = T.offset[lev - 1];
+      for (int64_t c = cb; c < ce; ++c) {
+        const float4 B = T.na[off + c];
+        if (!(B.w > 0.f)) continue;
+        const float dC = tangent::dist32(zx, zy, zz, B);
+        if (dC - tangent::err32(az, B, dC, B.w) - B.w <= rc32) stack[sp++] = pack_node(lev - 1, c);
+      }
+    }
+  }
+}
+
+// Every circle C_ij, j > i, of sphere i (input index; uncov: the per-sphere
+// exact test, 0 = covered), with its uncovered points.  stacks: 3 kStack
+// entries (the walk over j, the certificate's and the point walk's, the
+// point tests'); M: kMaxSet entries.
+__device__ inline void sphere_intersections(const QueryArgs& a, int i, const uint8_t* uncov, int* M,
+                                            uint32_t* stacks, const UDOut& o) {
   const D4 P = a.sph64[i];
-  if (fabs(P.w) == 0.0) return tangent::covered_except(a, P.x, P.y, P.z, i, -1, -1) < 0 ? 1 : 0;
-  if (nn < 0) return 2;
-  if (nn == 0) return 1;
-  return -1;
-}
-
-// 1: sphere i (input index) keeps an uncovered point; 0: it does not;
-// 2: undecided (more than kMaxMeet balls meet it).  One thread.
-__device__ inline int sphere_uncovered(const QueryArgs& a, int i) {
-  int meet[kMaxMeet];
-  const int nn = fabs(a.sph64[i].w) == 0.0 ? 0 : gather_meet(a, i, meet);
-  const int t = trivial_case(a, i, nn);
-  if (t >= 0) return t;
-  return lane_candidates(a, i, meet, nn, 0, 1, nullptr) ? 1 : 0;
+  const double ri = fabs(P.w);
+  if (!(ri > 0.0)) return;
+  const double pi[3] = {P.x, P.y, P.z};
+  const double e_ref[3] = {0.36, 0.48, 0.8};
+  double ref[3];
+  for (int c = 0; c < 3; ++c) ref[c] = __dadd_rn(pi[c], __dmul_rn(__dadd_rn(ri, 1.0), e_ref[c]));
+  const float x32 = float(P.x), y32 = float(P.y), z32 = float(P.z), ax = tangent::amax3(x32, y32, z32);
+  const float ri32 = tangent::f_up(ri);
+  uint32_t* stack = stacks;
+  const Tree& T = a.st;
+  int sp = 0;
+  const int top = T.nlevels - 1;
+  for (int64_t u = 0; u < T.count[top]; ++u) stack[sp++] = pack_node(top, u);
+  while (sp > 0) {
+    const uint32_t nd = stack[--sp];
+    const int lev = node_level(nd);
+    const int64_t idx = node_index(nd);
+    if (lev == 0) {
+      const int64_t b = idx * kLeaf, e = tangent::imin64(b + kLeaf, a.n);
+      for (int64_t u = b; u < e; ++u) {
+        const int j = a.sid[u];
+        if (j <= i || uncov[j] == 0) continue;
+        const D4 Q = a.sph64[j];
+        const double rj = fabs(Q.w);
+        if (!(rj > 0.0)) continue;
+        const double pj[3] = {Q.x, Q.y, Q.z};
+        double q[6];
+        if (!circle_points(pi, ri, pj, rj, ref, q)) continue;
+        int r = circle_uncovered(a, i, j, pi, ri, pj, rj, q, M, stacks + kStack);
+        if (r < 0) {
+          atomicOr(o.status, 1u);
+          r = 1;
+        }
+        if (r == 0) continue;
+        ud_record_circle(o, i, j);
+        circle_points_u(a, i, j, pi, ri, pj, rj, stacks + kStack, stacks + 2 * kStack, o);
+      }
+    } else {
+      const int64_t cb = idx * kFan, ce = tangent::imin64(cb + kFan, T.count[lev - 1]);
+      const int64_t off = T.offset[lev - 1];
+      for (int64_t c = cb; c < ce; ++c) {
+        const float4 B = T.na[off + c];
+        if (!(B.w > 0.f)) continue;
+        const float dC = tangent::dist32(x32, y32, z32, B);
+        if (dC - tangent::err32(ax, B, dC, B.w + ri32) < B.w + ri32) stack[sp++] = pack_node(lev - 1, c);
+      }
+    }
+  }
 }
 
 }  // namespace exact

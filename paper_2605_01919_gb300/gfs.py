@@ -19,9 +19,11 @@ FLAG_LB_VIOL, FLAG_FAR_VIOL, FLAG_OPP_VIOL, FLAG_LOST_WITNESS = 0x10, 0x20, 0x40
 FLAG_SCORE_FALLBACK = 0x200
 
 EXPORTED = ["gfs_default_options", "gfs_create", "gfs_set_stream", "gfs_build", "gfs_query", "gfs_query_tangent",
-            "gfs_query_backward", "gfs_query_backward_noalloc", "gfs_insert", "gfs_insert_known", "gfs_survivors", "gfs_batch_build", "gfs_batch_query",
-            "gfs_batch_survivors", "gfs_stats", "gfs_solve_host", "gfs_icosphere", "gfs_strerror",
-            "gfs_destroy", "gfs_cell_coverage", "gfs_flood_order", "gfs_batch_query_tangent", "gfs_sphere_uncovered", "gfs_query_points"]
+            "gfs_query_scored", "gfs_query_points", "gfs_query_backward", "gfs_query_backward_noalloc", "gfs_insert",
+            "gfs_insert_known", "gfs_survivors", "gfs_batch_build", "gfs_batch_rebuild", "gfs_batch_status",
+            "gfs_batch_query", "gfs_batch_query_tangent", "gfs_batch_survivors", "gfs_stats", "gfs_solve_host",
+            "gfs_icosphere", "gfs_strerror", "gfs_destroy", "gfs_cell_coverage", "gfs_flood_order",
+            "gfs_sphere_uncovered", "gfs_uncovered_intersections", "gfs_fma_probe"]
 
 
 class Options(ctypes.Structure):
@@ -117,7 +119,9 @@ def load(build_if_missing: bool = True):
     L.gfs_solve_host.restype = i32
     L.gfs_query_points.argtypes = [P, P, i32, i64, P, P, P]
     L.gfs_query_points.restype = i32
-    L.gfs_sphere_uncovered.argtypes = [P, P]
+    L.gfs_sphere_uncovered.argtypes = [P, P, P]
+    L.gfs_uncovered_intersections.argtypes = [P, i64, P, i64, P, P, P]
+    L.gfs_uncovered_intersections.restype = i32
     L.gfs_sphere_uncovered.restype = i32
     L.gfs_cell_coverage.argtypes = [P, P, i64, P, f64, i32, P]
     L.gfs_cell_coverage.restype = i32
@@ -335,14 +339,37 @@ class Context:
         return out
 
     # -- exact coverage of the sample spheres (Prop. 1 (ii)) ----------------------
-    def sphere_uncovered(self) -> torch.Tensor:
+    def sphere_uncovered(self, witness: bool = False):
         """Per sphere of the current state (input order): 1 keeps a point
-        outside every other shrunk ball, 0 fully covered, 2 undecided (more
-        than 512 balls meet it)."""
-        out = torch.empty(self.stats()["n_spheres"], dtype=torch.uint8, device="cuda")
+        outside every other shrunk ball, 0 fully covered, 2 undecided (its
+        covering certificate outgrew 512 balls).  With witness=True also the
+        (n, 3) float64 uncovered points (NaN rows where not uncovered)."""
+        n = self.stats()["n_spheres"]
+        out = torch.empty(n, dtype=torch.uint8, device="cuda")
+        wit = torch.empty((n, 3), dtype=torch.float64, device="cuda") if witness else None
         self._sync_stream()
-        _check(load().gfs_sphere_uncovered(self._h, _ptr(out)))
-        return out
+        _check(load().gfs_sphere_uncovered(self._h, _ptr(out), _ptr(wit) if wit is not None else None))
+        return (out, wit) if witness else out
+
+    def uncovered_intersections(self):
+        """The U and D precomputation of Sec. 4.1: (circles (c, 2) int64 pairs
+        i < j whose intersection circle keeps a point in no other shrunk ball,
+        quads (u, 4) int64 (i, j, m, side) of the uncovered points shared by
+        three spheres, points (u, 3) float64, status word), all on the device,
+        sorted lexicographically."""
+        L = load()
+        counts = (ctypes.c_int64 * 3)()
+        self._sync_stream()
+        rc = L.gfs_uncovered_intersections(self._h, 0, None, 0, None, None, counts)
+        if rc not in (0, 1):   # 1 = GFS_ERR_ARG: the counts are set
+            _check(rc)
+        nc, npt = int(counts[0]), int(counts[1])
+        circ = torch.empty((nc, 2), dtype=torch.int64, device="cuda")
+        quads = torch.empty((npt, 4), dtype=torch.int64, device="cuda")
+        pts = torch.empty((npt, 3), dtype=torch.float64, device="cuda")
+        _check(L.gfs_uncovered_intersections(self._h, nc, _ptr(circ) if nc else None, npt,
+                                             _ptr(quads) if npt else None, _ptr(pts) if npt else None, counts))
+        return circ, quads, pts, int(counts[2])
 
     # -- refinement order (Sec. 4.2) ------------------------------------------------
     def cell_coverage(self, cells: torch.Tensor, origin, h: float, sub: int = 8) -> torch.Tensor:

@@ -32,6 +32,11 @@ inline unsigned atomicOr(unsigned* p, unsigned v) {
   *p |= v;
   return o;
 }
+inline unsigned long long atomicAdd(unsigned long long* p, unsigned long long v) {
+  const unsigned long long o = *p;
+  *p += v;
+  return o;
+}
 inline unsigned __float_as_uint(float f) {
   unsigned u;
   std::memcpy(&u, &f, sizeof(u));

@@ -174,30 +174,36 @@ extern "C" int coverage_host(const double* p, const double* s, int64_t n, double
 }
 
 extern "C" int uncovered_host(const double* p, const double* s, int64_t n, double tol, uint8_t* out,
-                              unsigned order_seed) {
+                              double* witness, unsigned order_seed) {
   HostTree H;
   if (!build_tree(p, s, n, order_seed, H)) return -1;
   const QueryArgs a = args_for(H, n, tol);
-  for (int64_t i = 0; i < n; ++i) out[i] = uint8_t(exact::sphere_uncovered(a, int(i)));
+  std::vector<int> S(exact::kMaxSet);
+  std::vector<uint32_t> stack(kStack);
+  for (int64_t i = 0; i < n; ++i)
+    out[i] = uint8_t(exact::sphere_uncovered(a, int(i), S.data(), stack.data(), witness + 3 * i));
   return 0;
 }
 
-// the warp kernel's split: 32 lanes each testing their share of the points
-extern "C" int uncovered_host_lanes(const double* p, const double* s, int64_t n, double tol, uint8_t* out,
-                                    unsigned order_seed) {
+// uncovered intersection circles and points: the per-sphere test, then the
+// intersections routine for every uncovered sphere (in hierarchy order);
+// outputs unsorted, counts in cnt[0..1], status in *status
+extern "C" int intersections_host(const double* p, const double* s, int64_t n, double tol, int64_t cap_c,
+                                  int64_t* circ, int64_t cap_p, int64_t* quad, double* pts,
+                                  unsigned long long* cnt, unsigned* status, unsigned order_seed) {
   HostTree H;
   if (!build_tree(p, s, n, order_seed, H)) return -1;
   const QueryArgs a = args_for(H, n, tol);
-  std::vector<int> meet(exact::kMaxMeet);
-  for (int64_t i = 0; i < n; ++i) {
-    const int nn = std::fabs(H.sph[i].w) == 0.0 ? 0 : exact::gather_meet(a, int(i), meet.data());
-    int res = exact::trivial_case(a, int(i), nn);
-    if (res < 0) {
-      res = 0;
-      for (int lane = 0; lane < 32; ++lane)
-        if (exact::lane_candidates(a, int(i), meet.data(), nn, lane, 32, nullptr)) res = 1;
-    }
-    out[i] = uint8_t(res);
+  std::vector<int> S(exact::kMaxSet);
+  std::vector<uint32_t> stacks(3 * kStack);
+  std::vector<uint8_t> uncov(size_t(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) uncov[i] = uint8_t(exact::sphere_uncovered(a, int(i), S.data(), stacks.data(), nullptr));
+  cnt[0] = cnt[1] = 0;
+  *status = 0;
+  const exact::UDOut o{cnt, cap_c, cap_p, circ, quad, pts, status};
+  for (int64_t u = 0; u < n; ++u) {
+    const int i = a.sid[u];
+    if (uncov[i] != 0) exact::sphere_intersections(a, i, uncov.data(), S.data(), stacks.data(), o);
   }
   return 0;
 }

@@ -168,3 +168,18 @@ def test_insert_lost_witness_without_clamp(G, orc):
     xq = np.random.default_rng(7).uniform(-1, 1, size=(300, 3))
     fl = _compare(G, orc, w.p, w.s, w.tau, y, xq, clamp_opp=False)
     assert np.sum((fl & 0x80) != 0) >= 5
+
+
+def test_insert_exact_removal_repair(G, orc):
+    """Sec. 6 repair with the exact removal set: on the 10^3 CSG pseudo-SDF
+    the spheres that the other balls cover exactly (the oracle's Prop. 1
+    (ii) test: 117 of 1,000) are removed and re-inserted with their values
+    known, in index order and in a seeded permutation, step by step against
+    the sequential oracle."""
+    w = W.csg_pseudo_grid(N=10, tau=1)
+    covered = orc.sphere_uncovered(w.p, w.s) == 0
+    assert covered.sum() == 117
+    idx = np.nonzero(covered)[0]
+    xq = np.random.default_rng(12).uniform(-1, 1, size=(300, 3))
+    for sel in (idx, np.random.default_rng(13).permutation(idx)):
+        _compare(G, orc, w.p[~covered], w.s[~covered], w.tau, w.p[sel], xq, known=w.s[sel])

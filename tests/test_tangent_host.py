@@ -45,10 +45,11 @@ def host(tmp_path_factory):
     L.coverage_host.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, P, ctypes.c_int64, P, ctypes.c_double,
                                 ctypes.c_int, P, ctypes.c_uint]
     L.coverage_host.restype = ctypes.c_int
-    L.uncovered_host.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, P, ctypes.c_uint]
+    L.uncovered_host.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, P, P, ctypes.c_uint]
     L.uncovered_host.restype = ctypes.c_int
-    L.uncovered_host_lanes.argtypes = L.uncovered_host.argtypes
-    L.uncovered_host_lanes.restype = ctypes.c_int
+    L.intersections_host.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_int64, P, ctypes.c_int64, P,
+                                     P, P, P, ctypes.c_uint]
+    L.intersections_host.restype = ctypes.c_int
     L.points_host.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int, P, ctypes.c_int64, P, P, P]
     L.points_host.restype = ctypes.c_int
     L.scored_host.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int, ctypes.c_double, ctypes.c_int, P, P, P,
@@ -162,37 +163,119 @@ def test_host_cell_coverage_lattice_shells(host, orc):
         assert _coverage(host, centre[None], s, cell, origin, h, 8, 0.0, 0)[0] == count
 
 
-def _uncovered(host, p, s, tol, order, lanes=False):
+def _uncovered(host, p, s, tol, order):
     p, s = np.ascontiguousarray(p, np.float64), np.ascontiguousarray(s, np.float64)
     out = np.zeros(s.shape[0], np.uint8)
-    fn = host.uncovered_host_lanes if lanes else host.uncovered_host
-    assert fn(_ptr(p), _ptr(s), s.shape[0], tol, _ptr(out), order) == 0
-    return out
+    wit = np.full((s.shape[0], 3), np.nan)
+    assert host.uncovered_host(_ptr(p), _ptr(s), s.shape[0], tol, _ptr(out), _ptr(wit), order) == 0
+    return out, wit
+
+
+def check_witnesses(p, s, tol, out, wit):
+    """Each uncovered sphere's witness lies on the sphere and in no other
+    shrunk ball beyond rounding (it is a test point built on up to two other
+    spheres, which the test leaves out)."""
+    for i in np.nonzero(out == 1)[0]:
+        t = wit[i]
+        assert abs(np.linalg.norm(t - p[i]) - abs(s[i])) <= 1e-9 * (1 + abs(s[i]))
+        d = np.linalg.norm(p - t, axis=1)
+        rho = np.abs(s) - tol
+        inside = (d < rho - 1e-9) & (rho > 0)
+        inside[i] = False
+        assert not inside.any(), (i, np.nonzero(inside)[0][:4])
 
 
 def test_host_sphere_uncovered(host, orc):
     """Octahedral caps around the threshold rho = 0.919401, the 8^3 sphere
-    grid inflated by 1.2 (covered spheres), and valid and invalid tiny random
-    inputs, for tol = 0 and 1e-6: equal to the oracle sphere by sphere."""
+    grid inflated by 1.2 (covered spheres), and valid and invalid tiny
+    random inputs, for tol = 0 and 1e-6, and grids of exactly touching SDF
+    samples (sphere, CSG: a few covered spheres among many that are not)
+    for tol = 1e-6: equal to the oracle sphere by sphere, in eight hierarchy
+    orders, and every witness valid."""
     e = np.eye(3)
     cases = []
     for rho in (0.91, 0.9194, 0.9195, 0.93):
         cases.append((np.concatenate([np.zeros((1, 3)), e, -e]), np.array([1.0] + [rho] * 6)))
     w = W.sphere_grid(N=8, up=2, tau=2)
     cases.append((w.p, 1.2 * w.s))
-    cases.append((w.p, w.s))
+    # grids of SDF samples touch exactly: with tol = 0 some spheres keep only
+    # tangency points, where rounding decides; compared at the method's tol
+    exact_touch = [(w.p, w.s)]
+    for N in (6, 8):
+        w = W.csg_pseudo_grid(N=N, tau=1)
+        exact_touch.append((w.p, w.s))
     for seed in range(4):
         cases.append(W.tiny_random(40, seed, valid=(seed % 2 == 0), spread=0.35))
     p = np.array([[0.0, 0, 0], [0.1, 0, 0], [0.9, 0, 0], [0.0, 0, 0]])
     cases.append((p, np.array([0.5, 0.0, 0.0, 0.5])))      # zero samples, a duplicated ball
     cases.append((np.array([[0.0, 0, 0], [0.3, 0, 0]]), np.array([0.25, 0.25])))   # one circle each
-    for p, s in cases:
-        for tol in (0.0, 1e-6):
+    for (p, s), tols in [(c, (0.0, 1e-6)) for c in cases] + [(c, (1e-6,)) for c in exact_touch]:
+        for tol in tols:
             want = orc.sphere_uncovered(p, s, tol=tol)
-            for order in (0, 5):
-                assert np.array_equal(_uncovered(host, p, s, tol, order), want)
-            # the warp kernel's split of the test points over 32 lanes
-            assert np.array_equal(_uncovered(host, p, s, tol, 0, lanes=True), want)
+            for order in range(8):
+                got, wit = _uncovered(host, p, s, tol, order)
+                assert np.array_equal(got, want), (np.nonzero(got != want)[0][:8], got[got != want][:8])
+                check_witnesses(p, s, tol, got, wit)
+                assert np.all(np.isnan(wit[got != 1]))
+
+
+def test_host_sphere_uncovered_csg10(host, orc):
+    """The 10^3 CSG pseudo-SDF grid: 117 of 1,000 spheres are exactly
+    covered; the certificate decides every sphere as the full enumeration
+    does, in eight hierarchy orders."""
+    w = W.csg_pseudo_grid(N=10, tau=1)
+    want = orc.sphere_uncovered(w.p, w.s)
+    for order in range(8):
+        got, wit = _uncovered(host, w.p, w.s, 1e-6, order)
+        assert np.array_equal(got, want)
+    assert int(np.sum(want == 0)) == 117
+    check_witnesses(w.p, w.s, 1e-6, got, wit)
+
+
+def _intersections(host, p, s, tol, order):
+    p, s = np.ascontiguousarray(p, np.float64), np.ascontiguousarray(s, np.float64)
+    cap = 200000
+    circ = np.zeros((cap, 2), np.int64)
+    quad = np.zeros((cap, 4), np.int64)
+    pts = np.zeros((cap, 3), np.float64)
+    cnt = np.zeros(2, np.uint64)
+    status = np.zeros(1, np.uint32)
+    assert host.intersections_host(_ptr(p), _ptr(s), s.shape[0], tol, cap, _ptr(circ), cap, _ptr(quad), _ptr(pts),
+                                   _ptr(cnt), _ptr(status), order) == 0
+    nc, npt = int(cnt[0]), int(cnt[1])
+    assert nc <= cap and npt <= cap and status[0] == 0
+    circ, quad, pts = circ[:nc], quad[:npt], pts[:npt]
+    oc = np.lexsort((circ[:, 1], circ[:, 0]))
+    oq = np.lexsort((quad[:, 3], quad[:, 2], quad[:, 1], quad[:, 0]))
+    return circ[oc], quad[oq], pts[oq]
+
+
+def test_host_uncovered_intersections(host, orc):
+    """Uncovered circles and points: the triangle and octahedral cases, the
+    inflated sphere grid and valid and invalid tiny random inputs for tol 0
+    and 1e-6, grids of exactly touching SDF samples (sphere, CSG) for tol
+    1e-6, eight hierarchy orders: the same sorted lists as the oracle,
+    points bit for bit."""
+    h = np.sqrt(3) / 2
+    cases = [(np.array([[0.0, 0, 0], [1.0, 0, 0], [0.5, h, 0], [0.5, h / 3, 1.3]]), np.array([1.0, 1, 1, 0.6]))]
+    e = np.eye(3)
+    for rho in (0.91, 0.93):
+        cases.append((np.concatenate([np.zeros((1, 3)), e, -e]), np.array([1.0] + [rho] * 6)))
+    w = W.sphere_grid(N=6, up=2, tau=2)
+    cases += [(w.p, 1.2 * w.s)]
+    exact_touch = [(w.p, w.s)]
+    w = W.csg_pseudo_grid(N=6, tau=1)
+    exact_touch.append((w.p, w.s))
+    for seed in range(4):
+        cases.append(W.tiny_random(40, seed, valid=(seed % 2 == 0), spread=0.35))
+    for (p, s), tols in [(c, (0.0, 1e-6)) for c in cases] + [(c, (1e-6,)) for c in exact_touch]:
+        for tol in tols:
+            wc, wq, wp = orc.uncovered_intersections(p, s, tol=tol)
+            for order in range(8):
+                gc, gq, gp = _intersections(host, p, s, tol, order)
+                assert np.array_equal(gc, wc), (len(gc), len(wc))
+                assert np.array_equal(gq, wq), (len(gq), len(wq))
+                assert np.array_equal(gp, wp)
 
 
 def test_host_argmin_points(host, orc):
