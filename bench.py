@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--tangent-every", type=int, default=256,
                     help="tangent sub-benchmark: use every k-th of the 253^3 points (the pass is FP64, one "
                          "thread per point)")
+    ap.add_argument("--exact-csg", type=int, default=64,
+                    help="exact-coverage sub-benchmark: side of the CSG grid")
+    ap.add_argument("--exact-only-csg", action="store_true",
+                    help="exact-coverage sub-benchmark: the CSG grid alone (small cases for profiler captures)")
     ap.add_argument("--scored-every", type=int, default=256,
                     help="scored sub-benchmark: use every k-th of the 253^3 points")
     ap.add_argument("--query-subsample", type=int, default=1,
@@ -741,7 +745,7 @@ def extra_refine_order(N=64):
     return res
 
 
-def extra_exact_coverage():
+def extra_exact_coverage(csg_n=64, only_csg=False):
     """Exact coverage of each sample sphere (gfs_sphere_uncovered, Prop. 1
     (ii)): the 12^3 sphere grid (exact SDF samples: all keep an uncovered
     point), the 10^3 sphere grid with every value scaled by 1.2 (covered
@@ -751,9 +755,9 @@ def extra_exact_coverage():
     from paper_2605_01919_gb300 import gfs
     from paper_2605_01919_gb300 import workloads as W
     res = {}
-    cases = [("sphere12_exact_sdf", W.sphere_grid(N=12, up=2, tau=2), 1.0),
-             ("sphere10_inflated_1.2", W.sphere_grid(N=10, up=2, tau=2), 1.2),
-             ("csg64_pseudo_sdf", W.csg_pseudo_grid(N=64, tau=2), 1.0)]
+    cases = [] if only_csg else [("sphere12_exact_sdf", W.sphere_grid(N=12, up=2, tau=2), 1.0),
+                                 ("sphere10_inflated_1.2", W.sphere_grid(N=10, up=2, tau=2), 1.2)]
+    cases.append((f"csg{csg_n}_pseudo_sdf", W.csg_pseudo_grid(N=csg_n, tau=2), 1.0))
     for name, w, f in cases:
         s = np.ascontiguousarray(f * w.s)
         ctx = gfs.Context(tau=2)
@@ -990,7 +994,7 @@ if __name__ == "__main__":
               "scored": lambda: extra_scored(a.scored_every),
               "tangent": lambda: extra_tangent(a.tangent_every),
               "refine_order": extra_refine_order,
-              "exact_coverage": extra_exact_coverage}[a.only]
+              "exact_coverage": lambda: extra_exact_coverage(a.exact_csg, a.exact_only_csg)}[a.only]
         print(json.dumps(_finite({a.only: fn()})), flush=True)
     elif a.impl == "reference":
         run_reference(a)

@@ -147,7 +147,7 @@ struct gfs_ctx {
   // valid while csr_state equals state_id (every build or insertion changes it)
   DevBuf csr_ids, csr_off, scored_status;
   // uncovered intersection circles and points (raw outputs, sort buffers)
-  DevBuf ud_uncov, ud_cnt, ud_circ, ud_quad, ud_pts, ud_k0, ud_k1, ud_v0, ud_v1;
+  DevBuf ud_uncov, ud_cnt, ud_pairs, ud_circ, ud_quad, ud_pts, ud_k0, ud_k1, ud_v0, ud_v1;
   int64_t state_id = 0, csr_state = -1;
   int64_t ins_rounds = 0, ins_steps = 0, ins_rebuilds = 0, ins_queried = 0;  // of the last insertion call
   double ins_ms_total = 0.0, ins_ms_rebuild = 0.0, ins_ms_final = 0.0;  // host wall time of its phases
@@ -618,6 +618,21 @@ int gfs_uncovered_intersections(gfs_ctx* c, int64_t cap_circles, int64_t* circle
   GFS_TRY(ensure(c->ud_uncov, size_t(c->n) + 16));
   GFS_TRY(ensure(c->ud_cnt, 32));
   GFS_CK(launch_sphere_uncovered(a, c->ud_uncov.as<uint8_t>(), nullptr, st));
+  // the pairs of uncovered spheres that cut in a circle: a first guess of
+  // the capacity, then exactly the count (the walk is deterministic)
+  int64_t cap_pairs = std::max<int64_t>(1 << 20, 16 * c->n);
+  unsigned long long hpairs = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    GFS_TRY(ensure(c->ud_pairs, size_t(cap_pairs) * 8));
+    GFS_CK(cudaMemsetAsync(c->ud_cnt.p, 0, 32, st));
+    GFS_CK(launch_ud_pairs(a, c->ud_uncov.as<uint8_t>(), c->ud_pairs.as<unsigned long long>(), cap_pairs,
+                           c->ud_cnt.as<unsigned long long>() + 3, st));
+    GFS_CK(cudaMemcpyAsync(&hpairs, c->ud_cnt.as<unsigned long long>() + 3, 8, cudaMemcpyDeviceToHost, st));
+    GFS_CK(cudaStreamSynchronize(st));
+    if (int64_t(hpairs) <= cap_pairs) break;
+    if (pass == 1) return GFS_ERR_CUDA;  // cannot happen: the second walk finds the same pairs
+    cap_pairs = int64_t(hpairs);
+  }
   // raw outputs: a first guess, then exactly the counts (the decisions do not
   // depend on the capacities, so a second run finds the same entries)
   int64_t cap_c = std::max<int64_t>(4096, c->n), cap_p = std::max<int64_t>(4096, c->n);
@@ -630,7 +645,7 @@ int gfs_uncovered_intersections(gfs_ctx* c, int64_t cap_circles, int64_t* circle
     GFS_CK(cudaMemsetAsync(c->ud_cnt.p, 0, 32, st));
     exact::UDOut o{c->ud_cnt.as<unsigned long long>(), cap_c, cap_p, c->ud_circ.as<int64_t>(), c->ud_quad.as<int64_t>(),
                    c->ud_pts.as<double>(), reinterpret_cast<unsigned*>(c->ud_cnt.as<unsigned long long>() + 2)};
-    GFS_CK(launch_intersections(a, c->ud_uncov.as<uint8_t>(), o, st));
+    GFS_CK(launch_intersections(a, c->ud_pairs.as<unsigned long long>(), int64_t(hpairs), o, st));
     GFS_CK(cudaMemcpyAsync(hc, c->ud_cnt.p, 16, cudaMemcpyDeviceToHost, st));
     GFS_CK(cudaMemcpyAsync(&hstatus, c->ud_cnt.as<unsigned long long>() + 2, 4, cudaMemcpyDeviceToHost, st));
     GFS_CK(cudaStreamSynchronize(st));

@@ -165,11 +165,57 @@ __device__ inline int first_member(const QueryArgs& a, int i, uint32_t* stack) {
   return -1;
 }
 
+// The test points of certificate entry (n, u), u <= n: for u < n the two
+// points S_i shares with the shrunk spheres of members S[u] and S[n] (taken
+// in increasing index order, as the full enumeration does), for u = n the
+// two points of S[n]'s circle nearest to and farthest from ref.  k and m
+// receive the members the points were built from (m = -1 for a circle).
+__device__ inline bool entry_points(const QueryArgs& a, const double* pi, double ri, const double* ref, const int* S,
+                                    int n, int u, double* pts, int& k, int& m) {
+  k = S[n];
+  m = u < n ? S[u] : -1;
+  const D4 Q = a.sph64[k];
+  const double pk[3] = {Q.x, Q.y, Q.z};
+  const double rk = __dsub_rn(fabs(Q.w), a.tol);
+  if (m < 0) return circle_points(pi, ri, pk, rk, ref, pts);
+  const D4 R = a.sph64[m];
+  const double pm[3] = {R.x, R.y, R.z};
+  const double rm = __dsub_rn(fabs(R.w), a.tol);
+  const bool km = k < m;
+  return triple_points(pi, ri, km ? pk : pm, km ? rk : rm, km ? pm : pk, km ? rm : rk, pts);
+}
+
+// Is t held by a member of S[0, ns) other than k and m?  last: the member
+// that held the previous point (tested first; updated).
+__device__ inline bool held_by_member(const QueryArgs& a, const double* t, const int* S, int ns, int k, int m,
+                                      int& last) {
+  if (last >= 0) {
+    const int o = S[last];
+    if (o != k && o != m && ex_cov(t[0], t[1], t[2], a.sph64[o], a.tol)) return true;
+  }
+  for (int u = 0; u < ns; ++u) {
+    const int o = S[u];
+    if (u == last || o == k || o == m) continue;
+    if (ex_cov(t[0], t[1], t[2], a.sph64[o], a.tol)) {
+      last = u;
+      return true;
+    }
+  }
+  return false;
+}
+
+// The reference point of sphere i's circles: p_i + (|s_i| + 1) e.
+__device__ inline void circle_ref(const double* pi, double ri, double* ref) {
+  const double e_ref[3] = {0.36, 0.48, 0.8};
+  for (int c = 0; c < 3; ++c) ref[c] = __dadd_rn(pi[c], __dmul_rn(__dadd_rn(ri, 1.0), e_ref[c]));
+}
+
 // The certificate: members in the order they joined.
 struct Cert {
   int* S;
   int ns;
   uint32_t* stack;  // kStack entries for the hierarchy walks
+  int last;         // the member that held the latest covered point (tested first)
 };
 
 // Add ball j (found to hold a point of sphere i) to the certificate when it
@@ -188,11 +234,8 @@ __device__ inline bool join(const QueryArgs& a, const D4& P, double ri, int j, C
 // not a member); -1 when the certificate is full.
 __device__ inline int test_point(const QueryArgs& a, const D4& P, double ri, int i, const double* t, int k, int m,
                                  Cert& C) {
-  for (int u = 0; u < C.ns; ++u) {
-    const int o = C.S[u];
-    if (o == k || o == m) continue;
-    if (ex_cov(t[0], t[1], t[2], a.sph64[o], a.tol)) return 0;
-  }
+  // neighbouring test points are mostly held by the same member
+  if (held_by_member(a, t, C.S, C.ns, k, m, C.last)) return 0;
   const int j = tangent::covered_except_on(C.stack, a, t[0], t[1], t[2], i, k, m);
   if (j < 0) return 1;
   return join(a, P, ri, j, C) ? 0 : -1;
@@ -201,7 +244,8 @@ __device__ inline int test_point(const QueryArgs& a, const D4& P, double ri, int
 // 1: sphere i (input index) keeps an uncovered point (witness, when not
 // null, receives it: a test point, or p_i for a zero sample); 0: every point
 // is covered; 2: undecided (the certificate outgrew kMaxSet members).
-// S: kMaxSet entries; stack: kStack entries.
+// S: kMaxSet entries; stack: kStack entries.  One thread; the GPU kernel
+// runs the same steps with the 32 lanes of a warp sharing one certificate.
 __device__ inline int sphere_uncovered(const QueryArgs& a, int i, int* S, uint32_t* stack, double* witness) {
   const D4 P = a.sph64[i];
   const double pi[3] = {P.x, P.y, P.z};
@@ -212,7 +256,7 @@ __device__ inline int sphere_uncovered(const QueryArgs& a, int i, int* S, uint32
       for (int c = 0; c < 3; ++c) witness[c] = pi[c];
     return 1;
   }
-  Cert C{S, 0, stack};
+  Cert C{S, 0, stack, -1};
   // probe points p_i +- r_i e_c: the balls that hold them start the
   // certificate (they are not test points: an uncovered probe decides nothing)
   for (int c = 0; c < 6; ++c) {
@@ -230,30 +274,14 @@ __device__ inline int sphere_uncovered(const QueryArgs& a, int i, int* S, uint32
     }
     S[C.ns++] = k;
   }
-  const double e_ref[3] = {0.36, 0.48, 0.8};
   double ref[3];
-  for (int c = 0; c < 3; ++c) ref[c] = __dadd_rn(pi[c], __dmul_rn(__dadd_rn(ri, 1.0), e_ref[c]));
+  circle_ref(pi, ri, ref);
   double pts[6];
   for (int n = 0; n < C.ns; ++n) {
-    const int k = S[n];
-    const D4 Q = a.sph64[k];
-    const double pk[3] = {Q.x, Q.y, Q.z};
-    const double rk = __dsub_rn(fabs(Q.w), a.tol);
-    // the pairs of k with the members before it, then k's circle
+    // the pairs of member n with the members before it, then its circle
     for (int u = 0; u <= n; ++u) {
-      const int m = u < n ? S[u] : -1;
-      bool have;
-      if (m < 0) {
-        have = circle_points(pi, ri, pk, rk, ref, pts);
-      } else {
-        const D4 R = a.sph64[m];
-        const double pm[3] = {R.x, R.y, R.z};
-        const double rm = __dsub_rn(fabs(R.w), a.tol);
-        // the full enumeration takes each pair in increasing index order
-        const bool km = k < m;
-        have = triple_points(pi, ri, km ? pk : pm, km ? rk : rm, km ? pm : pk, km ? rm : rk, pts);
-      }
-      if (!have) continue;
+      int k, m;
+      if (!entry_points(a, pi, ri, ref, S, n, u, pts, k, m)) continue;
       for (int h = 0; h < 2; ++h) {
         const int r = test_point(a, P, ri, i, pts + 3 * h, k, m, C);
         if (r < 0) return 2;
@@ -296,7 +324,7 @@ __device__ inline int sphere_uncovered(const QueryArgs& a, int i, int* S, uint32
 // M: kMaxSet entries; stack: kStack entries.
 __device__ inline int circle_uncovered(const QueryArgs& a, int i, int j, const double* pi, double ri,
                                        const double* pj, double rj, const double* q, int* M, uint32_t* stack) {
-  int nm = 0;
+  int nm = 0, last = -1;
   // ball b holds a point of C_ij: joins M; 2 when it holds the whole circle
   auto join = [&](int b) -> int {
     for (int u = 0; u < nm; ++u)
@@ -311,9 +339,14 @@ __device__ inline int circle_uncovered(const QueryArgs& a, int i, int j, const d
   };
   // 1: no ball holds t; 0: held; 2: held by a ball that holds the circle; -1: full
   auto test = [&](const double* t, int m) -> int {
+    if (last >= 0 && M[last] != m && ex_cov(t[0], t[1], t[2], a.sph64[M[last]], a.tol)) return 0;
     for (int u = 0; u < nm; ++u) {
       const int o = M[u];
-      if (o != m && ex_cov(t[0], t[1], t[2], a.sph64[o], a.tol)) return 0;
+      if (u == last || o == m) continue;
+      if (ex_cov(t[0], t[1], t[2], a.sph64[o], a.tol)) {
+        last = u;
+        return 0;
+      }
     }
     const int b = tangent::covered_except_on(stack, a, t[0], t[1], t[2], i, j, m);
     if (b < 0) return 1;
@@ -415,12 +448,11 @@ __device__ inline void circle_points_u(const QueryArgs& a, int i, int j, const d
   }
 }
 
-// Every circle C_ij, j > i, of sphere i (input index; uncov: the per-sphere
-// exact test, 0 = covered), with its uncovered points.  stacks: 3 kStack
-// entries (the walk over j, the certificate's and the point walk's, the
-// point tests'); M: kMaxSet entries.
-__device__ inline void sphere_intersections(const QueryArgs& a, int i, const uint8_t* uncov, int* M,
-                                            uint32_t* stacks, const UDOut& o) {
+// The circles of sphere i (input index) with the spheres after it: every
+// j > i with uncov[j] != 0 whose sphere cuts sphere i in a circle (the
+// construction of circle_points), passed to emit(j).  stack: kStack entries.
+template <class Emit>
+__device__ inline void sphere_pairs(const QueryArgs& a, int i, const uint8_t* uncov, uint32_t* stack, Emit emit) {
   const D4 P = a.sph64[i];
   const double ri = fabs(P.w);
   if (!(ri > 0.0)) return;
@@ -430,7 +462,6 @@ __device__ inline void sphere_intersections(const QueryArgs& a, int i, const uin
   for (int c = 0; c < 3; ++c) ref[c] = __dadd_rn(pi[c], __dmul_rn(__dadd_rn(ri, 1.0), e_ref[c]));
   const float x32 = float(P.x), y32 = float(P.y), z32 = float(P.z), ax = tangent::amax3(x32, y32, z32);
   const float ri32 = tangent::f_up(ri);
-  uint32_t* stack = stacks;
   const Tree& T = a.st;
   int sp = 0;
   const int top = T.nlevels - 1;
@@ -449,15 +480,7 @@ __device__ inline void sphere_intersections(const QueryArgs& a, int i, const uin
         if (!(rj > 0.0)) continue;
         const double pj[3] = {Q.x, Q.y, Q.z};
         double q[6];
-        if (!circle_points(pi, ri, pj, rj, ref, q)) continue;
-        int r = circle_uncovered(a, i, j, pi, ri, pj, rj, q, M, stacks + kStack);
-        if (r < 0) {
-          atomicOr(o.status, 1u);
-          r = 1;
-        }
-        if (r == 0) continue;
-        ud_record_circle(o, i, j);
-        circle_points_u(a, i, j, pi, ri, pj, rj, stacks + kStack, stacks + 2 * kStack, o);
+        if (circle_points(pi, ri, pj, rj, ref, q)) emit(j);
       }
     } else {
       const int64_t cb = idx * kFan, ce = tangent::imin64(cb + kFan, T.count[lev - 1]);
@@ -470,6 +493,29 @@ __device__ inline void sphere_intersections(const QueryArgs& a, int i, const uin
       }
     }
   }
+}
+
+// Circle C_ij (i < j, both spheres cut in a circle): its certificate, and on
+// an uncovered circle its uncovered points.  stacks: 2 kStack entries (the
+// certificate's and the point walk's, the point tests'); M: kMaxSet entries.
+__device__ inline void circle_intersections(const QueryArgs& a, int i, int j, int* M, uint32_t* stacks,
+                                            const UDOut& o) {
+  const D4 P = a.sph64[i], Q = a.sph64[j];
+  const double ri = fabs(P.w), rj = fabs(Q.w);
+  const double pi[3] = {P.x, P.y, P.z}, pj[3] = {Q.x, Q.y, Q.z};
+  const double e_ref[3] = {0.36, 0.48, 0.8};
+  double ref[3];
+  for (int c = 0; c < 3; ++c) ref[c] = __dadd_rn(pi[c], __dmul_rn(__dadd_rn(ri, 1.0), e_ref[c]));
+  double q[6];
+  if (!circle_points(pi, ri, pj, rj, ref, q)) return;
+  int r = circle_uncovered(a, i, j, pi, ri, pj, rj, q, M, stacks);
+  if (r < 0) {
+    atomicOr(o.status, 1u);
+    r = 1;
+  }
+  if (r == 0) return;
+  ud_record_circle(o, i, j);
+  circle_points_u(a, i, j, pi, ri, pj, rj, stacks, stacks + kStack, o);
 }
 
 }  // namespace exact

@@ -24,9 +24,14 @@ struct UDOut {
 };
 }  // namespace exact
 
-// circles with an uncovered point and uncovered points (unsorted, appended
-// through o.cnt) of the spheres with uncov[i] != 0
-cudaError_t launch_intersections(const QueryArgs& a, const uint8_t* uncov, const exact::UDOut& o, cudaStream_t st);
+// pairs i < j of spheres with uncov != 0 that cut in a circle, as
+// (i << 32) | j, appended through *count (written below cap)
+cudaError_t launch_ud_pairs(const QueryArgs& a, const uint8_t* uncov, unsigned long long* pairs, int64_t cap,
+                            unsigned long long* count, cudaStream_t st);
+// the circles of the pairs with an uncovered point, and their uncovered
+// points (unsorted, appended through o.cnt)
+cudaError_t launch_intersections(const QueryArgs& a, const unsigned long long* pairs, int64_t np,
+                                 const exact::UDOut& o, cudaStream_t st);
 cudaError_t launch_ud_circle_keys(const int64_t* circ, int64_t nc, unsigned long long* key, cudaStream_t st);
 // primary = 0: keys (m << 1) | side of quad[order[k]] (order may be null);
 // primary = 1: keys (i << 32) | j; val[k] = the quad index

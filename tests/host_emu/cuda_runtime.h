@@ -19,6 +19,7 @@ struct float4 {
 struct uint4 {
   unsigned x, y, z, w;
 };
+inline float4 make_float4(float x, float y, float z, float w) { return float4{x, y, z, w}; }
 typedef int cudaError_t;
 typedef void* cudaStream_t;
 static const int cudaSuccess = 0;

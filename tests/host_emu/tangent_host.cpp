@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <random>
+#include <utility>
 #include <vector>
 
 #include "gfs_exact.cuh"
@@ -201,10 +202,14 @@ extern "C" int intersections_host(const double* p, const double* s, int64_t n, d
   cnt[0] = cnt[1] = 0;
   *status = 0;
   const exact::UDOut o{cnt, cap_c, cap_p, circ, quad, pts, status};
+  // the pair list of the first kernel, then one circle at a time
+  std::vector<std::pair<int, int>> pairs;
   for (int64_t u = 0; u < n; ++u) {
     const int i = a.sid[u];
-    if (uncov[i] != 0) exact::sphere_intersections(a, i, uncov.data(), S.data(), stacks.data(), o);
+    if (uncov[i] != 0)
+      exact::sphere_pairs(a, i, uncov.data(), stacks.data() + 2 * kStack, [&](int j) { pairs.emplace_back(i, j); });
   }
+  for (const auto& pr : pairs) exact::circle_intersections(a, pr.first, pr.second, S.data(), stacks.data(), o);
   return 0;
 }
 
