@@ -275,7 +275,10 @@ int gfs_insert(gfs_ctx* ctx, const double* y, int64_t T, double* s_out, int64_t*
  *    overlaps on the GPU (different streams, or different contexts on the
  *    same device) race on it and must be ordered by the caller.
  *  - The first call on a device looks up the array's device address (no
- *    allocation); make that first call before any stream capture.
+ *    allocation); make that first call before any stream capture.  The
+ *    address is kept for the life of the process: it stays valid while the
+ *    device's primary context lives (after cudaDeviceReset the library must
+ *    not be used without reloading it).
  * Arguments and other errors: as gfs_query_backward. */
 #define GFS_NOALLOC_MAX_SPHERES 262144
 int gfs_query_backward_noalloc(gfs_ctx* ctx, const void* x, int x_is_fp32, int64_t m, const float* s,

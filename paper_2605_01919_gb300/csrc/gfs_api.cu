@@ -75,6 +75,15 @@ void release(DevBuf& b) {
   b.bytes = 0;
 }
 
+// A scratch buffer of one call, released when the call returns.
+struct Scratch {
+  DevBuf b;
+  Scratch() = default;
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  ~Scratch() { release(b); }
+};
+
 // Level sizes of the implicit hierarchy over nitems items.
 void tree_layout(Tree& T, int64_t nitems) {
   std::memset(&T, 0, sizeof(T));
@@ -633,6 +642,23 @@ int gfs_uncovered_intersections(gfs_ctx* c, int64_t cap_circles, int64_t* circle
     if (pass == 1) return GFS_ERR_CUDA;  // cannot happen: the second walk finds the same pairs
     cap_pairs = int64_t(hpairs);
   }
+  // pairs in (i, j) order: a warp's circles then share sphere i and walk
+  // the same part of the hierarchy (the decisions do not depend on it)
+  if (hpairs > 1) {
+    if (hpairs >= (1ull << 31)) return GFS_ERR_TOO_LARGE;
+    GFS_TRY(ensure(c->ud_k1, size_t(hpairs) * 8));
+    GFS_TRY(ensure(c->ud_v0, size_t(hpairs) * 4));
+    GFS_TRY(ensure(c->ud_v1, size_t(hpairs) * 4));
+    size_t bytes = 0;
+    GFS_CK(sort_pairs64(nullptr, bytes, c->ud_pairs.as<unsigned long long>(), c->ud_k1.as<unsigned long long>(),
+                        c->ud_v0.as<int>(), c->ud_v1.as<int>(), int64_t(hpairs), 64, st));
+    GFS_TRY(cub_ensure(c, bytes));
+    bytes = c->cub_temp.bytes;
+    GFS_CK(sort_pairs64(c->cub_temp.p, bytes, c->ud_pairs.as<unsigned long long>(),
+                        c->ud_k1.as<unsigned long long>(), c->ud_v0.as<int>(), c->ud_v1.as<int>(), int64_t(hpairs), 64,
+                        st));
+    std::swap(c->ud_pairs, c->ud_k1);
+  }
   // raw outputs: a first guess, then exactly the counts (the decisions do not
   // depend on the capacities, so a second run finds the same entries)
   int64_t cap_c = std::max<int64_t>(4096, c->n), cap_p = std::max<int64_t>(4096, c->n);
@@ -747,7 +773,9 @@ int gfs_query_scored(gfs_ctx* c, const void* x, int x_is_fp32, int64_t m, float*
   // per-sphere survivor lists of the current state (built once per state)
   if (c->csr_state != c->state_id) {
     const int64_t tot = int64_t(c->nsurv[0]) + c->nsurv[1];
-    DevBuf ids, cnt;
+    Scratch ids_s, cnt_s;  // released on every return
+    DevBuf& ids = ids_s.b;
+    DevBuf& cnt = cnt_s.b;
     GFS_TRY(ensure(ids, size_t(tot) * 4 + 16));
     GFS_TRY(ensure(cnt, 16));
     GFS_TRY(ensure(c->csr_ids, size_t(tot) * 4 + 16));
@@ -809,16 +837,16 @@ constexpr int kInsNear = 1024;  // the kernels' per-new-sphere list capacity (kN
 // tombstone, then the dynamic lists) into surv_raw.
 int ins_compact_survivors(gfs_ctx* c, const InsMisc& hm) {
   cudaStream_t st = c->stream;
-  DevBuf cnt;
+  Scratch cnt_s;  // released on every return
+  DevBuf& cnt = cnt_s.b;
   GFS_TRY(ensure(cnt, 16));
   for (int k = 0; k < 2; ++k) {
     const unsigned nd = unsigned(hm.ndyn) * unsigned(c->KS);
     const unsigned need = c->nsurv[k] + nd;
     if (size_t(need) * sizeof(float4) > c->surv_raw[k].bytes) {
-      DevBuf fresh;
-      GFS_TRY(ensure(fresh, size_t(need) * sizeof(float4) + 16));
-      std::swap(fresh, c->surv_raw[k]);
-      release(fresh);
+      Scratch fresh;
+      GFS_TRY(ensure(fresh.b, size_t(need) * sizeof(float4) + 16));
+      std::swap(fresh.b, c->surv_raw[k]);  // the old buffer is released with fresh
     }
     unsigned hc = 0;
     GFS_CK(cudaMemsetAsync(cnt.p, 0, 4, st));
@@ -827,14 +855,10 @@ int ins_compact_survivors(gfs_ctx* c, const InsMisc& hm) {
                               c->surv_raw[k].as<float4>(), cnt.as<unsigned>(), st));
     GFS_CK(cudaMemcpyAsync(&hc, cnt.p, 4, cudaMemcpyDeviceToHost, st));
     GFS_CK(cudaStreamSynchronize(st));
-    if (hc > kMaxSurvivors) {
-      release(cnt);
-      return GFS_ERR_TOO_LARGE;
-    }
+    if (hc > kMaxSurvivors) return GFS_ERR_TOO_LARGE;
     c->nsurv[k] = hc;
     c->cap = std::max(c->cap, hc);
   }
-  release(cnt);
   return GFS_OK;
 }
 
@@ -1076,15 +1100,13 @@ int gfs_insert_known(gfs_ctx* c, const double* y, const double* known, int64_t T
   }
   const int64_t n_final = n0 + hm.ninserted;
   {
-    DevBuf sph_new, wit_new;
-    GFS_TRY(ensure(sph_new, std::max(c->sph64.bytes, size_t(cap) * sizeof(D4))));
-    GFS_TRY(ensure(wit_new, std::max(c->witness64.bytes, size_t(cap) * 24)));
-    GFS_CK(launch_ins_renumber(a, c->ins_scan.as<int>(), sph_new.as<D4>(), wit_new.as<double>(), st));
+    Scratch sph_new, wit_new;  // after the swaps they hold (and release) the old arrays
+    GFS_TRY(ensure(sph_new.b, std::max(c->sph64.bytes, size_t(cap) * sizeof(D4))));
+    GFS_TRY(ensure(wit_new.b, std::max(c->witness64.bytes, size_t(cap) * 24)));
+    GFS_CK(launch_ins_renumber(a, c->ins_scan.as<int>(), sph_new.b.as<D4>(), wit_new.b.as<double>(), st));
     GFS_CK(cudaStreamSynchronize(st));
-    std::swap(sph_new, c->sph64);
-    std::swap(wit_new, c->witness64);
-    release(sph_new);
-    release(wit_new);
+    std::swap(sph_new.b, c->sph64);
+    std::swap(wit_new.b, c->witness64);
   }
   for (int k = 0; k < 2; ++k)
     GFS_CK(launch_ins_remap_survivors(c->surv_raw[k].as<float4>(), c->nsurv[k], c->ins_scan.as<int>(), int(n0),
@@ -1823,7 +1845,8 @@ void gfs_destroy(gfs_ctx* c) {
                     &c->ins_dtomb[1], &c->ins_misc, &c->ins_maxrem, &c->ins_slot_t, &c->ins_slots, &c->ins_cbuf,
                     &c->ins_new, &c->ins_lost, &c->ins_inserted, &c->ins_codes, &c->ins_dyn, &c->ins_present,
                     &c->ins_scan, &c->ins_cmp, &c->ins_dynf4, &c->ins_near, &c->ins_nearcnt, &c->csr_ids,
-                    &c->csr_off, &c->scored_status,
+                    &c->csr_off, &c->scored_status, &c->ud_uncov, &c->ud_cnt, &c->ud_pairs, &c->ud_circ,
+                    &c->ud_quad, &c->ud_pts, &c->ud_k0, &c->ud_k1, &c->ud_v0, &c->ud_v1,
                     &c->b_desc, &c->b_offd, &c->b_qoffd, &c->b_sph64, &c->b_k64in, &c->b_k64out, &c->b_sph,
                     &c->b_thr, &c->b_sid, &c->b_bits, &c->b_bcs, &c->b_lo, &c->b_hi, &c->b_na, &c->b_nb, &c->b_nf,
                     &c->b_stdev, &c->b_prefix, &c->b_ctr, &c->b_cnt, &c->b_cviews, &c->b_cw, &c->b_sraw[0],

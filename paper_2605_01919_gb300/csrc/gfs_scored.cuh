@@ -255,6 +255,46 @@ __device__ inline void scored_one(const QueryArgs& a, int box_cull, const uint32
     uint32_t stack[2 * kStack];
     uint32_t* const cstack = stack + kStack;
     int sp = 0;
+    // the balls that covered the latest tangent points: neighbouring
+    // tangent points are mostly covered by the same few large balls, so
+    // these are tested before a walk (a ball found here is one the walk
+    // could have returned: the decision is the same)
+    int hint[4] = {-1, -1, -1, -1};
+    float4 hintf[4];  // their centres in FP32 and radius - tol rounded down
+    int hint_at = 0;
+    auto uncovered_tan = [&](double tx, double ty, double tz, int j) -> bool {
+      for (int u = 0; u < 4; ++u) {
+        const int c = hint[u];
+        if (c >= 0 && c != j && ex_cov(tx, ty, tz, a.sph64[c], a.tol)) return false;
+      }
+      const int o = tangent::covered_except_on(cstack, a, tx, ty, tz, j, -1, -1);
+      if (o < 0) return true;
+      const D4 Q = a.sph64[o];
+      hint[hint_at] = o;
+      hintf[hint_at] = make_float4(float(Q.x), float(Q.y), float(Q.z), tangent::f_dn(__dsub_rn(fabs(Q.w), tol)));
+      hint_at = (hint_at + 1) & 3;
+      return false;
+    };
+    // Is the tangent point p + sr (x - p)/d of sphere j (FP32 copy S) surely
+    // inside a cached ball other than j?  t32 is within mt of the exact
+    // point (roundings of x, p, the direction and the sum, taken four
+    // times over); the distance test keeps err32's margin on top.
+    auto surely_covered = [&](const float4& S, float d32, float sr, int j) -> bool {
+      const float ap = amax3(S.x, S.y, S.z), r = fabsf(sr);
+      if (!(d32 > 1e-3f * (F.ax + ap + r))) return false;
+      const float inv = 1.f / d32;
+      const float tx = S.x + sr * ((F.x32 - S.x) * inv), ty = S.y + sr * ((F.y32 - S.y) * inv),
+                  tz = S.z + sr * ((F.z32 - S.z) * inv);
+      const float mt = 64.f * 5.9604645e-8f * (F.ax + ap + r) * (1.f + r * inv);
+      const float at = amax3(tx, ty, tz);
+      for (int u = 0; u < 4; ++u) {
+        if (hint[u] < 0 || hint[u] == j) continue;
+        const float4 H = hintf[u];
+        const float dd = dist32(tx, ty, tz, H);
+        if (dd + mt + err32(at, H, dd, 0.f) < H.w) return true;
+      }
+      return false;
+    };
     const int top = T.nlevels - 1;
     for (int64_t j = 0; j < T.count[top] && sp < kStack; ++j) stack[sp++] = pack_node(top, j);
     while (sp > 0 && Bu.spend(4u)) {
@@ -269,9 +309,45 @@ __device__ inline void scored_one(const QueryArgs& a, int box_cull, const uint32
           if (S.w == 0.f) continue;
           const float d32 = dist32(F.x32, F.y32, F.z32, S), r32 = fabsf(S.w);
           const float er = err32(F.ax, S, d32, r32);
-          const bool near_ok = fabsf(d32 - r32) - er <= R32, far_ok = d32 + r32 - er <= R32;
+          bool near_ok = fabsf(d32 - r32) - er <= R32, far_ok = d32 + r32 - er <= R32;
           if (!near_ok && !far_ok) continue;
           const int j = a.sid[jj];
+          // FP32 screen against the best so far: a side whose radius (within
+          // er of r32 +- d32) and type class cannot beat it for any allowed
+          // sign, or that intersects an opposite ball for every allowed sign
+          // (V1), needs no FP64 evaluation (the FP64 test would reject it)
+          {
+            const int si = S.w > 0.f ? 1 : -1;
+            for (int side = 0; side < 2; ++side) {
+              bool& ok = side == 0 ? near_ok : far_ok;
+              if (!ok) continue;
+              const float rr = side == 0 ? fabsf(d32 - r32) : d32 + r32;
+              const float r_hi = rr + er, r_lo = rr - er;
+              // near point: the normals agree when sign * si * sign(d - r) < 0;
+              // far point: when sign * si > 0 (undecided near d = r)
+              const int dr = side == 1 ? 0 : (d32 - r32 > er ? 1 : (r32 - d32 > er ? -1 : 2));
+              bool any = false;
+              for (int sgi = 0; sgi < 2 && !any; ++sgi) {
+                const int sign = sgi == 0 ? 1 : -1;
+                if (F.sig != 0 && sign != F.sig) continue;
+                if (double(r_lo) - tol > F.ub[sgi]) continue;  // V1 fails for sure
+                if (B.cls < 0) {
+                  any = true;
+                  break;
+                }
+                int cls;
+                if (side == 1) cls = sign * si > 0 ? 3 : 0;
+                else if (dr == 2) cls = 3;  // undecided: the highest it could be
+                else cls = sign * si * dr < 0 ? 3 : 0;
+                const double sr_hi = double(r_hi) * (sign > 0 ? 1.0 : 2.0);
+                if (cls > B.cls || (cls == B.cls && sr_hi >= B.sr)) any = true;
+              }
+              if (!any) ok = false;
+              // a tangent point inside another ball is no grow-to point
+              else if (surely_covered(S, d32, side == 0 ? r32 : -r32, j)) ok = false;
+            }
+            if (!near_ok && !far_ok) continue;
+          }
           const D4 P = a.sph64[j];
           const double r = fabs(P.w);
           const double vx = __dsub_rn(F.x, P.x), vy = __dsub_rn(F.y, P.y), vz = __dsub_rn(F.z, P.z);
@@ -287,7 +363,7 @@ __device__ inline void scored_one(const QueryArgs& a, int box_cull, const uint32
             if (box_cull && !ex_inbox(tx, ty, tz)) continue;
             // the coverage walk runs only for a point that would become the best
             try_candidate(a, F, tx, ty, tz, int64_t(j), true, kTanKey + 2 * int64_t(j) + side, B, [&]() {
-              return Bu.spend(4u) && tangent::covered_except_on(cstack, a, tx, ty, tz, j, -1, -1) < 0;
+              return Bu.spend(4u) && uncovered_tan(tx, ty, tz, j);
             });
           }
         }
