@@ -642,23 +642,6 @@ int gfs_uncovered_intersections(gfs_ctx* c, int64_t cap_circles, int64_t* circle
     if (pass == 1) return GFS_ERR_CUDA;  // cannot happen: the second walk finds the same pairs
     cap_pairs = int64_t(hpairs);
   }
-  // pairs in (i, j) order: a warp's circles then share sphere i and walk
-  // the same part of the hierarchy (the decisions do not depend on it)
-  if (hpairs > 1) {
-    if (hpairs >= (1ull << 31)) return GFS_ERR_TOO_LARGE;
-    GFS_TRY(ensure(c->ud_k1, size_t(hpairs) * 8));
-    GFS_TRY(ensure(c->ud_v0, size_t(hpairs) * 4));
-    GFS_TRY(ensure(c->ud_v1, size_t(hpairs) * 4));
-    size_t bytes = 0;
-    GFS_CK(sort_pairs64(nullptr, bytes, c->ud_pairs.as<unsigned long long>(), c->ud_k1.as<unsigned long long>(),
-                        c->ud_v0.as<int>(), c->ud_v1.as<int>(), int64_t(hpairs), 64, st));
-    GFS_TRY(cub_ensure(c, bytes));
-    bytes = c->cub_temp.bytes;
-    GFS_CK(sort_pairs64(c->cub_temp.p, bytes, c->ud_pairs.as<unsigned long long>(),
-                        c->ud_k1.as<unsigned long long>(), c->ud_v0.as<int>(), c->ud_v1.as<int>(), int64_t(hpairs), 64,
-                        st));
-    std::swap(c->ud_pairs, c->ud_k1);
-  }
   // raw outputs: a first guess, then exactly the counts (the decisions do not
   // depend on the capacities, so a second run finds the same entries)
   int64_t cap_c = std::max<int64_t>(4096, c->n), cap_p = std::max<int64_t>(4096, c->n);

@@ -153,7 +153,7 @@ struct Counters {
   unsigned long long query_rechecks;
   unsigned int nsurv[2];
   unsigned int ndefer;
-  unsigned int pad;
+  unsigned int walk_err;  // bit 0: a warp walk's stack guard tripped (cannot happen)
   unsigned long long q_sphere_ntests;  // child-node bound tests of the query sphere pass
   unsigned long long q_sphere_items;   // spheres tested by the query sphere pass
   unsigned long long q_surv_ntests;    // child-node bound tests of the survivor pass

@@ -5,17 +5,23 @@
 #include "gfs.h"
 #include "gfs_tangent.cuh"
 #include "gfs_tangent.h"
+#include "gfs_tangent_warp.cuh"
 
 namespace gfs {
 
 namespace {
 
-// one thread per point, points taken in the order a.perm gives (Morton
-// order: a warp's points are neighbours and walk similar paths)
-__global__ void __launch_bounds__(128) k_query_tangent(QueryArgs a, int box_cull) {
-  const int64_t slot = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (slot >= a.m) return;
-  tangent::tangent_one(a, box_cull, a.perm ? int64_t(a.perm[slot]) : slot);
+// one warp per point (the lanes walk the hierarchy together, gfs_tangent_warp.cuh),
+// points taken in the order a.perm gives (Morton order: consecutive warps
+// walk similar paths)
+constexpr int kTanWarps = 4;
+
+__global__ void __launch_bounds__(32 * kTanWarps) k_query_tangent(QueryArgs a, int box_cull) {
+  __shared__ uint32_t s_stk[kTanWarps][tangent::kWarpStack + kFan];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t slot = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  if (slot >= a.m) return;  // the same for the whole warp
+  tangent::warp_tangent_one(a, box_cull, a.perm ? int64_t(a.perm[slot]) : slot, s_stk[w], lane);
 }
 
 __global__ void __launch_bounds__(128) k_argmin_points(QueryArgs a, const int64_t* __restrict__ argmin,
@@ -88,7 +94,7 @@ inline unsigned int blocks(int64_t n, int b) { return (unsigned int)((n + b - 1)
 
 cudaError_t launch_query_tangent(const QueryArgs& a, int box_cull, cudaStream_t st) {
   if (a.m <= 0) return cudaSuccess;
-  k_query_tangent<<<blocks(a.m, 128), 128, 0, st>>>(a, box_cull);
+  k_query_tangent<<<blocks(a.m, kTanWarps), 32 * kTanWarps, 0, st>>>(a, box_cull);
   ++g_tangent_launches;
   return cudaGetLastError();
 }
