@@ -781,6 +781,33 @@ def extra_exact_coverage(csg_n=64, only_csg=False):
             res[name]["intersections"] = {"s": time.perf_counter() - t0, "circles": int(circ.shape[0]),
                                           "points": int(quads.shape[0]), "status": status}
             ctx.close()
+    if only_csg:
+        return res
+    # the exact minimum valid radius over T, U, D (Sec. 6) against the
+    # discrete value, on the 16^3 union grid at 1,024 of its upsampled points
+    # (a moderate input: every point scans all uncovered points, circles
+    # and spheres)
+    w = W.union_grid(N=16, up=2, tau=3)
+    ctx = gfs.Context(tau=w.tau)
+    ctx.build(torch.from_numpy(w.p).cuda(), torch.from_numpy(w.s).cuda())
+    xq = w.make_queries()
+    x = torch.from_numpy(np.ascontiguousarray(xq[np.random.default_rng(5).choice(len(xq), 1024, replace=False)])).cuda()
+    out = ctx.query(x)
+    sig = torch.sign(out["s64"]).to(torch.int8)
+    t0 = time.perf_counter()
+    ctx.exact_rmin(x[:1], sig[:1])  # the state's U and D lists
+    torch.cuda.synchronize()
+    t_lists = time.perf_counter() - t0
+    t = _ev_time(lambda: ctx.exact_rmin(x, sig), reps=1)
+    rmin = ctx.exact_rmin(x, sig).cpu().numpy()
+    v = np.abs(out["s64"].cpu().numpy())
+    fl = out["flags"].cpu().numpy().astype(np.int32) & 15
+    ok = np.isin(fl, [0, 1]) & np.isfinite(rmin)
+    res["exact_rmin_union16"] = {"spheres": int(w.n), "points": int(x.shape[0]), "lists_s": t_lists, "ms": t,
+                                 "points_per_s": x.shape[0] / (t / 1e3),
+                                 "mean_discrete_minus_exact": float(np.mean(v[ok] - rmin[ok])),
+                                 "max_discrete_minus_exact": float(np.max(v[ok] - rmin[ok]))}
+    ctx.close()
     return res
 
 

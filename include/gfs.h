@@ -342,6 +342,26 @@ int gfs_sphere_uncovered(gfs_ctx* ctx, uint8_t* out, double* witness);
 int gfs_uncovered_intersections(gfs_ctx* ctx, int64_t cap_circles, int64_t* circles_out, int64_t cap_points,
                                 int64_t* quads_out, double* points_out, int64_t* counts_host);
 
+/* ---- exact minimum valid radius (Sec. 6, over T u U u D) ------------------ */
+/* rmin_out[q] (device, m doubles) = the least distance from x[q] (device,
+ * m*3 doubles) to a grow-to point of Def. 1 that no other ball shrunk by tol
+ * holds, for the sign sigma[q] (device, m int8: +1, -1, or 0 for no sign
+ * filter) -- the minimum valid radius for a known sign of Sec. 6
+ * (min_valid_radius_for_known_sign), exactly, not over icosphere
+ * candidates: the uncovered points U shared by three spheres none of whose
+ * signs is opposite to sigma, the points of their uncovered circles nearest
+ * to and farthest from x (D), and the near and far tangent points of every
+ * sphere (T), in the box when the context culls by it; INFINITY when no
+ * candidate exists.  U and the uncovered circles come from the state's U
+ * and D precomputation (gfs_uncovered_intersections, computed on the first
+ * call for a state: that call synchronises the stream and allocates);
+ * every point is then built and tested in FP64 as Def. 1 states.  One warp
+ * per point scans every uncovered point, circle and sphere, so this is for
+ * moderate inputs (thousands of spheres) and for checking the discrete
+ * values against the exact ones.  Errors: GFS_ERR_STATE (no build),
+ * GFS_ERR_ARG, GFS_ERR_CUDA. */
+int gfs_exact_rmin(gfs_ctx* ctx, const double* x, const int8_t* sigma, int64_t m, double* rmin_out);
+
 /* ---- refinement order (Sec. 4.2) ------------------------------------------ */
 /* The greedy refinement depends on the order of the new points.  The paper
  * orders the interesting cells by a flood fill that starts at the least

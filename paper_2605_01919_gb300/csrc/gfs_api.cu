@@ -157,6 +157,8 @@ struct gfs_ctx {
   DevBuf csr_ids, csr_off, scored_status;
   // uncovered intersection circles and points (raw outputs, sort buffers)
   DevBuf ud_uncov, ud_cnt, ud_pairs, ud_circ, ud_quad, ud_pts, ud_k0, ud_k1, ud_v0, ud_v1;
+  int64_t ud_state = -1, ud_nc = 0, ud_np = 0;  // the raw lists hold state ud_state
+  unsigned ud_status = 0;
   int64_t state_id = 0, csr_state = -1;
   int64_t ins_rounds = 0, ins_steps = 0, ins_rebuilds = 0, ins_queried = 0;  // of the last insertion call
   double ins_ms_total = 0.0, ins_ms_rebuild = 0.0, ins_ms_final = 0.0;  // host wall time of its phases
@@ -614,13 +616,19 @@ int gfs_sphere_uncovered(gfs_ctx* c, uint8_t* out, double* witness) {
   return GFS_OK;
 }
 
-int gfs_uncovered_intersections(gfs_ctx* c, int64_t cap_circles, int64_t* circles_out, int64_t cap_points,
-                                int64_t* quads_out, double* points_out, int64_t* counts_host) {
-  if (!c || !counts_host || cap_circles < 0 || cap_points < 0) return GFS_ERR_ARG;
-  if ((cap_circles > 0 && !circles_out) || (cap_points > 0 && (!quads_out || !points_out))) return GFS_ERR_ARG;
-  if (!c->built) return GFS_ERR_STATE;
-  counts_host[0] = counts_host[1] = counts_host[2] = 0;
-  if (c->n == 0) return GFS_OK;
+namespace {
+
+// The uncovered circles and points of the current state in c->ud_circ /
+// ud_quad / ud_pts (unsorted), computed once per state: the per-sphere
+// test, the cutting pairs of uncovered spheres, then the circles.
+int ud_compute(gfs_ctx* c) {
+  if (c->ud_state == c->state_id) return GFS_OK;
+  c->ud_nc = c->ud_np = 0;
+  c->ud_status = 0;
+  if (c->n == 0) {
+    c->ud_state = c->state_id;
+    return GFS_OK;
+  }
   cudaStream_t st = c->stream;
   QueryArgs a;
   fill_query_args(c, a);
@@ -663,7 +671,26 @@ int gfs_uncovered_intersections(gfs_ctx* c, int64_t cap_circles, int64_t* circle
     cap_c = std::max<int64_t>(cap_c, int64_t(hc[0]));
     cap_p = std::max<int64_t>(cap_p, int64_t(hc[1]));
   }
-  const int64_t nc = int64_t(hc[0]), np = int64_t(hc[1]);
+  c->ud_nc = int64_t(hc[0]);
+  c->ud_np = int64_t(hc[1]);
+  c->ud_status = hstatus;
+  c->ud_state = c->state_id;
+  return GFS_OK;
+}
+
+}  // namespace
+
+int gfs_uncovered_intersections(gfs_ctx* c, int64_t cap_circles, int64_t* circles_out, int64_t cap_points,
+                                int64_t* quads_out, double* points_out, int64_t* counts_host) {
+  if (!c || !counts_host || cap_circles < 0 || cap_points < 0) return GFS_ERR_ARG;
+  if ((cap_circles > 0 && !circles_out) || (cap_points > 0 && (!quads_out || !points_out))) return GFS_ERR_ARG;
+  if (!c->built) return GFS_ERR_STATE;
+  counts_host[0] = counts_host[1] = counts_host[2] = 0;
+  if (c->n == 0) return GFS_OK;
+  cudaStream_t st = c->stream;
+  GFS_TRY(ud_compute(c));
+  const int64_t nc = c->ud_nc, np = c->ud_np;
+  const unsigned hstatus = c->ud_status;
   counts_host[0] = nc;
   counts_host[1] = np;
   counts_host[2] = int64_t(hstatus);
@@ -703,6 +730,19 @@ int gfs_uncovered_intersections(gfs_ctx* c, int64_t cap_circles, int64_t* circle
                             nullptr, st));
   }
   GFS_CK(cudaStreamSynchronize(st));
+  return GFS_OK;
+}
+
+int gfs_exact_rmin(gfs_ctx* c, const double* x, const int8_t* sigma, int64_t m, double* rmin_out) {
+  if (!c || m < 0 || (m > 0 && (!x || !sigma || !rmin_out))) return GFS_ERR_ARG;
+  if (!c->built) return GFS_ERR_STATE;
+  if (m == 0) return GFS_OK;
+  GFS_TRY(ud_compute(c));
+  QueryArgs a;
+  fill_query_args(c, a);
+  const exact::UDLists L{c->ud_quad.as<int64_t>(), c->ud_pts.as<double>(), c->ud_np, c->ud_circ.as<int64_t>(),
+                         c->ud_nc};
+  GFS_CK(launch_exact_rmin(a, c->opt.box_cull, L, x, sigma, m, rmin_out, c->stream));
   return GFS_OK;
 }
 

@@ -212,9 +212,37 @@ __global__ void k_ud_gather(const unsigned long long* __restrict__ ckey, int64_t
   }
 }
 
+// One warp per query point: the lanes split each candidate set (U, D, T in
+// that order) and take the warp's minimum after each, so that later sets are
+// tested against the best point so far.
+__global__ void __launch_bounds__(128) k_exact_rmin(QueryArgs a, int box_cull, exact::UDLists L,
+                                                   const double* __restrict__ x, const int8_t* __restrict__ sigma,
+                                                   int64_t m, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  if (q >= m) return;  // the same for the whole warp
+  uint32_t stack[kStack];
+  const double xq[3] = {x[3 * q], x[3 * q + 1], x[3 * q + 2]};
+  const int sg = sigma[q];
+  double best = INFINITY;
+  for (int phase = 0; phase < 3; ++phase) {
+    best = exact::rmin_phase(a, box_cull, L, xq, sg, phase, lane, 32, best, stack);
+    for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  }
+  if (lane == 0) out[q] = best;
+}
+
 unsigned long long g_exact_launches = 0;
 
 }  // namespace
+
+cudaError_t launch_exact_rmin(const QueryArgs& a, int box_cull, const exact::UDLists& L, const double* x,
+                              const int8_t* sigma, int64_t m, double* out, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  k_exact_rmin<<<(unsigned int)((m + 3) / 4), 128, 0, st>>>(a, box_cull, L, x, sigma, m, out);
+  ++g_exact_launches;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ud_pairs(const QueryArgs& a, const uint8_t* uncov, unsigned long long* pairs, int64_t cap,
                             unsigned long long* count, cudaStream_t st) {

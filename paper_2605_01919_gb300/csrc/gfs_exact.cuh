@@ -518,5 +518,85 @@ __device__ inline void circle_intersections(const QueryArgs& a, int i, int j, in
   circle_points_u(a, i, j, pi, ri, pj, rj, stacks, stacks + kStack, o);
 }
 
+// ---------------------------------------------------------------------------
+// Exact minimum valid radius for a known sign (Sec. 6,
+// min_valid_radius_for_known_sign; Def. 1 P = T u U u D): the least distance
+// from x to a grow-to point that no other ball, shrunk by tol, holds:
+//  - U: the points shared by three spheres none of whose signs is opposite
+//    to sigma -- the precomputed uncovered points (tested there against
+//    every ball but their three);
+//  - D: the points of each circle of two such spheres nearest to and
+//    farthest from x -- on the precomputed uncovered circles (a circle that
+//    other balls cover entirely has no uncovered point), tested against
+//    every ball but the two;
+//  - T: the near and far tangent points p_i -+ r_i (x - p_i)/|x - p_i| of
+//    every sphere (either sign), tested against every ball but i;
+// in the box when the context culls by it.  Every point and distance is
+// computed in FP64 in the order written (the oracle's constructions), so
+// the minimum is the oracle's bit for bit.  INFINITY when there is no
+// candidate.  A point is coverage-tested only when it is nearer than the
+// best so far (the minimum does not depend on the order).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int sgn64(double v) { return v > 0.0 ? 1 : (v < 0.0 ? -1 : 0); }
+
+// Candidates lane, lane + stride, ... of each set (lane 0, stride 1: all);
+// returns min(best, the nearest uncovered one).  phase: 0 U, 1 D, 2 T.
+__device__ inline double rmin_phase(const QueryArgs& a, int box_cull, const UDLists& L, const double* x, int sigma,
+                                    int phase, int64_t lane, int64_t stride, double best, uint32_t* stack) {
+  if (phase == 0) {
+    for (int64_t u = lane; u < L.np; u += stride) {
+      const int64_t* qd = L.quad + 4 * u;
+      if (sigma * sgn64(a.sph64[qd[0]].w) < 0 || sigma * sgn64(a.sph64[qd[1]].w) < 0 ||
+          sigma * sgn64(a.sph64[qd[2]].w) < 0)
+        continue;
+      const double* q = L.pts + 3 * u;
+      if (box_cull && !ex_inbox(q[0], q[1], q[2])) continue;
+      const double dd = __dsqrt_rn(ex_d2(x[0], x[1], x[2], q[0], q[1], q[2]));
+      if (dd < best) best = dd;
+    }
+  } else if (phase == 1) {
+    for (int64_t u = lane; u < L.nc; u += stride) {
+      const int i = int(L.circ[2 * u]), j = int(L.circ[2 * u + 1]);
+      const D4 P = a.sph64[i], Q = a.sph64[j];
+      if (sigma * sgn64(P.w) < 0 || sigma * sgn64(Q.w) < 0) continue;
+      const double pi[3] = {P.x, P.y, P.z}, pj[3] = {Q.x, Q.y, Q.z};
+      double q[6];
+      if (!circle_points(pi, fabs(P.w), pj, fabs(Q.w), x, q)) continue;
+      for (int h = 0; h < 2; ++h) {
+        const double* t = q + 3 * h;
+        if (box_cull && !ex_inbox(t[0], t[1], t[2])) continue;
+        const double dd = __dsqrt_rn(ex_d2(x[0], x[1], x[2], t[0], t[1], t[2]));
+        if (!(dd < best)) continue;
+        if (tangent::covered_except_on(stack, a, t[0], t[1], t[2], i, j, -1) >= 0) continue;
+        best = dd;
+      }
+    }
+  } else {
+    for (int64_t i = lane; i < a.n; i += stride) {
+      const D4 P = a.sph64[i];
+      const double w[3] = {__dsub_rn(x[0], P.x), __dsub_rn(x[1], P.y), __dsub_rn(x[2], P.z)};
+      const double d = norm(w);
+      if (!(d > 0.0)) continue;
+      const double r = fabs(P.w);
+      // the two points lie |d -+ r| from x (up to rounding): skip the pair
+      // when both are clearly beyond the best
+      const double lo = fabs(__dsub_rn(d, r));
+      if (lo > best + 1e-12 * (d + r + best)) continue;
+      for (int c = -1; c <= 1; c += 2) {
+        const double cr = c * r;
+        const double t[3] = {__dadd_rn(P.x, __ddiv_rn(__dmul_rn(cr, w[0]), d)),
+                             __dadd_rn(P.y, __ddiv_rn(__dmul_rn(cr, w[1]), d)),
+                             __dadd_rn(P.z, __ddiv_rn(__dmul_rn(cr, w[2]), d))};
+        if (box_cull && !ex_inbox(t[0], t[1], t[2])) continue;
+        const double dd = __dsqrt_rn(ex_d2(x[0], x[1], x[2], t[0], t[1], t[2]));
+        if (!(dd < best)) continue;
+        if (tangent::covered_except_on(stack, a, t[0], t[1], t[2], int(i), -1, -1) >= 0) continue;
+        best = dd;
+      }
+    }
+  }
+  return best;
+}
+
 }  // namespace exact
 }  // namespace gfs

@@ -22,6 +22,15 @@ struct UDOut {
   double* pts;              // (x, y, z) per point
   unsigned* status;         // bit 0: a circle's certificate outgrew its capacity (taken as uncovered)
 };
+// The precomputed uncovered points and circles an exact minimum radius
+// draws from (device pointers)
+struct UDLists {
+  const int64_t* quad;  // (i, j, m, side) per uncovered point
+  const double* pts;    // (x, y, z) per uncovered point
+  int64_t np;
+  const int64_t* circ;  // (i, j) per uncovered circle
+  int64_t nc;
+};
 }  // namespace exact
 
 // pairs i < j of spheres with uncov != 0 that cut in a circle, as
@@ -40,6 +49,10 @@ cudaError_t launch_ud_point_keys(const int64_t* quad, const int* order, int64_t 
 cudaError_t launch_ud_gather(const unsigned long long* ckey, int64_t nc, int64_t* circ_out, const int* order,
                              const int64_t* quad, const double* pts, int64_t np, int64_t* quad_out, double* pts_out,
                              cudaStream_t st);
+
+// rmin_out[q]: the exact minimum valid radius at x[q] for sign sigma[q]
+cudaError_t launch_exact_rmin(const QueryArgs& a, int box_cull, const exact::UDLists& L, const double* x,
+                              const int8_t* sigma, int64_t m, double* out, cudaStream_t st);
 
 unsigned long long exact_launch_count();
 

@@ -23,7 +23,7 @@ EXPORTED = ["gfs_default_options", "gfs_create", "gfs_set_stream", "gfs_build", 
             "gfs_insert_known", "gfs_survivors", "gfs_batch_build", "gfs_batch_rebuild", "gfs_batch_status",
             "gfs_batch_query", "gfs_batch_query_tangent", "gfs_batch_survivors", "gfs_stats", "gfs_solve_host",
             "gfs_icosphere", "gfs_strerror", "gfs_destroy", "gfs_cell_coverage", "gfs_flood_order",
-            "gfs_sphere_uncovered", "gfs_uncovered_intersections", "gfs_fma_probe"]
+            "gfs_sphere_uncovered", "gfs_uncovered_intersections", "gfs_exact_rmin", "gfs_fma_probe"]
 
 
 class Options(ctypes.Structure):
@@ -122,6 +122,8 @@ def load(build_if_missing: bool = True):
     L.gfs_sphere_uncovered.argtypes = [P, P, P]
     L.gfs_uncovered_intersections.argtypes = [P, i64, P, i64, P, P, P]
     L.gfs_uncovered_intersections.restype = i32
+    L.gfs_exact_rmin.argtypes = [P, P, P, i64, P]
+    L.gfs_exact_rmin.restype = i32
     L.gfs_sphere_uncovered.restype = i32
     L.gfs_cell_coverage.argtypes = [P, P, i64, P, f64, i32, P]
     L.gfs_cell_coverage.restype = i32
@@ -370,6 +372,17 @@ class Context:
         _check(L.gfs_uncovered_intersections(self._h, nc, _ptr(circ) if nc else None, npt,
                                              _ptr(quads) if npt else None, _ptr(pts) if npt else None, counts))
         return circ, quads, pts, int(counts[2])
+
+    def exact_rmin(self, x: torch.Tensor, sigma: torch.Tensor) -> torch.Tensor:
+        """Exact minimum valid radius for a known sign (Sec. 6) over T, U, D
+        at points x ((m, 3) float64 cuda) for signs sigma ((m,) int8 cuda:
+        +1, -1, 0); (m,) float64, inf where no candidate exists."""
+        x = x.contiguous()
+        sigma = sigma.to(torch.int8).contiguous()
+        out = torch.empty(x.shape[0], dtype=torch.float64, device="cuda")
+        self._sync_stream()
+        _check(load().gfs_exact_rmin(self._h, _ptr(x), _ptr(sigma), int(x.shape[0]), _ptr(out)))
+        return out
 
     # -- refinement order (Sec. 4.2) ------------------------------------------------
     def cell_coverage(self, cells: torch.Tensor, origin, h: float, sub: int = 8) -> torch.Tensor:

@@ -213,6 +213,40 @@ extern "C" int intersections_host(const double* p, const double* s, int64_t n, d
   return 0;
 }
 
+// exact minimum valid radius at each point for its sign: the uncovered
+// circles and points as above, then the three candidate sets in turn
+extern "C" int exact_rmin_host(const double* p, const double* s, int64_t n, double tol, int box_cull, const double* x,
+                               const int8_t* sigma, int64_t m, double* out, unsigned order_seed) {
+  HostTree H;
+  if (!build_tree(p, s, n, order_seed, H)) return -1;
+  const QueryArgs a = args_for(H, n, tol);
+  std::vector<int> S(exact::kMaxSet);
+  std::vector<uint32_t> stacks(3 * kStack);
+  std::vector<uint8_t> uncov(size_t(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) uncov[i] = uint8_t(exact::sphere_uncovered(a, int(i), S.data(), stacks.data(), nullptr));
+  const int64_t cap = 1 << 20;
+  std::vector<int64_t> circ(2 * cap), quad(4 * cap);
+  std::vector<double> pts(3 * cap);
+  unsigned long long cnt[2] = {0, 0};
+  unsigned status = 0;
+  const exact::UDOut o{cnt, cap, cap, circ.data(), quad.data(), pts.data(), &status};
+  for (int64_t u = 0; u < n; ++u) {
+    const int i = a.sid[u];
+    if (uncov[i] != 0)
+      exact::sphere_pairs(a, i, uncov.data(), stacks.data() + 2 * kStack,
+                          [&](int j) { exact::circle_intersections(a, i, j, S.data(), stacks.data(), o); });
+  }
+  if (cnt[0] > (unsigned long long)cap || cnt[1] > (unsigned long long)cap) return -2;
+  const exact::UDLists L{quad.data(), pts.data(), int64_t(cnt[1]), circ.data(), int64_t(cnt[0])};
+  for (int64_t q = 0; q < m; ++q) {
+    double best = INFINITY;
+    for (int phase = 0; phase < 3; ++phase)
+      best = exact::rmin_phase(a, box_cull, L, x + 3 * q, sigma[q], phase, 0, 1, best, stacks.data());
+    out[q] = best;
+  }
+  return 0;
+}
+
 // q* of each point from the argmin and flags (argmin_point)
 extern "C" int points_host(const double* p, const double* s, int64_t n, const double* U, int K, const double* x,
                            int64_t m, const int64_t* argmin, const uint16_t* flags, double* out) {

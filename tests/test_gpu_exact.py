@@ -228,3 +228,66 @@ def test_uncovered_intersections_csg32_properties(G):
         assert (dq < rho[near][None, :]).any(axis=1).all(), (i, j)
         checked += 1
     assert checked == 300
+
+
+def test_exact_rmin_parity(G, orc):
+    """Exact minimum valid radius over T, U, D (Sec. 6) on the GPU: equal to
+    the oracle's brute force bit for bit, for both signs and no sign, with
+    and without the box, on random and hand-made inputs (tol 0 and 1e-6)
+    and on the 6^3 sphere grid (tol 1e-6)."""
+    cases = [(W.tiny_random(n, seed, valid=(seed % 2 == 0), spread=0.35), (0.0, 1e-6))
+             for n, seed in ((12, 0), (25, 1), (40, 2))]
+    h = np.sqrt(3) / 2
+    cases.append(((np.array([[0.0, 0, 0], [1.0, 0, 0], [0.5, h, 0], [0.5, h / 3, 1.3]]) * 0.5,
+                   np.array([0.5, 0.5, 0.5, -0.3])), (0.0, 1e-6)))
+    w = W.sphere_grid(N=6, up=2, tau=2)
+    cases.append(((w.p, w.s), (1e-6,)))
+    rng = np.random.default_rng(31)
+    for (p, s), tols in cases:
+        x = rng.uniform(-0.8, 0.8, size=(10, 3))
+        for tol in tols:
+            for box in (False, True):
+                ctx = G.Context(tau=1, tol=tol, box_cull=box)
+                ctx.build(torch.from_numpy(np.ascontiguousarray(p)).cuda(),
+                          torch.from_numpy(np.ascontiguousarray(s)).cuda())
+                for sg in (1, -1, 0):
+                    got = ctx.exact_rmin(torch.from_numpy(x).cuda(),
+                                         torch.full((x.shape[0],), sg, dtype=torch.int8, device="cuda")).cpu().numpy()
+                    want = np.array([orc.exact_rmin(p, s, x[t], sg, tol=tol, box_cull=box) for t in range(len(x))])
+                    assert np.array_equal(got, want), (tol, box, sg, got[got != want], want[got != want])
+                ctx.close()
+
+
+def test_exact_rmin_brackets_the_discrete_value(G):
+    """The bracket LB <= exact r_min <= |s_tau| of the oracle's pins (valid
+    input, no box: the survivors and the opposite tangent point are contour
+    points, every contour point lies outside each containing ball) on
+    random valid inputs of 300 samples (exact SDF of two spheres' union at
+    random points), at every one of 400 random points where the plain query
+    finds a survivor or an opposite tangent point, at the method's tol.
+    (On grids of SDF samples, nested spheres touching at one surface point
+    meet in "circles" a few ulps wide, whose decision rounding takes; the
+    bracket is a statement about inputs in general position.)"""
+    checked = 0
+    for seed in range(3):
+        p, s = W.tiny_random(300, 500 + seed, valid=True, spread=0.5)
+        xs = np.random.default_rng(600 + seed).uniform(-0.5, 0.5, size=(400, 3))
+        ctx = G.Context(tau=2, tol=1e-6, box_cull=False)
+        ctx.build(torch.from_numpy(np.ascontiguousarray(p)).cuda(), torch.from_numpy(np.ascontiguousarray(s)).cuda())
+        x = torch.from_numpy(xs).cuda()
+        out = ctx.query(x)
+        fl = out["flags"].cpu().numpy().astype(np.int32) & 0xFFFF
+        v = out["s64"].cpu().numpy()
+        ok = np.isin(fl & 15, [0, 1])
+        sig = torch.from_numpy(np.sign(v).astype(np.int8)).cuda()
+        rmin = ctx.exact_rmin(x, sig).cpu().numpy()
+        ctx.close()
+        assert np.all(np.isfinite(rmin[ok]))
+        assert np.all(rmin[ok] <= np.abs(v[ok]) + 1e-9)
+        for t in np.nonzero(ok)[0]:
+            same = np.sign(s) == np.sign(v[t])
+            lb = np.max(np.abs(s[same]) - np.linalg.norm(p[same] - xs[t], axis=1))
+            assert lb <= rmin[t] + 1e-9
+        assert np.mean(np.abs(v[ok]) - rmin[ok]) > 0
+        checked += int(ok.sum())
+    assert checked > 1000

@@ -125,6 +125,7 @@ def test_every_context_call_rejects_a_null_context(gfs):
         lambda: L.gfs_survivors(None, None, 0, ctypes.byref(ctypes.c_int64())),
         lambda: L.gfs_sphere_uncovered(None, None, None),
         lambda: L.gfs_uncovered_intersections(None, 0, None, 0, None, None, None),
+        lambda: L.gfs_exact_rmin(None, None, None, 1, None),
         lambda: L.gfs_cell_coverage(None, None, 1, origin.ctypes.data_as(ctypes.c_void_p), 0.1, 8, None),
         lambda: L.gfs_batch_build(None, None, 1),
         lambda: L.gfs_batch_query(None),

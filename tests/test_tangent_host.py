@@ -50,6 +50,9 @@ def host(tmp_path_factory):
     L.intersections_host.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_int64, P, ctypes.c_int64, P,
                                      P, P, P, ctypes.c_uint]
     L.intersections_host.restype = ctypes.c_int
+    L.exact_rmin_host.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_int, P, P, ctypes.c_int64, P,
+                                  ctypes.c_uint]
+    L.exact_rmin_host.restype = ctypes.c_int
     L.points_host.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int, P, ctypes.c_int64, P, P, P]
     L.points_host.restype = ctypes.c_int
     L.scored_host.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int, ctypes.c_double, ctypes.c_int, P, P, P,
@@ -276,6 +279,36 @@ def test_host_uncovered_intersections(host, orc):
                 assert np.array_equal(gc, wc), (len(gc), len(wc))
                 assert np.array_equal(gq, wq), (len(gq), len(wq))
                 assert np.array_equal(gp, wp)
+
+
+def _exact_rmin(host, p, s, tol, box, x, sig, order):
+    p, s, x = (np.ascontiguousarray(v, np.float64) for v in (p, s, x))
+    sig = np.ascontiguousarray(sig, np.int8)
+    out = np.zeros(x.shape[0])
+    assert host.exact_rmin_host(_ptr(p), _ptr(s), s.shape[0], tol, int(box), _ptr(x), _ptr(sig), x.shape[0],
+                                _ptr(out), order) == 0
+    return out
+
+
+def test_host_exact_rmin(host, orc):
+    """Exact minimum valid radius over T, U, D (Sec. 6) from the uncovered
+    circles and points: equal to the oracle's brute force bit for bit, for
+    both signs and no sign, with and without the box, tol 0 and 1e-6."""
+    cases = [W.tiny_random(n, seed, valid=(seed % 2 == 0), spread=0.35) for n, seed in ((12, 0), (25, 1), (40, 2))]
+    h = np.sqrt(3) / 2
+    cases.append((np.array([[0.0, 0, 0], [1.0, 0, 0], [0.5, h, 0], [0.5, h / 3, 1.3]]) * 0.5,
+                  np.array([0.5, 0.5, 0.5, -0.3])))
+    rng = np.random.default_rng(31)
+    for p, s in cases:
+        x = rng.uniform(-0.8, 0.8, size=(12, 3))
+        for tol in (0.0, 1e-6):
+            for box in (False, True):
+                for sg in (1, -1, 0):
+                    sig = np.full(x.shape[0], sg, np.int8)
+                    want = np.array([orc.exact_rmin(p, s, x[t], sg, tol=tol, box_cull=box) for t in range(len(x))])
+                    for order in (0, 5):
+                        got = _exact_rmin(host, p, s, tol, box, x, sig, order)
+                        assert np.array_equal(got, want), (tol, box, sg, got[got != want], want[got != want])
 
 
 def test_host_argmin_points(host, orc):
