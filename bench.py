@@ -358,9 +358,12 @@ def recorded_traffic(kernel: str):
 # ----------------------------------------------------------------------------
 # sub-benchmarks of the other rows of the hot path (rank 0, one GPU)
 # ----------------------------------------------------------------------------
-def _ev_time(fn, reps=3):
+def _ev_time(fn, reps=3, warm=True):
+    """Median CUDA-event time (ms) of fn over reps runs, after one untimed
+    run unless warm is False (fn has just run)."""
     import torch
-    fn()
+    if warm:
+        fn()
     torch.cuda.synchronize()
     ts = []
     for _ in range(reps):
@@ -582,9 +585,10 @@ def extra_batch(count=256, scale=1.0, peaks=None):
     M = sum(int(sh["x"].shape[0]) for sh in shapes)
     Nn = sum(int(sh["p"].shape[0]) for sh in shapes)
     ctx = gfs.Context(tau=3)
+    # the launches of the full batch take seconds each: one warm run, one timed
     ctx.batch_build(shapes)            # first build also autotunes the persistent grids
-    t_build = _ev_time(lambda: ctx.batch_build(shapes), reps=1)
-    t_query = _ev_time(lambda: ctx.batch_query())
+    t_build = _ev_time(lambda: ctx.batch_build(shapes), reps=1, warm=False)
+    t_query = _ev_time(lambda: ctx.batch_query(), reps=1)
     st = torch.cuda.Stream()
     st.wait_stream(torch.cuda.current_stream())
     g = torch.cuda.CUDAGraph()
@@ -592,7 +596,7 @@ def extra_batch(count=256, scale=1.0, peaks=None):
         with torch.cuda.graph(g, stream=st):
             ctx.batch_query()
     torch.cuda.synchronize()
-    t_graph = _ev_time(lambda: g.replay())
+    t_graph = _ev_time(lambda: g.replay(), reps=1)
     bst = ctx.stats()
     # the whole batched path (rebuild from the samples + query) as one graph
     g2 = torch.cuda.CUDAGraph()
@@ -601,7 +605,7 @@ def extra_batch(count=256, scale=1.0, peaks=None):
             ctx.batch_rebuild()
             ctx.batch_query()
     torch.cuda.synchronize()
-    t_graph_full = _ev_time(lambda: g2.replay(), reps=2)
+    t_graph_full = _ev_time(lambda: g2.replay(), reps=1)
     status = ctx.batch_status()
     single = gfs.Context(tau=3)
 
